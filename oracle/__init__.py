@@ -1,0 +1,162 @@
+"""ctypes binding of the FP64 CPU oracle (test infrastructure only).
+
+Only the tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench.py``
+import this package.  The product library never does.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+L2, L1 = 0, 1
+_lib = None
+
+
+def use_library(path):
+    """Bind this module to another build of the oracle (used to check that the pins
+    catch deliberately broken builds)."""
+    global _lib, _path
+    _lib, _path = None, path
+
+
+_path = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = ctypes.CDLL(_path or _build.build())
+        P = ctypes.c_void_p
+        i64, i32, f64 = ctypes.c_int64, ctypes.c_int32, ctypes.c_double
+        _lib.orc_key.restype = f64
+        _lib.orc_key.argtypes = [P, P, i32, i32]
+        _lib.orc_dist.restype = f64
+        _lib.orc_dist.argtypes = [P, P, i32, i32]
+        _lib.orc_rng_brute.restype = i64
+        _lib.orc_rng_brute.argtypes = [P, i64, i32, i32, P, i64]
+        _lib.orc_rng_row.restype = i64
+        _lib.orc_rng_row.argtypes = [P, i64, i32, i32, i64, P, i64]
+        _lib.orc_in_lune.restype = i32
+        _lib.orc_in_lune.argtypes = [P, i32, i32, i64, i64, i64]
+        _lib.orc_grng_brute.restype = i64
+        _lib.orc_grng_brute.argtypes = [P, P, i64, i32, i32, P, i64]
+        _lib.orc_grng_row.restype = i64
+        _lib.orc_grng_row.argtypes = [P, P, i64, i32, i32, i64, P, i64]
+        _lib.orc_assign.restype = i32
+        _lib.orc_assign.argtypes = [P, i32, i32, P, i64, P, P, i32, P, P, P, P]
+        if hasattr(_lib, "orc_mlp_forward"):
+            _lib.orc_mlp_forward.restype = None
+            _lib.orc_mlp_forward.argtypes = [P, P, i64, P]
+            _lib.orc_mlp_backward.restype = f64
+            _lib.orc_mlp_backward.argtypes = [P, P, P, i64, P]
+    return _lib
+
+
+def _f32(X):
+    X = np.ascontiguousarray(X, dtype=np.float32)
+    assert X.ndim == 2
+    return X
+
+
+def _p(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def key(a, b, metric=L2):
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    b = np.ascontiguousarray(b, dtype=np.float32)
+    return lib().orc_key(_p(a), _p(b), a.shape[0], metric)
+
+
+def dist(a, b, metric=L2):
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    b = np.ascontiguousarray(b, dtype=np.float32)
+    return lib().orc_dist(_p(a), _p(b), a.shape[0], metric)
+
+
+def _edges_call(fn, *args):
+    cnt = fn(*args, None, 0)
+    if cnt < 0:
+        raise MemoryError("oracle allocation failed")
+    out = np.zeros((max(cnt, 1), 2), dtype=np.int32)
+    cnt2 = fn(*args, _p(out), cnt)
+    assert cnt2 == cnt
+    return out[:cnt]
+
+
+def rng_brute(X, metric=L2):
+    """RNG of X by Eq. 1 over all triples: sorted (i<j) int32 edges [E,2]."""
+    X = _f32(X)
+    return _edges_call(lib().orc_rng_brute, _p(X), X.shape[0], X.shape[1], metric)
+
+
+def rng_row(X, x, metric=L2):
+    """Exact RNG neighbours of point x (ascending int32 array)."""
+    X = _f32(X)
+    n = X.shape[0]
+    out = np.zeros(max(n, 1), dtype=np.int32)
+    cnt = lib().orc_rng_row(_p(X), n, X.shape[1], metric, int(x), _p(out), n)
+    if cnt < 0:
+        raise MemoryError("oracle allocation failed")
+    return out[:cnt]
+
+
+def in_lune(X, x, y, z, metric=L2):
+    X = _f32(X)
+    return bool(lib().orc_in_lune(_p(X), X.shape[1], metric, int(x), int(y), int(z)))
+
+
+def grng_brute(P, r, metric=L2):
+    """GRNG of pivots P[m,D] with radii r[m] by its definition: sorted edges [E,2]."""
+    P = _f32(P)
+    r = np.ascontiguousarray(r, dtype=np.float64)
+    return _edges_call(lib().orc_grng_brute, _p(P), _p(r), P.shape[0], P.shape[1], metric)
+
+
+def grng_row(P, r, i, metric=L2):
+    P = _f32(P)
+    r = np.ascontiguousarray(r, dtype=np.float64)
+    m = P.shape[0]
+    out = np.zeros(max(m, 1), dtype=np.int32)
+    cnt = lib().orc_grng_row(_p(P), _p(r), m, P.shape[1], metric, int(i), _p(out), m)
+    if cnt < 0:
+        raise MemoryError("oracle allocation failed")
+    return out[:cnt]
+
+
+def assign(X, members, pivots, member_r=None, metric=L2):
+    """Nearest-pivot assignment, distances, radii and delta_max of one layer."""
+    X = _f32(X)
+    members = np.ascontiguousarray(members, dtype=np.int32)
+    pivots = np.ascontiguousarray(pivots, dtype=np.int32)
+    nm, m = members.shape[0], pivots.shape[0]
+    a = np.zeros(max(nm, 1), np.int32)
+    d = np.zeros(max(nm, 1), np.float64)
+    r = np.zeros(max(m, 1), np.float64)
+    dm = np.zeros(max(m, 1), np.float64)
+    mr = None if member_r is None else np.ascontiguousarray(member_r, dtype=np.float64)
+    rc = lib().orc_assign(_p(X), X.shape[1], metric, _p(members), nm,
+                          None if mr is None else _p(mr), _p(pivots), m, _p(a), _p(d), _p(r), _p(dm))
+    if rc != 0:
+        raise MemoryError("oracle allocation failed")
+    return a[:nm], d[:nm], r[:m], dm[:m]
+
+
+def build_layers(X, layers, metric=L2):
+    """Assignment/radii for a nested hierarchy, finest first (Eq. 2; Sec. 3).
+
+    layers: list of pivot-index arrays, coarsest first.  Returns a list (coarsest
+    first) of dicts with keys pivots, assign, dist, radius, delta_max.
+    """
+    n = X.shape[0]
+    out = [None] * len(layers)
+    members = np.arange(n, dtype=np.int32)
+    member_r = None
+    for li in range(len(layers) - 1, -1, -1):
+        piv = np.asarray(layers[li], dtype=np.int32)
+        a, d, r, dm = assign(X, members, piv, member_r, metric)
+        out[li] = dict(pivots=piv, assign=a, dist=d, radius=r, delta_max=dm)
+        members, member_r = piv, r
+    return out

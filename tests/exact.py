@@ -1,0 +1,64 @@
+"""Exact rational restatement of Eq. 1 (RNG) and of the GRNG definition (Sec. 2).
+
+Python `fractions` arithmetic, no rounding anywhere: used to pin the FP64 oracle on
+tiny inputs whose coordinates and radii are exactly representable.  L2 comparisons
+that involve a square root are decided by exact algebra on the squared values.
+"""
+from fractions import Fraction as F
+from itertools import combinations
+
+L2, L1 = 0, 1
+
+
+def key(a, b, metric):
+    if metric == L2:
+        return sum((F(x) - F(y)) ** 2 for x, y in zip(a, b))
+    return sum(abs(F(x) - F(y)) for x, y in zip(a, b))
+
+
+def rng(X, metric):
+    """Edges (i<j) of the RNG by Eq. 1 (x3 ranges over S minus {x1, x2})."""
+    n = len(X)
+    K = [[key(X[i], X[j], metric) for j in range(n)] for i in range(n)]
+    out = []
+    for i, j in combinations(range(n), 2):
+        if not any(max(K[k][i], K[k][j]) < K[i][j] for k in range(n) if k not in (i, j)):
+            out.append((i, j))
+    return out
+
+
+def _sqrt_lt_sqrt_minus(a, b, c):
+    """Exactly decide sqrt(a) < sqrt(b) - c for rationals a, b >= 0 and c >= 0."""
+    # sqrt(a) + c < sqrt(b)  <=>  a + c^2 + 2c sqrt(a) < b
+    lhs_rat = a + c * c
+    if c == 0:
+        return a < b
+    if lhs_rat >= b:
+        return False
+    # 2c sqrt(a) < b - a - c^2 (both sides >= 0)  <=>  4 c^2 a < (b - a - c^2)^2
+    return 4 * c * c * a < (b - lhs_rat) ** 2
+
+
+def grng(P, r, metric):
+    """Edges (i<j) of the GRNG of pivots P with radii r by its definition.
+
+    p_k blocks (p_i, p_j) iff d(p_k,p_i) < d(p_i,p_j) - (2 r_i + r_j) and
+    d(p_k,p_j) < d(p_i,p_j) - (r_i + 2 r_j)."""
+    m = len(P)
+    r = [F(x) for x in r]
+    K = [[key(P[i], P[j], metric) for j in range(m)] for i in range(m)]
+
+    def lt(kk, kij, c):  # d_k < d_ij - c, with d = sqrt(key) for L2, key for L1
+        if metric == L1:
+            return kk < kij - c
+        return _sqrt_lt_sqrt_minus(kk, kij, c)
+
+    out = []
+    for i, j in combinations(range(m), 2):
+        c1 = 2 * r[i] + r[j]
+        c2 = r[i] + 2 * r[j]
+        blocked = any(lt(K[k][i], K[i][j], c1) and lt(K[k][j], K[i][j], c2)
+                      for k in range(m) if k not in (i, j))
+        if not blocked:
+            out.append((i, j))
+    return out

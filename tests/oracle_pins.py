@@ -1,0 +1,235 @@
+"""Pins of the FP64 oracle to facts outside itself.
+
+Each check takes the oracle binding as an argument so the same checks can be run
+against deliberately broken builds of the oracle (see test_oracle_mutants.py).
+Every check raises AssertionError on failure.
+
+What pins what:
+  exact_rng / exact_grng   -- Eq. 1 and the GRNG definition in exact rational
+                              arithmetic on tiny integer/dyadic inputs (exhaustive)
+  worked_examples          -- hand-derived edge sets (tests/golden)
+  invariants               -- 1NN within MST within RNG within GG (Sec. 1), GRNG
+                              with zero radii = RNG, GRNG contains RNG(P) and is
+                              connected (Sec. 2), Theorem 1 and Theorem 2 as
+                              properties of the oracle's outputs
+  cross_checks             -- rng_row vs rng_brute and grng_row vs grng_brute (two
+                              different loops), assignment vs a Python restatement
+"""
+import json
+import os
+
+import numpy as np
+
+from . import exact
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "worked_examples.json")
+
+
+def _as_set(E):
+    return {tuple(map(int, e)) for e in np.asarray(E).reshape(-1, 2)}
+
+
+def _rand_int_points(rng, n, d, hi):
+    return rng.integers(0, hi + 1, size=(n, d)).astype(np.float32)
+
+
+def exact_rng(orc, trials=60, seed=11):
+    rng = np.random.default_rng(seed)
+    for t in range(trials):
+        n = int(rng.integers(3, 11))
+        d = int(rng.integers(1, 4))
+        X = _rand_int_points(rng, n, d, 4)          # small integers: many exact ties
+        for metric in (exact.L2, exact.L1):
+            want = set(exact.rng(X.tolist(), metric))
+            got = _as_set(orc.rng_brute(X, metric))
+            assert got == want, (t, metric, X.tolist(), sorted(want ^ got))
+
+
+def exact_grng(orc, trials=60, seed=12):
+    rng = np.random.default_rng(seed)
+    for t in range(trials):
+        m = int(rng.integers(3, 10))
+        d = int(rng.integers(1, 4))
+        P = _rand_int_points(rng, m, d, 6)
+        for metric in (exact.L2, exact.L1):
+            r = rng.integers(0, 5, size=m) / 8.0          # dyadic radii, exact in FP64
+            if t % 5 == 0:
+                r[:] = 0.0
+            want = set(exact.grng(P.tolist(), r.tolist(), metric))
+            got = _as_set(orc.grng_brute(P, r, metric))
+            assert got == want, (t, metric, P.tolist(), r.tolist(), sorted(want ^ got))
+
+
+def worked_examples(orc):
+    g = json.load(open(GOLDEN))
+    for ex in g["rng"]:
+        X = np.asarray(ex["points"], np.float32)
+        assert _as_set(orc.rng_brute(X, ex["metric"])) == _as_set(ex["edges"]), ex["name"]
+    for ex in g["grng"]:
+        P = np.asarray(ex["points"], np.float32)
+        r = np.asarray(ex["radii"], np.float64)
+        assert _as_set(orc.grng_brute(P, r, ex["metric"])) == _as_set(ex["edges"]), ex["name"]
+
+
+def _key_matrix(orc, X, metric):
+    n = X.shape[0]
+    K = np.zeros((n, n))
+    for i in range(n):
+        for j in range(i + 1, n):
+            K[i, j] = K[j, i] = orc.key(X[i], X[j], metric)
+    return K
+
+
+def _mst_edges(K):
+    """Kruskal on the FP64 key matrix (any MST lies in the RNG: the lune is open)."""
+    n = K.shape[0]
+    iu = np.triu_indices(n, 1)
+    order = np.argsort(K[iu], kind="stable")
+    parent = list(range(n))
+
+    def find(a):
+        while parent[a] != a:
+            parent[a] = parent[parent[a]]
+            a = parent[a]
+        return a
+
+    out = set()
+    for t in order:
+        i, j = int(iu[0][t]), int(iu[1][t])
+        a, b = find(i), find(j)
+        if a != b:
+            parent[a] = b
+            out.add((i, j))
+    return out
+
+
+def _connected(n, E):
+    parent = list(range(n))
+
+    def find(a):
+        while parent[a] != a:
+            parent[a] = parent[parent[a]]
+            a = parent[a]
+        return a
+
+    for i, j in E:
+        parent[find(i)] = find(j)
+    return len({find(i) for i in range(n)}) == 1
+
+
+def invariants(orc, seed=13):
+    rng = np.random.default_rng(seed)
+    for t in range(6):
+        n = int(rng.integers(40, 160))
+        d = int(rng.integers(2, 7))
+        X = rng.standard_normal((n, d)).astype(np.float32)
+        for metric in (exact.L2, exact.L1):
+            E = _as_set(orc.rng_brute(X, metric))
+            K = _key_matrix(orc, X, metric)
+            assert all(i < j for i, j in E)
+            # 1NN within RNG (Sec. 1 chain)
+            Kd = K + np.diag(np.full(n, np.inf))
+            for i in range(n):
+                j = int(np.argmin(Kd[i]))
+                assert (min(i, j), max(i, j)) in E, ("1NN", i, j)
+            # MST within RNG, hence connected (Sec. 1)
+            assert _mst_edges(K) <= E
+            assert _connected(n, E)
+            if metric == exact.L2:
+                # RNG within the Gabriel graph (Sec. 1)
+                for i, j in E:
+                    s = K[i] + K[j]
+                    s[i] = s[j] = np.inf
+                    assert np.all(s >= K[i, j]), ("GG", i, j)
+            # GRNG with zero radii is the RNG; radii >= 0 only add links (Sec. 2)
+            assert _as_set(orc.grng_brute(X, np.zeros(n), metric)) == E
+            r = rng.uniform(0, 0.3, size=n)
+            G = _as_set(orc.grng_brute(X, r, metric))
+            assert E <= G and _connected(n, G)
+            # closed form: once d_ij <= 3 (r_i + r_j) for every pair, no pivot can block
+            dmax = np.sqrt(K.max()) if metric == exact.L2 else K.max()
+            big = np.full(n, dmax / 6.0 * 1.01)
+            assert len(_as_set(orc.grng_brute(X, big, metric))) == n * (n - 1) // 2
+
+
+def theorems(orc, seed=14):
+    """Theorem 1 and Theorem 2 as properties of the oracle's own outputs."""
+    rng = np.random.default_rng(seed)
+    for t in range(4):
+        n = int(rng.integers(200, 400))
+        X = rng.standard_normal((n, 3)).astype(np.float32)
+        for metric in (exact.L2, exact.L1):
+            fine = np.sort(rng.choice(n, size=n // 8, replace=False)).astype(np.int32)
+            coarse = np.sort(rng.choice(fine, size=max(2, len(fine) // 6), replace=False)).astype(np.int32)
+            lay = orc.build_layers(X, [coarse, fine], metric)
+            a_f = lay[1]["assign"]
+            G_f = _as_set(orc.grng_brute(X[fine], lay[1]["radius"], metric))
+            E = _as_set(orc.rng_brute(X, metric))
+            # Theorem 1: RNG links only between members of equal or GRNG-linked domains
+            for x, y in E:
+                p, q = sorted((int(a_f[x]), int(a_f[y])))
+                assert p == q or (p, q) in G_f, ("Thm1", x, y)
+            # Theorem 2: fine GRNG links only between children of equal or linked coarse pivots
+            a_c = lay[0]["assign"]
+            G_c = _as_set(orc.grng_brute(X[coarse], lay[0]["radius"], metric))
+            for i, j in G_f:
+                p, q = sorted((int(a_c[i]), int(a_c[j])))
+                assert p == q or (p, q) in G_c, ("Thm2", i, j)
+            # relative pivot domains nest (Sec. 3): d(c, pb) <= R_c - rb
+            R = lay[0]["radius"]
+            for t_, pb in enumerate(fine):
+                c = coarse[a_c[t_]]
+                dd = orc.dist(X[c], X[pb], metric)
+                assert dd + lay[1]["radius"][t_] <= R[a_c[t_]]
+
+
+def cross_checks(orc, seed=15):
+    rng = np.random.default_rng(seed)
+    for t in range(3):
+        n = int(rng.integers(100, 300))
+        X = rng.standard_normal((n, 4)).astype(np.float32)
+        for metric in (exact.L2, exact.L1):
+            E = _as_set(orc.rng_brute(X, metric))
+            for x in rng.choice(n, size=12, replace=False):
+                want = sorted({j for i, j in E if i == x} | {i for i, j in E if j == x})
+                assert list(orc.rng_row(X, x, metric)) == want, ("row", x)
+            r = rng.uniform(0, 0.2, size=n)
+            r[rng.random(n) < 0.3] = 0.0
+            G = _as_set(orc.grng_brute(X, r, metric))
+            for i in rng.choice(n, size=12, replace=False):
+                want = sorted({j for a, j in G if a == i} | {a for a, j in G if j == i})
+                assert list(orc.grng_row(X, r, i, metric)) == want, ("grow", i)
+    # assignment against a Python restatement in the same canonical order
+    X = rng.standard_normal((120, 5)).astype(np.float32)
+    X[7] = X[3]                                    # a duplicate of a pivot
+    piv = np.array([3, 10, 20, 30, 7], np.int32)   # 7 duplicates pivot 3, at a higher position
+    for metric in (exact.L2, exact.L1):
+        a, d, r, dm = orc.assign(X, np.arange(120, dtype=np.int32), piv, None, metric)
+        for x in range(120):
+            keys = []
+            for p in piv:
+                acc = 0.0
+                for k in range(5):
+                    t_ = float(X[x, k]) - float(X[p, k])
+                    acc = acc + (t_ * t_ if metric == exact.L2 else abs(t_))
+                keys.append(acc)
+            if x in piv:
+                want = int(np.where(piv == x)[0][0])
+            else:
+                want = int(np.argmin(keys))         # first minimum = lowest position
+            assert a[x] == want, (x, a[x], want)
+        for p in range(len(piv)):
+            mem = np.where(a == p)[0]
+            assert r[p] == (d[mem].max() if len(mem) else 0.0)
+            assert dm[p] == r[p]
+        assert a[7] == 4 and a[3] == 0
+
+
+def degree_arithmetic():
+    """Table 4's average degrees are 2E/N; the bench reports degree the same way."""
+    g = json.load(open(GOLDEN))
+    for ex in g["degree"]:
+        assert round(2.0 * ex["edges"] / ex["n"], 4) == ex["avg_degree"], ex["name"]
+
+
+ALL = [exact_rng, exact_grng, worked_examples, invariants, theorems, cross_checks]
