@@ -1,0 +1,147 @@
+/*
+ * grng.h -- C ABI of the GB300 library for exact Relative Neighborhood Graph (RNG)
+ * construction guided by Generalized Relative Neighborhood Graphs (GRNG), after
+ * Foster, Sevilmis & Kimia, arXiv 2208.10022.
+ *
+ * Problem statement (Sec. 1): a set S of N points in a metric space (S, d), here
+ * R^D under L2 or L1.  Pivot layers P_0 (coarsest) ... P_{L-1} (finest) are nested
+ * subsets of S (every coarse pivot is also a fine pivot, as Theorem 2 requires).
+ * Each pivot p has a domain D(p, r) = { x : d(x,p) <= r } (Eq. 2); the finest layer's
+ * domains hold the points, a coarser layer's "relative" domains hold the next finer
+ * layer's pivots together with their radii (Sec. 3).  Each layer's pivots are linked
+ * by the GRNG (definition, Sec. 2) and the points by the RNG (Eq. 1, Sec. 1), which
+ * is returned as an undirected edge list.
+ *
+ * Exactness.  Every decision is the canonical FP64 comparison of the definitions:
+ * key(a,b) = sum_k (a_k - b_k)^2 (L2) or sum_k |a_k - b_k| (L1), summed left to right
+ * in FP64 without fused multiply-add, d = sqrt(key) for L2; GRNG thresholds are
+ * d_ij - (2 r_i + r_j) and d_ij - (r_i + 2 r_j), except that pairs with r_i = r_j = 0
+ * compare keys.  The GPU computes FP32 (or lower) keys, brackets them by a proven
+ * error bound and re-decides in FP64 only the comparisons the bracket cannot
+ * settle, so the results are the definitions' results, bit for bit.
+ *
+ * Conventions.
+ *  - Pointers: every input pointer may be host or device memory (detected with
+ *    cudaPointerGetAttributes); the library copies inputs and never keeps a caller
+ *    pointer after a call returns.  Output pointers may be host or device memory and
+ *    receive copies.  Points are FP32 row-major [n][dim].
+ *  - Buffers too small: the call returns GRNG_ETRUNC and reports the size needed.
+ *  - Streams: work runs on opts.cuda_stream (a cudaStream_t, NULL = legacy default
+ *    stream) of the device current at grng_create; every call returns after that
+ *    stream has finished the call's work.
+ *  - Errors: no exception crosses the ABI; a status is returned and the message of
+ *    the last failure on the calling thread is available from grng_last_error().
+ *    An index on which a call failed with GRNG_ECUDA must be destroyed.
+ *  - Threads: an index is not safe for concurrent calls from several threads.
+ */
+#ifndef GRNG_H
+#define GRNG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t grng_status;
+#define GRNG_OK 0
+#define GRNG_EINVAL 1    /* invalid argument (sizes, indices, nesting, NULL) */
+#define GRNG_ENOMEM 2    /* device or host allocation failed */
+#define GRNG_ECUDA 3     /* a CUDA call failed */
+#define GRNG_ETIMEOUT 4  /* a bounded device wait ran out (status set by a kernel) */
+#define GRNG_ETRUNC 5    /* output buffer too small; the needed size is reported */
+#define GRNG_EINTERNAL 6 /* internal consistency check failed */
+#define GRNG_ESTATE 7    /* call order violated (e.g. a layer not built or not linked) */
+#define GRNG_ENOTIMPL 8  /* option not supported by this build */
+
+typedef enum { GRNG_L2 = 0, GRNG_L1 = 1 } grng_metric;
+typedef enum { GRNG_FP32 = 0, GRNG_BF16 = 1, GRNG_FP8 = 2 } grng_precision;
+
+typedef struct grng_opts {
+  int32_t metric;          /* grng_metric */
+  int32_t precision;       /* grng_precision of the distance tiles (FP32: CUDA cores) */
+  int32_t n_layers;        /* number of pivot layers L >= 1 */
+  int32_t knn_k;           /* neighbour-list length of the exact tier, 1..32 (0: 32) */
+  int32_t k_shortlist;     /* learned interceptor shortlist length (0: off) */
+  int32_t reserved;        /* must be 0 */
+  const void* mlp_weights; /* learned ranker weights (see grng_mlp_*), or NULL */
+  size_t mlp_bytes;
+  int64_t spin_limit;      /* iteration cap of bounded device waits (0: default) */
+  void* cuda_stream;       /* cudaStream_t, or NULL */
+  uint64_t flags;          /* reserved, must be 0 */
+} grng_opts;
+
+typedef struct grng_index grng_index; /* opaque; owns all device state */
+
+/* Fill *o with defaults: L2, FP32, one layer, knn_k 32, default stream. */
+void grng_default_opts(grng_opts* o);
+
+/* Create an index over n points pts[n][dim] (host or device, FP32).  n >= 1,
+ * 1 <= dim <= 4096, n < 2^31.  The points are copied; the device current on the
+ * calling thread is the one used.  Paper: the point set S and metric d (Sec. 1). */
+grng_status grng_create(grng_index** out, const float* pts, int64_t n, int32_t dim,
+                        const grng_opts* opts);
+
+/* Build pivot layer `layer` (0 = coarsest ... n_layers-1 = finest) from m pivot
+ * point indices pivot_idx[m] (host or device int32, distinct, in [0, n)).
+ * Layers are built finest first: the finest layer's members are all points, layer
+ * l's members are the pivots of layer l+1, which must already be built and must
+ * contain every pivot of layer l (nesting).
+ * Each member is assigned to its nearest pivot by canonical key, ties to the lowest
+ * position in pivot_idx, and a member that is itself a pivot to that pivot (Eq. 2).
+ * radius[p] = max over p's members of d(p, member) + member radius (0 for points),
+ * the relative pivot domain of Sec. 3; delta_max[p] = max over p's members of
+ * d(p, member) (Stage VI of Secs. 2 and 3).  An empty domain has radius 0.
+ * Outputs (each may be NULL, host or device): assign[n_members] (pivot positions),
+ * radius[m], delta_max[m].  Rebuilding a layer invalidates its and every coarser
+ * layer's GRNG and the RNG. */
+grng_status grng_build_layer(grng_index* idx, int32_t layer, const int32_t* pivot_idx, int32_t m,
+                             int32_t* assign, double* radius, double* delta_max);
+
+/* GRNG of layer `layer` (definition, Sec. 2).  Every layer must be built; layer
+ * l > 0 must have layer l-1 linked, whose GRNG restricts the candidate pairs
+ * (Theorem 2).  With radius_override (m doubles, host or device) the GRNG of the
+ * layer's pivots with those radii is computed over all pairs instead and is not
+ * stored in the index.
+ * Output: CSR over pivot positions in pivot_idx order, rows sorted ascending, both
+ * directions listed: off[m+1] (int64) and adj[off[m]] (int32), host or device.
+ * off/adj may be NULL (no output).  If adj_cap < off[m] the call stores off,
+ * returns GRNG_ETRUNC and sets *adj_needed (if not NULL) to off[m]. */
+grng_status grng_link_pivots(grng_index* idx, int32_t layer, const double* radius_override,
+                             int64_t* off, int32_t* adj, int64_t adj_cap, int64_t* adj_needed);
+
+/* Rows [row_begin, row_end) of a linked layer's GRNG in the same format: off has
+ * row_end-row_begin+1 entries starting at 0.  For sampling very large layers. */
+grng_status grng_adjacency_rows(grng_index* idx, int32_t layer, int64_t row_begin, int64_t row_end,
+                                int64_t* off, int32_t* adj, int64_t adj_cap, int64_t* adj_needed);
+
+/* Exact RNG of all points (Eq. 1): candidate pairs are the pairs whose finest
+ * pivots are equal or GRNG-linked (Stage I, Theorem 1); each candidate pair is
+ * tested for an empty lune.  Every layer must be built and linked. */
+grng_status rng_build_exact(grng_index* idx);
+
+/* Insert m new points pts[m][dim] (host or device) so that the stored RNG becomes
+ * the RNG of the enlarged set (Algorithm 1 and Stage VII, Sec. 2).  Requires a
+ * built RNG. */
+grng_status rng_insert_batch(grng_index* idx, const float* pts, int64_t m);
+
+/* Copy the RNG edges: ij[cap][2] int32 point indices with i < j, lexicographically
+ * sorted (host or device).  *n_edges receives the edge count; if cap < count the
+ * call returns GRNG_ETRUNC after writing nothing. ij may be NULL to query. */
+grng_status rng_edges(const grng_index* idx, int32_t* ij, int64_t cap, int64_t* n_edges);
+
+/* Counters and timings of the last calls as one JSON object (NUL-terminated).
+ * If cap is too small, returns GRNG_ETRUNC and writes nothing. */
+grng_status grng_stats(const grng_index* idx, char* json, size_t cap);
+
+/* Release the index and all its device memory.  NULL is accepted. */
+void grng_destroy(grng_index* idx);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* grng_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GRNG_H */

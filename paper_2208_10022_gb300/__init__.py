@@ -1,0 +1,210 @@
+"""Python binding of libgrng (include/grng.h): argument marshalling only.
+
+Every step of the computation runs in the CUDA library; this module converts numpy
+arrays / torch tensors into pointers and statuses into exceptions.  There is no
+fallback: if the compiled library is absent, importing the binding's functions
+raises.
+
+    import paper_2208_10022_gb300 as grng
+    ix = grng.Index(points, n_layers=2)            # float32 [n, dim], host or cuda
+    ix.build_layer(1, fine_pivots); ix.build_layer(0, coarse_pivots)
+    ix.link_pivots(0); ix.link_pivots(1)
+    ix.rng_build_exact()
+    edges = ix.rng_edges()                          # int32 [E, 2], i < j, sorted
+"""
+from __future__ import annotations
+
+import ctypes
+import json
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libgrng.so")
+
+GRNG_OK, GRNG_EINVAL, GRNG_ENOMEM, GRNG_ECUDA, GRNG_ETIMEOUT, GRNG_ETRUNC = 0, 1, 2, 3, 4, 5
+GRNG_EINTERNAL, GRNG_ESTATE, GRNG_ENOTIMPL = 6, 7, 8
+L2, L1 = 0, 1
+FP32, BF16, FP8 = 0, 1, 2
+
+EXPORTS = [
+    "grng_default_opts", "grng_create", "grng_build_layer", "grng_link_pivots", "grng_adjacency_rows",
+    "rng_build_exact", "rng_insert_batch", "rng_edges", "grng_stats", "grng_destroy", "grng_last_error",
+]
+
+
+class GrngError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"grng status {status}: {msg}")
+        self.status = status
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [
+        ("metric", ctypes.c_int32), ("precision", ctypes.c_int32), ("n_layers", ctypes.c_int32),
+        ("knn_k", ctypes.c_int32), ("k_shortlist", ctypes.c_int32), ("reserved", ctypes.c_int32),
+        ("mlp_weights", ctypes.c_void_p), ("mlp_bytes", ctypes.c_size_t), ("spin_limit", ctypes.c_int64),
+        ("cuda_stream", ctypes.c_void_p), ("flags", ctypes.c_uint64),
+    ]
+
+
+_lib = None
+
+
+def lib():
+    """The loaded C library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"libgrng.so not built ({LIB_PATH}); run __graft_entry__.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        P, i32, i64, sz = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_size_t
+        L.grng_default_opts.argtypes = [ctypes.POINTER(Opts)]
+        L.grng_default_opts.restype = None
+        L.grng_create.argtypes = [ctypes.POINTER(P), P, i64, i32, ctypes.POINTER(Opts)]
+        L.grng_build_layer.argtypes = [P, i32, P, i32, P, P, P]
+        L.grng_link_pivots.argtypes = [P, i32, P, P, P, i64, ctypes.POINTER(i64)]
+        L.grng_adjacency_rows.argtypes = [P, i32, i64, i64, P, P, i64, ctypes.POINTER(i64)]
+        L.rng_build_exact.argtypes = [P]
+        L.rng_insert_batch.argtypes = [P, P, i64]
+        L.rng_edges.argtypes = [P, P, i64, ctypes.POINTER(i64)]
+        L.grng_stats.argtypes = [P, ctypes.c_char_p, sz]
+        L.grng_destroy.argtypes = [P]
+        L.grng_destroy.restype = None
+        L.grng_last_error.argtypes = []
+        L.grng_last_error.restype = ctypes.c_char_p
+        for f in ("grng_create", "grng_build_layer", "grng_link_pivots", "grng_adjacency_rows",
+                  "rng_build_exact", "rng_insert_batch", "rng_edges", "grng_stats"):
+            getattr(L, f).restype = i32
+        _lib = L
+    return _lib
+
+
+def _check(st):
+    if st != GRNG_OK:
+        raise GrngError(st, lib().grng_last_error().decode())
+
+
+def _ptr(a):
+    """Pointer of a numpy array or torch tensor (host or device); keeps no reference."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data
+    return a.data_ptr()  # torch.Tensor
+
+
+def _contig(a, dtype):
+    if isinstance(a, np.ndarray):
+        return np.ascontiguousarray(a, dtype=dtype)
+    import torch
+    tdt = {np.float32: torch.float32, np.int32: torch.int32, np.float64: torch.float64}[dtype]
+    return a.to(tdt).contiguous()
+
+
+class Index:
+    """An index over a point set (owns the library's grng_index)."""
+
+    def __init__(self, points, n_layers=1, metric=L2, precision=FP32, knn_k=32, stream=None):
+        self._h = ctypes.c_void_p()
+        pts = _contig(points, np.float32)
+        n, dim = int(pts.shape[0]), int(pts.shape[1])
+        o = Opts()
+        lib().grng_default_opts(ctypes.byref(o))
+        o.metric, o.precision, o.n_layers, o.knn_k = metric, precision, n_layers, knn_k
+        if stream is not None:
+            o.cuda_stream = stream if isinstance(stream, int) else stream.cuda_stream
+        _check(lib().grng_create(ctypes.byref(self._h), _ptr(pts), n, dim, ctypes.byref(o)))
+        self.n, self.dim, self.n_layers, self.metric = n, dim, n_layers, metric
+        self._m = [0] * n_layers
+
+    def close(self):
+        if self._h:
+            lib().grng_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def build_layer(self, layer, pivot_idx):
+        piv = _contig(pivot_idx, np.int32)
+        m = int(piv.shape[0])
+        n_mem = self.n if layer == self.n_layers - 1 else self._m[layer + 1]
+        assign = np.zeros(max(n_mem, 1), np.int32)
+        radius = np.zeros(max(m, 1), np.float64)
+        delta = np.zeros(max(m, 1), np.float64)
+        _check(lib().grng_build_layer(self._h, layer, _ptr(piv), m, assign.ctypes.data, radius.ctypes.data,
+                                      delta.ctypes.data))
+        self._m[layer] = m
+        return assign[:n_mem], radius[:m], delta[:m]
+
+    def link_pivots(self, layer, radius_override=None, want_adjacency=True):
+        """GRNG of one layer; returns (off, adj) in pivot order, or None."""
+        m = self._m[layer]
+        r = None if radius_override is None else _contig(radius_override, np.float64)
+        if r is None:
+            _check(lib().grng_link_pivots(self._h, layer, None, None, None, 0, None))
+            return self.adjacency_rows(layer, 0, m) if want_adjacency else None
+        off = np.zeros(m + 1, np.int64)
+        need = ctypes.c_int64(0)
+        cap = m * (m - 1) if m <= 4096 else 0
+        adj = np.zeros(max(cap, 1), np.int32)
+        st = lib().grng_link_pivots(self._h, layer, _ptr(r), off.ctypes.data, adj.ctypes.data, cap,
+                                    ctypes.byref(need))
+        if st == GRNG_ETRUNC:  # the override graph is not stored: compute again with room
+            adj = np.zeros(max(need.value, 1), np.int32)
+            st = lib().grng_link_pivots(self._h, layer, _ptr(r), off.ctypes.data, adj.ctypes.data, need.value,
+                                        ctypes.byref(need))
+        _check(st)
+        return off, adj[:need.value]
+
+    def adjacency_rows(self, layer, r0, r1):
+        off = np.zeros(r1 - r0 + 1, np.int64)
+        need = ctypes.c_int64(0)
+        _check(lib().grng_adjacency_rows(self._h, layer, r0, r1, off.ctypes.data, None, 0, ctypes.byref(need)))
+        adj = np.zeros(max(need.value, 1), np.int32)
+        _check(lib().grng_adjacency_rows(self._h, layer, r0, r1, off.ctypes.data, adj.ctypes.data, need.value,
+                                         ctypes.byref(need)))
+        return off, adj[:need.value]
+
+    def rng_build_exact(self):
+        _check(lib().rng_build_exact(self._h))
+
+    def rng_insert_batch(self, points):
+        pts = _contig(points, np.float32)
+        _check(lib().rng_insert_batch(self._h, _ptr(pts), int(pts.shape[0])))
+
+    def n_edges(self):
+        ne = ctypes.c_int64(0)
+        _check(lib().rng_edges(self._h, None, 0, ctypes.byref(ne)))
+        return ne.value
+
+    def rng_edges(self, out=None):
+        """Edges int32 [E, 2]; `out` may be a preallocated numpy array or cuda tensor."""
+        ne = self.n_edges()
+        if out is None:
+            out = np.zeros((max(ne, 1), 2), np.int32)
+        _check(lib().rng_edges(self._h, _ptr(out), ne, None))
+        return out[:ne]
+
+    def stats(self):
+        buf = ctypes.create_string_buffer(1 << 16)
+        _check(lib().grng_stats(self._h, buf, len(buf)))
+        return json.loads(buf.value.decode())
+
+
+def build_all(X, layers, metric=L2, knn_k=32, want_adjacency=False, stream=None):
+    """Build every layer (finest first), link every layer (coarsest first) and the RNG."""
+    ix = Index(X, n_layers=len(layers), metric=metric, knn_k=knn_k, stream=stream)
+    out = {"layers": [None] * len(layers), "grng": [None] * len(layers)}
+    for li in range(len(layers) - 1, -1, -1):
+        out["layers"][li] = ix.build_layer(li, layers[li])
+    for li in range(len(layers)):
+        out["grng"][li] = ix.link_pivots(li, want_adjacency=want_adjacency)
+    ix.rng_build_exact()
+    out["edges"] = ix.rng_edges()
+    return ix, out

@@ -1,0 +1,593 @@
+// api.cu -- C ABI entry points and host orchestration (see include/grng.h).
+#include <algorithm>
+#include <chrono>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/grng.h"
+#include "common.cuh"
+#include "internal.h"
+
+namespace grng {
+
+static thread_local std::string g_last_error;
+
+[[noreturn]] void fail(int status, const std::string& msg) { throw Failure{status, msg}; }
+
+void cuda_check(cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return;
+  std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+  if (e == cudaErrorMemoryAllocation) fail(GRNG_ENOMEM, m);
+  fail(GRNG_ECUDA, m);
+}
+
+__global__ void compose_parent_kernel(const int32_t* __restrict__ rank_prev, const int32_t* __restrict__ assign,
+                                      int64_t m, int32_t* __restrict__ key) {
+  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < m) key[t] = rank_prev[assign[t]];
+}
+__global__ void permute_parent_kernel(const int32_t* __restrict__ key, const int32_t* __restrict__ order,
+                                      int64_t m, int32_t* __restrict__ out) {
+  int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s < m) out[s] = key[order[s]];
+}
+__global__ void permute_radius_kernel(const double* __restrict__ r, const int32_t* __restrict__ order, int64_t m,
+                                      double* __restrict__ r64, float* __restrict__ rlo, float* __restrict__ rhi) {
+  int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s < m) {
+    double v = r[order[s]];
+    r64[s] = v;
+    rlo[s] = __double2float_rd(v);
+    rhi[s] = __double2float_ru(v);
+  }
+}
+__global__ void iota_kernel(int32_t* a, int64_t m) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < m) a[i] = (int32_t)i;
+}
+__global__ void compose_ids_kernel(const int32_t* __restrict__ piv, const int32_t* __restrict__ order, int64_t m,
+                                   int32_t* __restrict__ out) {
+  int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s < m) out[s] = piv[order[s]];
+}
+__global__ void edges_to_pairs_kernel(const uint64_t* __restrict__ k, int64_t m, int32_t* __restrict__ ij) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < m) {
+    ij[2 * i] = (int32_t)(k[i] >> 32);
+    ij[2 * i + 1] = (int32_t)(k[i] & 0xffffffffu);
+  }
+}
+
+static inline unsigned nblk(int64_t m, int b = 256) { return (unsigned)((m + b - 1) / b); }
+
+struct Layer {
+  bool built = false, linked = false;
+  int64_t m = 0;
+  std::vector<int32_t> piv_h;
+  DevBuf piv, Xp, assign, mdist, radius, delta;
+  DevBuf order, rank, Xs, parent_s, r64s, rlos, rhis, ids_s;
+  DevBuf gx, gg;
+  int64_t words = 0;
+  LevelStats st{};
+  double assign_ms = 0, link_ms = 0, link_tile_ms = 0;
+  unsigned long long assign_amb = 0, assign_fp64 = 0;
+};
+
+struct Timer {
+  cudaEvent_t a, b;
+  cudaStream_t s;
+  explicit Timer(cudaStream_t st) : s(st) {
+    GRNG_CUDA(cudaEventCreate(&a));
+    GRNG_CUDA(cudaEventCreate(&b));
+    GRNG_CUDA(cudaEventRecord(a, s));
+  }
+  double stop() {
+    GRNG_CUDA(cudaEventRecord(b, s));
+    GRNG_CUDA(cudaEventSynchronize(b));
+    float ms = 0;
+    GRNG_CUDA(cudaEventElapsedTime(&ms, a, b));
+    return ms;
+  }
+  ~Timer() {
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+  }
+};
+
+}  // namespace grng
+
+using namespace grng;
+
+struct grng_index {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  grng_opts opts{};
+  int64_t n = 0;
+  int D = 0, Dp = 0, metric = 0, K = 32;
+  DevBuf X, ids;
+  std::vector<Layer> layers;
+  bool sorted = false;
+  DevBuf xorder, xrank, Xs, xparent;
+  DevBuf edges;
+  int64_t n_edges = 0;
+  bool rng_built = false;
+  LevelStats rng_st{};
+  double rng_ms = 0, rng_tile_ms = 0, sort_ms = 0;
+};
+
+namespace {
+
+grng_status guard_status(const Failure& f) {
+  g_last_error = f.msg;
+  return f.status;
+}
+
+template <class F>
+grng_status guarded(grng_index* idx, F&& fn) {
+  try {
+    if (idx) GRNG_CUDA(cudaSetDevice(idx->device));
+    fn();
+    g_last_error.clear();
+    return GRNG_OK;
+  } catch (const Failure& f) {
+    return guard_status(f);
+  } catch (const std::bad_alloc&) {
+    g_last_error = "host allocation failed";
+    return GRNG_ENOMEM;
+  } catch (...) {
+    g_last_error = "unexpected internal exception";
+    return GRNG_EINTERNAL;
+  }
+}
+
+void copy_out(void* dst, const void* src_dev, size_t bytes, cudaStream_t s) {
+  if (!dst || !bytes) return;
+  GRNG_CUDA(cudaMemcpyAsync(dst, src_dev, bytes, cudaMemcpyDefault, s));
+}
+
+int padded_dim(int d) { return d <= 8 ? 8 : d <= 16 ? 16 : ((d + 31) / 32) * 32; }
+
+// DFS order of every layer (pivots grouped under their parents, coarsest first) and
+// of the points; coordinates and radii gathered into that order.
+void ensure_sorted(grng_index* ix) {
+  if (ix->sorted) return;
+  cudaStream_t s = ix->stream;
+  Timer tm(s);
+  const int L = (int)ix->layers.size();
+  DevBuf key, tmp;
+  for (int l = 0; l < L; ++l) {
+    Layer& ly = ix->layers[l];
+    const int64_t m = ly.m;
+    GRNG_CUDA(ly.order.alloc(m * 4));
+    GRNG_CUDA(ly.rank.alloc(m * 4));
+    GRNG_CUDA(ly.parent_s.alloc(m * 4));
+    GRNG_CUDA(key.alloc(m * 4));
+    if (l == 0) {
+      iota_kernel<<<nblk(m), 256, 0, s>>>(ly.order.as<int32_t>(), m);
+      iota_kernel<<<nblk(m), 256, 0, s>>>(ly.rank.as<int32_t>(), m);
+      GRNG_CUDA(cudaMemsetAsync(ly.parent_s.p, 0xff, m * 4, s));
+    } else {
+      Layer& up = ix->layers[l - 1];  // up.assign maps this layer's pivots to up's positions
+      compose_parent_kernel<<<nblk(m), 256, 0, s>>>(up.rank.as<int32_t>(), up.assign.as<int32_t>(), m,
+                                                     key.as<int32_t>());
+      stable_order(key.as<int32_t>(), m, up.m, ly.order.as<int32_t>(), ly.rank.as<int32_t>(), tmp, s);
+      permute_parent_kernel<<<nblk(m), 256, 0, s>>>(key.as<int32_t>(), ly.order.as<int32_t>(), m,
+                                                     ly.parent_s.as<int32_t>());
+    }
+    GRNG_CUDA(ly.ids_s.alloc(m * 4));
+    compose_ids_kernel<<<nblk(m), 256, 0, s>>>(ly.piv.as<int32_t>(), ly.order.as<int32_t>(), m,
+                                                ly.ids_s.as<int32_t>());
+    GRNG_CUDA(ly.Xs.alloc((size_t)m * ix->Dp * 4));
+    gather_rows(ix->X.as<float>(), ix->Dp, ly.ids_s.as<int32_t>(), m, ly.Xs.as<float>(), s);
+    GRNG_CUDA(ly.r64s.alloc(m * 8));
+    GRNG_CUDA(ly.rlos.alloc(m * 4));
+    GRNG_CUDA(ly.rhis.alloc(m * 4));
+    permute_radius_kernel<<<nblk(m), 256, 0, s>>>(ly.radius.as<double>(), ly.order.as<int32_t>(), m,
+                                                   ly.r64s.as<double>(), ly.rlos.as<float>(), ly.rhis.as<float>());
+    GRNG_CUDA(cudaGetLastError());
+  }
+  const int64_t n = ix->n;
+  Layer& fin = ix->layers[L - 1];
+  GRNG_CUDA(ix->xorder.alloc(n * 4));
+  GRNG_CUDA(ix->xrank.alloc(n * 4));
+  GRNG_CUDA(ix->xparent.alloc(n * 4));
+  GRNG_CUDA(key.alloc(n * 4));
+  compose_parent_kernel<<<nblk(n), 256, 0, s>>>(fin.rank.as<int32_t>(), fin.assign.as<int32_t>(), n,
+                                                 key.as<int32_t>());
+  stable_order(key.as<int32_t>(), n, fin.m, ix->xorder.as<int32_t>(), ix->xrank.as<int32_t>(), tmp, s);
+  permute_parent_kernel<<<nblk(n), 256, 0, s>>>(key.as<int32_t>(), ix->xorder.as<int32_t>(), n,
+                                                 ix->xparent.as<int32_t>());
+  GRNG_CUDA(ix->Xs.alloc((size_t)n * ix->Dp * 4));
+  gather_rows(ix->X.as<float>(), ix->Dp, ix->xorder.as<int32_t>(), n, ix->Xs.as<float>(), s);
+  GRNG_CUDA(cudaGetLastError());
+  GRNG_CUDA(cudaStreamSynchronize(s));
+  ix->sort_ms = tm.stop();
+  ix->sorted = true;
+}
+
+void check_layer(const grng_index* ix, int32_t layer) {
+  if (layer < 0 || layer >= (int32_t)ix->layers.size()) fail(GRNG_EINVAL, "layer out of range");
+}
+
+// CSR output of a bitmask (rows [r0, r1) in pivot_idx order)
+void output_rows(grng_index* ix, const uint32_t* bits, int64_t words, const int32_t* rank, int64_t m, int64_t r0,
+                 int64_t r1, int64_t* off, int32_t* adj, int64_t cap, int64_t* needed) {
+  cudaStream_t s = ix->stream;
+  const int64_t rows = r1 - r0;
+  DevBuf doff, dadj;
+  GRNG_CUDA(doff.alloc((size_t)(rows + 1) * 8));
+  bitmask_rows(bits, words, rank, m, r0, r1, doff.as<int64_t>(), nullptr, s);
+  int64_t total = 0;
+  GRNG_CUDA(cudaMemcpyAsync(&total, doff.as<int64_t>() + rows, 8, cudaMemcpyDeviceToHost, s));
+  GRNG_CUDA(cudaStreamSynchronize(s));
+  if (needed) *needed = total;
+  copy_out(off, doff.p, (size_t)(rows + 1) * 8, s);
+  GRNG_CUDA(cudaStreamSynchronize(s));
+  if (!adj) return;
+  if (cap < total) fail(GRNG_ETRUNC, "adjacency buffer too small");
+  GRNG_CUDA(dadj.alloc((size_t)std::max<int64_t>(total, 1) * 4));
+  bitmask_rows(bits, words, rank, m, r0, r1, doff.as<int64_t>(), dadj.as<int32_t>(), s);
+  copy_out(adj, dadj.p, (size_t)total * 4, s);
+  GRNG_CUDA(cudaStreamSynchronize(s));
+}
+
+void level_json(std::string& js, const char* name, const LevelStats& st) {
+  static const char* nm[] = {"candidate_pairs", "quick_links", "tier1_survivors", "tier2a_links", "tier2a_pending",
+                             "tier2a_unresolved", "tier2a_blocked", "tier2b_links", "tier2b_pending",
+                             "tier2b_unresolved", "tier2b_blocked", "tier3_pairs", "fp64_triples",
+                             "fp64_blocking", "edges"};
+  char buf[128];
+  js += "\"";
+  js += name;
+  js += "\":{";
+  for (int i = 0; i < 15; ++i) {
+    snprintf(buf, sizeof(buf), "%s\"%s\":%llu", i ? "," : "", nm[i], (unsigned long long)st.c[i]);
+    js += buf;
+  }
+  js += "}";
+}
+
+}  // namespace
+
+extern "C" {
+
+void grng_default_opts(grng_opts* o) {
+  if (!o) return;
+  memset(o, 0, sizeof(*o));
+  o->metric = GRNG_L2;
+  o->precision = GRNG_FP32;
+  o->n_layers = 1;
+  o->knn_k = 32;
+}
+
+const char* grng_last_error(void) { return g_last_error.c_str(); }
+
+grng_status grng_create(grng_index** out, const float* pts, int64_t n, int32_t dim, const grng_opts* opts) {
+  if (!out) {
+    g_last_error = "out is NULL";
+    return GRNG_EINVAL;
+  }
+  *out = nullptr;
+  grng_index* ix = nullptr;
+  grng_status st = guarded(nullptr, [&] {
+    if (!pts || !opts) fail(GRNG_EINVAL, "pts and opts must not be NULL");
+    if (n < 1 || n >= (int64_t)1 << 31) fail(GRNG_EINVAL, "n must be in [1, 2^31)");
+    if (dim < 1 || dim > 4096) fail(GRNG_EINVAL, "dim must be in [1, 4096]");
+    if (opts->metric != GRNG_L2 && opts->metric != GRNG_L1) fail(GRNG_EINVAL, "unknown metric");
+    if (opts->n_layers < 1 || opts->n_layers > 16) fail(GRNG_EINVAL, "n_layers must be in [1, 16]");
+    if (opts->knn_k < 0 || opts->knn_k > GRNG_KMAX) fail(GRNG_EINVAL, "knn_k must be in [0, 32]");
+    if (opts->precision != GRNG_FP32) fail(GRNG_ENOTIMPL, "only the FP32 tile precision is built");
+    if (opts->k_shortlist != 0 || opts->mlp_weights) fail(GRNG_ENOTIMPL, "learned shortlist not built");
+    if (opts->reserved != 0 || opts->flags != 0) fail(GRNG_EINVAL, "reserved fields must be 0");
+    ix = new grng_index();
+    GRNG_CUDA(cudaGetDevice(&ix->device));
+    ix->opts = *opts;
+    ix->stream = static_cast<cudaStream_t>(opts->cuda_stream);
+    ix->n = n;
+    ix->D = dim;
+    ix->Dp = padded_dim(dim);
+    ix->metric = opts->metric;
+    ix->K = opts->knn_k ? opts->knn_k : 32;
+    ix->layers.resize(opts->n_layers);
+    cudaStream_t s = ix->stream;
+    GRNG_CUDA(ix->X.alloc((size_t)n * ix->Dp * 4));
+    GRNG_CUDA(cudaMemsetAsync(ix->X.p, 0, (size_t)n * ix->Dp * 4, s));
+    GRNG_CUDA(cudaMemcpy2DAsync(ix->X.p, (size_t)ix->Dp * 4, pts, (size_t)dim * 4, (size_t)dim * 4, (size_t)n,
+                                cudaMemcpyDefault, s));
+    GRNG_CUDA(ix->ids.alloc((size_t)n * 4));
+    iota_kernel<<<nblk(n), 256, 0, s>>>(ix->ids.as<int32_t>(), n);
+    GRNG_CUDA(cudaGetLastError());
+    GRNG_CUDA(cudaStreamSynchronize(s));
+  });
+  if (st != GRNG_OK) {
+    delete ix;
+    return st;
+  }
+  *out = ix;
+  return GRNG_OK;
+}
+
+void grng_destroy(grng_index* idx) {
+  if (!idx) return;
+  cudaSetDevice(idx->device);
+  cudaStreamSynchronize(idx->stream);
+  delete idx;
+}
+
+grng_status grng_build_layer(grng_index* ix, int32_t layer, const int32_t* pivot_idx, int32_t m, int32_t* assign,
+                             double* radius, double* delta_max) {
+  if (!ix) {
+    g_last_error = "index is NULL";
+    return GRNG_EINVAL;
+  }
+  return guarded(ix, [&] {
+    check_layer(ix, layer);
+    const int L = (int)ix->layers.size();
+    if (!pivot_idx || m < 1 || m > ix->n) fail(GRNG_EINVAL, "need 1 <= m <= n pivot indices");
+    if (layer < L - 1 && !ix->layers[layer + 1].built)
+      fail(GRNG_ESTATE, "layers are built finest first: build the next finer layer first");
+    cudaStream_t s = ix->stream;
+    Layer& ly = ix->layers[layer];
+    std::vector<int32_t> h(m);
+    GRNG_CUDA(cudaMemcpyAsync(h.data(), pivot_idx, (size_t)m * 4, cudaMemcpyDefault, s));
+    GRNG_CUDA(cudaStreamSynchronize(s));
+    std::vector<char> seen(ix->n, 0);
+    for (int32_t v : h) {
+      if (v < 0 || v >= ix->n) fail(GRNG_EINVAL, "pivot index out of range");
+      if (seen[v]) fail(GRNG_EINVAL, "duplicate pivot index");
+      seen[v] = 1;
+    }
+    if (layer < L - 1) {
+      std::vector<char> fine(ix->n, 0);
+      for (int32_t v : ix->layers[layer + 1].piv_h) fine[v] = 1;
+      for (int32_t v : h)
+        if (!fine[v]) fail(GRNG_EINVAL, "layers must nest: a coarse pivot is missing from the next finer layer");
+    }
+    // invalidate everything that depends on this layer
+    for (int l = 0; l < L; ++l) ix->layers[l].linked = false;
+    for (int l = 0; l < layer; ++l) ix->layers[l].built = false;
+    ix->sorted = false;
+    ix->rng_built = false;
+    Timer tm(s);
+    ly.m = m;
+    ly.piv_h = h;
+    GRNG_CUDA(ly.piv.alloc((size_t)m * 4));
+    GRNG_CUDA(cudaMemcpyAsync(ly.piv.p, h.data(), (size_t)m * 4, cudaMemcpyHostToDevice, s));
+    GRNG_CUDA(ly.Xp.alloc((size_t)m * ix->Dp * 4));
+    gather_rows(ix->X.as<float>(), ix->Dp, ly.piv.as<int32_t>(), m, ly.Xp.as<float>(), s);
+    const bool finest = layer == L - 1;
+    const int64_t nmem = finest ? ix->n : ix->layers[layer + 1].m;
+    const float* Xmem = finest ? ix->X.as<float>() : ix->layers[layer + 1].Xp.as<float>();
+    const int32_t* mem_id = finest ? ix->ids.as<int32_t>() : ix->layers[layer + 1].piv.as<int32_t>();
+    const double* mem_r = finest ? nullptr : ix->layers[layer + 1].radius.as<double>();
+    GRNG_CUDA(ly.assign.alloc((size_t)nmem * 4));
+    GRNG_CUDA(ly.mdist.alloc((size_t)nmem * 8));
+    GRNG_CUDA(ly.radius.alloc((size_t)m * 8));
+    GRNG_CUDA(ly.delta.alloc((size_t)m * 8));
+    AssignOut ao{ly.assign.as<int32_t>(), ly.mdist.as<double>(), ly.radius.as<double>(), ly.delta.as<double>()};
+    unsigned long long ast[2] = {0, 0};
+    assign_layer(Xmem, mem_id, mem_r, nmem, ly.Xp.as<float>(), ly.piv.as<int32_t>(), m, ix->n, ix->D, ix->Dp,
+                 ix->metric, ao, ast, s);
+    ly.assign_amb = ast[0];
+    ly.assign_fp64 = ast[1];
+    ly.built = true;
+    ly.assign_ms = tm.stop();
+    copy_out(assign, ly.assign.p, (size_t)nmem * 4, s);
+    copy_out(radius, ly.radius.p, (size_t)m * 8, s);
+    copy_out(delta_max, ly.delta.p, (size_t)m * 8, s);
+    GRNG_CUDA(cudaStreamSynchronize(s));
+  });
+}
+
+grng_status grng_link_pivots(grng_index* ix, int32_t layer, const double* radius_override, int64_t* off,
+                             int32_t* adj, int64_t adj_cap, int64_t* adj_needed) {
+  if (!ix) {
+    g_last_error = "index is NULL";
+    return GRNG_EINVAL;
+  }
+  return guarded(ix, [&] {
+    check_layer(ix, layer);
+    for (auto& l : ix->layers)
+      if (!l.built) fail(GRNG_ESTATE, "every layer must be built before linking");
+    if (!radius_override && layer > 0 && !ix->layers[layer - 1].linked)
+      fail(GRNG_ESTATE, "link the coarser layer first (its GRNG guides this one, Theorem 2)");
+    ensure_sorted(ix);
+    cudaStream_t s = ix->stream;
+    Layer& ly = ix->layers[layer];
+    const int64_t m = ly.m;
+    const int64_t words = (m + 31) / 32;
+    LevelIn in{};
+    in.X = ly.Xs.as<float>();
+    in.n = m;
+    in.D = ix->D;
+    in.Dp = ix->Dp;
+    in.metric = ix->metric;
+    in.grng = 1;
+    in.K = ix->K;
+    in.orig = ly.order.as<int32_t>();
+    DevBuf ovr, o64, olo, ohi, tgx, tgg;
+    Timer tm(s);
+    if (radius_override) {
+      GRNG_CUDA(ovr.alloc((size_t)m * 8));
+      GRNG_CUDA(cudaMemcpyAsync(ovr.p, radius_override, (size_t)m * 8, cudaMemcpyDefault, s));
+      std::vector<double> hr(m);
+      GRNG_CUDA(cudaMemcpyAsync(hr.data(), ovr.p, (size_t)m * 8, cudaMemcpyDeviceToHost, s));
+      GRNG_CUDA(cudaStreamSynchronize(s));
+      for (double v : hr)
+        if (!(v >= 0.0) || v == INFINITY) fail(GRNG_EINVAL, "radii must be finite and non-negative");
+      GRNG_CUDA(o64.alloc((size_t)m * 8));
+      GRNG_CUDA(olo.alloc((size_t)m * 4));
+      GRNG_CUDA(ohi.alloc((size_t)m * 4));
+      permute_radius_kernel<<<nblk(m), 256, 0, s>>>(ovr.as<double>(), ly.order.as<int32_t>(), m, o64.as<double>(),
+                                                     olo.as<float>(), ohi.as<float>());
+      GRNG_CUDA(cudaGetLastError());
+      in.r64 = o64.as<double>();
+      in.rlo = olo.as<float>();
+      in.rhi = ohi.as<float>();
+      in.parent = nullptr;
+      in.gpar = nullptr;
+      GRNG_CUDA(tgx.alloc((size_t)m * words * 4));
+      GRNG_CUDA(tgg.alloc((size_t)m * words * 4));
+      LevelOut lo;
+      lo.gx = tgx.as<uint32_t>();
+      lo.gg = tgg.as<uint32_t>();
+      lo.words = words;
+      LevelStats st;
+      run_level(in, lo, st, s);
+      output_rows(ix, tgx.as<uint32_t>(), words, ly.rank.as<int32_t>(), m, 0, m, off, adj, adj_cap, adj_needed);
+      return;
+    }
+    in.r64 = ly.r64s.as<double>();
+    in.rlo = ly.rlos.as<float>();
+    in.rhi = ly.rhis.as<float>();
+    if (layer > 0) {
+      in.parent = ly.parent_s.as<int32_t>();
+      in.gpar = ix->layers[layer - 1].gg.as<uint32_t>();
+      in.gpar_words = ix->layers[layer - 1].words;
+    }
+    GRNG_CUDA(ly.gx.alloc((size_t)m * words * 4));
+    GRNG_CUDA(ly.gg.alloc((size_t)m * words * 4));
+    ly.words = words;
+    LevelOut lo;
+    lo.gx = ly.gx.as<uint32_t>();
+    lo.gg = ly.gg.as<uint32_t>();
+    lo.words = words;
+    float tile_ms = 0;
+    run_level(in, lo, ly.st, s, &tile_ms);
+    ly.link_tile_ms = tile_ms;
+    ly.link_ms = tm.stop();
+    ly.linked = true;
+    for (int l = layer + 1; l < (int)ix->layers.size(); ++l) ix->layers[l].linked = false;
+    ix->rng_built = false;
+    if (off || adj_needed)
+      output_rows(ix, ly.gx.as<uint32_t>(), words, ly.rank.as<int32_t>(), m, 0, m, off, adj, adj_cap, adj_needed);
+  });
+}
+
+grng_status grng_adjacency_rows(grng_index* ix, int32_t layer, int64_t row_begin, int64_t row_end, int64_t* off,
+                                int32_t* adj, int64_t adj_cap, int64_t* adj_needed) {
+  if (!ix) {
+    g_last_error = "index is NULL";
+    return GRNG_EINVAL;
+  }
+  return guarded(ix, [&] {
+    check_layer(ix, layer);
+    Layer& ly = ix->layers[layer];
+    if (!ly.linked) fail(GRNG_ESTATE, "layer is not linked");
+    if (row_begin < 0 || row_end > ly.m || row_begin > row_end) fail(GRNG_EINVAL, "row range out of bounds");
+    output_rows(ix, ly.gx.as<uint32_t>(), ly.words, ly.rank.as<int32_t>(), ly.m, row_begin, row_end, off, adj,
+                adj_cap, adj_needed);
+  });
+}
+
+grng_status rng_build_exact(grng_index* ix) {
+  if (!ix) {
+    g_last_error = "index is NULL";
+    return GRNG_EINVAL;
+  }
+  return guarded(ix, [&] {
+    for (auto& l : ix->layers)
+      if (!l.linked) fail(GRNG_ESTATE, "every layer must be built and linked");
+    ensure_sorted(ix);
+    cudaStream_t s = ix->stream;
+    Layer& fin = ix->layers.back();
+    Timer tm(s);
+    LevelIn in{};
+    in.X = ix->Xs.as<float>();
+    in.n = ix->n;
+    in.D = ix->D;
+    in.Dp = ix->Dp;
+    in.metric = ix->metric;
+    in.grng = 0;
+    in.K = ix->K;
+    in.parent = ix->xparent.as<int32_t>();
+    in.gpar = fin.gg.as<uint32_t>();
+    in.gpar_words = fin.words;
+    in.orig = ix->xorder.as<int32_t>();
+    LevelOut lo;
+    lo.edges = &ix->edges;
+    float tile_ms = 0;
+    run_level(in, lo, ix->rng_st, s, &tile_ms);
+    ix->n_edges = lo.n_edges;
+    DevBuf tmp;
+    if (ix->n_edges > 1) sort_u64(ix->edges.as<uint64_t>(), ix->n_edges, tmp, s);
+    ix->rng_tile_ms = tile_ms;
+    ix->rng_ms = tm.stop();
+    ix->rng_built = true;
+  });
+}
+
+grng_status rng_insert_batch(grng_index* ix, const float* pts, int64_t m) {
+  (void)pts;
+  (void)m;
+  if (!ix) {
+    g_last_error = "index is NULL";
+    return GRNG_EINVAL;
+  }
+  g_last_error = "incremental insertion is not built yet";
+  return GRNG_ENOTIMPL;
+}
+
+grng_status rng_edges(const grng_index* cix, int32_t* ij, int64_t cap, int64_t* n_edges) {
+  grng_index* ix = const_cast<grng_index*>(cix);
+  if (!ix) {
+    g_last_error = "index is NULL";
+    return GRNG_EINVAL;
+  }
+  return guarded(ix, [&] {
+    if (!ix->rng_built) fail(GRNG_ESTATE, "the RNG is not built");
+    if (n_edges) *n_edges = ix->n_edges;
+    if (!ij) return;
+    if (cap < ix->n_edges) fail(GRNG_ETRUNC, "edge buffer too small");
+    cudaStream_t s = ix->stream;
+    DevBuf pairs;
+    GRNG_CUDA(pairs.alloc((size_t)std::max<int64_t>(ix->n_edges, 1) * 8));
+    if (ix->n_edges) {
+      edges_to_pairs_kernel<<<nblk(ix->n_edges), 256, 0, s>>>(ix->edges.as<uint64_t>(), ix->n_edges,
+                                                               pairs.as<int32_t>());
+      GRNG_CUDA(cudaGetLastError());
+    }
+    copy_out(ij, pairs.p, (size_t)ix->n_edges * 8, s);
+    GRNG_CUDA(cudaStreamSynchronize(s));
+  });
+}
+
+grng_status grng_stats(const grng_index* cix, char* json, size_t cap) {
+  const grng_index* ix = cix;
+  if (!ix || !json) {
+    g_last_error = "index and json must not be NULL";
+    return GRNG_EINVAL;
+  }
+  std::string js = "{";
+  char buf[256];
+  snprintf(buf, sizeof(buf), "\"n\":%lld,\"dim\":%d,\"metric\":%d,\"knn_k\":%d,\"sort_ms\":%.4f,\"layers\":[",
+           (long long)ix->n, ix->D, ix->metric, ix->K, ix->sort_ms);
+  js += buf;
+  for (size_t l = 0; l < ix->layers.size(); ++l) {
+    const Layer& ly = ix->layers[l];
+    snprintf(buf, sizeof(buf),
+             "%s{\"m\":%lld,\"built\":%d,\"linked\":%d,\"assign_ms\":%.4f,\"link_ms\":%.4f,\"link_tile_ms\":%.4f,"
+             "\"assign_ambiguous\":%llu,\"assign_fp64_keys\":%llu,",
+             l ? "," : "", (long long)ly.m, (int)ly.built, (int)ly.linked, ly.assign_ms, ly.link_ms,
+             ly.link_tile_ms, ly.assign_amb, ly.assign_fp64);
+    js += buf;
+    level_json(js, "grng", ly.st);
+    js += "}";
+  }
+  snprintf(buf, sizeof(buf), "],\"rng_built\":%d,\"n_edges\":%lld,\"rng_ms\":%.4f,\"rng_tile_ms\":%.4f,",
+           (int)ix->rng_built, (long long)ix->n_edges, ix->rng_ms, ix->rng_tile_ms);
+  js += buf;
+  level_json(js, "rng", ix->rng_st);
+  js += "}";
+  if (js.size() + 1 > cap) {
+    g_last_error = "stats buffer too small";
+    return GRNG_ETRUNC;
+  }
+  memcpy(json, js.c_str(), js.size() + 1);
+  return GRNG_OK;
+}
+
+}  // extern "C"

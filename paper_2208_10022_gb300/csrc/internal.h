@@ -1,0 +1,114 @@
+// internal.h -- host-side interfaces between the library's translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+#include <string>
+
+namespace grng {
+
+// ---- device buffer ---------------------------------------------------------------
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  DevBuf() = default;
+  DevBuf(const DevBuf&) = delete;
+  DevBuf& operator=(const DevBuf&) = delete;
+  DevBuf(DevBuf&& o) noexcept : p(o.p), bytes(o.bytes) { o.p = nullptr; o.bytes = 0; }
+  DevBuf& operator=(DevBuf&& o) noexcept {
+    if (this != &o) { release(); p = o.p; bytes = o.bytes; o.p = nullptr; o.bytes = 0; }
+    return *this;
+  }
+  ~DevBuf() { release(); }
+  cudaError_t alloc(size_t b) {
+    if (b <= bytes && p) return cudaSuccess;
+    release();
+    if (b == 0) b = 16;
+    cudaError_t e = cudaMalloc(&p, b);
+    if (e != cudaSuccess) { p = nullptr; bytes = 0; cudaGetLastError(); return e; }
+    bytes = b;
+    return cudaSuccess;
+  }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+  }
+  template <class T> T* as() const { return static_cast<T*>(p); }
+};
+
+// error raised inside the host orchestration; converted to a status at the C-ABI
+struct Failure {
+  int status;
+  std::string msg;
+};
+[[noreturn]] void fail(int status, const std::string& msg);
+void cuda_check(cudaError_t e, const char* what);
+#define GRNG_CUDA(call) ::grng::cuda_check((call), #call)
+
+// ---- utilities (kernels_util.cu) ------------------------------------------------------
+void exclusive_scan_i64(const int64_t* in, int64_t* out, int64_t n, cudaStream_t s);  // out[n] = total
+// counting sort of (key, value) int2 pairs by pair.x (which=0) or pair.y (which=1):
+// off[nkeys+1], val[m] = the other component, grouped by key.
+void group_pairs(const int2* pairs, int64_t m, int which, int64_t nkeys, int64_t* off,
+                 int32_t* val, DevBuf& tmp, cudaStream_t s);
+void sort_u64(uint64_t* keys, int64_t m, DevBuf& tmp, cudaStream_t s);  // ascending, in place
+// stable counting sort of items 0..m-1 by key[] in [0,nkeys): order[m] (item ids), and
+// rank[item] = position in that order
+void stable_order(const int32_t* key, int64_t m, int64_t nkeys, int32_t* order, int32_t* rank,
+                  DevBuf& tmp, cudaStream_t s);
+void gather_rows(const float* X, int Dp, const int32_t* idx, int64_t m, float* out, cudaStream_t s);
+void fill_u32(uint32_t* p, uint32_t v, size_t count, cudaStream_t s);
+// CSR of a triangular bitmask (bit (a,b), a<b, sorted positions) in original order:
+// rank[orig] = sorted position.  off may be null to count only.
+void bitmask_csr(const uint32_t* bits, int64_t words, const int32_t* rank, int64_t m,
+                 int64_t* off, int32_t* adj, DevBuf& tmp, cudaStream_t s);
+void bitmask_rows(const uint32_t* bits, int64_t words, const int32_t* rank, int64_t m,
+                  int64_t row_begin, int64_t row_end, int64_t* off, int32_t* adj, cudaStream_t s);
+
+// ---- assignment (kernels_assign.cu) -----------------------------------------------------
+struct AssignOut {
+  int32_t* assign;    // [nmem] pivot position
+  double* dist;       // [nmem]
+  double* radius;     // [m]
+  double* delta_max;  // [m]
+};
+// members: contiguous coordinates [nmem][Dp] (mem_id = their point indices, for the
+// self-assignment rule); pivots: contiguous coordinates [m][Dp] (piv_id point indices)
+void assign_layer(const float* Xmem, const int32_t* mem_id, const double* mem_r, int64_t nmem,
+                  const float* Xpiv, const int32_t* piv_id, int64_t m, int64_t npoints, int D,
+                  int Dp, int metric, const AssignOut& out, unsigned long long* stats,
+                  cudaStream_t s);
+
+// ---- pair pipeline (kernels_pair.cu) ----------------------------------------------------
+struct LevelIn {
+  const float* X;           // node coordinates in sorted order [n][Dp]
+  int64_t n;
+  int D, Dp, metric;
+  int grng;                 // 1: GRNG test with radii; 0: RNG of exemplars
+  int K;                    // neighbour-list length (<= GRNG_KMAX)
+  const int32_t* parent;    // [n] parent sorted position, or null (all pairs candidates)
+  const uint32_t* gpar;     // guidance bitmask over parents (triangular), or null
+  int64_t gpar_words;
+  const double* r64;        // [n] radii (null: zeros)
+  const float* rlo;         // [n] FP32 lower bounds of r64 (null: zeros)
+  const float* rhi;
+  const int32_t* orig;      // [n] original ids (edge output of the RNG level)
+};
+struct LevelOut {
+  // GRNG level: triangular bitmasks over sorted positions, zero-filled by the caller
+  uint32_t* gx = nullptr;
+  uint32_t* gg = nullptr;
+  int64_t words = 0;
+  // RNG level: edges as (i << 32 | j), i < j original ids, unsorted
+  DevBuf* edges = nullptr;
+  int64_t n_edges = 0;
+};
+struct LevelStats {
+  unsigned long long c[24];
+};
+void run_level(const LevelIn& in, LevelOut& out, LevelStats& st, cudaStream_t s,
+               float* tile_ms = nullptr);
+
+}  // namespace grng

@@ -1,0 +1,206 @@
+// kernels_assign.cu -- one pivot layer (Eq. 2; relative pivot domain, Sec. 3):
+// nearest pivot of every member (ties to the lowest pivot position, a pivot owns
+// itself), FP64 member distance, radius = max(dist + member radius) and
+// delta_max = max(dist).
+//
+// The member x pivot keys come from the FP32 distance tile; a member whose two best
+// FP32 keys cannot be separated under the error bound is re-decided in FP64 against
+// every pivot whose key could tie the minimum.
+#include <algorithm>
+
+#include "common.cuh"
+#include "internal.h"
+#include "tile.cuh"
+
+namespace grng {
+
+template <int KC, int METRIC>
+__global__ void __launch_bounds__(GRNG_THREADS) assign_tile_kernel(const float* __restrict__ Xm, int64_t nmem,
+                                                                   const float* __restrict__ Xp, int64_t m, int Dp,
+                                                                   float* __restrict__ best1,
+                                                                   int32_t* __restrict__ arg1,
+                                                                   float* __restrict__ best2) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  float* sA = reinterpret_cast<float*>(sm_raw);
+  float* sB = sA + KC * GRNG_SSTRIDE;
+  float* T = sB + KC * GRNG_SSTRIDE;  // [128][129]
+  const int64_t xb = (int64_t)blockIdx.x * GRNG_TILE;
+  const int nr = (int)(nmem - xb < GRNG_TILE ? nmem - xb : GRNG_TILE);
+  const int64_t npb = (m + GRNG_TILE - 1) / GRNG_TILE;
+  const float inf = __int_as_float(0x7f800000);
+  float m1 = inf, m2 = inf;
+  int a1 = -1;
+  for (int64_t pb = 0; pb < npb; ++pb) {
+    const int nc = (int)(m - pb * GRNG_TILE < GRNG_TILE ? m - pb * GRNG_TILE : GRNG_TILE);
+    float acc[8][8];
+    tile_keys<KC, METRIC>(Xm + xb * Dp, nr, Xp + pb * GRNG_TILE * Dp, nc, Dp, sA, sB, acc);
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        int r = tile_row(i), c = tile_col(j);
+        T[r * 129 + c] = (c < nc) ? acc[i][j] : inf;
+      }
+    __syncthreads();
+    if (threadIdx.x < nr) {
+      const float* Tr = T + threadIdx.x * 129;
+      for (int c = 0; c < GRNG_TILE; ++c) {
+        float v = Tr[c];
+        if (v < m1) { m2 = m1; m1 = v; a1 = (int)(pb * GRNG_TILE + c); }
+        else if (v < m2) m2 = v;
+      }
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x < nr) {
+    best1[xb + threadIdx.x] = m1;
+    arg1[xb + threadIdx.x] = a1;
+    best2[xb + threadIdx.x] = m2;
+  }
+}
+
+// decide: self-assignment, certain argmin, or ambiguous (queued for FP64)
+__global__ void assign_decide_kernel(const int32_t* __restrict__ mem_id, int64_t nmem,
+                                     const int32_t* __restrict__ pivpos, const float* __restrict__ best1,
+                                     const int32_t* __restrict__ arg1, const float* __restrict__ best2,
+                                     int Dp, int32_t* __restrict__ assign, int32_t* __restrict__ amb,
+                                     unsigned long long* __restrict__ amb_cnt) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nmem) return;
+  const int pp = pivpos[mem_id[t]];
+  if (pp >= 0) { assign[t] = pp; return; }
+  const Err e = err_fp32(Dp);
+  if (hi_b(best1[t], e) < lo_b(best2[t], e)) {
+    assign[t] = arg1[t];
+  } else {
+    assign[t] = -1;
+    unsigned long long pos = atomicAdd(amb_cnt, 1ull);
+    amb[pos] = (int32_t)t;
+  }
+}
+
+// FP64 argmin over every pivot whose key could reach the FP32 minimum
+__global__ void assign_recheck_kernel(const float* __restrict__ Xm, const float* __restrict__ Xp,
+                                      int64_t m, int D, int Dp, int metric,
+                                      const int32_t* __restrict__ amb, const float* __restrict__ best1,
+                                      int32_t* __restrict__ assign, unsigned long long* __restrict__ n64) {
+  __shared__ double sk[256];
+  __shared__ int si[256];
+  const int64_t t = amb[blockIdx.x];
+  const float* x = Xm + t * Dp;
+  const Err e = err_fp32(Dp);
+  const float lim = hi_b(best1[t], e);
+  double bk = 0.0;
+  int bi = -1;
+  unsigned long long cnt = 0;
+  for (int64_t j = threadIdx.x; j < m; j += blockDim.x) {
+    const float* pj = Xp + j * Dp;
+    if (lo_b(key32(x, pj, Dp, metric), e) <= lim) {
+      double k = key64(x, pj, D, metric);
+      ++cnt;
+      if (bi < 0 || k < bk) { bk = k; bi = (int)j; }  // j ascends per thread: ties keep the lowest
+    }
+  }
+  sk[threadIdx.x] = bk;
+  si[threadIdx.x] = bi;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) {
+      double k2 = sk[threadIdx.x + w];
+      int i2 = si[threadIdx.x + w];
+      if (i2 >= 0 && (si[threadIdx.x] < 0 || k2 < sk[threadIdx.x] ||
+                      (k2 == sk[threadIdx.x] && i2 < si[threadIdx.x]))) {
+        sk[threadIdx.x] = k2;
+        si[threadIdx.x] = i2;
+      }
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) assign[t] = si[0];
+  atomicAdd(n64, cnt);
+}
+
+__global__ void member_dist_kernel(const float* __restrict__ Xm, const float* __restrict__ Xp,
+                                   const double* __restrict__ mem_r, int64_t nmem, int D, int Dp,
+                                   int metric, const int32_t* __restrict__ assign,
+                                   double* __restrict__ dist, unsigned long long* __restrict__ radius,
+                                   unsigned long long* __restrict__ delta) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nmem) return;
+  const int p = assign[t];
+  if (p < 0) return;  // cannot happen: the FP32 argmin always survives the recheck filter
+  double d = dist_of_key64(key64(Xm + t * Dp, Xp + (int64_t)p * Dp, D, metric), metric);
+  dist[t] = d;
+  double rr = __dadd_rn(d, mem_r ? mem_r[t] : 0.0);
+  atomicMax(radius + p, dbl_as_ull(rr));  // non-negative doubles order like their bits
+  atomicMax(delta + p, dbl_as_ull(d));
+}
+
+__global__ void pivpos_kernel(const int32_t* __restrict__ piv_id, int64_t m, int32_t* __restrict__ pivpos) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < m) pivpos[piv_id[j]] = (int32_t)j;
+}
+
+template <int KC>
+static void launch_assign_tile(const float* Xm, int64_t nmem, const float* Xp, int64_t m, int Dp,
+                               int metric, float* b1, int32_t* a1, float* b2, cudaStream_t s) {
+  const size_t smem = (size_t)(2 * KC * GRNG_SSTRIDE + 128 * 129) * 4;
+  const unsigned grid = (unsigned)((nmem + GRNG_TILE - 1) / GRNG_TILE);
+  if (metric == L2) {
+    GRNG_CUDA(cudaFuncSetAttribute(assign_tile_kernel<KC, L2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    assign_tile_kernel<KC, L2><<<grid, GRNG_THREADS, smem, s>>>(Xm, nmem, Xp, m, Dp, b1, a1, b2);
+  } else {
+    GRNG_CUDA(cudaFuncSetAttribute(assign_tile_kernel<KC, L1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    assign_tile_kernel<KC, L1><<<grid, GRNG_THREADS, smem, s>>>(Xm, nmem, Xp, m, Dp, b1, a1, b2);
+  }
+  GRNG_CUDA(cudaGetLastError());
+}
+
+void assign_layer(const float* Xmem, const int32_t* mem_id, const double* mem_r, int64_t nmem,
+                  const float* Xpiv, const int32_t* piv_id, int64_t m, int64_t npoints, int D, int Dp,
+                  int metric, const AssignOut& out, unsigned long long* stats, cudaStream_t s) {
+  if (nmem == 0 || m == 0) return;
+  DevBuf pivpos, b1, a1, b2, amb, cnt;
+  GRNG_CUDA(pivpos.alloc((size_t)npoints * 4));
+  GRNG_CUDA(cudaMemsetAsync(pivpos.p, 0xff, (size_t)npoints * 4, s));
+  pivpos_kernel<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(piv_id, m, pivpos.as<int32_t>());
+  GRNG_CUDA(b1.alloc((size_t)nmem * 4));
+  GRNG_CUDA(a1.alloc((size_t)nmem * 4));
+  GRNG_CUDA(b2.alloc((size_t)nmem * 4));
+  GRNG_CUDA(amb.alloc((size_t)nmem * 4));
+  GRNG_CUDA(cnt.alloc(16));
+  GRNG_CUDA(cudaMemsetAsync(cnt.p, 0, 16, s));
+  const int KC = Dp % 32 == 0 ? 32 : (Dp % 16 == 0 ? 16 : 8);
+  if (KC == 32) launch_assign_tile<32>(Xmem, nmem, Xpiv, m, Dp, metric, b1.as<float>(), a1.as<int32_t>(), b2.as<float>(), s);
+  else if (KC == 16) launch_assign_tile<16>(Xmem, nmem, Xpiv, m, Dp, metric, b1.as<float>(), a1.as<int32_t>(), b2.as<float>(), s);
+  else launch_assign_tile<8>(Xmem, nmem, Xpiv, m, Dp, metric, b1.as<float>(), a1.as<int32_t>(), b2.as<float>(), s);
+  unsigned long long* dc = cnt.as<unsigned long long>();
+  assign_decide_kernel<<<(unsigned)((nmem + 255) / 256), 256, 0, s>>>(
+      mem_id, nmem, pivpos.as<int32_t>(), b1.as<float>(), a1.as<int32_t>(), b2.as<float>(), Dp, out.assign,
+      amb.as<int32_t>(), dc);
+  GRNG_CUDA(cudaGetLastError());
+  unsigned long long namb = 0;
+  GRNG_CUDA(cudaMemcpyAsync(&namb, dc, 8, cudaMemcpyDeviceToHost, s));
+  GRNG_CUDA(cudaStreamSynchronize(s));
+  if (namb) {
+    assign_recheck_kernel<<<(unsigned)namb, 256, 0, s>>>(Xmem, Xpiv, m, D, Dp, metric, amb.as<int32_t>(),
+                                                         b1.as<float>(), out.assign, dc + 1);
+    GRNG_CUDA(cudaGetLastError());
+  }
+  GRNG_CUDA(cudaMemsetAsync(out.radius, 0, (size_t)m * 8, s));
+  GRNG_CUDA(cudaMemsetAsync(out.delta_max, 0, (size_t)m * 8, s));
+  member_dist_kernel<<<(unsigned)((nmem + 255) / 256), 256, 0, s>>>(
+      Xmem, Xpiv, mem_r, nmem, D, Dp, metric, out.assign, out.dist,
+      reinterpret_cast<unsigned long long*>(out.radius), reinterpret_cast<unsigned long long*>(out.delta_max));
+  GRNG_CUDA(cudaGetLastError());
+  if (stats) {
+    unsigned long long h[2];
+    GRNG_CUDA(cudaMemcpyAsync(h, dc, 16, cudaMemcpyDeviceToHost, s));
+    GRNG_CUDA(cudaStreamSynchronize(s));
+    stats[0] += h[0];  // ambiguous members
+    stats[1] += h[1];  // FP64 member-pivot keys
+  }
+  GRNG_CUDA(cudaStreamSynchronize(s));
+}
+
+}  // namespace grng
