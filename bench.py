@@ -1,0 +1,305 @@
+#!/usr/bin/env python
+"""Exact RNG construction throughput (edges/s) on one GB300 per rank.
+
+One step = the whole hot path over one synthetic workload: every pivot layer built
+(assignment, radii, delta_max), every layer's GRNG linked (coarsest first), the
+exemplar RNG built and its sorted edge list produced, all through the C ABI.
+
+Workload: "lin96" -- 1,000,000 points in R^96 with intrinsic dimension 8
+(x = A z + 0.01 eps, z ~ N(0, I_8), A_ij ~ N(0, 1/8)), L2, three nested random pivot
+layers of 1,024 / 16,384 / 131,072 pivots.  The points (384 MB) exceed the 129 MB L2,
+so no flush is needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gpu|reference]
+
+Under torchrun each rank builds its own replica (the build is not split across GPUs);
+value = edges of all ranks / the slowest rank's time.
+"""
+import argparse
+import csv
+import io
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "exact RNG edges/s at 1M pts: BF16+learned vs plain FP32, edges = oracle"
+UNIT = "edges/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--n", type=int, default=None, help="points (default: the full 1,000,000)")
+    ap.add_argument("--kind", default="lin96")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample", type=int, default=12000, help="points of the oracle's bounded sample")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class Clocks:
+    """nvidia-smi samples of the SM clock and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        self.p.wait()
+        self.f.flush()
+        rows = list(csv.reader(io.StringIO(open(self.f.name).read())))
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, r[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def load_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+def cpu_baseline(kind, n_sample, seed=3002):
+    """The FP64 oracle (brute force over all triples, Eq. 1) on a bounded sample."""
+    import oracle
+    from paper_2208_10022_gb300 import workloads as wl
+    w = wl.make(kind, n=n_sample, data_seed=seed)
+    t0 = time.perf_counter()
+    E = oracle.rng_brute(w.X)
+    dt = time.perf_counter() - t0
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": len(E) / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"rng_brute on a seeded {n_sample}-point sample of the {kind} generator "
+                      f"({len(E)} edges in {dt:.2f} s)", "seconds": dt, "edges": int(len(E))}
+
+
+def run_reference(a, rank, world):
+    if rank != 0:
+        return 0
+    from paper_2208_10022_gb300 import workloads as wl
+    N0, D, sizes, _, _ = wl.SPECS[a.kind]
+    n = a.n or N0
+    last = None
+    for _ in range(a.warmup):
+        last = cpu_baseline(a.kind, a.cpu_sample)
+    times, edges = [], 0
+    for _ in range(a.steps):
+        last = cpu_baseline(a.kind, a.cpu_sample)
+        times.append(last["seconds"])
+        edges += last["edges"]
+    tot = sum(times)
+    v = edges / tot
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": a.gpus, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": 1000 * tot / max(a.steps, 1), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"{a.kind}: {n} x {D}, layers {sizes}", "oracle_sample_points": a.cpu_sample},
+            "cpu_baseline": {k: last[k] for k in ("kind", "cores", "sample")} | {"value": v, "unit": UNIT},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_gpu(a, rank, world, local):
+    import numpy as np
+    import torch
+
+    import paper_2208_10022_gb300 as g
+    from paper_2208_10022_gb300 import build as gb
+    from paper_2208_10022_gb300 import workloads as wl
+
+    gb.build()
+    torch.cuda.set_device(local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+        pg = dist
+    N0, D, sizes0, _, _ = wl.SPECS[a.kind]
+    w = wl.make(a.kind, n=a.n)
+    n, L = w.n, len(w.layers)
+    sizes = [len(l) for l in w.layers]
+    stream = torch.cuda.current_stream()
+    Xd = torch.from_numpy(w.X).cuda()
+    piv_d = [torch.from_numpy(l).cuda() for l in w.layers]
+
+    def step_device():
+        ix = g.Index(Xd, n_layers=L, stream=stream)
+        for li in range(L - 1, -1, -1):
+            ix.build_layer(li, piv_d[li], outputs=False)
+        for li in range(L):
+            ix.link_pivots(li, want_adjacency=False)
+        ix.rng_build_exact()
+        ne = ix.n_edges()
+        out = torch.empty((max(ne, 1), 2), dtype=torch.int32, device="cuda")
+        ix.rng_edges(out=out)
+        st = ix.stats()
+        ix.close()
+        return ne, st
+
+    def barrier():
+        if pg:
+            pg.barrier()
+        torch.cuda.synchronize()
+
+    wst = None
+    for _ in range(a.warmup):
+        _, wst = step_device()
+    barrier()
+    if wst is not None:
+        launches0 = wst["kernel_launches"]           # counter after the last warm-up step
+    else:
+        probe = g.Index(np.zeros((1, 1), np.float32))  # its creation launches one kernel
+        launches0 = probe.stats()["kernel_launches"]
+        probe.close()
+    clk = Clocks(local)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    tile_ms, edges, stats = [], 0, None
+    for _ in range(a.steps):
+        ne, stats = step_device()
+        edges += ne
+        tile_ms.append(stats["rng_tile_ms"])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    launches1 = stats["kernel_launches"]  # counter after the last timed step
+    ms = e0.elapsed_time(e1)
+    if pg:
+        t = torch.tensor([ms], device="cuda")
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        ms = float(t.item())
+    value = edges * world / (ms / 1000.0)
+
+    # end to end through the C ABI with host buffers: H2D of points and pivots, D2H of edges
+    e2e = None
+    if not a.no_e2e:
+        Xh = torch.from_numpy(w.X).pin_memory()
+        pivh = [torch.from_numpy(l).pin_memory() for l in w.layers]
+        eh = torch.empty((max(edges // max(a.steps, 1), 1) + 16, 2), dtype=torch.int32).pin_memory()
+        barrier()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        e_edges = 0
+        for _ in range(a.steps):
+            ix = g.Index(Xh, n_layers=L, stream=stream)
+            for li in range(L - 1, -1, -1):
+                ix.build_layer(li, pivh[li], outputs=False)
+            for li in range(L):
+                ix.link_pivots(li, want_adjacency=False)
+            ix.rng_build_exact()
+            ne = ix.n_edges()
+            if ne > eh.shape[0]:
+                eh = torch.empty((ne, 2), dtype=torch.int32).pin_memory()
+            ix.rng_edges(out=eh)
+            e_edges += ne
+            ix.close()
+        f1.record(stream)
+        torch.cuda.synchronize()
+        ems = f0.elapsed_time(f1)
+        if pg:
+            t = torch.tensor([ems], device="cuda")
+            pg.all_reduce(t, op=pg.ReduceOp.MAX)
+            ems = float(t.item())
+        e2e = {"value": e_edges * world / (ems / 1000.0), "unit": UNIT,
+               "h2d_bytes_per_step": int(w.X.nbytes + sum(l.nbytes for l in w.layers)),
+               "d2h_bytes_per_step": int(8 * (e_edges // max(a.steps, 1)))}
+
+    # roofline of the dominant kernel: the exemplar distance-tile sweep (FP32 CUDA cores).
+    # Algorithmic work: one FP32 subtract and one FMA per dimension for every unordered
+    # pair of points; peak: 128 FP32 lanes x SMs x the maximum SM clock.
+    peaks = load_peaks()
+    sm_max = peaks.get("sm_max_mhz", 2070.0)
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    peak_gops = sms * 128 * sm_max / 1000.0
+    tile_s = statistics.mean(tile_ms) / 1000.0
+    ops = n * (n - 1) / 2 * 2 * D
+    achieved = ops / tile_s / 1e9
+    traffic = None
+    prof = os.path.join(ROOT, "profiles", "tile_pass_traffic.json")
+    if os.path.exists(prof):
+        try:
+            tp = json.load(open(prof))
+            if tp.get("n") == n and tp.get("kernel_version") == "fp32-v1":
+                traffic = tp.get("dram_bytes_per_launch")
+        except ValueError:
+            traffic = None
+    roof = {"kernel": "tile_pass_kernel (exemplar level)", "bound": "alu", "achieved": achieved,
+            "peak": peak_gops, "unit": "Gop/s", "frac": achieved / peak_gops, "traffic": traffic,
+            "peak_source": f"derived: {sms} SMs x 128 FP32 lanes x {sm_max:.0f} MHz (MEASURED_PEAKS sm_max_mhz)",
+            "ops_per_launch": ops, "launch_ms": 1000 * tile_s}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
+            "ms_per_step": ms / a.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"{a.kind}: {n:,} x {D} FP32, intrinsic dim 8, L2, nested random pivot layers "
+                                   f"{'/'.join(str(s) for s in sizes)}", "n": n, "dim": D, "layers": sizes,
+                       "metric": "L2", "precision": "fp32 tiles + fp64 near-tie recheck",
+                       "l2_flush": "inputs larger than L2 (points alone are %d MB)" % (w.X.nbytes >> 20),
+                       "parallelism": f"replicas x{world}"},
+            "edges_per_step": edges // max(a.steps, 1), "roofline": roof, "clocks": clocks,
+            "gpu_launches": launches1 - launches0, "e2e": e2e,
+            "detail": {"rng": stats["rng"], "layers": stats["layers"],
+                       "rng_ms": stats["rng_ms"], "rng_tile_ms": stats["rng_tile_ms"], "sort_ms": stats["sort_ms"]}}
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        cb = cpu_baseline(a.kind, a.cpu_sample)
+        line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if pg:
+        pg.destroy_process_group()
+    return 0
+
+
+def main():
+    a = parse()
+    rank, world, local = dist_env()
+    if a.impl == "reference":
+        return run_reference(a, rank, world)
+    return run_gpu(a, rank, world, local)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -69,8 +69,12 @@ typedef struct grng_opts {
   size_t mlp_bytes;
   int64_t spin_limit;      /* iteration cap of bounded device waits (0: default) */
   void* cuda_stream;       /* cudaStream_t, or NULL */
-  uint64_t flags;          /* reserved, must be 0 */
+  uint64_t flags;          /* 0, or GRNG_FLAG_SHORT_LISTS (testing) */
 } grng_opts;
+
+/* Testing aid: cap the pivot layers' range lists at 16 nodes so that more pairs take
+ * the hierarchical exhaustive tier.  Results are identical; only the work changes. */
+#define GRNG_FLAG_SHORT_LISTS 1ull
 
 typedef struct grng_index grng_index; /* opaque; owns all device state */
 

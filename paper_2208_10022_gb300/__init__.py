@@ -106,13 +106,13 @@ def _contig(a, dtype):
 class Index:
     """An index over a point set (owns the library's grng_index)."""
 
-    def __init__(self, points, n_layers=1, metric=L2, precision=FP32, knn_k=32, stream=None):
+    def __init__(self, points, n_layers=1, metric=L2, precision=FP32, knn_k=32, stream=None, flags=0):
         self._h = ctypes.c_void_p()
         pts = _contig(points, np.float32)
         n, dim = int(pts.shape[0]), int(pts.shape[1])
         o = Opts()
         lib().grng_default_opts(ctypes.byref(o))
-        o.metric, o.precision, o.n_layers, o.knn_k = metric, precision, n_layers, knn_k
+        o.metric, o.precision, o.n_layers, o.knn_k, o.flags = metric, precision, n_layers, knn_k, flags
         if stream is not None:
             o.cuda_stream = stream if isinstance(stream, int) else stream.cuda_stream
         _check(lib().grng_create(ctypes.byref(self._h), _ptr(pts), n, dim, ctypes.byref(o)))
@@ -130,9 +130,14 @@ class Index:
         except Exception:
             pass
 
-    def build_layer(self, layer, pivot_idx):
+    def build_layer(self, layer, pivot_idx, outputs=True):
+        """Assignment, radii and delta_max of one layer (copied to numpy if outputs)."""
         piv = _contig(pivot_idx, np.int32)
         m = int(piv.shape[0])
+        if not outputs:
+            _check(lib().grng_build_layer(self._h, layer, _ptr(piv), m, None, None, None))
+            self._m[layer] = m
+            return None
         n_mem = self.n if layer == self.n_layers - 1 else self._m[layer + 1]
         assign = np.zeros(max(n_mem, 1), np.int32)
         radius = np.zeros(max(m, 1), np.float64)
@@ -197,9 +202,12 @@ class Index:
         return json.loads(buf.value.decode())
 
 
-def build_all(X, layers, metric=L2, knn_k=32, want_adjacency=False, stream=None):
+GRNG_FLAG_SHORT_LISTS = 1
+
+
+def build_all(X, layers, metric=L2, knn_k=32, want_adjacency=False, stream=None, flags=0):
     """Build every layer (finest first), link every layer (coarsest first) and the RNG."""
-    ix = Index(X, n_layers=len(layers), metric=metric, knn_k=knn_k, stream=stream)
+    ix = Index(X, n_layers=len(layers), metric=metric, knn_k=knn_k, stream=stream, flags=flags)
     out = {"layers": [None] * len(layers), "grng": [None] * len(layers)}
     for li in range(len(layers) - 1, -1, -1):
         out["layers"][li] = ix.build_layer(li, layers[li])

@@ -1,5 +1,6 @@
 // api.cu -- C ABI entry points and host orchestration (see include/grng.h).
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cstdio>
 #include <cstring>
@@ -16,6 +17,10 @@ namespace grng {
 static thread_local std::string g_last_error;
 
 [[noreturn]] void fail(int status, const std::string& msg) { throw Failure{status, msg}; }
+
+static std::atomic<unsigned long long> g_launches{0};
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+unsigned long long launches() { return g_launches.load(std::memory_order_relaxed); }
 
 void cuda_check(cudaError_t e, const char* what) {
   if (e == cudaSuccess) return;
@@ -44,6 +49,11 @@ __global__ void permute_radius_kernel(const double* __restrict__ r, const int32_
     rhi[s] = __double2float_ru(v);
   }
 }
+__global__ void permute_hi_kernel(const double* __restrict__ r, const int32_t* __restrict__ order, int64_t m,
+                                  float* __restrict__ hi) {
+  int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s < m) hi[s] = __double2float_ru(r[order[s]]);
+}
 __global__ void iota_kernel(int32_t* a, int64_t m) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < m) a[i] = (int32_t)i;
@@ -69,6 +79,9 @@ struct Layer {
   std::vector<int32_t> piv_h;
   DevBuf piv, Xp, assign, mdist, radius, delta;
   DevBuf order, rank, Xs, parent_s, r64s, rlos, rhis, ids_s;
+  DevBuf dhis;    // FP32 upper bound of delta_max, sorted order
+  DevBuf pdh;     // FP32 upper bound of d(pivot, its parent pivot), sorted order (layers > 0)
+  DevBuf cstart;  // [m+1] children range in the next finer level (points for the finest)
   DevBuf gx, gg;
   int64_t words = 0;
   LevelStats st{};
@@ -110,7 +123,7 @@ struct grng_index {
   DevBuf X, ids;
   std::vector<Layer> layers;
   bool sorted = false;
-  DevBuf xorder, xrank, Xs, xparent;
+  DevBuf xorder, xrank, Xs, xparent, xpdh;
   DevBuf edges;
   int64_t n_edges = 0;
   bool rng_built = false;
@@ -166,28 +179,40 @@ void ensure_sorted(grng_index* ix) {
     GRNG_CUDA(ly.parent_s.alloc(m * 4));
     GRNG_CUDA(key.alloc(m * 4));
     if (l == 0) {
-      iota_kernel<<<nblk(m), 256, 0, s>>>(ly.order.as<int32_t>(), m);
-      iota_kernel<<<nblk(m), 256, 0, s>>>(ly.rank.as<int32_t>(), m);
+      iota_kernel<<<nblk(m), 256, 0, s>>>(ly.order.as<int32_t>(), m); note_launch();
+      iota_kernel<<<nblk(m), 256, 0, s>>>(ly.rank.as<int32_t>(), m); note_launch();
       GRNG_CUDA(cudaMemsetAsync(ly.parent_s.p, 0xff, m * 4, s));
     } else {
       Layer& up = ix->layers[l - 1];  // up.assign maps this layer's pivots to up's positions
       compose_parent_kernel<<<nblk(m), 256, 0, s>>>(up.rank.as<int32_t>(), up.assign.as<int32_t>(), m,
-                                                     key.as<int32_t>());
+                                                     key.as<int32_t>()); note_launch();
       stable_order(key.as<int32_t>(), m, up.m, ly.order.as<int32_t>(), ly.rank.as<int32_t>(), tmp, s);
       permute_parent_kernel<<<nblk(m), 256, 0, s>>>(key.as<int32_t>(), ly.order.as<int32_t>(), m,
-                                                     ly.parent_s.as<int32_t>());
+                                                     ly.parent_s.as<int32_t>()); note_launch();
     }
     GRNG_CUDA(ly.ids_s.alloc(m * 4));
     compose_ids_kernel<<<nblk(m), 256, 0, s>>>(ly.piv.as<int32_t>(), ly.order.as<int32_t>(), m,
-                                                ly.ids_s.as<int32_t>());
+                                                ly.ids_s.as<int32_t>()); note_launch();
     GRNG_CUDA(ly.Xs.alloc((size_t)m * ix->Dp * 4));
     gather_rows(ix->X.as<float>(), ix->Dp, ly.ids_s.as<int32_t>(), m, ly.Xs.as<float>(), s);
     GRNG_CUDA(ly.r64s.alloc(m * 8));
     GRNG_CUDA(ly.rlos.alloc(m * 4));
     GRNG_CUDA(ly.rhis.alloc(m * 4));
     permute_radius_kernel<<<nblk(m), 256, 0, s>>>(ly.radius.as<double>(), ly.order.as<int32_t>(), m,
-                                                   ly.r64s.as<double>(), ly.rlos.as<float>(), ly.rhis.as<float>());
+                                                   ly.r64s.as<double>(), ly.rlos.as<float>(), ly.rhis.as<float>()); note_launch();
+    GRNG_CUDA(ly.dhis.alloc(m * 4));
+    permute_hi_kernel<<<nblk(m), 256, 0, s>>>(ly.delta.as<double>(), ly.order.as<int32_t>(), m,
+                                               ly.dhis.as<float>()); note_launch();
     GRNG_CUDA(cudaGetLastError());
+  }
+  for (int l = 0; l + 1 < L; ++l) {
+    Layer& ly = ix->layers[l];
+    Layer& nx = ix->layers[l + 1];
+    GRNG_CUDA(nx.pdh.alloc(nx.m * 4));  // ly.mdist is indexed by the finer layer's pivot positions
+    permute_hi_kernel<<<nblk(nx.m), 256, 0, s>>>(ly.mdist.as<double>(), nx.order.as<int32_t>(), nx.m,
+                                                  nx.pdh.as<float>()); note_launch();
+    GRNG_CUDA(ly.cstart.alloc((ly.m + 1) * 4));
+    child_ranges(ix->layers[l + 1].parent_s.as<int32_t>(), ix->layers[l + 1].m, ly.m, ly.cstart.as<int32_t>(), s);
   }
   const int64_t n = ix->n;
   Layer& fin = ix->layers[L - 1];
@@ -196,16 +221,36 @@ void ensure_sorted(grng_index* ix) {
   GRNG_CUDA(ix->xparent.alloc(n * 4));
   GRNG_CUDA(key.alloc(n * 4));
   compose_parent_kernel<<<nblk(n), 256, 0, s>>>(fin.rank.as<int32_t>(), fin.assign.as<int32_t>(), n,
-                                                 key.as<int32_t>());
+                                                 key.as<int32_t>()); note_launch();
   stable_order(key.as<int32_t>(), n, fin.m, ix->xorder.as<int32_t>(), ix->xrank.as<int32_t>(), tmp, s);
   permute_parent_kernel<<<nblk(n), 256, 0, s>>>(key.as<int32_t>(), ix->xorder.as<int32_t>(), n,
-                                                 ix->xparent.as<int32_t>());
+                                                 ix->xparent.as<int32_t>()); note_launch();
+  GRNG_CUDA(fin.cstart.alloc((fin.m + 1) * 4));
+  child_ranges(ix->xparent.as<int32_t>(), n, fin.m, fin.cstart.as<int32_t>(), s);
+  GRNG_CUDA(ix->xpdh.alloc(n * 4));
+  permute_hi_kernel<<<nblk(n), 256, 0, s>>>(fin.mdist.as<double>(), ix->xorder.as<int32_t>(), n,
+                                             ix->xpdh.as<float>()); note_launch();
   GRNG_CUDA(ix->Xs.alloc((size_t)n * ix->Dp * 4));
   gather_rows(ix->X.as<float>(), ix->Dp, ix->xorder.as<int32_t>(), n, ix->Xs.as<float>(), s);
   GRNG_CUDA(cudaGetLastError());
   GRNG_CUDA(cudaStreamSynchronize(s));
   ix->sort_ms = tm.stop();
   ix->sorted = true;
+}
+
+// layers 0..count-1 as the ancestors of a level (the last one is the direct parent,
+// whose delta_max bounds the distance to its members; higher ones use their radius)
+Ancestors ancestors_of(grng_index* ix, int count) {
+  Ancestors a;
+  a.n = count;
+  for (int l = 0; l < count; ++l) {
+    Layer& ly = ix->layers[l];
+    a.X[l] = ly.Xs.as<float>();
+    a.Rhi[l] = (l == count - 1) ? ly.dhis.as<float>() : ly.rhis.as<float>();
+    a.cstart[l] = ly.cstart.as<int32_t>();
+    a.m[l] = ly.m;
+  }
+  return a;
 }
 
 void check_layer(const grng_index* ix, int32_t layer) {
@@ -238,15 +283,22 @@ void level_json(std::string& js, const char* name, const LevelStats& st) {
   static const char* nm[] = {"candidate_pairs", "quick_links", "tier1_survivors", "tier2a_links", "tier2a_pending",
                              "tier2a_unresolved", "tier2a_blocked", "tier2b_links", "tier2b_pending",
                              "tier2b_unresolved", "tier2b_blocked", "tier3_pairs", "fp64_triples",
-                             "fp64_blocking", "edges"};
+                             "fp64_blocking", "edges", "tier3_overflows", "tier3_nodes_tested",
+                             "list_certified", "range_pairs", "range_lists_over_cap", "range_listed_nodes",
+                             "range_links", "range_nodes_tested"};
   char buf[128];
   js += "\"";
   js += name;
   js += "\":{";
-  for (int i = 0; i < 15; ++i) {
+  for (int i = 0; i < 23; ++i) {
     snprintf(buf, sizeof(buf), "%s\"%s\":%llu", i ? "," : "", nm[i], (unsigned long long)st.c[i]);
     js += buf;
   }
+  snprintf(buf, sizeof(buf),
+           ",\"phase_ms\":{\"prep\":%.3f,\"tiles\":%.3f,\"tier2a\":%.3f,\"tier2b\":%.3f,\"range\":%.3f,"
+           "\"tier3\":%.3f,\"recheck_emit\":%.3f}",
+           st.ms[0], st.ms[1], st.ms[2], st.ms[3], st.ms[4], st.ms[5], st.ms[6]);
+  js += buf;
   js += "}";
 }
 
@@ -281,7 +333,8 @@ grng_status grng_create(grng_index** out, const float* pts, int64_t n, int32_t d
     if (opts->knn_k < 0 || opts->knn_k > GRNG_KMAX) fail(GRNG_EINVAL, "knn_k must be in [0, 32]");
     if (opts->precision != GRNG_FP32) fail(GRNG_ENOTIMPL, "only the FP32 tile precision is built");
     if (opts->k_shortlist != 0 || opts->mlp_weights) fail(GRNG_ENOTIMPL, "learned shortlist not built");
-    if (opts->reserved != 0 || opts->flags != 0) fail(GRNG_EINVAL, "reserved fields must be 0");
+    if (opts->reserved != 0 || (opts->flags & ~(uint64_t)GRNG_FLAG_SHORT_LISTS) != 0)
+      fail(GRNG_EINVAL, "reserved fields must be 0");
     ix = new grng_index();
     GRNG_CUDA(cudaGetDevice(&ix->device));
     ix->opts = *opts;
@@ -298,7 +351,7 @@ grng_status grng_create(grng_index** out, const float* pts, int64_t n, int32_t d
     GRNG_CUDA(cudaMemcpy2DAsync(ix->X.p, (size_t)ix->Dp * 4, pts, (size_t)dim * 4, (size_t)dim * 4, (size_t)n,
                                 cudaMemcpyDefault, s));
     GRNG_CUDA(ix->ids.alloc((size_t)n * 4));
-    iota_kernel<<<nblk(n), 256, 0, s>>>(ix->ids.as<int32_t>(), n);
+    iota_kernel<<<nblk(n), 256, 0, s>>>(ix->ids.as<int32_t>(), n); note_launch();
     GRNG_CUDA(cudaGetLastError());
     GRNG_CUDA(cudaStreamSynchronize(s));
   });
@@ -408,6 +461,9 @@ grng_status grng_link_pivots(grng_index* ix, int32_t layer, const double* radius
     in.grng = 1;
     in.K = ix->K;
     in.orig = ly.order.as<int32_t>();
+    in.anc = ancestors_of(ix, layer);
+    in.lmax = (ix->opts.flags & GRNG_FLAG_SHORT_LISTS) ? 16 : 0;
+    in.pdist_hi = layer > 0 ? ly.pdh.as<float>() : nullptr;
     DevBuf ovr, o64, olo, ohi, tgx, tgg;
     Timer tm(s);
     if (radius_override) {
@@ -422,7 +478,7 @@ grng_status grng_link_pivots(grng_index* ix, int32_t layer, const double* radius
       GRNG_CUDA(olo.alloc((size_t)m * 4));
       GRNG_CUDA(ohi.alloc((size_t)m * 4));
       permute_radius_kernel<<<nblk(m), 256, 0, s>>>(ovr.as<double>(), ly.order.as<int32_t>(), m, o64.as<double>(),
-                                                     olo.as<float>(), ohi.as<float>());
+                                                     olo.as<float>(), ohi.as<float>()); note_launch();
       GRNG_CUDA(cudaGetLastError());
       in.r64 = o64.as<double>();
       in.rlo = olo.as<float>();
@@ -507,6 +563,8 @@ grng_status rng_build_exact(grng_index* ix) {
     in.gpar = fin.gg.as<uint32_t>();
     in.gpar_words = fin.words;
     in.orig = ix->xorder.as<int32_t>();
+    in.anc = ancestors_of(ix, (int)ix->layers.size());
+    in.pdist_hi = ix->xpdh.as<float>();
     LevelOut lo;
     lo.edges = &ix->edges;
     float tile_ms = 0;
@@ -547,7 +605,7 @@ grng_status rng_edges(const grng_index* cix, int32_t* ij, int64_t cap, int64_t* 
     GRNG_CUDA(pairs.alloc((size_t)std::max<int64_t>(ix->n_edges, 1) * 8));
     if (ix->n_edges) {
       edges_to_pairs_kernel<<<nblk(ix->n_edges), 256, 0, s>>>(ix->edges.as<uint64_t>(), ix->n_edges,
-                                                               pairs.as<int32_t>());
+                                                               pairs.as<int32_t>()); note_launch();
       GRNG_CUDA(cudaGetLastError());
     }
     copy_out(ij, pairs.p, (size_t)ix->n_edges * 8, s);
@@ -563,8 +621,9 @@ grng_status grng_stats(const grng_index* cix, char* json, size_t cap) {
   }
   std::string js = "{";
   char buf[256];
-  snprintf(buf, sizeof(buf), "\"n\":%lld,\"dim\":%d,\"metric\":%d,\"knn_k\":%d,\"sort_ms\":%.4f,\"layers\":[",
-           (long long)ix->n, ix->D, ix->metric, ix->K, ix->sort_ms);
+  snprintf(buf, sizeof(buf),
+           "\"n\":%lld,\"dim\":%d,\"metric\":%d,\"knn_k\":%d,\"sort_ms\":%.4f,\"kernel_launches\":%llu,\"layers\":[",
+           (long long)ix->n, ix->D, ix->metric, ix->K, ix->sort_ms, launches());
   js += buf;
   for (size_t l = 0; l < ix->layers.size(); ++l) {
     const Layer& ly = ix->layers[l];

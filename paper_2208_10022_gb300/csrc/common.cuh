@@ -138,7 +138,11 @@ __device__ __forceinline__ PairThr pair_thresholds(float v, float rxlo, float rx
   float tau = (float)GRNG_TAU_REL * 4.0f * (dhi + 2.0f * (rxhi + ryhi));
   float t1lo = dlo - c1hi - s1 - (guide ? tau : 0.0f), t1hi = dhi - c1lo + s1;
   float t2lo = dlo - c2hi - s2 - (guide ? tau : 0.0f), t2hi = dhi - c2lo + s2;
-  if (t1hi <= 0.0f || t2hi <= 0.0f) {  // a distance is never negative: linked
+  // Quick accept (exact in the reals): a blocker k needs d(x,y) <= d(k,x) + d(k,y) <
+  // t1 + t2, impossible once t1 + t2 <= d(x,y), i.e. d(x,y) <= 3 (rx + ry); likewise
+  // once a threshold is not positive.  The margin dwarfs the FP64 rounding of the
+  // canonical comparisons, so the FP64 definition agrees.
+  if (t1hi <= 0.0f || t2hi <= 0.0f || t1hi + t2hi <= dlo * (1.0f - 2.0f * u2)) {
     p.quick = 1;
     p.t1lo = p.t2lo = -1.0f;
     p.t1hi = p.t2hi = 0.0f;

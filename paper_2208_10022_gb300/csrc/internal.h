@@ -45,7 +45,12 @@ struct Failure {
 };
 [[noreturn]] void fail(int status, const std::string& msg);
 void cuda_check(cudaError_t e, const char* what);
-#define GRNG_CUDA(call) ::grng::cuda_check((call), #call)
+#define GRNG_STR2(x) #x
+#define GRNG_STR(x) GRNG_STR2(x)
+#define GRNG_CUDA(call) ::grng::cuda_check((call), __FILE__ ":" GRNG_STR(__LINE__) ": " #call)
+// every kernel launch of the library is counted (reported by grng_stats)
+void note_launch();
+unsigned long long launches();
 
 // ---- utilities (kernels_util.cu) ------------------------------------------------------
 void exclusive_scan_i64(const int64_t* in, int64_t* out, int64_t n, cudaStream_t s);  // out[n] = total
@@ -82,6 +87,18 @@ void assign_layer(const float* Xmem, const int32_t* mem_id, const double* mem_r,
                   cudaStream_t s);
 
 // ---- pair pipeline (kernels_pair.cu) ----------------------------------------------------
+#define GRNG_MAXL 16
+// The coarser layers above a level, coarsest first, for the hierarchical exhaustive
+// tier: sorted coordinates, an FP32 upper bound of the distance from each node to
+// anything below it, and the range of its children in the next finer level.
+struct Ancestors {
+  int n = 0;
+  const float* X[GRNG_MAXL];
+  const float* Rhi[GRNG_MAXL];
+  const int32_t* cstart[GRNG_MAXL];  // [m+1]
+  int64_t m[GRNG_MAXL];
+  int64_t toff[GRNG_MAXL];           // column of layer a in the node x ancestor key table
+};
 struct LevelIn {
   const float* X;           // node coordinates in sorted order [n][Dp]
   int64_t n;
@@ -95,7 +112,12 @@ struct LevelIn {
   const float* rlo;         // [n] FP32 lower bounds of r64 (null: zeros)
   const float* rhi;
   const int32_t* orig;      // [n] original ids (edge output of the RNG level)
+  Ancestors anc;            // layers above this level (none for the top GRNG layer)
+  int64_t lmax = 0;         // cap of the range lists (0: the default)
+  const float* pdist_hi = nullptr;  // [n] FP32 upper bound of d(node, parent), or null
 };
+// children ranges: parent[] (non-decreasing, values in [0, m)) -> cstart[m+1]
+void child_ranges(const int32_t* parent, int64_t n, int64_t m, int32_t* cstart, cudaStream_t s);
 struct LevelOut {
   // GRNG level: triangular bitmasks over sorted positions, zero-filled by the caller
   uint32_t* gx = nullptr;
@@ -107,6 +129,7 @@ struct LevelOut {
 };
 struct LevelStats {
   unsigned long long c[24];
+  double ms[8];  // prep, tile sweeps, tier-2 grouping + 2a, tier 2b, range lists, tier 3, recheck + emit
 };
 void run_level(const LevelIn& in, LevelOut& out, LevelStats& st, cudaStream_t s,
                float* tile_ms = nullptr);

@@ -148,10 +148,10 @@ static void launch_assign_tile(const float* Xm, int64_t nmem, const float* Xp, i
   const unsigned grid = (unsigned)((nmem + GRNG_TILE - 1) / GRNG_TILE);
   if (metric == L2) {
     GRNG_CUDA(cudaFuncSetAttribute(assign_tile_kernel<KC, L2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    assign_tile_kernel<KC, L2><<<grid, GRNG_THREADS, smem, s>>>(Xm, nmem, Xp, m, Dp, b1, a1, b2);
+    assign_tile_kernel<KC, L2><<<grid, GRNG_THREADS, smem, s>>>(Xm, nmem, Xp, m, Dp, b1, a1, b2); note_launch();
   } else {
     GRNG_CUDA(cudaFuncSetAttribute(assign_tile_kernel<KC, L1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    assign_tile_kernel<KC, L1><<<grid, GRNG_THREADS, smem, s>>>(Xm, nmem, Xp, m, Dp, b1, a1, b2);
+    assign_tile_kernel<KC, L1><<<grid, GRNG_THREADS, smem, s>>>(Xm, nmem, Xp, m, Dp, b1, a1, b2); note_launch();
   }
   GRNG_CUDA(cudaGetLastError());
 }
@@ -163,7 +163,7 @@ void assign_layer(const float* Xmem, const int32_t* mem_id, const double* mem_r,
   DevBuf pivpos, b1, a1, b2, amb, cnt;
   GRNG_CUDA(pivpos.alloc((size_t)npoints * 4));
   GRNG_CUDA(cudaMemsetAsync(pivpos.p, 0xff, (size_t)npoints * 4, s));
-  pivpos_kernel<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(piv_id, m, pivpos.as<int32_t>());
+  pivpos_kernel<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(piv_id, m, pivpos.as<int32_t>()); note_launch();
   GRNG_CUDA(b1.alloc((size_t)nmem * 4));
   GRNG_CUDA(a1.alloc((size_t)nmem * 4));
   GRNG_CUDA(b2.alloc((size_t)nmem * 4));
@@ -177,21 +177,21 @@ void assign_layer(const float* Xmem, const int32_t* mem_id, const double* mem_r,
   unsigned long long* dc = cnt.as<unsigned long long>();
   assign_decide_kernel<<<(unsigned)((nmem + 255) / 256), 256, 0, s>>>(
       mem_id, nmem, pivpos.as<int32_t>(), b1.as<float>(), a1.as<int32_t>(), b2.as<float>(), Dp, out.assign,
-      amb.as<int32_t>(), dc);
+      amb.as<int32_t>(), dc); note_launch();
   GRNG_CUDA(cudaGetLastError());
   unsigned long long namb = 0;
   GRNG_CUDA(cudaMemcpyAsync(&namb, dc, 8, cudaMemcpyDeviceToHost, s));
   GRNG_CUDA(cudaStreamSynchronize(s));
   if (namb) {
     assign_recheck_kernel<<<(unsigned)namb, 256, 0, s>>>(Xmem, Xpiv, m, D, Dp, metric, amb.as<int32_t>(),
-                                                         b1.as<float>(), out.assign, dc + 1);
+                                                         b1.as<float>(), out.assign, dc + 1); note_launch();
     GRNG_CUDA(cudaGetLastError());
   }
   GRNG_CUDA(cudaMemsetAsync(out.radius, 0, (size_t)m * 8, s));
   GRNG_CUDA(cudaMemsetAsync(out.delta_max, 0, (size_t)m * 8, s));
   member_dist_kernel<<<(unsigned)((nmem + 255) / 256), 256, 0, s>>>(
       Xmem, Xpiv, mem_r, nmem, D, Dp, metric, out.assign, out.dist,
-      reinterpret_cast<unsigned long long*>(out.radius), reinterpret_cast<unsigned long long*>(out.delta_max));
+      reinterpret_cast<unsigned long long*>(out.radius), reinterpret_cast<unsigned long long*>(out.delta_max)); note_launch();
   GRNG_CUDA(cudaGetLastError());
   if (stats) {
     unsigned long long h[2];

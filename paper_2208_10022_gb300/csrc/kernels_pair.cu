@@ -18,6 +18,8 @@
 //   tier 3  exhaustive scan of all nodes (Stage VI) for the few pairs left.
 // Comparisons whose FP32 brackets overlap are re-decided in canonical FP64.
 #include <algorithm>
+#include <chrono>
+#include <cstring>
 #include <vector>
 
 #include "common.cuh"
@@ -28,6 +30,45 @@ namespace grng {
 
 #define FULLMASK 0xffffffffu
 static __device__ __forceinline__ float finf() { return __int_as_float(0x7f800000); }
+
+// Lower bound E of d(x,y) - t_other, the other condition's threshold t_other given as
+// an upper bound in key units: a node k with d(k,x) <= E has, by the triangle
+// inequality, d(k,y) >= d(x,y) - d(k,x) >= t_other, so it cannot satisfy the other
+// condition (GRNG definition, Sec. 2).
+static __device__ __forceinline__ float excl_dist(float v, float t_other_key_hi, int metric, Err e) {
+  const float u2 = 1.1920928955078125e-07f;
+  const float vlo = fmaxf(lo_b(v, e), 0.0f);
+  const float dlo = metric == L2 ? sqrtf(vlo) * (1.0f - u2) : vlo;
+  const float t = metric == L2 ? sqrtf(fmaxf(t_other_key_hi, 0.0f)) * (1.0f + u2) : t_other_key_hi;
+  return dlo - t - u2 * (dlo + t);
+}
+
+// 1 when no node can block through this side: the side's sorted neighbour keys kl[K]
+// reach past the condition's threshold (so every node that could satisfy it is in the
+// list) and every listed node that could satisfy it lies within E, where the other
+// condition is impossible.  thr_hi: the condition's threshold, upper bound, key units.
+// keys with hi_b(key) <= excl_key(E) belong to distances within E
+static __device__ __forceinline__ float excl_key(float E, int metric) {
+  const float u2 = 1.1920928955078125e-07f;
+  if (!(E > 0.0f)) return -1.0f;
+  if (metric == L2) {
+    const float q = E * (1.0f - u2);
+    return q * q * (1.0f - u2);
+  }
+  return E * (1.0f - u2);
+}
+
+static __device__ __forceinline__ bool side_certified(const float* kl, int K, float thr_hi, float E, int metric,
+                                                      Err e) {
+  if (lo_b(kl[K - 1], e) < thr_hi) return false;
+  const float ekey = excl_key(E, metric);
+  for (int j = 0; j < K; ++j) {
+    const float kj = kl[j];
+    if (lo_b(kj, e) >= thr_hi) break;  // ascending: no later entry satisfies the condition
+    if (hi_b(kj, e) > ekey) return false;
+  }
+  return true;
+}
 
 // ---------------------------------------------------------------------------------
 // Block preparation: intra-block keys (FP16 rounded up: a safe upper bound for the
@@ -111,7 +152,8 @@ struct TileParams {
   uint32_t* gg;
   int64_t words;
   int* strip_ctr;
-  unsigned long long* stats;
+  unsigned long long* stats;  // [0] candidate pairs [1] linked in the tile [2] of which certified by a list
+  int mode;  // 0: lists + filter in one sweep; 1: lists only; 2: filter with the lists of sweep 1
 };
 
 // shared-memory layout of the tile sweep (bytes)
@@ -161,7 +203,7 @@ __global__ void __launch_bounds__(GRNG_THREADS, 1) tile_pass_kernel(TileParams p
   const int Dp = p.Dp;
   const int64_t nb = (n + GRNG_TILE - 1) / GRNG_TILE;
   const Err e = err_fp32(Dp);
-  unsigned long long st_cand = 0, st_quick = 0;
+  unsigned long long st_cand = 0, st_quick = 0, st_cert = 0;
 
   for (;;) {
     __syncthreads();
@@ -188,8 +230,13 @@ __global__ void __launch_bounds__(GRNG_THREADS, 1) tile_pass_kernel(TileParams p
         rxhi[tid] = (p.rhi && ok) ? p.rhi[xb + tid] : 0.0f;
       }
       for (int i = tid; i < GRNG_TILE * (K + 1); i += GRNG_THREADS) {
-        knnK[i] = finf();
-        knnI[i] = -1;
+        if (p.mode == 2) {  // the final lists of the row nodes, from the first sweep
+          int r = i / (K + 1), j = i % (K + 1);
+          knnK[i] = (r < nr && j < K) ? p.knn_key[(xb + r) * K + j] : finf();
+        } else {
+          knnK[i] = finf();
+          knnI[i] = -1;
+        }
       }
     }
     int done = 0;
@@ -200,7 +247,7 @@ __global__ void __launch_bounds__(GRNG_THREADS, 1) tile_pass_kernel(TileParams p
       ++done;
       const int64_t yb = by * GRNG_TILE;
       const int nc = (int)(n - yb < GRNG_TILE ? n - yb : GRNG_TILE);
-      const bool filt = by >= bx;
+      const bool filt = p.mode != 1 && by >= bx;
       float acc[8][8];
       tile_keys<KC, METRIC>(p.X + xb * Dp, nr, p.X + yb * Dp, nc, Dp, sA, sB, acc);
       __syncthreads();  // every thread is done with sA/sB: T may overwrite them
@@ -229,6 +276,13 @@ __global__ void __launch_bounds__(GRNG_THREADS, 1) tile_pass_kernel(TileParams p
           rylo[tid] = (p.rlo && ok) ? p.rlo[yb + tid] : 0.0f;
           ryhi[tid] = (p.rhi && ok) ? p.rhi[yb + tid] : 0.0f;
         }
+        if (p.mode == 2) {  // the column nodes' lists (in the space of the row lists' indices)
+          float* knnKY = reinterpret_cast<float*>(knnI);
+          for (int i = tid; i < GRNG_TILE * (K + 1); i += GRNG_THREADS) {
+            int c = i / (K + 1), j = i % (K + 1);
+            knnKY[i] = (c < nc && j < K) ? p.knn_key[(yb + c) * K + j] : finf();
+          }
+        }
       }
       __syncthreads();
       // ---- neighbour lists (rows) and row / column minima --------------------------
@@ -247,7 +301,7 @@ __global__ void __launch_bounds__(GRNG_THREADS, 1) tile_pass_kernel(TileParams p
               if (v < m1) { m2 = m1; a2 = a1; m1 = v; a1 = c; }
               else { m2 = v; a2 = c; }
             }
-            if (v < thr) {
+            if (p.mode != 2 && v < thr) {
               int pos = K - 1;
               while (pos > 0 && kk[pos - 1] > v) { kk[pos] = kk[pos - 1]; ki[pos] = ki[pos - 1]; --pos; }
               kk[pos] = v;
@@ -298,6 +352,12 @@ __global__ void __launch_bounds__(GRNG_THREADS, 1) tile_pass_kernel(TileParams p
               PairThr P = pair_thresholds(v, rxl, rxh, rylo[c], ryhi[c], METRIC, e, p.guide);
               if (P.quick) {
                 quick = true;
+              } else if (p.mode == 2 &&
+                         (side_certified(knnK + r * (K + 1), K, P.t1hi, excl_dist(v, P.t2hi, METRIC, e), METRIC, e) ||
+                          side_certified(reinterpret_cast<const float*>(knnI) + c * (K + 1), K, P.t2hi,
+                                         excl_dist(v, P.t1hi, METRIC, e), METRIC, e))) {
+                quick = true;
+                ++st_cert;
               } else {
                 bool blocked = false;
                 {  // row minimum of x over the column block
@@ -354,7 +414,7 @@ __global__ void __launch_bounds__(GRNG_THREADS, 1) tile_pass_kernel(TileParams p
       }
       __syncthreads();
     }
-    if (tid < nr) {
+    if (p.mode != 2 && tid < nr) {
       const float* kk = knnK + tid * (K + 1);
       const int* ki = knnI + tid * (K + 1);
       for (int j = 0; j < K; ++j) {
@@ -367,10 +427,12 @@ __global__ void __launch_bounds__(GRNG_THREADS, 1) tile_pass_kernel(TileParams p
   for (int o = 16; o > 0; o >>= 1) {
     st_cand += __shfl_down_sync(FULLMASK, st_cand, o);
     st_quick += __shfl_down_sync(FULLMASK, st_quick, o);
+    st_cert += __shfl_down_sync(FULLMASK, st_cert, o);
   }
   if (lane == 0) {
     atomicAdd(p.stats + 0, st_cand);
     atomicAdd(p.stats + 1, st_quick);
+    atomicAdd(p.stats + 2, st_cert);
   }
 }
 
@@ -446,7 +508,10 @@ __global__ void __launch_bounds__(128) tier2_kernel(Tier2Params p) {
         continue;
       }
       int stt = 0;
-      if (kidl >= 0 && kidl != o) {
+      // a listed node is tested only if it may satisfy the first condition and is not
+      // excluded from the second by the triangle inequality
+      const float ekey = excl_key(excl_dist(v, P.t2hi, p.metric, e), p.metric);
+      if (kidl >= 0 && kidl != o && lo_b(akey, e) < P.t1hi && hi_b(akey, e) > ekey) {
         float b = 0.0f;
         if (p.metric == L2) {
           for (int d = 0; d < Dp; ++d) { float tt = KT[d * 32 + lane] - ow[d]; b = fmaf(tt, tt, b); }
@@ -491,6 +556,13 @@ __global__ void __launch_bounds__(128) tier2_kernel(Tier2Params p) {
 // Tier 3: exhaustive scan over all nodes (Stage VI) for the pairs tier 2 left open.
 // Each pair owns the pending slot slot0 + its index.
 // ---------------------------------------------------------------------------------
+// a range of nodes below one domain c, with lower bounds of d(c, g), d(c, o) and, for
+// L2, of |c - c*| (0 when unknown)
+struct Front {
+  int s, e;
+  float dg, dq, dcs, pad;
+};
+
 struct Tier3Params {
   const float* X;
   int64_t n;
@@ -503,15 +575,42 @@ struct Tier3Params {
   int* pflag;
   int64_t slot0;
   int2* amb; unsigned long long* amb_cnt; unsigned long long amb_cap;
+  Ancestors anc;
+  Front* fbuf;     // per CTA: two frontier buffers of fcap ranges
+  const float* pdist_hi;  // [n] upper bound of d(node, its parent), or null
+  const float* atab;      // [n][tabw] FP32 keys node x ancestor (columns anc.toff[a] + c), or null
+  int64_t tabw;
+  int fcap;
+  unsigned long long* stats;  // [0] frontier overflows, [1] nodes tested
 };
 
+// lower / upper bound of the distance whose FP32 key is k
+__device__ __forceinline__ float dist_lo(float k, int metric, Err e) {
+  float lo = fmaxf(lo_b(k, e), 0.0f);
+  return metric == L2 ? sqrtf(lo) * (1.0f - 1.1920928955078125e-07f) : lo;
+}
+__device__ __forceinline__ float dist_hi(float k, int metric, Err e) {
+  float hi = hi_b(k, e);
+  return metric == L2 ? sqrtf(hi) * (1.0f + 1.1920928955078125e-07f) : hi;
+}
+
+// Stage VI (Prop. 4 at the exemplar level, Prop. GRNG_S6 for pivot layers): a whole
+// domain of ancestor c is skipped when d(c,x) - rho_c >= t1 or d(c,y) - rho_c >= t2,
+// with rho_c bounding the distance from c to any node below it (its radius; delta_max
+// for the direct parent).  Descendants of a node are contiguous in the layer order, so
+// the frontier is a list of index ranges, refined layer by layer down to the nodes.
 __global__ void __launch_bounds__(256) tier3_kernel(Tier3Params p) {
   extern __shared__ __align__(16) float sm3[];
   float* gs = sm3;
   float* os = gs + p.Dp;
-  __shared__ int s_block;
+  __shared__ int s_block, s_cur_n, s_nxt_n;
   __shared__ float s_v;
   const Err e = err_fp32(p.Dp);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const float u2 = 1.1920928955078125e-07f;
+  Front* bufA = p.fbuf + (int64_t)blockIdx.x * 2 * p.fcap;
+  Front* bufB = bufA + p.fcap;
+  unsigned long long n_over = 0, n_tested = 0;
   for (int64_t t = blockIdx.x; t < p.m; t += gridDim.x) {
     const int2 pr = p.pairs[t];
     const int64_t g = pr.x, o = pr.y;
@@ -520,7 +619,11 @@ __global__ void __launch_bounds__(256) tier3_kernel(Tier3Params p) {
       gs[d] = p.X[g * p.Dp + d];
       os[d] = p.X[o * p.Dp + d];
     }
-    if (threadIdx.x == 0) s_block = 0;
+    if (threadIdx.x == 0) {
+      s_block = 0;
+      bufA[0] = Front{0, (int)(p.anc.n ? p.anc.m[0] : p.n), 0.0f, 0.0f, 0.0f, 0.0f};
+      s_cur_n = 1;
+    }
     __syncthreads();
     if (threadIdx.x == 0) s_v = key32(gs, os, p.Dp, p.metric);
     __syncthreads();
@@ -530,16 +633,104 @@ __global__ void __launch_bounds__(256) tier3_kernel(Tier3Params p) {
                                 p.guide);
     const int64_t slot = p.slot0 + t;
     if (!P.quick) {
-      for (int64_t k0 = 0; k0 < p.n; k0 += blockDim.x) {
-        if (*(volatile int*)&s_block) break;
-        const int64_t k = k0 + threadIdx.x;
-        if (k < p.n && k != g && k != o) {
-          const float* pk = p.X + k * p.Dp;
+      // thresholds as upper bounds in distance units
+      const float t1d = p.metric == L2 ? sqrtf(fmaxf(P.t1hi, 0.0f)) * (1.0f + u2) : P.t1hi;
+      const float t2d = p.metric == L2 ? sqrtf(fmaxf(P.t2hi, 0.0f)) * (1.0f + u2) : P.t2hi;
+      // nodes within Eg of g (Eo of o) cannot satisfy the other condition (triangle)
+      const float Eg = excl_dist(v, P.t2hi, p.metric, e), Eo = excl_dist(v, P.t1hi, p.metric, e);
+      // L2: the G-lune lies in the ball B(c*, rho), c* = (1-lam) g + lam o, because
+      // |k-c*|^2 = (1-lam)|k-g|^2 + lam |k-o|^2 - lam (1-lam) |g-o|^2 (Stewart) for any
+      // point k; the same identity gives |c-c*| from the distances of c to g and o.
+      const float vlo = fmaxf(lo_b(v, e), 0.0f), vhi = hi_b(v, e);
+      float lam = 0.5f, rho2 = -1.0f;
+      if (p.metric == L2) {
+        lam = fminf(fmaxf((vhi + P.t1hi - P.t2hi) / (2.0f * fmaxf(vhi, 1e-30f)), 0.0f), 1.0f);
+        const float m1 = (1.0f - lam) * P.t1hi + lam * P.t2hi;
+        rho2 = m1 - lam * (1.0f - lam) * vlo + 8.0f * u2 * (m1 + lam * (1.0f - lam) * vhi);
+      }
+      Front* cur = bufA;
+      Front* nxt = bufB;
+      for (int a = 0; a < p.anc.n; ++a) {
+        if (threadIdx.x == 0) s_nxt_n = 0;
+        __syncthreads();
+        const float* Xa = p.anc.X[a];
+        const float* Ra = p.anc.Rhi[a];
+        const int32_t* cs = p.anc.cstart[a];
+        const int ncur = s_cur_n;
+        for (int r = warp; r < ncur; r += nwarps) {
+          const Front rg = cur[r];
+          for (int c = rg.s + lane; c < rg.e; c += 32) {
+            float kg, kq;
+            if (p.atab) {
+              kg = p.atab[g * p.tabw + p.anc.toff[a] + c];
+              kq = p.atab[o * p.tabw + p.anc.toff[a] + c];
+            } else {
+              const float* pc = Xa + (int64_t)c * p.Dp;
+              kg = key32(pc, gs, p.Dp, p.metric);
+              kq = key32(pc, os, p.Dp, p.metric);
+            }
+            const float dg = dist_lo(kg, p.metric, e);
+            const float dq = dist_lo(kq, p.metric, e);
+            const float R = Ra[c];
+            bool skip = (dg - R - u2 * (dg + R) >= t1d) || (dq - R - u2 * (dq + R) >= t2d);
+            if (!skip) {  // the whole domain lies within the exclusion ball of g or of o
+              const float dgh = dist_hi(kg, p.metric, e), dqh = dist_hi(kq, p.metric, e);
+              skip = (dgh + R + u2 * (dgh + R) <= Eg) || (dqh + R + u2 * (dqh + R) <= Eo);
+            }
+            float dcs = 0.0f;
+            if (!skip && rho2 >= 0.0f) {  // L2: the domain misses the ball around the G-lune
+              const float Alo = fmaxf(lo_b(kg, e), 0.0f), Blo = fmaxf(lo_b(kq, e), 0.0f);
+              const float Ahi = hi_b(kg, e), Bhi = hi_b(kq, e);
+              const float mm = (1.0f - lam) * Ahi + lam * Bhi + lam * (1.0f - lam) * vhi;
+              const float q = (1.0f - lam) * Alo + lam * Blo - lam * (1.0f - lam) * vhi - 8.0f * u2 * mm;
+              const float rr = sqrtf(rho2) + R;
+              skip = q > 0.0f && q >= rr * rr * (1.0f + 4.0f * u2);
+              dcs = q > 0.0f ? sqrtf(q) * (1.0f - u2) : 0.0f;
+            }
+            if (!skip) {
+              int idx = atomicAdd(&s_nxt_n, 1);
+              if (idx < p.fcap) nxt[idx] = Front{cs[c], cs[c + 1], dg, dq, dcs, 0.0f};
+            }
+          }
+        }
+        __syncthreads();
+        if (s_nxt_n > p.fcap) {  // frontier too large: scan every node (still exact)
+          __syncthreads();
+          if (threadIdx.x == 0) {
+            bufA[0] = Front{0, (int)p.n, 0.0f, 0.0f, 0.0f, 0.0f};
+            s_cur_n = 1;
+          }
+          cur = bufA;
+          n_over += threadIdx.x == 0;
+          __syncthreads();
+          break;
+        }
+        Front* tmp = cur; cur = nxt; nxt = tmp;
+        __syncthreads();
+        if (threadIdx.x == 0) s_cur_n = s_nxt_n;
+        __syncthreads();
+      }
+      const int ncur = s_cur_n;
+      const float rho = rho2 >= 0.0f ? sqrtf(rho2) * (1.0f + u2) : 0.0f;
+      for (int r = warp; r < ncur; r += nwarps) {
+        const Front rg = cur[r];
+        for (int k = rg.s + lane; k < rg.e; k += 32) {
+          if (*(volatile int*)&s_block) break;
+          if (k == g || k == o) continue;
+          if (p.pdist_hi && (rg.dg > 0.0f || rg.dq > 0.0f || rg.dcs > 0.0f)) {
+            // Prop. 5 / GRNG_S6 (assisted): |k - g| >= d(c,g) - d(k,c), and so on
+            const float mk = p.pdist_hi[k];
+            const float sl = u2 * (rg.dg + rg.dq + rg.dcs + mk);
+            if (rg.dg - mk - sl >= t1d || rg.dq - mk - sl >= t2d || (rho2 >= 0.0f && rg.dcs - mk - sl >= rho))
+              continue;
+          }
+          const float* pk = p.X + (int64_t)k * p.Dp;
           float a = key32(pk, gs, p.Dp, p.metric);
           float b = key32(pk, os, p.Dp, p.metric);
+          ++n_tested;
           int stt = block_state(a, b, P, e);
           if (stt == 2) s_block = 1;
-          else if (stt == 1) push_pair(p.amb, p.amb_cnt, p.amb_cap, make_int2((int)slot, (int)k));
+          else if (stt == 1) push_pair(p.amb, p.amb_cnt, p.amb_cap, make_int2((int)slot, k));
         }
       }
     }
@@ -548,6 +739,263 @@ __global__ void __launch_bounds__(256) tier3_kernel(Tier3Params p) {
       p.pend[slot] = make_int2((int)g, (int)o);
       p.pflag[slot] = s_block ? 3 : 0;
     }
+  }
+  for (int sh = 16; sh > 0; sh >>= 1) n_tested += __shfl_down_sync(FULLMASK, n_tested, sh);
+  if (lane == 0) atomicAdd(p.stats + 1, n_tested);
+  if (threadIdx.x == 0 && n_over) atomicAdd(p.stats + 0, n_over);
+}
+
+// node x ancestor keys: out[r * ld + c] = key(Xr[r], Xc[c]) for a 128 x 128 tile per CTA
+template <int KC, int METRIC>
+__global__ void __launch_bounds__(GRNG_THREADS) cross_keys_kernel(const float* __restrict__ Xr, int64_t nr_all,
+                                                                  const float* __restrict__ Xc, int64_t nc_all,
+                                                                  int Dp, float* __restrict__ out, int64_t ld) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  float* sA = reinterpret_cast<float*>(sm_raw);
+  float* sB = sA + KC * GRNG_SSTRIDE;
+  float* T = sB + KC * GRNG_SSTRIDE;
+  const int64_t rb = (int64_t)blockIdx.x * GRNG_TILE, cb = (int64_t)blockIdx.y * GRNG_TILE;
+  const int nr = (int)(nr_all - rb < GRNG_TILE ? nr_all - rb : GRNG_TILE);
+  const int nc = (int)(nc_all - cb < GRNG_TILE ? nc_all - cb : GRNG_TILE);
+  float acc[8][8];
+  tile_keys<KC, METRIC>(Xr + rb * Dp, nr, Xc + cb * Dp, nc, Dp, sA, sB, acc);
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) T[tile_row(i) * 129 + tile_col(j)] = acc[i][j];
+  __syncthreads();
+  for (int i = threadIdx.x; i < GRNG_TILE * GRNG_TILE; i += GRNG_THREADS) {
+    const int r = i >> 7, c = i & 127;
+    if (r < nr && c < nc) out[(rb + r) * ld + cb + c] = T[r * 129 + c];
+  }
+}
+
+template <int KC>
+static void launch_cross_kc(const float* Xr, int64_t nr, const float* Xc, int64_t nc, int Dp, int metric, float* out,
+                            int64_t ld, cudaStream_t s) {
+  const size_t smem = (size_t)(2 * KC * GRNG_SSTRIDE + 128 * 129) * 4;
+  dim3 grid((unsigned)((nr + GRNG_TILE - 1) / GRNG_TILE), (unsigned)((nc + GRNG_TILE - 1) / GRNG_TILE));
+  if (metric == L2) {
+    GRNG_CUDA(cudaFuncSetAttribute(cross_keys_kernel<KC, L2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    cross_keys_kernel<KC, L2><<<grid, GRNG_THREADS, smem, s>>>(Xr, nr, Xc, nc, Dp, out, ld); note_launch();
+  } else {
+    GRNG_CUDA(cudaFuncSetAttribute(cross_keys_kernel<KC, L1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    cross_keys_kernel<KC, L1><<<grid, GRNG_THREADS, smem, s>>>(Xr, nr, Xc, nc, Dp, out, ld); note_launch();
+  }
+  GRNG_CUDA(cudaGetLastError());
+}
+static void launch_cross(const float* Xr, int64_t nr, const float* Xc, int64_t nc, int Dp, int metric, float* out,
+                         int64_t ld, cudaStream_t s) {
+  const int KC = Dp % 32 == 0 ? 32 : (Dp % 16 == 0 ? 16 : 8);
+  if (KC == 32) launch_cross_kc<32>(Xr, nr, Xc, nc, Dp, metric, out, ld, s);
+  else if (KC == 16) launch_cross_kc<16>(Xr, nr, Xc, nc, Dp, metric, out, ld, s);
+  else launch_cross_kc<8>(Xr, nr, Xc, nc, Dp, metric, out, ld, s);
+}
+
+// ---------------------------------------------------------------------------------
+// Range lists (pivot layers): pairs that neither endpoint's neighbour list covers.
+// Each such pair picks the endpoint s whose threshold is smallest relative to its
+// K-th neighbour distance; one more sweep lists, for every such s, all nodes that
+// could lie within T_s (the largest threshold of its pairs); each pair then tests the
+// listed nodes of its annulus only.
+// ---------------------------------------------------------------------------------
+#define GRNG_LMAX 8192  // longest range list; nodes beyond it leave their pairs to tier 3
+
+struct SideParams {
+  const float* X;
+  int Dp, metric, guide, K;
+  const float* rlo;
+  const float* rhi;
+  const float* knn_key;
+  const int2* pairs;
+  int64_t m;
+  int8_t* side;               // 0: list of pairs[t].x, 1: list of .y, 3: linked
+  unsigned int* tkey;         // [n] float bits of T_s (key units)
+};
+
+__device__ __forceinline__ PairThr thr_of(const SideParams& p, int a, int b, float v, Err e) {
+  return pair_thresholds(v, p.rlo ? p.rlo[a] : 0.0f, p.rhi ? p.rhi[a] : 0.0f, p.rlo ? p.rlo[b] : 0.0f,
+                         p.rhi ? p.rhi[b] : 0.0f, p.metric, e, p.guide);
+}
+
+__global__ void choose_side_kernel(SideParams p) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= p.m) return;
+  const Err e = err_fp32(p.Dp);
+  const int a = p.pairs[t].x, b = p.pairs[t].y;
+  const float v = key32(p.X + (int64_t)a * p.Dp, p.X + (int64_t)b * p.Dp, p.Dp, p.metric);
+  PairThr P = thr_of(p, a, b, v, e);
+  if (P.quick) { p.side[t] = 3; return; }
+  // thresholds relative to the K-th neighbour key: the smaller ratio, the fewer nodes
+  const float ra = P.t1hi / fmaxf(p.knn_key[(int64_t)a * p.K + p.K - 1], 1e-30f);
+  const float rb = P.t2hi / fmaxf(p.knn_key[(int64_t)b * p.K + p.K - 1], 1e-30f);
+  const int sd = rb < ra ? 1 : 0;
+  p.side[t] = (int8_t)sd;
+  atomicMax(p.tkey + (sd ? b : a), __float_as_uint(sd ? P.t2hi : P.t1hi));  // positive floats
+}
+
+// one sweep over the node x node tiles of the rows with T_s > 0: count, or fill
+template <int KC, int METRIC>
+__global__ void __launch_bounds__(GRNG_THREADS) range_sweep_kernel(const float* __restrict__ X, int64_t n, int Dp,
+                                                                   const unsigned int* __restrict__ tkey,
+                                                                   int64_t* __restrict__ cnt,
+                                                                   const int64_t* __restrict__ off,
+                                                                   unsigned long long* __restrict__ cursor,
+                                                                   int32_t* __restrict__ lidx,
+                                                                   float* __restrict__ lkey, int fill) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  float* sA = reinterpret_cast<float*>(sm_raw);
+  float* sB = sA + KC * GRNG_SSTRIDE;
+  float* T = sB + KC * GRNG_SSTRIDE;
+  const int64_t xb = (int64_t)blockIdx.x * GRNG_TILE;
+  const int nr = (int)(n - xb < GRNG_TILE ? n - xb : GRNG_TILE);
+  const int tid = threadIdx.x;
+  const float Tr = tid < nr ? __uint_as_float(tkey[xb + tid]) : 0.0f;
+  // a row whose list overflowed has cnt < 0 and is skipped by the fill
+  const bool act = tid < nr && Tr > 0.0f && (!fill || cnt[xb + tid] >= 0);
+  if (!__syncthreads_or(act)) return;
+  const Err e = err_fp32(Dp);
+  const int64_t nb = (n + GRNG_TILE - 1) / GRNG_TILE;
+  int64_t c_row = 0;
+  for (int64_t by = 0; by < nb; ++by) {
+    const int64_t yb = by * GRNG_TILE;
+    const int nc = (int)(n - yb < GRNG_TILE ? n - yb : GRNG_TILE);
+    float acc[8][8];
+    tile_keys<KC, METRIC>(X + xb * Dp, nr, X + yb * Dp, nc, Dp, sA, sB, acc);
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+      for (int j = 0; j < 8; ++j) T[tile_row(i) * 129 + tile_col(j)] = acc[i][j];
+    __syncthreads();
+    if (act) {
+      for (int c = 0; c < nc; ++c) {
+        const int64_t k = yb + c;
+        if (k == xb + tid) continue;
+        const float v = T[tid * 129 + c];
+        if (lo_b(v, e) < Tr) {
+          if (fill) {
+            const unsigned long long pos = atomicAdd(cursor + xb + tid, 1ull);
+            lidx[pos] = (int32_t)k;
+            lkey[pos] = v;
+          }
+          ++c_row;
+        }
+      }
+    }
+    __syncthreads();
+  }
+  if (!fill && tid < nr) cnt[xb + tid] = act ? c_row : 0;
+}
+
+__global__ void cap_lists_kernel(int64_t* cnt, int64_t n, int64_t lmax, unsigned long long* n_over) {
+  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s < n && cnt[s] > lmax) {
+    cnt[s] = -1;
+    atomicAdd(n_over, 1ull);
+  }
+}
+__global__ void clamp_counts_kernel(const int64_t* cnt, int64_t n, int64_t* out) {
+  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s < n) out[s] = cnt[s] > 0 ? cnt[s] : 0;
+}
+
+struct ListParams {
+  const float* X;
+  int Dp, metric, guide;
+  const float* rlo;
+  const float* rhi;
+  const int2* pairs;
+  int64_t m;
+  const int8_t* side;
+  const int64_t* cnt;   // -1: list overflowed
+  const int64_t* loff;
+  const int32_t* lidx;
+  const float* lkey;
+  int2* links; unsigned long long* link_cnt; unsigned long long link_cap;
+  int2* unres; unsigned long long* unres_cnt; unsigned long long unres_cap;
+  int2* pend; unsigned long long* pend_cnt; unsigned long long pend_cap;
+  int2* amb; unsigned long long* amb_cnt; unsigned long long amb_cap;
+  unsigned long long* stats;  // [0] links [1] pending [2] to tier 3 [3] blocked [4] listed nodes tested
+};
+
+// one warp per pair
+__global__ void __launch_bounds__(256) list_tier_kernel(ListParams p) {
+  const int lane = threadIdx.x & 31;
+  const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const Err e = err_fp32(p.Dp);
+  unsigned long long c_link = 0, c_pend = 0, c_un = 0, c_blk = 0, c_test = 0;
+  for (int64_t t = wid; t < p.m; t += nw) {
+    const int sd = p.side[t];
+    const int2 pr = p.pairs[t];
+    if (sd == 3) {
+      if (lane == 0) push_pair(p.links, p.link_cnt, p.link_cap, pr);
+      c_link += lane == 0;
+      continue;
+    }
+    const int s = sd ? pr.y : pr.x, o = sd ? pr.x : pr.y;
+    if (p.cnt[s] < 0) {
+      if (lane == 0) push_pair(p.unres, p.unres_cnt, p.unres_cap, pr);
+      c_un += lane == 0;
+      continue;
+    }
+    const float* xs = p.X + (int64_t)s * p.Dp;
+    const float* xo = p.X + (int64_t)o * p.Dp;
+    const float v = key32(xs, xo, p.Dp, p.metric);
+    const PairThr P = pair_thresholds(v, p.rlo ? p.rlo[s] : 0.0f, p.rhi ? p.rhi[s] : 0.0f,
+                                      p.rlo ? p.rlo[o] : 0.0f, p.rhi ? p.rhi[o] : 0.0f, p.metric, e, p.guide);
+    if (P.quick) {
+      if (lane == 0) push_pair(p.links, p.link_cnt, p.link_cap, pr);
+      c_link += lane == 0;
+      continue;
+    }
+    const float ekey = excl_key(excl_dist(v, P.t2hi, p.metric, e), p.metric);
+    const int64_t j0 = p.loff[s], j1 = p.loff[s + 1];
+    bool blocked = false, anyamb = false;
+    for (int64_t jb = j0; jb < j1 && !blocked; jb += 32) {
+      const int64_t j = jb + lane;
+      int stt = 0;
+      if (j < j1) {
+        const float kk = p.lkey[j];
+        const int k = p.lidx[j];
+        if (k != o && lo_b(kk, e) < P.t1hi && hi_b(kk, e) > ekey) {
+          stt = block_state(kk, key32(p.X + (int64_t)k * p.Dp, xo, p.Dp, p.metric), P, e);
+          ++c_test;
+        }
+      }
+      blocked = __any_sync(FULLMASK, stt == 2);
+      anyamb |= __any_sync(FULLMASK, stt == 1);
+    }
+    if (blocked) {
+      c_blk += lane == 0;
+    } else if (!anyamb) {
+      if (lane == 0) push_pair(p.links, p.link_cnt, p.link_cap, pr);
+      c_link += lane == 0;
+    } else {  // rare: record the ambiguous triples for the FP64 recheck
+      unsigned long long slot = 0;
+      if (lane == 0) slot = atomicAdd(p.pend_cnt, 1ull);
+      slot = __shfl_sync(FULLMASK, slot, 0);
+      if (lane == 0 && slot < p.pend_cap) p.pend[slot] = pr;
+      for (int64_t jb = j0; jb < j1; jb += 32) {
+        const int64_t j = jb + lane;
+        if (j < j1) {
+          const float kk = p.lkey[j];
+          const int k = p.lidx[j];
+          if (k != o && lo_b(kk, e) < P.t1hi && hi_b(kk, e) > ekey &&
+              block_state(kk, key32(p.X + (int64_t)k * p.Dp, xo, p.Dp, p.metric), P, e) == 1)
+            push_pair(p.amb, p.amb_cnt, p.amb_cap, make_int2((int)slot, k));
+        }
+      }
+      c_pend += lane == 0;
+    }
+  }
+  for (int sh = 16; sh > 0; sh >>= 1) c_test += __shfl_down_sync(FULLMASK, c_test, sh);
+  if (lane == 0) {
+    atomicAdd(p.stats + 0, c_link);
+    atomicAdd(p.stats + 1, c_pend);
+    atomicAdd(p.stats + 2, c_un);
+    atomicAdd(p.stats + 3, c_blk);
+    atomicAdd(p.stats + 4, c_test);
   }
 }
 
@@ -601,10 +1049,10 @@ static void launch_prep(const LevelIn& in, __half* A, uint8_t* ni, float* nk, cu
   size_t smem = (size_t)(2 * KC * GRNG_SSTRIDE + 128 * 129) * 4;
   if (in.metric == L2) {
     GRNG_CUDA(cudaFuncSetAttribute(block_prep_kernel<KC, L2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    block_prep_kernel<KC, L2><<<(unsigned)nb, GRNG_THREADS, smem, s>>>(in.X, in.n, in.Dp, A, ni, nk);
+    block_prep_kernel<KC, L2><<<(unsigned)nb, GRNG_THREADS, smem, s>>>(in.X, in.n, in.Dp, A, ni, nk); note_launch();
   } else {
     GRNG_CUDA(cudaFuncSetAttribute(block_prep_kernel<KC, L1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    block_prep_kernel<KC, L1><<<(unsigned)nb, GRNG_THREADS, smem, s>>>(in.X, in.n, in.Dp, A, ni, nk);
+    block_prep_kernel<KC, L1><<<(unsigned)nb, GRNG_THREADS, smem, s>>>(in.X, in.n, in.Dp, A, ni, nk); note_launch();
   }
   GRNG_CUDA(cudaGetLastError());
 }
@@ -614,12 +1062,34 @@ static void launch_tile(const LevelIn& in, TileParams tp, int grid, cudaStream_t
   size_t smem = tp_bytes(in.K);
   if (in.metric == L2) {
     GRNG_CUDA(cudaFuncSetAttribute(tile_pass_kernel<KC, L2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    tile_pass_kernel<KC, L2><<<grid, GRNG_THREADS, smem, s>>>(tp);
+    tile_pass_kernel<KC, L2><<<grid, GRNG_THREADS, smem, s>>>(tp); note_launch();
   } else {
     GRNG_CUDA(cudaFuncSetAttribute(tile_pass_kernel<KC, L1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    tile_pass_kernel<KC, L1><<<grid, GRNG_THREADS, smem, s>>>(tp);
+    tile_pass_kernel<KC, L1><<<grid, GRNG_THREADS, smem, s>>>(tp); note_launch();
   }
   GRNG_CUDA(cudaGetLastError());
+}
+
+template <int KC>
+static void launch_range_kc(const LevelIn& in, const unsigned int* tk, int64_t* cnt, const int64_t* off,
+                            unsigned long long* cur, int32_t* li, float* lk, int fill, cudaStream_t s) {
+  const int64_t nb = (in.n + GRNG_TILE - 1) / GRNG_TILE;
+  const size_t smem = (size_t)(2 * KC * GRNG_SSTRIDE + 128 * 129) * 4;
+  if (in.metric == L2) {
+    GRNG_CUDA(cudaFuncSetAttribute(range_sweep_kernel<KC, L2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    range_sweep_kernel<KC, L2><<<(unsigned)nb, GRNG_THREADS, smem, s>>>(in.X, in.n, in.Dp, tk, cnt, off, cur, li, lk, fill); note_launch();
+  } else {
+    GRNG_CUDA(cudaFuncSetAttribute(range_sweep_kernel<KC, L1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    range_sweep_kernel<KC, L1><<<(unsigned)nb, GRNG_THREADS, smem, s>>>(in.X, in.n, in.Dp, tk, cnt, off, cur, li, lk, fill); note_launch();
+  }
+  GRNG_CUDA(cudaGetLastError());
+}
+static void launch_range(const LevelIn& in, const unsigned int* tk, int64_t* cnt, const int64_t* off,
+                         unsigned long long* cur, int32_t* li, float* lk, int fill, cudaStream_t s) {
+  const int KC = in.Dp % 32 == 0 ? 32 : (in.Dp % 16 == 0 ? 16 : 8);
+  if (KC == 32) launch_range_kc<32>(in, tk, cnt, off, cur, li, lk, fill, s);
+  else if (KC == 16) launch_range_kc<16>(in, tk, cnt, off, cur, li, lk, fill, s);
+  else launch_range_kc<8>(in, tk, cnt, off, cur, li, lk, fill, s);
 }
 
 static unsigned long long read_u64(const unsigned long long* d, cudaStream_t s) {
@@ -641,6 +1111,13 @@ static int num_sms() {
 
 void run_level(const LevelIn& in, LevelOut& out, LevelStats& st, cudaStream_t s, float* tile_ms) {
   memset(&st, 0, sizeof(st));
+  auto t_last = std::chrono::steady_clock::now();
+  auto tick = [&](int slot) {  // host time of one phase (the phases end in a synchronisation)
+    GRNG_CUDA(cudaStreamSynchronize(s));
+    auto now = std::chrono::steady_clock::now();
+    st.ms[slot] += std::chrono::duration<double, std::milli>(now - t_last).count();
+    t_last = now;
+  };
   const int64_t n = in.n;
   if (n < 2) {
     out.n_edges = 0;
@@ -665,8 +1142,9 @@ void run_level(const LevelIn& in, LevelOut& out, LevelStats& st, cudaStream_t s,
   else if (KC == 16) launch_prep<16>(in, A.as<__half>(), nbi.as<uint8_t>(), nbk.as<float>(), s);
   else launch_prep<8>(in, A.as<__half>(), nbi.as<uint8_t>(), nbk.as<float>(), s);
 
+  tick(0);
   // ---- tier 1 -------------------------------------------------------------------------
-  unsigned long long surv_cap = (unsigned long long)std::max<int64_t>(1 << 20, 16 * n);
+  unsigned long long surv_cap = (unsigned long long)std::max<int64_t>(1 << 20, 256 * n);
   DevBuf surv;
   unsigned long long nsurv = 0;
   for (int attempt = 0;; ++attempt) {
@@ -691,9 +1169,18 @@ void run_level(const LevelIn& in, LevelOut& out, LevelStats& st, cudaStream_t s,
       GRNG_CUDA(cudaEventCreate(&e1));
       GRNG_CUDA(cudaEventRecord(e0, s));
     }
-    if (KC == 32) launch_tile<32>(in, tp, grid, s);
-    else if (KC == 16) launch_tile<16>(in, tp, grid, s);
-    else launch_tile<8>(in, tp, grid, s);
+    // pivot layers: a first sweep for the neighbour lists, then the filter, which can
+    // certify links from the final lists; exemplars: one sweep doing both
+    tp.mode = in.grng ? 1 : 0;
+    for (int sweep = 0; sweep < (in.grng ? 2 : 1); ++sweep) {
+      if (sweep == 1) {
+        GRNG_CUDA(cudaMemsetAsync(dc, 0, sizeof(unsigned long long), s));  // strip counter
+        tp.mode = 2;
+      }
+      if (KC == 32) launch_tile<32>(in, tp, grid, s);
+      else if (KC == 16) launch_tile<16>(in, tp, grid, s);
+      else launch_tile<8>(in, tp, grid, s);
+    }
     if (tile_ms) {
       GRNG_CUDA(cudaEventRecord(e1, s));
       GRNG_CUDA(cudaEventSynchronize(e1));
@@ -712,9 +1199,12 @@ void run_level(const LevelIn& in, LevelOut& out, LevelStats& st, cudaStream_t s,
   st.c[0] = hst[0];  // candidate pairs
   st.c[1] = hst[1];  // quick links
   st.c[2] = nsurv;
+  st.c[17] = hst[2];  // links certified from the neighbour lists in the tile
 
+  tick(1);
   // ---- tiers 2 and 3 ---------------------------------------------------------------------
-  DevBuf off, oth, tmp, links, unres, pend, amb, pflag, unres2, off2, oth2;
+  DevBuf off, oth, tmp, links, unres, pend, amb, pflag, unres2, off2, oth2, fbuf;
+  DevBuf side, tkey, lcnt, lcnt2, loff, lidx, lkey, lcur, unres3, atab;
   GRNG_CUDA(off.alloc((size_t)(n + 1) * 8));
   GRNG_CUDA(oth.alloc(std::max<size_t>(nsurv, 1) * 4));
   group_pairs(surv.as<int2>(), (int64_t)nsurv, 0, n, off.as<int64_t>(), oth.as<int32_t>(), tmp, s);
@@ -738,10 +1228,11 @@ void run_level(const LevelIn& in, LevelOut& out, LevelStats& st, cudaStream_t s,
     size_t smem2 = (size_t)(in.Dp * 32 + in.Dp + 4 * in.Dp) * 4;
     int grid2 = (int)std::min<int64_t>(n, 32 * num_sms());
     if (nsurv) {
-      tier2_kernel<<<grid2, 128, smem2, s>>>(t2);
+      tier2_kernel<<<grid2, 128, smem2, s>>>(t2); note_launch();
       GRNG_CUDA(cudaGetLastError());
     }
     unsigned long long nun = read_u64(dc + 18, s);
+    tick(2);
     // tier 2b: the other endpoint's neighbours
     GRNG_CUDA(off2.alloc((size_t)(n + 1) * 8));
     GRNG_CUDA(oth2.alloc(std::max<unsigned long long>(nun, 1) * 4));
@@ -752,10 +1243,66 @@ void run_level(const LevelIn& in, LevelOut& out, LevelStats& st, cudaStream_t s,
     t2.unres = unres2.as<int2>(); t2.unres_cnt = dc + 20; t2.unres_cap = std::max<unsigned long long>(nun, 1);
     t2.stats = dc + 12;
     if (nun) {
-      tier2_kernel<<<grid2, 128, smem2, s>>>(t2);
+      tier2_kernel<<<grid2, 128, smem2, s>>>(t2); note_launch();
       GRNG_CUDA(cudaGetLastError());
     }
     unsigned long long nun2 = read_u64(dc + 20, s);
+    tick(3);
+    const int2* t3pairs = unres2.as<int2>();
+    GRNG_CUDA(cudaMemsetAsync(dc + 26, 0, 8 * sizeof(unsigned long long), s));
+    if (in.grng && nun2) {
+      // range lists for the pairs no neighbour list covers
+      GRNG_CUDA(side.alloc(nun2));
+      GRNG_CUDA(tkey.alloc((size_t)n * 4));
+      GRNG_CUDA(cudaMemsetAsync(tkey.p, 0, (size_t)n * 4, s));
+      SideParams sp;
+      sp.X = in.X; sp.Dp = in.Dp; sp.metric = in.metric; sp.guide = in.grng; sp.K = in.K;
+      sp.rlo = in.rlo; sp.rhi = in.rhi; sp.knn_key = knnk.as<float>(); sp.pairs = unres2.as<int2>();
+      sp.m = (int64_t)nun2; sp.side = side.as<int8_t>(); sp.tkey = tkey.as<unsigned int>();
+      choose_side_kernel<<<(unsigned)((nun2 + 255) / 256), 256, 0, s>>>(sp); note_launch();
+      GRNG_CUDA(cudaGetLastError());
+      GRNG_CUDA(lcnt.alloc((size_t)n * 8));
+      GRNG_CUDA(lcnt2.alloc((size_t)n * 8));
+      GRNG_CUDA(loff.alloc((size_t)(n + 1) * 8));
+      launch_range(in, tkey.as<unsigned int>(), lcnt.as<int64_t>(), nullptr, nullptr, nullptr, nullptr, 0, s);
+      cap_lists_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(lcnt.as<int64_t>(), n,
+                                                                 in.lmax > 0 ? in.lmax : GRNG_LMAX, dc + 26); note_launch();
+      clamp_counts_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(lcnt.as<int64_t>(), n, lcnt2.as<int64_t>()); note_launch();
+      GRNG_CUDA(cudaGetLastError());
+      exclusive_scan_i64(lcnt2.as<int64_t>(), loff.as<int64_t>(), n, s);
+      int64_t ltot = 0;
+      GRNG_CUDA(cudaMemcpyAsync(&ltot, loff.as<int64_t>() + n, 8, cudaMemcpyDeviceToHost, s));
+      GRNG_CUDA(cudaStreamSynchronize(s));
+      GRNG_CUDA(lidx.alloc((size_t)std::max<int64_t>(ltot, 1) * 4));
+      GRNG_CUDA(lkey.alloc((size_t)std::max<int64_t>(ltot, 1) * 4));
+      GRNG_CUDA(lcur.alloc((size_t)n * 8));
+      GRNG_CUDA(cudaMemcpyAsync(lcur.p, loff.p, (size_t)n * 8, cudaMemcpyDeviceToDevice, s));
+      launch_range(in, tkey.as<unsigned int>(), lcnt.as<int64_t>(), loff.as<int64_t>(),
+                   lcur.as<unsigned long long>(), lidx.as<int32_t>(), lkey.as<float>(), 1, s);
+      GRNG_CUDA(unres3.alloc(nun2 * 8));
+      ListParams lp;
+      lp.X = in.X; lp.Dp = in.Dp; lp.metric = in.metric; lp.guide = in.grng; lp.rlo = in.rlo; lp.rhi = in.rhi;
+      lp.pairs = unres2.as<int2>(); lp.m = (int64_t)nun2; lp.side = side.as<int8_t>(); lp.cnt = lcnt.as<int64_t>();
+      lp.loff = loff.as<int64_t>(); lp.lidx = lidx.as<int32_t>(); lp.lkey = lkey.as<float>();
+      lp.links = links.as<int2>(); lp.link_cnt = dc + 16; lp.link_cap = cap;
+      lp.unres = unres3.as<int2>(); lp.unres_cnt = dc + 27; lp.unres_cap = nun2;
+      lp.pend = pend.as<int2>(); lp.pend_cnt = dc + 17; lp.pend_cap = 2 * cap;
+      lp.amb = amb.as<int2>(); lp.amb_cnt = dc + 19; lp.amb_cap = amb_cap;
+      lp.stats = dc + 28;
+      list_tier_kernel<<<(unsigned)std::min<unsigned long long>((nun2 + 7) / 8, 64ull * num_sms()), 256, 0, s>>>(lp); note_launch();
+      GRNG_CUDA(cudaGetLastError());
+      unsigned long long h8[8];  // over, to tier 3, links, pending, (to tier 3), blocked, tested
+      GRNG_CUDA(cudaMemcpyAsync(h8, dc + 26, sizeof(h8), cudaMemcpyDeviceToHost, s));
+      GRNG_CUDA(cudaStreamSynchronize(s));
+      st.c[18] = nun2;    // pairs given range lists
+      st.c[19] = h8[0];   // lists over the cap
+      st.c[20] = (unsigned long long)ltot;  // listed nodes
+      st.c[21] = h8[2];   // links from the lists
+      st.c[22] = h8[6];   // listed nodes tested
+      nun2 = h8[1];       // left for tier 3
+      t3pairs = unres3.as<int2>();
+    }
+    tick(4);
     unsigned long long npend = read_u64(dc + 17, s);
     unsigned long long nlink = read_u64(dc + 16, s);
     if (npend + nun2 > 2 * cap || nlink > cap || nun > cap) fail(6, "tier-2 buffer overflow");
@@ -765,14 +1312,34 @@ void run_level(const LevelIn& in, LevelOut& out, LevelStats& st, cudaStream_t s,
     if (nun2) {
       Tier3Params t3;
       t3.X = in.X; t3.n = n; t3.Dp = in.Dp; t3.metric = in.metric; t3.guide = in.grng;
-      t3.rlo = in.rlo; t3.rhi = in.rhi; t3.pairs = unres2.as<int2>(); t3.m = (int64_t)nun2;
+      t3.rlo = in.rlo; t3.rhi = in.rhi; t3.pairs = t3pairs; t3.m = (int64_t)nun2;
       t3.pend = pend.as<int2>(); t3.pflag = pflag.as<int>(); t3.slot0 = (int64_t)npend;
       t3.amb = amb.as<int2>(); t3.amb_cnt = dc + 19; t3.amb_cap = amb_cap;
+      t3.anc = in.anc;
       int grid3 = (int)std::min<unsigned long long>(nun2, 8ull * num_sms());
-      tier3_kernel<<<grid3, 256, 2 * in.Dp * 4, s>>>(t3);
+      t3.fcap = 1 << 15;
+      GRNG_CUDA(fbuf.alloc((size_t)grid3 * 2 * t3.fcap * sizeof(Front)));
+      t3.fbuf = fbuf.as<Front>();
+      t3.pdist_hi = in.pdist_hi;
+      t3.atab = nullptr;
+      t3.tabw = 0;
+      if (in.grng && in.anc.n > 0) {
+        // pivot layers: node x ancestor keys once, instead of per pair
+        int64_t w = 0;
+        for (int a = 0; a < in.anc.n; ++a) { t3.anc.toff[a] = w; w += in.anc.m[a]; }
+        GRNG_CUDA(atab.alloc((size_t)n * w * 4));
+        for (int a = 0; a < in.anc.n; ++a)
+          launch_cross(in.X, n, in.anc.X[a], in.anc.m[a], in.Dp, in.metric, atab.as<float>() + t3.anc.toff[a], w, s);
+        t3.atab = atab.as<float>();
+        t3.tabw = w;
+      }
+      t3.stats = dc + 24;
+      GRNG_CUDA(cudaMemsetAsync(dc + 24, 0, 2 * sizeof(unsigned long long), s));
+      tier3_kernel<<<grid3, 256, 2 * in.Dp * 4, s>>>(t3); note_launch();
       GRNG_CUDA(cudaGetLastError());
     }
     unsigned long long namb = read_u64(dc + 19, s);
+    tick(5);
     if (namb > amb_cap) {
       if (attempt >= 3) fail(2, "ambiguity buffer overflow");
       amb_cap = namb + namb / 4;
@@ -781,7 +1348,7 @@ void run_level(const LevelIn& in, LevelOut& out, LevelStats& st, cudaStream_t s,
     if (namb) {
       recheck_kernel<<<(unsigned)((namb + 255) / 256), 256, 0, s>>>(
           in.X, in.D, in.Dp, in.metric, in.r64, amb.as<int2>(), (int64_t)namb, pend.as<int2>(),
-          pflag.as<int>(), dc + 22);
+          pflag.as<int>(), dc + 22); note_launch();
       GRNG_CUDA(cudaGetLastError());
     }
     // ---- emission ----------------------------------------------------------------------
@@ -793,14 +1360,16 @@ void run_level(const LevelIn& in, LevelOut& out, LevelStats& st, cudaStream_t s,
     if (nlink)
       resolve_emit_kernel<<<(unsigned)((nlink + 255) / 256), 256, 0, s>>>(
           links.as<int2>(), nullptr, (int64_t)nlink, in.grng, out.gx, out.gg, out.words, in.orig,
-          dc + 21, ecap, in.grng ? nullptr : out.edges->as<uint64_t>());
+          dc + 21, ecap, in.grng ? nullptr : out.edges->as<uint64_t>()); note_launch();
     if (npp)
       resolve_emit_kernel<<<(unsigned)((npp + 255) / 256), 256, 0, s>>>(
           pend.as<int2>(), pflag.as<int>(), (int64_t)npp, in.grng, out.gx, out.gg, out.words,
-          in.orig, dc + 21, ecap, in.grng ? nullptr : out.edges->as<uint64_t>());
+          in.orig, dc + 21, ecap, in.grng ? nullptr : out.edges->as<uint64_t>()); note_launch();
     GRNG_CUDA(cudaGetLastError());
-    unsigned long long h[24];
+    unsigned long long h[26];
     GRNG_CUDA(cudaMemcpyAsync(h, dc, sizeof(h), cudaMemcpyDeviceToHost, s));
+    st.c[15] = nun2 ? h[24] : 0;  // tier-3 frontier overflows
+    st.c[16] = nun2 ? h[25] : 0;  // tier-3 nodes tested
     GRNG_CUDA(cudaStreamSynchronize(s));
     out.n_edges = (int64_t)h[21];
     st.c[3] = h[8];  st.c[4] = h[9];  st.c[5] = h[10]; st.c[6] = h[11];   // tier 2a
@@ -809,6 +1378,7 @@ void run_level(const LevelIn& in, LevelOut& out, LevelStats& st, cudaStream_t s,
     st.c[12] = namb;   // ambiguous triples rechecked in FP64
     st.c[13] = h[22];  // of which blocking
     st.c[14] = h[21];  // edges emitted (RNG level)
+    tick(6);
     break;
   }
 }

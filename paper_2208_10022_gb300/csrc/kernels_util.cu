@@ -49,17 +49,17 @@ void exclusive_scan_i64(const int64_t* in, int64_t* out, int64_t n, cudaStream_t
     DevBuf bs, bo;
     GRNG_CUDA(bs.alloc((size_t)(nb + 1) * 8));
     GRNG_CUDA(bo.alloc((size_t)(nb + 1) * 8));
-    scan_block_kernel<<<(unsigned)nb, 1024, 0, s>>>(in, out, n, bs.as<int64_t>());
+    scan_block_kernel<<<(unsigned)nb, 1024, 0, s>>>(in, out, n, bs.as<int64_t>()); note_launch();
     GRNG_CUDA(cudaGetLastError());
     if (nb > 1) {
       exclusive_scan_i64(bs.as<int64_t>(), bo.as<int64_t>(), nb, s);
-      scan_add_kernel<<<(unsigned)nb, 1024, 0, s>>>(out, n, bo.as<int64_t>());
+      scan_add_kernel<<<(unsigned)nb, 1024, 0, s>>>(out, n, bo.as<int64_t>()); note_launch();
       GRNG_CUDA(cudaGetLastError());
     }
     // the buffers must outlive the kernels that read them
     GRNG_CUDA(cudaStreamSynchronize(s));
   }
-  scan_total_kernel<<<1, 1, 0, s>>>(in, out, n);
+  scan_total_kernel<<<1, 1, 0, s>>>(in, out, n); note_launch();
   GRNG_CUDA(cudaGetLastError());
 }
 
@@ -85,13 +85,13 @@ void group_pairs(const int2* pairs, int64_t m, int which, int64_t nkeys, int64_t
   unsigned long long* cnt = tmp.as<unsigned long long>();
   GRNG_CUDA(cudaMemsetAsync(cnt, 0, (size_t)(nkeys + 1) * 8, s));
   if (m) {
-    count_pairs_kernel<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(pairs, m, which, cnt);
+    count_pairs_kernel<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(pairs, m, which, cnt); note_launch();
     GRNG_CUDA(cudaGetLastError());
   }
   exclusive_scan_i64(reinterpret_cast<const int64_t*>(cnt), off, nkeys, s);
   GRNG_CUDA(cudaMemcpyAsync(cnt, off, (size_t)nkeys * 8, cudaMemcpyDeviceToDevice, s));
   if (m) {
-    scatter_pairs_kernel<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(pairs, m, which, cnt, val);
+    scatter_pairs_kernel<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(pairs, m, which, cnt, val); note_launch();
     GRNG_CUDA(cudaGetLastError());
   }
   GRNG_CUDA(cudaStreamSynchronize(s));
@@ -138,13 +138,15 @@ void sort_u64(uint64_t* keys, int64_t m, DevBuf& tmp, cudaStream_t s) {
   GRNG_CUDA(tmp.alloc((size_t)n2 * 8));
   uint64_t* a = tmp.as<uint64_t>();
   GRNG_CUDA(cudaMemcpyAsync(a, keys, (size_t)m * 8, cudaMemcpyDeviceToDevice, s));
-  fill_u64_kernel<<<(unsigned)((n2 - m + 255) / 256), 256, 0, s>>>(a, m, n2, ~0ull);
+  if (n2 > m) {
+    fill_u64_kernel<<<(unsigned)((n2 - m + 255) / 256), 256, 0, s>>>(a, m, n2, ~0ull); note_launch();
+  }
   for (int64_t k = 2; k <= n2; k <<= 1) {
     int64_t j = k >> 1;
     for (; j >= 1024; j >>= 1) {
-      bitonic_global_kernel<<<(unsigned)((n2 / 2 + 255) / 256), 256, 0, s>>>(a, n2, k, j);
+      bitonic_global_kernel<<<(unsigned)((n2 / 2 + 255) / 256), 256, 0, s>>>(a, n2, k, j); note_launch();
     }
-    bitonic_shared_kernel<<<(unsigned)(n2 / 2048), 1024, 0, s>>>(a, k, j);
+    bitonic_shared_kernel<<<(unsigned)(n2 / 2048), 1024, 0, s>>>(a, k, j); note_launch();
   }
   GRNG_CUDA(cudaGetLastError());
   GRNG_CUDA(cudaMemcpyAsync(keys, a, (size_t)m * 8, cudaMemcpyDeviceToDevice, s));
@@ -171,10 +173,10 @@ void stable_order(const int32_t* key, int64_t m, int64_t nkeys, int32_t* order, 
   if (m == 0) return;
   DevBuf ks, t2;
   GRNG_CUDA(ks.alloc((size_t)m * 8));
-  compose_keys_kernel<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(key, m, ks.as<uint64_t>());
+  compose_keys_kernel<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(key, m, ks.as<uint64_t>()); note_launch();
   GRNG_CUDA(cudaGetLastError());
   sort_u64(ks.as<uint64_t>(), m, t2, s);
-  split_order_kernel<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(ks.as<uint64_t>(), m, order, rank);
+  split_order_kernel<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(ks.as<uint64_t>(), m, order, rank); note_launch();
   GRNG_CUDA(cudaGetLastError());
   GRNG_CUDA(cudaStreamSynchronize(s));
   (void)tmp;
@@ -193,7 +195,7 @@ __global__ void gather_rows_kernel(const float* __restrict__ X, int Dp, const in
 void gather_rows(const float* X, int Dp, const int32_t* idx, int64_t m, float* out, cudaStream_t s) {
   const int64_t tot = m * (Dp / 4);
   if (!tot) return;
-  gather_rows_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(X, Dp, idx, m, out);
+  gather_rows_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(X, Dp, idx, m, out); note_launch();
   GRNG_CUDA(cudaGetLastError());
 }
 __global__ void fill_u32_kernel(uint32_t* p, uint32_t v, size_t count) {
@@ -206,7 +208,7 @@ void fill_u32(uint32_t* p, uint32_t v, size_t count, cudaStream_t s) {
     GRNG_CUDA(cudaMemsetAsync(p, 0, count * 4, s));
     return;
   }
-  fill_u32_kernel<<<(unsigned)std::min<size_t>((count + 255) / 256, 65535), 256, 0, s>>>(p, v, count);
+  fill_u32_kernel<<<(unsigned)std::min<size_t>((count + 255) / 256, 65535), 256, 0, s>>>(p, v, count); note_launch();
   GRNG_CUDA(cudaGetLastError());
 }
 
@@ -250,15 +252,29 @@ void bitmask_rows(const uint32_t* bits, int64_t words, const int32_t* rank, int6
   if (rows <= 0) return;
   DevBuf cnt;
   GRNG_CUDA(cnt.alloc((size_t)rows * 8));
-  csr_count_kernel<<<(unsigned)((rows + 7) / 8), 256, 0, s>>>(bits, words, rank, m, r0, r1, cnt.as<int64_t>());
+  csr_count_kernel<<<(unsigned)((rows + 7) / 8), 256, 0, s>>>(bits, words, rank, m, r0, r1, cnt.as<int64_t>()); note_launch();
   GRNG_CUDA(cudaGetLastError());
   exclusive_scan_i64(cnt.as<int64_t>(), off, rows, s);
   if (adj) {
-    csr_write_kernel<<<(unsigned)((rows + 7) / 8), 256, 0, s>>>(bits, words, rank, m, r0, r1, off, adj);
+    csr_write_kernel<<<(unsigned)((rows + 7) / 8), 256, 0, s>>>(bits, words, rank, m, r0, r1, off, adj); note_launch();
     GRNG_CUDA(cudaGetLastError());
   }
   GRNG_CUDA(cudaStreamSynchronize(s));
 }
+// cstart[c] = first s with parent[s] == c (parent non-decreasing); cstart[m] = n
+__global__ void child_ranges_kernel(const int32_t* __restrict__ parent, int64_t n, int64_t m,
+                                    int32_t* __restrict__ cstart) {
+  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s > n) return;
+  const int64_t prev = s == 0 ? -1 : parent[s - 1];
+  const int64_t cur = s == n ? m : parent[s];
+  for (int64_t c = prev + 1; c <= cur; ++c) cstart[c] = (int32_t)s;
+}
+void child_ranges(const int32_t* parent, int64_t n, int64_t m, int32_t* cstart, cudaStream_t s) {
+  child_ranges_kernel<<<(unsigned)((n + 1 + 255) / 256), 256, 0, s>>>(parent, n, m, cstart); note_launch();
+  GRNG_CUDA(cudaGetLastError());
+}
+
 void bitmask_csr(const uint32_t* bits, int64_t words, const int32_t* rank, int64_t m, int64_t* off,
                  int32_t* adj, DevBuf& tmp, cudaStream_t s) {
   (void)tmp;

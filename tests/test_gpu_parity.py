@@ -42,10 +42,10 @@ def _rows_from_edges(E, m):
     return rows
 
 
-def check_full(X, layers, metric, knn_k=32, on_gpu=True):
+def check_full(X, layers, metric, knn_k=32, on_gpu=True, flags=0):
     """Build everything on the GPU and compare every output with the oracle."""
     Xin = torch.from_numpy(X).cuda() if on_gpu else X
-    ix, out = g.build_all(Xin, layers, metric=metric, knn_k=knn_k, want_adjacency=True)
+    ix, out = g.build_all(Xin, layers, metric=metric, knn_k=knn_k, want_adjacency=True, flags=flags)
     lay = oracle.build_layers(X, layers, metric)
     for li in range(len(layers)):
         a, r, dm = out["layers"][li]
@@ -120,9 +120,19 @@ def test_ties_and_duplicates():
 
 
 def test_small_knn_lists():
+    """Short neighbour lists push many pairs into the hierarchical exhaustive tier."""
     w = wl.make("mix16", n=1500)
     for k in (1, 4):
         check_full(w.X, w.layers, wl.L2, knn_k=k)
+    w = wl.make("lin96", n=2500)
+    ix = check_full(w.X, w.layers, wl.L2, knn_k=1)
+    st = ix.stats()
+    assert st["rng"]["tier3_pairs"] > 0 and st["layers"][2]["grng"]["range_pairs"] > 0
+    # capped range lists: the hierarchical exhaustive tier takes the pivot pairs
+    ix = check_full(w.X, w.layers, wl.L2, knn_k=1, flags=g.GRNG_FLAG_SHORT_LISTS)
+    st = ix.stats()
+    assert st["layers"][2]["grng"]["range_lists_over_cap"] > 0 and st["layers"][2]["grng"]["tier3_pairs"] > 0
+    check_full(w.X, w.layers, wl.L1, knn_k=2, flags=g.GRNG_FLAG_SHORT_LISTS)
 
 
 def test_zero_radius_override_is_rng_of_pivots():
