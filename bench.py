@@ -36,11 +36,14 @@ UNIT = "edges/s"
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--n", type=int, default=None, help="points (default: the full 1,000,000)")
     ap.add_argument("--kind", default="lin96")
+    ap.add_argument("--precision", default="bf16", choices=["fp32", "bf16"],
+                    help="distance tiles of the exemplar level: tensor cores (bf16) or CUDA cores (fp32)")
+    ap.add_argument("--no-compare", action="store_true", help="skip the one-step plain FP32 comparison")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=12000, help="points of the oracle's bounded sample")
@@ -165,8 +168,10 @@ def run_gpu(a, rank, world, local):
     Xd = torch.from_numpy(w.X).cuda()
     piv_d = [torch.from_numpy(l).cuda() for l in w.layers]
 
+    prec = g.BF16 if a.precision == "bf16" else g.FP32
+
     def step_device():
-        ix = g.Index(Xd, n_layers=L, stream=stream)
+        ix = g.Index(Xd, n_layers=L, stream=stream, precision=prec)
         for li in range(L - 1, -1, -1):
             ix.build_layer(li, piv_d[li], outputs=False)
         for li in range(L):
@@ -224,7 +229,7 @@ def run_gpu(a, rank, world, local):
         f0.record(stream)
         e_edges = 0
         for _ in range(a.steps):
-            ix = g.Index(Xh, n_layers=L, stream=stream)
+            ix = g.Index(Xh, n_layers=L, stream=stream, precision=prec)
             for li in range(L - 1, -1, -1):
                 ix.build_layer(li, pivh[li], outputs=False)
             for li in range(L):
@@ -273,16 +278,32 @@ def run_gpu(a, rank, world, local):
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
             "ms_per_step": ms / a.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32", "data": "synthetic",
+            "dtype": "bf16+f32" if a.precision == "bf16" else "f32", "data": "synthetic",
             "config": {"workload": f"{a.kind}: {n:,} x {D} FP32, intrinsic dim 8, L2, nested random pivot layers "
                                    f"{'/'.join(str(s) for s in sizes)}", "n": n, "dim": D, "layers": sizes,
-                       "metric": "L2", "precision": "fp32 tiles + fp64 near-tie recheck",
+                       "metric": "L2", "precision": ("split-bf16 tcgen05 exemplar tiles" if a.precision == "bf16" else "fp32 tiles") + "; fp32 exact tiers; fp64 near-tie recheck",
                        "l2_flush": "inputs larger than L2 (points alone are %d MB)" % (w.X.nbytes >> 20),
                        "parallelism": f"replicas x{world}"},
             "edges_per_step": edges // max(a.steps, 1), "roofline": roof, "clocks": clocks,
             "gpu_launches": launches1 - launches0, "e2e": e2e,
             "detail": {"rng": stats["rng"], "layers": stats["layers"],
                        "rng_ms": stats["rng_ms"], "rng_tile_ms": stats["rng_tile_ms"], "sort_ms": stats["sort_ms"]}}
+    if prec == g.BF16 and not a.no_compare:
+        # the plain build: FP32 CUDA-core tiles everywhere (one timed step, same workload)
+        prec_saved = prec
+        prec = g.FP32
+        barrier()
+        c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        c0.record(stream)
+        ne32, st32 = step_device()
+        c1.record(stream)
+        torch.cuda.synchronize()
+        ms32 = c0.elapsed_time(c1)
+        prec = prec_saved
+        line["compare"] = {"plain_fp32_value": ne32 / (ms32 / 1000.0), "plain_fp32_ms_per_step": ms32,
+                           "plain_fp32_edges": ne32, "same_edge_count": ne32 == line["edges_per_step"],
+                           "speedup_vs_plain_fp32": (ms32 / (ms / a.steps)),
+                           "plain_fp32_tile_ms": st32["rng_tile_ms"]}
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         cb = cpu_baseline(a.kind, a.cpu_sample)
         line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}

@@ -205,9 +205,10 @@ class Index:
 GRNG_FLAG_SHORT_LISTS = 1
 
 
-def build_all(X, layers, metric=L2, knn_k=32, want_adjacency=False, stream=None, flags=0):
+def build_all(X, layers, metric=L2, knn_k=32, want_adjacency=False, stream=None, flags=0, precision=FP32):
     """Build every layer (finest first), link every layer (coarsest first) and the RNG."""
-    ix = Index(X, n_layers=len(layers), metric=metric, knn_k=knn_k, stream=stream, flags=flags)
+    ix = Index(X, n_layers=len(layers), metric=metric, knn_k=knn_k, stream=stream, flags=flags,
+               precision=precision)
     out = {"layers": [None] * len(layers), "grng": [None] * len(layers)}
     for li in range(len(layers) - 1, -1, -1):
         out["layers"][li] = ix.build_layer(li, layers[li])

@@ -17,6 +17,7 @@ namespace grng {
 static thread_local std::string g_last_error;
 
 [[noreturn]] void fail(int status, const std::string& msg) { throw Failure{status, msg}; }
+void set_last_error(const std::string& msg) { g_last_error = msg; }
 
 static std::atomic<unsigned long long> g_launches{0};
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
@@ -286,7 +287,7 @@ void level_json(std::string& js, const char* name, const LevelStats& st) {
                              "fp64_blocking", "edges", "tier3_overflows", "tier3_nodes_tested",
                              "list_certified", "range_pairs", "range_lists_over_cap", "range_listed_nodes",
                              "range_links", "range_nodes_tested"};
-  char buf[128];
+  char buf[1024];
   js += "\"";
   js += name;
   js += "\":{";
@@ -331,7 +332,8 @@ grng_status grng_create(grng_index** out, const float* pts, int64_t n, int32_t d
     if (opts->metric != GRNG_L2 && opts->metric != GRNG_L1) fail(GRNG_EINVAL, "unknown metric");
     if (opts->n_layers < 1 || opts->n_layers > 16) fail(GRNG_EINVAL, "n_layers must be in [1, 16]");
     if (opts->knn_k < 0 || opts->knn_k > GRNG_KMAX) fail(GRNG_EINVAL, "knn_k must be in [0, 32]");
-    if (opts->precision != GRNG_FP32) fail(GRNG_ENOTIMPL, "only the FP32 tile precision is built");
+    if (opts->precision != GRNG_FP32 && opts->precision != GRNG_BF16)
+      fail(GRNG_ENOTIMPL, "FP32 and BF16 tile precisions are built");
     if (opts->k_shortlist != 0 || opts->mlp_weights) fail(GRNG_ENOTIMPL, "learned shortlist not built");
     if (opts->reserved != 0 || (opts->flags & ~(uint64_t)GRNG_FLAG_SHORT_LISTS) != 0)
       fail(GRNG_EINVAL, "reserved fields must be 0");
@@ -565,6 +567,8 @@ grng_status rng_build_exact(grng_index* ix) {
     in.orig = ix->xorder.as<int32_t>();
     in.anc = ancestors_of(ix, (int)ix->layers.size());
     in.pdist_hi = ix->xpdh.as<float>();
+    in.precision = ix->opts.precision == GRNG_BF16 ? 1 : 0;
+    if (ix->opts.spin_limit > 0) in.spin = ix->opts.spin_limit;
     LevelOut lo;
     lo.edges = &ix->edges;
     float tile_ms = 0;
@@ -620,7 +624,7 @@ grng_status grng_stats(const grng_index* cix, char* json, size_t cap) {
     return GRNG_EINVAL;
   }
   std::string js = "{";
-  char buf[256];
+  char buf[1024];
   snprintf(buf, sizeof(buf),
            "\"n\":%lld,\"dim\":%d,\"metric\":%d,\"knn_k\":%d,\"sort_ms\":%.4f,\"kernel_launches\":%llu,\"layers\":[",
            (long long)ix->n, ix->D, ix->metric, ix->K, ix->sort_ms, launches());

@@ -44,6 +44,7 @@ struct Failure {
   std::string msg;
 };
 [[noreturn]] void fail(int status, const std::string& msg);
+void set_last_error(const std::string& msg);  // message returned by grng_last_error()
 void cuda_check(cudaError_t e, const char* what);
 #define GRNG_STR2(x) #x
 #define GRNG_STR(x) GRNG_STR2(x)
@@ -115,7 +116,42 @@ struct LevelIn {
   Ancestors anc;            // layers above this level (none for the top GRNG layer)
   int64_t lmax = 0;         // cap of the range lists (0: the default)
   const float* pdist_hi = nullptr;  // [n] FP32 upper bound of d(node, parent), or null
+  int precision = 0;                // 1: tensor-core (split BF16) distance tiles for the RNG level
+  long long spin = 1ll << 24;       // poll limit of every bounded device wait
 };
+
+// ---- tensor-core tiles (kernels_tc.cu) ------------------------------------------------------
+struct TcLaunch {
+  const uint8_t* img;
+  const float* nrm;
+  const unsigned int* bmax;
+  int64_t n;
+  int Dp, K;
+  float nmax_all;
+  const int32_t* parent;
+  const uint32_t* gpar;
+  int64_t gpar_words;
+  const __half* A;
+  const uint8_t* nbr_idx;
+  const float* nbr_key;
+  int32_t* knn_idx;
+  float* knn_key;
+  float* knn_rb;
+  int2* surv;
+  unsigned long long* surv_cnt;
+  unsigned long long surv_cap;
+  int* strip_ctr;
+  unsigned long long* stats;
+  int* status;
+  long long spin;
+};
+bool tc_supported(int Dp);
+float tc_gamma(int Dp);
+void tc_prepare(const float* X, int64_t n, int Dp, DevBuf& img, DevBuf& nrm, DevBuf& bmax, float* nmax_all,
+                cudaStream_t s);
+void tc_sweep(const TcLaunch& L, cudaStream_t s);
+void tc_knn_fix(const float* X, int64_t n, int Dp, int K, int metric, const int32_t* knn_idx, float* knn_key,
+                cudaStream_t s);
 // children ranges: parent[] (non-decreasing, values in [0, m)) -> cstart[m+1]
 void child_ranges(const int32_t* parent, int64_t n, int64_t m, int32_t* cstart, cudaStream_t s);
 struct LevelOut {

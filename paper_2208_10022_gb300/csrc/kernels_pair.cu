@@ -447,6 +447,7 @@ struct Tier2Params {
   const float* rhi;
   const int32_t* knn_idx;
   const float* knn_key;
+  const float* knn_rb;   // [n] lower bound of unlisted keys, or null (the K-th listed key)
   const int64_t* off;    // [n+1] grouped by g
   const int32_t* other;  // partner o of each entry
   int2* links; unsigned long long* link_cnt; unsigned long long link_cap;
@@ -485,7 +486,9 @@ __global__ void __launch_bounds__(128) tier2_kernel(Tier2Params p) {
     const int kidl = lane < K ? p.knn_idx[g * K + lane] : -1;
     const float akey = lane < K ? p.knn_key[g * K + lane] : finf();
     const int lastid = p.knn_idx[g * K + K - 1];
-    const float Rk = lastid >= 0 ? p.knn_key[g * K + K - 1] : finf();
+    // every unlisted node has a key of at least lo_b(Rk): the K-th listed key, or the bound
+    // the tensor-core sweep leaves when the list was chosen from approximate keys
+    const float Rk = p.knn_rb ? p.knn_rb[g] : (lastid >= 0 ? p.knn_key[g * K + K - 1] : finf());
     const float rgl = p.rlo ? p.rlo[g] : 0.0f, rgh = p.rhi ? p.rhi[g] : 0.0f;
     float* ow = os + warp * Dp;
     for (int64_t t = s + warp; t < t_end; t += 4) {
@@ -1145,6 +1148,13 @@ void run_level(const LevelIn& in, LevelOut& out, LevelStats& st, cudaStream_t s,
   tick(0);
   // ---- tier 1 -------------------------------------------------------------------------
   unsigned long long surv_cap = (unsigned long long)std::max<int64_t>(1 << 20, 256 * n);
+  const bool use_tc = !in.grng && in.precision == 1 && in.metric == L2 && tc_supported(in.Dp);
+  DevBuf tcimg, tcnrm, tcbmax, knnrb;
+  float nmax_all = 0.0f;
+  if (use_tc) {
+    tc_prepare(in.X, n, in.Dp, tcimg, tcnrm, tcbmax, &nmax_all, s);
+    GRNG_CUDA(knnrb.alloc((size_t)n * 4));
+  }
   DevBuf surv;
   unsigned long long nsurv = 0;
   for (int attempt = 0;; ++attempt) {
@@ -1172,14 +1182,28 @@ void run_level(const LevelIn& in, LevelOut& out, LevelStats& st, cudaStream_t s,
     // pivot layers: a first sweep for the neighbour lists, then the filter, which can
     // certify links from the final lists; exemplars: one sweep doing both
     tp.mode = in.grng ? 1 : 0;
-    for (int sweep = 0; sweep < (in.grng ? 2 : 1); ++sweep) {
-      if (sweep == 1) {
-        GRNG_CUDA(cudaMemsetAsync(dc, 0, sizeof(unsigned long long), s));  // strip counter
-        tp.mode = 2;
+    if (use_tc) {
+      // precision form: tensor-core Gram tiles, then the listed keys again in FP32
+      TcLaunch L;
+      L.img = tcimg.as<uint8_t>(); L.nrm = tcnrm.as<float>(); L.bmax = tcbmax.as<unsigned int>();
+      L.n = n; L.Dp = in.Dp; L.K = in.K; L.nmax_all = nmax_all;
+      L.parent = in.parent; L.gpar = in.gpar; L.gpar_words = in.gpar_words;
+      L.A = A.as<__half>(); L.nbr_idx = nbi.as<uint8_t>(); L.nbr_key = nbk.as<float>();
+      L.knn_idx = knni.as<int32_t>(); L.knn_key = knnk.as<float>(); L.knn_rb = knnrb.as<float>();
+      L.surv = surv.as<int2>(); L.surv_cnt = dc + 1; L.surv_cap = surv_cap;
+      L.strip_ctr = reinterpret_cast<int*>(dc + 0); L.stats = dc + 2;
+      L.status = reinterpret_cast<int*>(dc + 40); L.spin = in.spin;
+      tc_sweep(L, s);
+    } else {
+      for (int sweep = 0; sweep < (in.grng ? 2 : 1); ++sweep) {
+        if (sweep == 1) {
+          GRNG_CUDA(cudaMemsetAsync(dc, 0, sizeof(unsigned long long), s));  // strip counter
+          tp.mode = 2;
+        }
+        if (KC == 32) launch_tile<32>(in, tp, grid, s);
+        else if (KC == 16) launch_tile<16>(in, tp, grid, s);
+        else launch_tile<8>(in, tp, grid, s);
       }
-      if (KC == 32) launch_tile<32>(in, tp, grid, s);
-      else if (KC == 16) launch_tile<16>(in, tp, grid, s);
-      else launch_tile<8>(in, tp, grid, s);
     }
     if (tile_ms) {
       GRNG_CUDA(cudaEventRecord(e1, s));
@@ -1189,6 +1213,10 @@ void run_level(const LevelIn& in, LevelOut& out, LevelStats& st, cudaStream_t s,
       cudaEventDestroy(e1);
     }
     nsurv = read_u64(dc + 1, s);
+    if (use_tc) {
+      if (read_u64(dc + 40, s) != 0) fail(4 /* GRNG_ETIMEOUT */, "a bounded tensor-core wait ran out");
+      if (nsurv <= surv_cap) tc_knn_fix(in.X, n, in.Dp, in.K, in.metric, knni.as<int32_t>(), knnk.as<float>(), s);
+    }
     if (nsurv <= surv_cap) break;
     if (attempt >= 3) fail(2, "tier-1 survivor buffer overflow");
     surv_cap = nsurv + nsurv / 4;
@@ -1219,6 +1247,7 @@ void run_level(const LevelIn& in, LevelOut& out, LevelStats& st, cudaStream_t s,
     Tier2Params t2;
     t2.X = in.X; t2.n = n; t2.Dp = in.Dp; t2.metric = in.metric; t2.guide = in.grng; t2.K = in.K;
     t2.rlo = in.rlo; t2.rhi = in.rhi; t2.knn_idx = knni.as<int32_t>(); t2.knn_key = knnk.as<float>();
+    t2.knn_rb = use_tc ? knnrb.as<float>() : nullptr;
     t2.off = off.as<int64_t>(); t2.other = oth.as<int32_t>();
     t2.links = links.as<int2>(); t2.link_cnt = dc + 16; t2.link_cap = cap;
     t2.unres = unres.as<int2>(); t2.unres_cnt = dc + 18; t2.unres_cap = cap;

@@ -1,0 +1,147 @@
+// tc.cuh -- Blackwell (sm_103a) tensor-core helpers: mbarriers, bulk (TMA) copies,
+// TMEM allocation, tcgen05.mma (kind::f16, BF16 inputs, FP32 accumulation) and
+// tcgen05.ld, as inline PTX.
+//
+// Operand layout.  Every 128-row block of points is stored as two BF16 images (the
+// "hi" and "lo" parts of x = hi + lo + O(2^-16 |x|)), each in the canonical K-major,
+// non-swizzled core-matrix layout the MMA reads: core matrices of 8 rows x 8 elements
+// (8 x 16 bytes, contiguous), consecutive along K every 128 bytes (leading byte offset),
+// consecutive along the rows every Dp*16 bytes (stride byte offset).  Element (r, k) of
+// an image sits at byte (r/8)*Dp*16 + (k/8)*128 + (r%8)*16 + (k%8)*2.  One block image is
+// therefore one contiguous 2*128*Dp*2-byte copy into shared memory.
+#pragma once
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+namespace grng {
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// byte offset of element (r, k) inside one image of a 128-row block
+__host__ __device__ __forceinline__ uint32_t img_off(int r, int k, int Dp) {
+  return (uint32_t)((r >> 3) * Dp * 16 + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2);
+}
+
+// ---- mbarrier -------------------------------------------------------------------------
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+// Wait for the phase with the given parity to complete; gives up after `limit` polls and
+// returns false, so that no wait can spin forever.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, long long limit) {
+  for (long long i = 0; i < limit; ++i) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+// ---- bulk copy global -> shared (the TMA engine, no tensor map) ---------------------------
+// dst, src 16-byte aligned; bytes a multiple of 16.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+// order this thread's generic-proxy shared-memory accesses before later async-proxy ones
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// ---- tensor memory ------------------------------------------------------------------------
+__device__ __forceinline__ void tmem_alloc(uint32_t* dst_smem, uint32_t ncols) {  // one full warp
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst_smem)),
+               "r"(ncols)
+               : "memory");
+}
+__device__ __forceinline__ void tmem_relinquish() {
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {  // the allocating warp
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// ---- MMA ------------------------------------------------------------------------------------
+// shared-memory matrix descriptor: start address, leading / stride byte offsets, no swizzle
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+// instruction descriptor: D = F32, A = B = BF16, both K-major, M x N
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+// D[tmem] (+)= A * B^T, issued by one thread
+__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                          uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+// arrive on the mbarrier once every MMA issued so far by this thread has completed
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   smem_u32(bar))
+               : "memory");
+}
+
+// 32 consecutive FP32 columns of this thread's TMEM lane (warp w reads lanes 32*(w%4)..)
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Issue the 3*Dp/16 MMAs of one 128 x 128 Gram tile: hi*hi + hi*lo + lo*hi, where sa / sb
+// point at a block's hi image followed by its lo image (128*Dp*2 bytes each).
+__device__ __forceinline__ void issue_gram_tile(uint32_t tmem_d, const void* sa, const void* sb, int Dp) {
+  const uint32_t img = 128u * (uint32_t)Dp * 2u;
+  const uint32_t a_hi = smem_u32(sa), a_lo = a_hi + img;
+  const uint32_t b_hi = smem_u32(sb), b_lo = b_hi + img;
+  const uint32_t sbo = (uint32_t)Dp * 16u, lbo = 128u;
+  const uint32_t idesc = idesc_bf16(128, 128);
+  uint32_t acc = 0;
+  for (int kc = 0; kc < Dp / 16; ++kc) {
+    const uint32_t off = (uint32_t)kc * 256u;  // 16 elements = two core matrices along K
+    umma_bf16(tmem_d, smem_desc(a_hi + off, lbo, sbo), smem_desc(b_hi + off, lbo, sbo), idesc, acc);
+    acc = 1;
+    umma_bf16(tmem_d, smem_desc(a_hi + off, lbo, sbo), smem_desc(b_lo + off, lbo, sbo), idesc, 1);
+    umma_bf16(tmem_d, smem_desc(a_lo + off, lbo, sbo), smem_desc(b_hi + off, lbo, sbo), idesc, 1);
+  }
+}
+
+}  // namespace grng
