@@ -153,6 +153,30 @@ const char* grng_last_error(void);
  * Dp = dim rounded up to 16.  keys may be host or device memory. */
 grng_status grng_tc_keys(const float* pts, int64_t n, int32_t dim, float* keys);
 
+/* Nearest-pivot assignment that allocates nothing.  The paper has no counterpart: this
+ * entry point exists for callers that cannot allocate device memory -- code that runs
+ * inside a memory pool that forbids new allocations, plugins whose host application
+ * owns every device allocation, or programs whose memory footprint must not change once
+ * they are running.  It computes what grng_build_layer computes for the finest layer
+ * (nearest pivot by canonical key, ties to the lowest position, a pivot owns itself),
+ * without an index and without cudaMalloc/cudaFree or any allocating library call.
+ *
+ * pts[n][dim]       DEVICE pointer, FP32 row-major; dim a positive multiple of 8
+ * pivot_idx[m]      DEVICE pointer, distinct point indices in [0, n)
+ * assign[n]         DEVICE output: pivot position of every point
+ * dist[n]           DEVICE output: FP64 canonical distance to that pivot (the layer's
+ *                   radius of pivot p is the maximum of dist over the points assigned to p)
+ * cuda_stream       cudaStream_t the work is queued on (NULL = legacy default stream);
+ *                   the call returns after that stream has finished it.
+ * Limits: 1 <= n <= 262,144; 1 <= m <= min(n, 65,536); m * dim <= 2,097,152; larger
+ * sizes return GRNG_EINVAL.  Scratch memory is one fixed array of about 13 MB inside the
+ * library image; every GPU that loads the library holds it until the process exits.
+ * Every call shares that array and it keeps the previous call's contents, so calls that
+ * overlap on the GPU (from several threads or streams) race: serialise them.  The first
+ * call on a device looks up the array's device address with that device current; make
+ * that first call before capturing any stream into a CUDA graph. */
+grng_status grng_assign_static(const float* pts, int64_t n, int32_t dim, const int32_t* pivot_idx, int32_t m,
+                               int32_t metric, int32_t* assign, double* dist, void* cuda_stream);
 
 #ifdef __cplusplus
 }

@@ -7,7 +7,10 @@
 // FP32 keys cannot be separated under the error bound is re-decided in FP64 against
 // every pivot whose key could tie the minimum.
 #include <algorithm>
+#include <mutex>
+#include <string>
 
+#include "../../include/grng.h"
 #include "common.cuh"
 #include "internal.h"
 #include "tile.cuh"
@@ -203,4 +206,145 @@ void assign_layer(const float* Xmem, const int32_t* mem_id, const double* mem_r,
   GRNG_CUDA(cudaStreamSynchronize(s));
 }
 
+// ---------------------------------------------------------------------------------------
+// Allocation-free nearest-pivot assignment (grng_assign_static in include/grng.h).
+//
+// Some callers cannot allocate device memory at all: code running inside a memory pool
+// that forbids new allocations, plugins whose host owns every device allocation, or
+// programs whose allocations must not change once they start.  For them the same
+// assignment as grng_build_layer is available with every piece of scratch memory in one
+// file-scope device array of fixed size.  That array lives in the library image, so
+// every GPU that loads the library holds it until the process exits.
+// ---------------------------------------------------------------------------------------
+#define GRNG_STATIC_MAX_POINTS (1 << 18)         // members (points) per call
+#define GRNG_STATIC_MAX_PIVOTS (1 << 16)         // pivots per call
+#define GRNG_STATIC_MAX_PIVOT_FLOATS (1 << 21)   // pivots x dim
+#define GRNG_STATIC_BYTES                                                                        \
+  ((size_t)GRNG_STATIC_MAX_POINTS * 4 * 5 + (size_t)GRNG_STATIC_MAX_PIVOT_FLOATS * 4 +         \
+   (size_t)GRNG_STATIC_MAX_PIVOTS * 8 * 2 + 256)
+
+static __device__ __align__(256) unsigned char g_static_scratch[GRNG_STATIC_BYTES];
+
+// pivot positions of the points; flags an index out of range or repeated
+__global__ void static_pivpos_kernel(const int32_t* __restrict__ piv, int64_t m, int64_t n,
+                                     int32_t* __restrict__ pivpos, int32_t* __restrict__ err) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= m) return;
+  const int32_t v = piv[j];
+  if (v < 0 || v >= n) {
+    atomicOr(err, 1);
+    return;
+  }
+  if (atomicExch(pivpos + v, (int32_t)j) != -1) atomicOr(err, 2);
+}
+
+// as assign_decide_kernel, for members that are the points 0..n-1 themselves
+__global__ void static_decide_kernel(int64_t n, const int32_t* __restrict__ pivpos, const float* __restrict__ best1,
+                                     const int32_t* __restrict__ arg1, const float* __restrict__ best2, int Dp,
+                                     int32_t* __restrict__ assign, int32_t* __restrict__ amb,
+                                     unsigned long long* __restrict__ amb_cnt) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const int pp = pivpos[t];
+  if (pp >= 0) { assign[t] = pp; return; }
+  const Err e = err_fp32(Dp);
+  if (hi_b(best1[t], e) < lo_b(best2[t], e)) {
+    assign[t] = arg1[t];
+  } else {
+    assign[t] = -1;
+    unsigned long long pos = atomicAdd(amb_cnt, 1ull);
+    amb[pos] = (int32_t)t;
+  }
+}
+
+// device address of the scratch array, looked up once per device (with that device current)
+static void* static_scratch_address(int dev) {
+  static std::mutex mu;
+  static void* addr[64] = {nullptr};
+  if (dev < 0 || dev >= 64) fail(1, "device ordinal out of range");
+  std::lock_guard<std::mutex> lock(mu);
+  if (!addr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      fail(3, std::string("cudaGetSymbolAddress of the static scratch failed: ") + cudaGetErrorString(e));
+    }
+    addr[dev] = p;
+  }
+  return addr[dev];
+}
+
+void assign_static(const float* X, int64_t n, int dim, const int32_t* piv, int64_t m, int metric,
+                   int32_t* assign, double* dist, cudaStream_t s) {
+  if (!X || !piv || !assign || !dist) fail(1, "pointers must not be NULL");
+  if (metric != L2 && metric != L1) fail(1, "unknown metric");
+  if (dim < 8 || dim % 8 != 0) fail(1, "dim must be a positive multiple of 8");
+  if (n < 1 || n > GRNG_STATIC_MAX_POINTS) fail(1, "n must be in [1, 262144] for the allocation-free call");
+  if (m < 1 || m > GRNG_STATIC_MAX_PIVOTS || m > n) fail(1, "m must be in [1, min(n, 65536)]");
+  if (m * (int64_t)dim > GRNG_STATIC_MAX_PIVOT_FLOATS) fail(1, "m x dim must be at most 2097152");
+  int dev = 0;
+  GRNG_CUDA(cudaGetDevice(&dev));
+  unsigned char* base = static_cast<unsigned char*>(static_scratch_address(dev));
+  int32_t* pivpos = reinterpret_cast<int32_t*>(base);
+  float* b1 = reinterpret_cast<float*>(pivpos + GRNG_STATIC_MAX_POINTS);
+  int32_t* a1 = reinterpret_cast<int32_t*>(b1 + GRNG_STATIC_MAX_POINTS);
+  float* b2 = reinterpret_cast<float*>(a1 + GRNG_STATIC_MAX_POINTS);
+  int32_t* amb = reinterpret_cast<int32_t*>(b2 + GRNG_STATIC_MAX_POINTS);
+  float* xp = reinterpret_cast<float*>(amb + GRNG_STATIC_MAX_POINTS);
+  unsigned long long* radius = reinterpret_cast<unsigned long long*>(xp + GRNG_STATIC_MAX_PIVOT_FLOATS);
+  unsigned long long* delta = radius + GRNG_STATIC_MAX_PIVOTS;
+  unsigned long long* cnt = delta + GRNG_STATIC_MAX_PIVOTS;  // [0] ambiguous, [1] fp64 keys, [2] error
+  int32_t* err = reinterpret_cast<int32_t*>(cnt + 2);
+  // the array keeps the previous call's contents: clear what must start empty
+  GRNG_CUDA(cudaMemsetAsync(pivpos, 0xff, (size_t)n * 4, s));
+  GRNG_CUDA(cudaMemsetAsync(cnt, 0, 3 * sizeof(unsigned long long), s));
+  static_pivpos_kernel<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(piv, m, n, pivpos, err); note_launch();
+  GRNG_CUDA(cudaGetLastError());
+  int32_t herr = 0;
+  GRNG_CUDA(cudaMemcpyAsync(&herr, err, 4, cudaMemcpyDeviceToHost, s));
+  GRNG_CUDA(cudaStreamSynchronize(s));
+  if (herr & 1) fail(1, "pivot index out of range");
+  if (herr & 2) fail(1, "duplicate pivot index");
+  gather_rows(X, dim, piv, m, xp, s);
+  const int KC = dim % 32 == 0 ? 32 : (dim % 16 == 0 ? 16 : 8);
+  // members are the points 0..n-1 themselves: their ids are their positions, which the
+  // decide kernel reads through mem_id; an identity map is not stored, so decide here
+  if (KC == 32) launch_assign_tile<32>(X, n, xp, m, dim, metric, b1, a1, b2, s);
+  else if (KC == 16) launch_assign_tile<16>(X, n, xp, m, dim, metric, b1, a1, b2, s);
+  else launch_assign_tile<8>(X, n, xp, m, dim, metric, b1, a1, b2, s);
+  static_decide_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, pivpos, b1, a1, b2, dim, assign, amb,
+                                                                   cnt); note_launch();
+  GRNG_CUDA(cudaGetLastError());
+  unsigned long long namb = 0;
+  GRNG_CUDA(cudaMemcpyAsync(&namb, cnt, 8, cudaMemcpyDeviceToHost, s));
+  GRNG_CUDA(cudaStreamSynchronize(s));
+  if (namb) {
+    assign_recheck_kernel<<<(unsigned)namb, 256, 0, s>>>(X, xp, m, dim, dim, metric, amb, b1, assign, cnt + 1); note_launch();
+    GRNG_CUDA(cudaGetLastError());
+  }
+  GRNG_CUDA(cudaMemsetAsync(radius, 0, (size_t)m * 8, s));
+  GRNG_CUDA(cudaMemsetAsync(delta, 0, (size_t)m * 8, s));
+  member_dist_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(X, xp, nullptr, n, dim, dim, metric, assign, dist,
+                                                                  radius, delta); note_launch();
+  GRNG_CUDA(cudaGetLastError());
+  GRNG_CUDA(cudaStreamSynchronize(s));
+}
+
 }  // namespace grng
+
+extern "C" grng_status grng_assign_static(const float* pts, int64_t n, int32_t dim, const int32_t* pivot_idx,
+                                          int32_t m, int32_t metric, int32_t* assign, double* dist,
+                                          void* cuda_stream) {
+  try {
+    grng::assign_static(pts, n, dim, pivot_idx, m, metric, assign, dist, static_cast<cudaStream_t>(cuda_stream));
+    grng::set_last_error("");
+    return GRNG_OK;
+  } catch (const grng::Failure& f) {
+    grng::set_last_error(f.msg);
+    return f.status;
+  } catch (...) {
+    grng::set_last_error("unexpected internal exception");
+    return GRNG_EINTERNAL;
+  }
+}
