@@ -285,7 +285,7 @@ void level_json(std::string& js, const char* name, const LevelStats& st) {
                              "tier2a_unresolved", "tier2a_blocked", "tier2b_links", "tier2b_pending",
                              "tier2b_unresolved", "tier2b_blocked", "tier3_pairs", "fp64_triples",
                              "fp64_blocking", "edges", "tier3_overflows", "tier3_nodes_tested",
-                             "list_certified", "range_pairs", "range_lists_over_cap", "range_listed_nodes",
+                             "list_certified", "range_pairs", "range_lists_cut", "range_listed_nodes",
                              "range_links", "range_nodes_tested"};
   char buf[1024];
   js += "\"";

@@ -797,23 +797,29 @@ static void launch_cross(const float* Xr, int64_t nr, const float* Xc, int64_t n
 
 // ---------------------------------------------------------------------------------
 // Range lists (pivot layers): pairs that neither endpoint's neighbour list covers.
-// Each such pair picks the endpoint s whose threshold is smallest relative to its
-// K-th neighbour distance; one more sweep lists, for every such s, all nodes that
-// could lie within T_s (the largest threshold of its pairs); each pair then tests the
-// listed nodes of its annulus only.
+// Every endpoint s of such a pair gets T_s, the largest threshold among its pairs.
+// One sweep histograms, per node, the keys below T_s (16 bins per octave of key);
+// the list radius is then cut to the largest bin edge T'_s that keeps at most
+// GRNG_LMAX nodes, and a second sweep lists every node with key < T'_s.  A pair is
+// covered from a side whose T'_s reaches past its threshold on that side: every node
+// that could satisfy that condition is then listed, and only the listed nodes of the
+// pair's annulus are tested.  Uncovered pairs go to the exhaustive tier.
 // ---------------------------------------------------------------------------------
-#define GRNG_LMAX 8192  // longest range list; nodes beyond it leave their pairs to tier 3
+#define GRNG_LMAX 1024  // target list length
+#define GRNG_LCAP 2048  // list capacity (bin-edge rounding can add a few nodes)
+#define GRNG_HBINS 128
 
 struct SideParams {
   const float* X;
   int Dp, metric, guide, K;
   const float* rlo;
   const float* rhi;
-  const float* knn_key;
   const int2* pairs;
   int64_t m;
-  int8_t* side;               // 0: list of pairs[t].x, 1: list of .y, 3: linked
+  int8_t* side;               // 3: linked; otherwise set by pick_side_kernel
   unsigned int* tkey;         // [n] float bits of T_s (key units)
+  const unsigned int* tcut;   // [n] float bits of T'_s
+  const int* lcnt;            // [n] listed nodes (> GRNG_LCAP: incomplete)
 };
 
 __device__ __forceinline__ PairThr thr_of(const SideParams& p, int a, int b, float v, Err e) {
@@ -821,45 +827,61 @@ __device__ __forceinline__ PairThr thr_of(const SideParams& p, int a, int b, flo
                          p.rhi ? p.rhi[b] : 0.0f, p.metric, e, p.guide);
 }
 
-__global__ void choose_side_kernel(SideParams p) {
+// thresholds of both sides raise T_s of both endpoints
+__global__ void range_thresholds_kernel(SideParams p) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= p.m) return;
   const Err e = err_fp32(p.Dp);
   const int a = p.pairs[t].x, b = p.pairs[t].y;
   const float v = key32(p.X + (int64_t)a * p.Dp, p.X + (int64_t)b * p.Dp, p.Dp, p.metric);
-  PairThr P = thr_of(p, a, b, v, e);
+  const PairThr P = thr_of(p, a, b, v, e);
   if (P.quick) { p.side[t] = 3; return; }
-  // thresholds relative to the K-th neighbour key: the smaller ratio, the fewer nodes
-  const float ra = P.t1hi / fmaxf(p.knn_key[(int64_t)a * p.K + p.K - 1], 1e-30f);
-  const float rb = P.t2hi / fmaxf(p.knn_key[(int64_t)b * p.K + p.K - 1], 1e-30f);
-  const int sd = rb < ra ? 1 : 0;
-  p.side[t] = (int8_t)sd;
-  atomicMax(p.tkey + (sd ? b : a), __float_as_uint(sd ? P.t2hi : P.t1hi));  // positive floats
+  p.side[t] = 2;
+  atomicMax(p.tkey + a, __float_as_uint(P.t1hi));  // positive floats order like their bits
+  atomicMax(p.tkey + b, __float_as_uint(P.t2hi));
 }
 
-// one sweep over the node x node tiles of the rows with T_s > 0: count, or fill
+// a covered side with the shorter list, or 2 (exhaustive tier)
+__global__ void pick_side_kernel(SideParams p) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= p.m || p.side[t] == 3) return;
+  const Err e = err_fp32(p.Dp);
+  const int a = p.pairs[t].x, b = p.pairs[t].y;
+  const float v = key32(p.X + (int64_t)a * p.Dp, p.X + (int64_t)b * p.Dp, p.Dp, p.metric);
+  const PairThr P = thr_of(p, a, b, v, e);
+  const bool ca = p.lcnt[a] <= GRNG_LCAP && lo_b(__uint_as_float(p.tcut[a]), e) >= P.t1hi;
+  const bool cb = p.lcnt[b] <= GRNG_LCAP && lo_b(__uint_as_float(p.tcut[b]), e) >= P.t2hi;
+  p.side[t] = (int8_t)(ca && cb ? (p.lcnt[b] < p.lcnt[a] ? 1 : 0) : ca ? 0 : cb ? 1 : 2);
+}
+
+__device__ __forceinline__ int hist_bin(float v, float T) {
+  const float l = log2f(fmaxf(v, 1e-37f) / T);  // < 0 for v < T
+  return max(0, min(GRNG_HBINS - 1, (int)floorf(16.0f * l) + GRNG_HBINS));
+}
+
+// mode 0: per-row histogram of keys below T_s; mode 1: list every node with key < T'_s
 template <int KC, int METRIC>
 __global__ void __launch_bounds__(GRNG_THREADS) range_sweep_kernel(const float* __restrict__ X, int64_t n, int Dp,
                                                                    const unsigned int* __restrict__ tkey,
-                                                                   int64_t* __restrict__ cnt,
-                                                                   const int64_t* __restrict__ off,
-                                                                   unsigned long long* __restrict__ cursor,
+                                                                   int* __restrict__ hist,
+                                                                   int* __restrict__ lcnt,
                                                                    int32_t* __restrict__ lidx,
                                                                    float* __restrict__ lkey, int fill) {
   extern __shared__ __align__(16) unsigned char sm_raw[];
   float* sA = reinterpret_cast<float*>(sm_raw);
   float* sB = sA + KC * GRNG_SSTRIDE;
   float* T = sB + KC * GRNG_SSTRIDE;
+  int* H = reinterpret_cast<int*>(T + 128 * 129);  // [GRNG_HBINS][128]: lanes = rows
   const int64_t xb = (int64_t)blockIdx.x * GRNG_TILE;
   const int nr = (int)(n - xb < GRNG_TILE ? n - xb : GRNG_TILE);
   const int tid = threadIdx.x;
   const float Tr = tid < nr ? __uint_as_float(tkey[xb + tid]) : 0.0f;
-  // a row whose list overflowed has cnt < 0 and is skipped by the fill
-  const bool act = tid < nr && Tr > 0.0f && (!fill || cnt[xb + tid] >= 0);
+  const bool act = tid < nr && Tr > 0.0f;
   if (!__syncthreads_or(act)) return;
-  const Err e = err_fp32(Dp);
+  if (!fill)
+    for (int i = tid; i < GRNG_HBINS * 128; i += GRNG_THREADS) H[i] = 0;
   const int64_t nb = (n + GRNG_TILE - 1) / GRNG_TILE;
-  int64_t c_row = 0;
+  int c_row = 0;
   for (int64_t by = 0; by < nb; ++by) {
     const int64_t yb = by * GRNG_TILE;
     const int nc = (int)(n - yb < GRNG_TILE ? n - yb : GRNG_TILE);
@@ -875,31 +897,46 @@ __global__ void __launch_bounds__(GRNG_THREADS) range_sweep_kernel(const float* 
         const int64_t k = yb + c;
         if (k == xb + tid) continue;
         const float v = T[tid * 129 + c];
-        if (lo_b(v, e) < Tr) {
+        if (v < Tr) {
           if (fill) {
-            const unsigned long long pos = atomicAdd(cursor + xb + tid, 1ull);
-            lidx[pos] = (int32_t)k;
-            lkey[pos] = v;
+            if (c_row < GRNG_LCAP) {
+              lidx[(xb + tid) * GRNG_LCAP + c_row] = (int32_t)k;
+              lkey[(xb + tid) * GRNG_LCAP + c_row] = v;
+            }
+            ++c_row;
+          } else {
+            ++H[hist_bin(v, Tr) * 128 + tid];
           }
-          ++c_row;
         }
       }
     }
     __syncthreads();
   }
-  if (!fill && tid < nr) cnt[xb + tid] = act ? c_row : 0;
-}
-
-__global__ void cap_lists_kernel(int64_t* cnt, int64_t n, int64_t lmax, unsigned long long* n_over) {
-  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (s < n && cnt[s] > lmax) {
-    cnt[s] = -1;
-    atomicAdd(n_over, 1ull);
+  if (tid < nr) {
+    if (fill) lcnt[xb + tid] = act ? c_row : 0;
+    else
+      for (int b = 0; b < GRNG_HBINS; ++b) hist[(xb + tid) * GRNG_HBINS + b] = H[b * 128 + tid];
   }
 }
-__global__ void clamp_counts_kernel(const int64_t* cnt, int64_t n, int64_t* out) {
+
+// T'_s = upper edge of the last histogram bin that keeps the cumulative count <= lmax
+__global__ void range_cut_kernel(const unsigned int* __restrict__ tkey, const int* __restrict__ hist, int64_t n,
+                                 unsigned int* __restrict__ tcut, int lmax) {
   const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (s < n) out[s] = cnt[s] > 0 ? cnt[s] : 0;
+  if (s >= n) return;
+  const float T = __uint_as_float(tkey[s]);
+  float cut = 0.0f;
+  if (T > 0.0f) {
+    int cum = 0, last = -1;
+    for (int b = 0; b < GRNG_HBINS; ++b) {
+      cum += hist[s * GRNG_HBINS + b];
+      if (cum > lmax) break;
+      last = b;
+    }
+    if (last == GRNG_HBINS - 1) cut = T;
+    else if (last >= 0) cut = T * exp2f((float)(last + 1 - GRNG_HBINS) / 16.0f);
+  }
+  tcut[s] = __float_as_uint(cut);
 }
 
 struct ListParams {
@@ -910,8 +947,7 @@ struct ListParams {
   const int2* pairs;
   int64_t m;
   const int8_t* side;
-  const int64_t* cnt;   // -1: list overflowed
-  const int64_t* loff;
+  const int* lcnt;      // listed nodes of each node (slots of GRNG_LCAP)
   const int32_t* lidx;
   const float* lkey;
   int2* links; unsigned long long* link_cnt; unsigned long long link_cap;
@@ -936,12 +972,12 @@ __global__ void __launch_bounds__(256) list_tier_kernel(ListParams p) {
       c_link += lane == 0;
       continue;
     }
-    const int s = sd ? pr.y : pr.x, o = sd ? pr.x : pr.y;
-    if (p.cnt[s] < 0) {
+    if (sd == 2) {
       if (lane == 0) push_pair(p.unres, p.unres_cnt, p.unres_cap, pr);
       c_un += lane == 0;
       continue;
     }
+    const int s = sd ? pr.y : pr.x, o = sd ? pr.x : pr.y;
     const float* xs = p.X + (int64_t)s * p.Dp;
     const float* xo = p.X + (int64_t)o * p.Dp;
     const float v = key32(xs, xo, p.Dp, p.metric);
@@ -953,7 +989,7 @@ __global__ void __launch_bounds__(256) list_tier_kernel(ListParams p) {
       continue;
     }
     const float ekey = excl_key(excl_dist(v, P.t2hi, p.metric, e), p.metric);
-    const int64_t j0 = p.loff[s], j1 = p.loff[s + 1];
+    const int64_t j0 = (int64_t)s * GRNG_LCAP, j1 = j0 + p.lcnt[s];
     bool blocked = false, anyamb = false;
     for (int64_t jb = j0; jb < j1 && !blocked; jb += 32) {
       const int64_t j = jb + lane;
@@ -1074,25 +1110,25 @@ static void launch_tile(const LevelIn& in, TileParams tp, int grid, cudaStream_t
 }
 
 template <int KC>
-static void launch_range_kc(const LevelIn& in, const unsigned int* tk, int64_t* cnt, const int64_t* off,
-                            unsigned long long* cur, int32_t* li, float* lk, int fill, cudaStream_t s) {
+static void launch_range_kc(const LevelIn& in, const unsigned int* tk, int* hist, int* lcnt, int32_t* li, float* lk,
+                            int fill, cudaStream_t s) {
   const int64_t nb = (in.n + GRNG_TILE - 1) / GRNG_TILE;
-  const size_t smem = (size_t)(2 * KC * GRNG_SSTRIDE + 128 * 129) * 4;
+  const size_t smem = (size_t)(2 * KC * GRNG_SSTRIDE + 128 * 129) * 4 + (size_t)GRNG_HBINS * 128 * 4;
   if (in.metric == L2) {
     GRNG_CUDA(cudaFuncSetAttribute(range_sweep_kernel<KC, L2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    range_sweep_kernel<KC, L2><<<(unsigned)nb, GRNG_THREADS, smem, s>>>(in.X, in.n, in.Dp, tk, cnt, off, cur, li, lk, fill); note_launch();
+    range_sweep_kernel<KC, L2><<<(unsigned)nb, GRNG_THREADS, smem, s>>>(in.X, in.n, in.Dp, tk, hist, lcnt, li, lk, fill); note_launch();
   } else {
     GRNG_CUDA(cudaFuncSetAttribute(range_sweep_kernel<KC, L1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    range_sweep_kernel<KC, L1><<<(unsigned)nb, GRNG_THREADS, smem, s>>>(in.X, in.n, in.Dp, tk, cnt, off, cur, li, lk, fill); note_launch();
+    range_sweep_kernel<KC, L1><<<(unsigned)nb, GRNG_THREADS, smem, s>>>(in.X, in.n, in.Dp, tk, hist, lcnt, li, lk, fill); note_launch();
   }
   GRNG_CUDA(cudaGetLastError());
 }
-static void launch_range(const LevelIn& in, const unsigned int* tk, int64_t* cnt, const int64_t* off,
-                         unsigned long long* cur, int32_t* li, float* lk, int fill, cudaStream_t s) {
+static void launch_range(const LevelIn& in, const unsigned int* tk, int* hist, int* lcnt, int32_t* li, float* lk,
+                         int fill, cudaStream_t s) {
   const int KC = in.Dp % 32 == 0 ? 32 : (in.Dp % 16 == 0 ? 16 : 8);
-  if (KC == 32) launch_range_kc<32>(in, tk, cnt, off, cur, li, lk, fill, s);
-  else if (KC == 16) launch_range_kc<16>(in, tk, cnt, off, cur, li, lk, fill, s);
-  else launch_range_kc<8>(in, tk, cnt, off, cur, li, lk, fill, s);
+  if (KC == 32) launch_range_kc<32>(in, tk, hist, lcnt, li, lk, fill, s);
+  else if (KC == 16) launch_range_kc<16>(in, tk, hist, lcnt, li, lk, fill, s);
+  else launch_range_kc<8>(in, tk, hist, lcnt, li, lk, fill, s);
 }
 
 static unsigned long long read_u64(const unsigned long long* d, cudaStream_t s) {
@@ -1232,7 +1268,7 @@ void run_level(const LevelIn& in, LevelOut& out, LevelStats& st, cudaStream_t s,
   tick(1);
   // ---- tiers 2 and 3 ---------------------------------------------------------------------
   DevBuf off, oth, tmp, links, unres, pend, amb, pflag, unres2, off2, oth2, fbuf;
-  DevBuf side, tkey, lcnt, lcnt2, loff, lidx, lkey, lcur, unres3, atab;
+  DevBuf side, tkey, tcut, hist, lcnt, lidx, lkey, unres3, atab;
   GRNG_CUDA(off.alloc((size_t)(n + 1) * 8));
   GRNG_CUDA(oth.alloc(std::max<size_t>(nsurv, 1) * 4));
   group_pairs(surv.as<int2>(), (int64_t)nsurv, 0, n, off.as<int64_t>(), oth.as<int32_t>(), tmp, s);
@@ -1283,36 +1319,33 @@ void run_level(const LevelIn& in, LevelOut& out, LevelStats& st, cudaStream_t s,
       // range lists for the pairs no neighbour list covers
       GRNG_CUDA(side.alloc(nun2));
       GRNG_CUDA(tkey.alloc((size_t)n * 4));
+      GRNG_CUDA(tcut.alloc((size_t)n * 4));
+      GRNG_CUDA(hist.alloc((size_t)n * GRNG_HBINS * 4));
+      GRNG_CUDA(lcnt.alloc((size_t)n * 4));
       GRNG_CUDA(cudaMemsetAsync(tkey.p, 0, (size_t)n * 4, s));
+      GRNG_CUDA(cudaMemsetAsync(lcnt.p, 0, (size_t)n * 4, s));
       SideParams sp;
       sp.X = in.X; sp.Dp = in.Dp; sp.metric = in.metric; sp.guide = in.grng; sp.K = in.K;
-      sp.rlo = in.rlo; sp.rhi = in.rhi; sp.knn_key = knnk.as<float>(); sp.pairs = unres2.as<int2>();
-      sp.m = (int64_t)nun2; sp.side = side.as<int8_t>(); sp.tkey = tkey.as<unsigned int>();
-      choose_side_kernel<<<(unsigned)((nun2 + 255) / 256), 256, 0, s>>>(sp); note_launch();
+      sp.rlo = in.rlo; sp.rhi = in.rhi; sp.pairs = unres2.as<int2>(); sp.m = (int64_t)nun2;
+      sp.side = side.as<int8_t>(); sp.tkey = tkey.as<unsigned int>(); sp.tcut = tcut.as<unsigned int>();
+      sp.lcnt = lcnt.as<int>();
+      range_thresholds_kernel<<<(unsigned)((nun2 + 255) / 256), 256, 0, s>>>(sp); note_launch();
       GRNG_CUDA(cudaGetLastError());
-      GRNG_CUDA(lcnt.alloc((size_t)n * 8));
-      GRNG_CUDA(lcnt2.alloc((size_t)n * 8));
-      GRNG_CUDA(loff.alloc((size_t)(n + 1) * 8));
-      launch_range(in, tkey.as<unsigned int>(), lcnt.as<int64_t>(), nullptr, nullptr, nullptr, nullptr, 0, s);
-      cap_lists_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(lcnt.as<int64_t>(), n,
-                                                                 in.lmax > 0 ? in.lmax : GRNG_LMAX, dc + 26); note_launch();
-      clamp_counts_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(lcnt.as<int64_t>(), n, lcnt2.as<int64_t>()); note_launch();
+      launch_range(in, tkey.as<unsigned int>(), hist.as<int>(), nullptr, nullptr, nullptr, 0, s);
+      range_cut_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(tkey.as<unsigned int>(), hist.as<int>(), n,
+                                                                  tcut.as<unsigned int>(),
+                                                                  in.lmax > 0 ? (int)in.lmax : GRNG_LMAX); note_launch();
       GRNG_CUDA(cudaGetLastError());
-      exclusive_scan_i64(lcnt2.as<int64_t>(), loff.as<int64_t>(), n, s);
-      int64_t ltot = 0;
-      GRNG_CUDA(cudaMemcpyAsync(&ltot, loff.as<int64_t>() + n, 8, cudaMemcpyDeviceToHost, s));
-      GRNG_CUDA(cudaStreamSynchronize(s));
-      GRNG_CUDA(lidx.alloc((size_t)std::max<int64_t>(ltot, 1) * 4));
-      GRNG_CUDA(lkey.alloc((size_t)std::max<int64_t>(ltot, 1) * 4));
-      GRNG_CUDA(lcur.alloc((size_t)n * 8));
-      GRNG_CUDA(cudaMemcpyAsync(lcur.p, loff.p, (size_t)n * 8, cudaMemcpyDeviceToDevice, s));
-      launch_range(in, tkey.as<unsigned int>(), lcnt.as<int64_t>(), loff.as<int64_t>(),
-                   lcur.as<unsigned long long>(), lidx.as<int32_t>(), lkey.as<float>(), 1, s);
+      GRNG_CUDA(lidx.alloc((size_t)n * GRNG_LCAP * 4));
+      GRNG_CUDA(lkey.alloc((size_t)n * GRNG_LCAP * 4));
+      launch_range(in, tcut.as<unsigned int>(), nullptr, lcnt.as<int>(), lidx.as<int32_t>(), lkey.as<float>(), 1, s);
+      pick_side_kernel<<<(unsigned)((nun2 + 255) / 256), 256, 0, s>>>(sp); note_launch();
+      GRNG_CUDA(cudaGetLastError());
       GRNG_CUDA(unres3.alloc(nun2 * 8));
       ListParams lp;
       lp.X = in.X; lp.Dp = in.Dp; lp.metric = in.metric; lp.guide = in.grng; lp.rlo = in.rlo; lp.rhi = in.rhi;
-      lp.pairs = unres2.as<int2>(); lp.m = (int64_t)nun2; lp.side = side.as<int8_t>(); lp.cnt = lcnt.as<int64_t>();
-      lp.loff = loff.as<int64_t>(); lp.lidx = lidx.as<int32_t>(); lp.lkey = lkey.as<float>();
+      lp.pairs = unres2.as<int2>(); lp.m = (int64_t)nun2; lp.side = side.as<int8_t>(); lp.lcnt = lcnt.as<int>();
+      lp.lidx = lidx.as<int32_t>(); lp.lkey = lkey.as<float>();
       lp.links = links.as<int2>(); lp.link_cnt = dc + 16; lp.link_cap = cap;
       lp.unres = unres3.as<int2>(); lp.unres_cnt = dc + 27; lp.unres_cap = nun2;
       lp.pend = pend.as<int2>(); lp.pend_cnt = dc + 17; lp.pend_cap = 2 * cap;
@@ -1320,12 +1353,22 @@ void run_level(const LevelIn& in, LevelOut& out, LevelStats& st, cudaStream_t s,
       lp.stats = dc + 28;
       list_tier_kernel<<<(unsigned)std::min<unsigned long long>((nun2 + 7) / 8, 64ull * num_sms()), 256, 0, s>>>(lp); note_launch();
       GRNG_CUDA(cudaGetLastError());
-      unsigned long long h8[8];  // over, to tier 3, links, pending, (to tier 3), blocked, tested
+      unsigned long long h8[8];  // -, to tier 3, links, pending, (to tier 3), blocked, tested
       GRNG_CUDA(cudaMemcpyAsync(h8, dc + 26, sizeof(h8), cudaMemcpyDeviceToHost, s));
+      std::vector<int> hl((size_t)n);
+      std::vector<unsigned int> htk((size_t)n), htc((size_t)n);
+      GRNG_CUDA(cudaMemcpyAsync(hl.data(), lcnt.p, (size_t)n * 4, cudaMemcpyDeviceToHost, s));
+      GRNG_CUDA(cudaMemcpyAsync(htk.data(), tkey.p, (size_t)n * 4, cudaMemcpyDeviceToHost, s));
+      GRNG_CUDA(cudaMemcpyAsync(htc.data(), tcut.p, (size_t)n * 4, cudaMemcpyDeviceToHost, s));
       GRNG_CUDA(cudaStreamSynchronize(s));
+      unsigned long long ltot = 0, lcut = 0;
+      for (size_t i = 0; i < hl.size(); ++i) {
+        ltot += (unsigned long long)std::min(hl[i], GRNG_LCAP);
+        lcut += htk[i] != 0 && (htc[i] < htk[i] || hl[i] > GRNG_LCAP);
+      }
       st.c[18] = nun2;    // pairs given range lists
-      st.c[19] = h8[0];   // lists over the cap
-      st.c[20] = (unsigned long long)ltot;  // listed nodes
+      st.c[19] = lcut;    // lists cut below their T_s or over the capacity
+      st.c[20] = ltot;    // listed nodes
       st.c[21] = h8[2];   // links from the lists
       st.c[22] = h8[6];   // listed nodes tested
       nun2 = h8[1];       // left for tier 3

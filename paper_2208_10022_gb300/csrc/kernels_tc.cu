@@ -159,8 +159,9 @@ __global__ void __launch_bounds__(128, 1) tc_sweep_kernel(TcParams p) {
     for (int i = tid; i < 128 * 128; i += 128) AX[(i >> 7) * 130 + (i & 127)] = p.A[bx * 16384 + i];
     for (int i = tid; i < 128 * GRNG_KIN; i += 128) {
       const bool ok = i / GRNG_KIN < nr;
-      nbrXi[i] = ok ? p.nbr_idx[xb * GRNG_KIN + i] : (uint8_t)255;
-      nbrXk[i] = ok ? p.nbr_key[xb * GRNG_KIN + i] : INF;
+      const int rr = i / GRNG_KIN, tt = i % GRNG_KIN;  // stored [t][row]: lanes = rows
+      nbrXi[tt * 128 + rr] = ok ? p.nbr_idx[xb * GRNG_KIN + i] : (uint8_t)255;
+      nbrXk[tt * 128 + rr] = ok ? p.nbr_key[xb * GRNG_KIN + i] : INF;
     }
     nx[tid] = tid < nr ? p.nrm[xb + tid] : 0.0f;
     parX[tid] = (p.parent && tid < nr) ? p.parent[xb + tid] : 0;
@@ -282,7 +283,7 @@ __global__ void __launch_bounds__(128, 1) tc_sweep_kernel(TcParams p) {
         for (int q = 0; q < 4; ++q) {
           float g[32];
           tmem_ld32(trow + (uint32_t)(q * 32), g);
-#pragma unroll 4
+#pragma unroll
           for (int j = 0; j < 32; ++j) {
             const int c = q * 32 + j;
             bool cand = vr && c < nc && (!diag || c > r);
@@ -314,10 +315,10 @@ __global__ void __launch_bounds__(128, 1) tc_sweep_kernel(TcParams p) {
                 }
               }
               for (int t = 0; t < GRNG_KIN && !blocked; ++t) {  // neighbours of x
-                const int z = nbrXi[r * GRNG_KIN + t];
+                const int z = nbrXi[t * 128 + r];
                 if (z == 255) break;
                 if (diag && z == c) continue;
-                blocked = hi_b(nbrXk[r * GRNG_KIN + t], e) < vlo &&
+                blocked = hi_b(nbrXk[t * 128 + r], e) < vlo &&
                           hi_b(__half2float(T16[z * 130 + c]) + E, e) < vlo;
               }
               for (int t = 0; t < GRNG_KIN && !blocked; ++t) {  // neighbours of y

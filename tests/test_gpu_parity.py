@@ -131,7 +131,7 @@ def test_small_knn_lists():
     # capped range lists: the hierarchical exhaustive tier takes the pivot pairs
     ix = check_full(w.X, w.layers, wl.L2, knn_k=1, flags=g.GRNG_FLAG_SHORT_LISTS)
     st = ix.stats()
-    assert st["layers"][2]["grng"]["range_lists_over_cap"] > 0 and st["layers"][2]["grng"]["tier3_pairs"] > 0
+    assert st["layers"][2]["grng"]["range_lists_cut"] > 0 and st["layers"][2]["grng"]["tier3_pairs"] > 0
     check_full(w.X, w.layers, wl.L1, knn_k=2, flags=g.GRNG_FLAG_SHORT_LISTS)
 
 
