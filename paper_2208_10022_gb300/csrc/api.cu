@@ -286,12 +286,13 @@ void level_json(std::string& js, const char* name, const LevelStats& st) {
                              "tier2b_unresolved", "tier2b_blocked", "tier3_pairs", "fp64_triples",
                              "fp64_blocking", "edges", "tier3_overflows", "tier3_nodes_tested",
                              "list_certified", "range_pairs", "range_lists_cut", "range_listed_nodes",
-                             "range_links", "range_nodes_tested"};
+                             "range_links", "range_nodes_tested", "tier3_blocked",
+                             "tier3_descent_blocked"};
   char buf[1024];
   js += "\"";
   js += name;
   js += "\":{";
-  for (int i = 0; i < 23; ++i) {
+  for (int i = 0; i < 25; ++i) {
     snprintf(buf, sizeof(buf), "%s\"%s\":%llu", i ? "," : "", nm[i], (unsigned long long)st.c[i]);
     js += buf;
   }

@@ -164,7 +164,7 @@ struct LevelOut {
   int64_t n_edges = 0;
 };
 struct LevelStats {
-  unsigned long long c[24];
+  unsigned long long c[32];
   double ms[8];  // prep, tile sweeps, tier-2 grouping + 2a, tier 2b, range lists, tier 3, recheck + emit
 };
 void run_level(const LevelIn& in, LevelOut& out, LevelStats& st, cudaStream_t s,

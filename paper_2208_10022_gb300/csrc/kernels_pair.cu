@@ -584,7 +584,8 @@ struct Tier3Params {
   const float* atab;      // [n][tabw] FP32 keys node x ancestor (columns anc.toff[a] + c), or null
   int64_t tabw;
   int fcap;
-  unsigned long long* stats;  // [0] frontier overflows, [1] nodes tested
+  int dense;              // ancestor levels scanned densely (needs atab, levels <= 65,536 nodes)
+  unsigned long long* stats;  // [0] frontier overflows, [1] nodes tested, [2] pairs blocked, [3] by the descent
 };
 
 // lower / upper bound of the distance whose FP32 key is k
@@ -597,38 +598,88 @@ __device__ __forceinline__ float dist_hi(float k, int metric, Err e) {
   return metric == L2 ? sqrtf(hi) * (1.0f + 1.1920928955078125e-07f) : hi;
 }
 
+// FP32 keys of node pk against g and o, summed by the 8 lanes of a group (lane l8 takes
+// the float4 columns l8, l8 + 8, ...): every lane of the group returns both sums.  The
+// summation order differs from key32's; the bracket err_fp32 bounds any order.
+__device__ __forceinline__ void group_keys(const float* __restrict__ pk, const float* gs, const float* os, int Dp,
+                                           int metric, int l8, unsigned gmask, float& a, float& b) {
+  const float4* x4 = reinterpret_cast<const float4*>(pk);
+  const float4* g4 = reinterpret_cast<const float4*>(gs);
+  const float4* o4 = reinterpret_cast<const float4*>(os);
+  float sa = 0.0f, sb = 0.0f;
+  for (int q = l8; q < (Dp >> 2); q += 8) {
+    const float4 x = __ldg(x4 + q), G = g4[q], O = o4[q];
+    if (metric == L2) {
+      float d;
+      d = x.x - G.x; sa = fmaf(d, d, sa); d = x.y - G.y; sa = fmaf(d, d, sa);
+      d = x.z - G.z; sa = fmaf(d, d, sa); d = x.w - G.w; sa = fmaf(d, d, sa);
+      d = x.x - O.x; sb = fmaf(d, d, sb); d = x.y - O.y; sb = fmaf(d, d, sb);
+      d = x.z - O.z; sb = fmaf(d, d, sb); d = x.w - O.w; sb = fmaf(d, d, sb);
+    } else {
+      sa += fabsf(x.x - G.x); sa += fabsf(x.y - G.y); sa += fabsf(x.z - G.z); sa += fabsf(x.w - G.w);
+      sb += fabsf(x.x - O.x); sb += fabsf(x.y - O.y); sb += fabsf(x.z - O.z); sb += fabsf(x.w - O.w);
+    }
+  }
+#pragma unroll
+  for (int sh = 4; sh > 0; sh >>= 1) {
+    sa += __shfl_xor_sync(gmask, sa, sh);
+    sb += __shfl_xor_sync(gmask, sb, sh);
+  }
+  a = sa;
+  b = sb;
+}
+
+#define T3_LIST 1024   // nodes gathered for one round of distance tests
+#define T3_MKW 2048    // words of a level's candidate bitmask (levels of at most 65,536 nodes)
+
 // Stage VI (Prop. 4 at the exemplar level, Prop. GRNG_S6 for pivot layers): a whole
 // domain of ancestor c is skipped when d(c,x) - rho_c >= t1 or d(c,y) - rho_c >= t2,
 // with rho_c bounding the distance from c to any node below it (its radius; delta_max
-// for the direct parent).  Descendants of a node are contiguous in the layer order, so
-// the frontier is a list of index ranges, refined layer by layer down to the nodes.
-__global__ void __launch_bounds__(256) tier3_kernel(Tier3Params p) {
+// for the direct parent).  Descendants of a node are contiguous in the layer order.
+// One CTA per pair.  Ancestor levels are scanned either densely (every node of the
+// level in order, the survivors of the level above marked in a shared-memory bitmask;
+// used when a node x ancestor key table exists and each level has at most 65,536
+// nodes), or as a list of index ranges flattened by a prefix sum.  The last ancestor
+// level hands the node level a list of ranges with its bounds; the surviving nodes are
+// gathered in shared memory and tested by groups of 8 lanes that read each node's
+// coordinates as whole 128-byte lines.  For L2, after the top level one greedy descent
+// towards the centre c* of the ball around the G-lune tests the nodes of a single
+// domain first: a blocker found there ends the pair early.
+__global__ void __launch_bounds__(256, 4) tier3_kernel(Tier3Params p) {
   extern __shared__ __align__(16) float sm3[];
   float* gs = sm3;
   float* os = gs + p.Dp;
-  __shared__ int s_block, s_cur_n, s_nxt_n;
+  __shared__ Front s_rg[256];
+  __shared__ int s_pre[257];
+  __shared__ int s_wsum[8];
+  __shared__ int s_list[T3_LIST];
+  __shared__ unsigned s_mk[2][T3_MKW];
+  __shared__ unsigned long long s_best;
+  __shared__ int s_block, s_nxt_n, s_nl;
   __shared__ float s_v;
   const Err e = err_fp32(p.Dp);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, tid = threadIdx.x;
+  const int gid = tid >> 3, l8 = tid & 7;
+  const unsigned gmask = 0xffu << (lane & 24);
   const float u2 = 1.1920928955078125e-07f;
   Front* bufA = p.fbuf + (int64_t)blockIdx.x * 2 * p.fcap;
   Front* bufB = bufA + p.fcap;
-  unsigned long long n_over = 0, n_tested = 0;
+  unsigned long long n_over = 0, n_tested = 0, n_blk = 0, n_probe = 0;
   for (int64_t t = blockIdx.x; t < p.m; t += gridDim.x) {
     const int2 pr = p.pairs[t];
     const int64_t g = pr.x, o = pr.y;
     __syncthreads();
-    for (int d = threadIdx.x; d < p.Dp; d += blockDim.x) {
+    for (int d = tid; d < p.Dp; d += blockDim.x) {
       gs[d] = p.X[g * p.Dp + d];
       os[d] = p.X[o * p.Dp + d];
     }
-    if (threadIdx.x == 0) {
+    if (tid == 0) {
       s_block = 0;
+      s_best = ~0ull;
       bufA[0] = Front{0, (int)(p.anc.n ? p.anc.m[0] : p.n), 0.0f, 0.0f, 0.0f, 0.0f};
-      s_cur_n = 1;
     }
     __syncthreads();
-    if (threadIdx.x == 0) s_v = key32(gs, os, p.Dp, p.metric);
+    if (tid == 0) s_v = key32(gs, os, p.Dp, p.metric);
     __syncthreads();
     const float v = s_v;
     PairThr P = pair_thresholds(v, p.rlo ? p.rlo[g] : 0.0f, p.rhi ? p.rhi[g] : 0.0f,
@@ -651,101 +702,304 @@ __global__ void __launch_bounds__(256) tier3_kernel(Tier3Params p) {
         const float m1 = (1.0f - lam) * P.t1hi + lam * P.t2hi;
         rho2 = m1 - lam * (1.0f - lam) * vlo + 8.0f * u2 * (m1 + lam * (1.0f - lam) * vhi);
       }
+      const float rho = rho2 >= 0.0f ? sqrtf(rho2) * (1.0f + u2) : 0.0f;
+
+      // test of one ancestor node c of level a from its keys; on survival, par = the
+      // range of its children with its bounds
+      auto test_node = [&](int a, int c, float kg, float kq, Front& par) -> bool {
+        const float dg = dist_lo(kg, p.metric, e);
+        const float dq = dist_lo(kq, p.metric, e);
+        const float R = p.anc.Rhi[a][c];
+        bool skip = (dg - R - u2 * (dg + R) >= t1d) || (dq - R - u2 * (dq + R) >= t2d);
+        if (!skip) {  // the whole domain lies within the exclusion ball of g or of o
+          const float dgh = dist_hi(kg, p.metric, e), dqh = dist_hi(kq, p.metric, e);
+          skip = (dgh + R + u2 * (dgh + R) <= Eg) || (dqh + R + u2 * (dqh + R) <= Eo);
+        }
+        float dcs = 0.0f;
+        if (!skip && rho2 >= 0.0f) {  // L2: the domain misses the ball around the G-lune
+          const float Alo = fmaxf(lo_b(kg, e), 0.0f), Blo = fmaxf(lo_b(kq, e), 0.0f);
+          const float Ahi = hi_b(kg, e), Bhi = hi_b(kq, e);
+          const float mm = (1.0f - lam) * Ahi + lam * Bhi + lam * (1.0f - lam) * vhi;
+          const float q = (1.0f - lam) * Alo + lam * Blo - lam * (1.0f - lam) * vhi - 8.0f * u2 * mm;
+          const float rr = sqrtf(rho2) + R;
+          skip = q > 0.0f && q >= rr * rr * (1.0f + 4.0f * u2);
+          dcs = q > 0.0f ? sqrtf(q) * (1.0f - u2) : 0.0f;
+        }
+        if (skip) return false;
+        const int32_t* cs = p.anc.cstart[a];
+        const int c0 = cs[c], c1 = cs[c + 1];
+        par = Front{c0, c1, dg, dq, dcs, 0.0f};
+        return c1 > c0;
+      };
+      // distance tests of nodes list[0..nl) (all threads; uniform call)
+      auto test_nodes = [&](const int* list, int nl) {
+        for (int i = gid; i < nl; i += 32) {
+          // one decision per group: its lanes must all reach the shuffles
+          if (__shfl_sync(gmask, *(volatile int*)&s_block, 0, 8)) break;
+          const int k = list[i];
+          float ka, kb;
+          group_keys(p.X + (int64_t)k * p.Dp, gs, os, p.Dp, p.metric, l8, gmask, ka, kb);
+          if (l8 == 0) {
+            ++n_tested;
+            const int stt = block_state(ka, kb, P, e);
+            if (stt == 2) s_block = 1;
+            else if (stt == 1) push_pair(p.amb, p.amb_cnt, p.amb_cap, make_int2((int)slot, k));
+          }
+        }
+      };
+
       Front* cur = bufA;
       Front* nxt = bufB;
-      for (int a = 0; a < p.anc.n; ++a) {
-        if (threadIdx.x == 0) s_nxt_n = 0;
-        __syncthreads();
-        const float* Xa = p.anc.X[a];
-        const float* Ra = p.anc.Rhi[a];
-        const int32_t* cs = p.anc.cstart[a];
-        const int ncur = s_cur_n;
-        for (int r = warp; r < ncur; r += nwarps) {
-          const Front rg = cur[r];
-          for (int c = rg.s + lane; c < rg.e; c += 32) {
-            float kg, kq;
-            if (p.atab) {
-              kg = p.atab[g * p.tabw + p.anc.toff[a] + c];
-              kq = p.atab[o * p.tabw + p.anc.toff[a] + c];
-            } else {
-              const float* pc = Xa + (int64_t)c * p.Dp;
-              kg = key32(pc, gs, p.Dp, p.metric);
-              kq = key32(pc, os, p.Dp, p.metric);
+      int ncur = 1;
+      bool all = false;
+      int a_leaf = 0;  // first level handled by the range loop below
+      if (p.dense) {
+        // ---- dense ancestor levels ------------------------------------------------------
+        const bool probe = rho2 >= 0.0f;
+        for (int a = 0; a < p.anc.n; ++a) {
+          const bool last = a == p.anc.n - 1;
+          const int ma = (int)p.anc.m[a];
+          const unsigned* mk_in = s_mk[a & 1];
+          unsigned* mk_out = s_mk[(a + 1) & 1];
+          __syncthreads();
+          if (!last)
+            for (int w = tid; w < (int)((p.anc.m[a + 1] + 31) >> 5); w += blockDim.x) mk_out[w] = 0u;
+          if (tid == 0) s_nxt_n = 0;
+          __syncthreads();
+          const float* rg_ = p.atab + g * p.tabw + p.anc.toff[a];
+          const float* ro_ = p.atab + o * p.tabw + p.anc.toff[a];
+          unsigned long long best = ~0ull;
+          for (int c0 = 0; c0 < ma; c0 += 4 * 256) {
+            const int c = c0 + 4 * tid;
+            unsigned vm = 0;  // candidate nodes among c .. c+3
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+              if (c + u < ma && (a == 0 || ((mk_in[(c + u) >> 5] >> ((c + u) & 31)) & 1u))) vm |= 1u << u;
+            float kgv[4], kqv[4];
+            if (vm) {
+              const float4 G4 = __ldg(reinterpret_cast<const float4*>(rg_ + c));
+              const float4 O4 = __ldg(reinterpret_cast<const float4*>(ro_ + c));
+              kgv[0] = G4.x; kgv[1] = G4.y; kgv[2] = G4.z; kgv[3] = G4.w;
+              kqv[0] = O4.x; kqv[1] = O4.y; kqv[2] = O4.z; kqv[3] = O4.w;
             }
-            const float dg = dist_lo(kg, p.metric, e);
-            const float dq = dist_lo(kq, p.metric, e);
-            const float R = Ra[c];
-            bool skip = (dg - R - u2 * (dg + R) >= t1d) || (dq - R - u2 * (dq + R) >= t2d);
-            if (!skip) {  // the whole domain lies within the exclusion ball of g or of o
-              const float dgh = dist_hi(kg, p.metric, e), dqh = dist_hi(kq, p.metric, e);
-              skip = (dgh + R + u2 * (dgh + R) <= Eg) || (dqh + R + u2 * (dqh + R) <= Eo);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              Front par;
+              const bool keep = ((vm >> u) & 1u) && test_node(a, c + u, kgv[u], kqv[u], par);
+              if (keep && a == 0 && probe) {  // Stewart estimate of |c - c*|^2
+                const float s2 = fmaxf((1.0f - lam) * kgv[u] + lam * kqv[u] - lam * (1.0f - lam) * v, 0.0f);
+                const unsigned long long key = ((unsigned long long)__float_as_uint(s2) << 32) | (unsigned)(c + u);
+                best = key < best ? key : best;
+              }
+              if (!last) {
+                if (keep)
+                  for (int w = par.s >> 5; w <= (par.e - 1) >> 5; ++w) {
+                    const int lo = max(par.s, w << 5), hi = min(par.e, (w << 5) + 32);
+                    const unsigned msk = (hi - lo == 32) ? ~0u : (((1u << (hi - lo)) - 1u) << (lo & 31));
+                    atomicOr(mk_out + w, msk);
+                  }
+              } else {
+                const unsigned bm = __ballot_sync(FULLMASK, keep);
+                int base = 0;
+                if (lane == 0 && bm) base = atomicAdd(&s_nxt_n, __popc(bm));
+                base = __shfl_sync(FULLMASK, base, 0);
+                const int pos = base + __popc(bm & ((1u << lane) - 1u));
+                if (keep && pos < p.fcap) nxt[pos] = par;
+              }
             }
-            float dcs = 0.0f;
-            if (!skip && rho2 >= 0.0f) {  // L2: the domain misses the ball around the G-lune
-              const float Alo = fmaxf(lo_b(kg, e), 0.0f), Blo = fmaxf(lo_b(kq, e), 0.0f);
-              const float Ahi = hi_b(kg, e), Bhi = hi_b(kq, e);
-              const float mm = (1.0f - lam) * Ahi + lam * Bhi + lam * (1.0f - lam) * vhi;
-              const float q = (1.0f - lam) * Alo + lam * Blo - lam * (1.0f - lam) * vhi - 8.0f * u2 * mm;
-              const float rr = sqrtf(rho2) + R;
-              skip = q > 0.0f && q >= rr * rr * (1.0f + 4.0f * u2);
-              dcs = q > 0.0f ? sqrtf(q) * (1.0f - u2) : 0.0f;
+          }
+          if (a == 0 && probe) {
+            for (int sh = 16; sh > 0; sh >>= 1) {
+              const unsigned long long y = __shfl_xor_sync(FULLMASK, best, sh);
+              best = y < best ? y : best;
             }
-            if (!skip) {
-              int idx = atomicAdd(&s_nxt_n, 1);
-              if (idx < p.fcap) nxt[idx] = Front{cs[c], cs[c + 1], dg, dq, dcs, 0.0f};
+            if (lane == 0 && best != ~0ull) atomicMin(&s_best, best);
+          }
+          __syncthreads();
+          if (a == 0 && probe && s_best != ~0ull) {
+            // ---- greedy descent to the domain nearest c*, whose nodes are tested now ----
+            if (warp == 0) {
+              int cn = (int)(s_best & 0xffffffffu);
+              int lvl = 0;
+              bool ok = true;
+              while (lvl < p.anc.n - 1) {
+                const int c0 = p.anc.cstart[lvl][cn], c1 = p.anc.cstart[lvl][cn + 1];
+                if (c1 <= c0) { ok = false; break; }
+                ++lvl;
+                unsigned long long bb = ~0ull;
+                for (int c = c0 + lane; c < c1; c += 32) {
+                  const float kg = p.atab[g * p.tabw + p.anc.toff[lvl] + c];
+                  const float kq = p.atab[o * p.tabw + p.anc.toff[lvl] + c];
+                  const float s2 = fmaxf((1.0f - lam) * kg + lam * kq - lam * (1.0f - lam) * v, 0.0f);
+                  const unsigned long long key = ((unsigned long long)__float_as_uint(s2) << 32) | (unsigned)c;
+                  bb = key < bb ? key : bb;
+                }
+                for (int sh = 16; sh > 0; sh >>= 1) {
+                  const unsigned long long y = __shfl_xor_sync(FULLMASK, bb, sh);
+                  bb = y < bb ? y : bb;
+                }
+                cn = (int)(bb & 0xffffffffu);
+              }
+              if (ok) {
+                const int k0 = p.anc.cstart[lvl][cn], k1 = p.anc.cstart[lvl][cn + 1];
+                for (int k = k0 + (lane >> 3); k < k1; k += 4) {
+                  if (k == g || k == o) continue;  // uniform within the group
+                  float ka, kb;
+                  group_keys(p.X + (int64_t)k * p.Dp, gs, os, p.Dp, p.metric, l8, gmask, ka, kb);
+                  if (l8 == 0) {
+                    ++n_tested;
+                    const int stt = block_state(ka, kb, P, e);
+                    if (stt == 2) s_block = 1;
+                    else if (stt == 1) push_pair(p.amb, p.amb_cnt, p.amb_cap, make_int2((int)slot, k));
+                  }
+                }
+              }
+            }
+            __syncthreads();
+            if (s_block) {  // uniform: read after a barrier
+              n_probe += tid == 0;
+              break;
             }
           }
         }
-        __syncthreads();
-        if (s_nxt_n > p.fcap) {  // frontier too large: scan every node (still exact)
-          __syncthreads();
-          if (threadIdx.x == 0) {
-            bufA[0] = Front{0, (int)p.n, 0.0f, 0.0f, 0.0f, 0.0f};
-            s_cur_n = 1;
+        a_leaf = p.anc.n;
+        if (!s_block) {
+          if (s_nxt_n > p.fcap) {
+            all = true;
+            n_over += tid == 0;
+          } else {
+            ncur = s_nxt_n;
+            Front* tmp = cur; cur = nxt; nxt = tmp;
           }
-          cur = bufA;
-          n_over += threadIdx.x == 0;
-          __syncthreads();
-          break;
         }
-        Front* tmp = cur; cur = nxt; nxt = tmp;
-        __syncthreads();
-        if (threadIdx.x == 0) s_cur_n = s_nxt_n;
-        __syncthreads();
       }
-      const int ncur = s_cur_n;
-      const float rho = rho2 >= 0.0f ? sqrtf(rho2) * (1.0f + u2) : 0.0f;
-      for (int r = warp; r < ncur; r += nwarps) {
-        const Front rg = cur[r];
-        for (int k = rg.s + lane; k < rg.e; k += 32) {
-          if (*(volatile int*)&s_block) break;
-          if (k == g || k == o) continue;
-          if (p.pdist_hi && (rg.dg > 0.0f || rg.dq > 0.0f || rg.dcs > 0.0f)) {
-            // Prop. 5 / GRNG_S6 (assisted): |k - g| >= d(c,g) - d(k,c), and so on
-            const float mk = p.pdist_hi[k];
-            const float sl = u2 * (rg.dg + rg.dq + rg.dcs + mk);
-            if (rg.dg - mk - sl >= t1d || rg.dq - mk - sl >= t2d || (rho2 >= 0.0f && rg.dcs - mk - sl >= rho))
-              continue;
+      // ---- range levels (a >= a_leaf); level a = anc.n is the layer's own nodes ----------
+      for (int a = a_leaf; a <= p.anc.n && !all && !s_block; ++a) {
+        const bool leaf = a == p.anc.n;
+        __syncthreads();  // every thread has read the previous level's count
+        if (tid == 0) { s_nxt_n = 0; s_nl = 0; }
+        for (int cb = 0; cb < ncur; cb += 256) {
+          // ---- flatten 256 ranges: s_pre = exclusive prefix of their lengths ----
+          __syncthreads();
+          int len = 0;
+          if (cb + tid < ncur) {
+            const Front f = cur[cb + tid];
+            s_rg[tid] = f;
+            len = f.e - f.s;
           }
-          const float* pk = p.X + (int64_t)k * p.Dp;
-          float a = key32(pk, gs, p.Dp, p.metric);
-          float b = key32(pk, os, p.Dp, p.metric);
-          ++n_tested;
-          int stt = block_state(a, b, P, e);
-          if (stt == 2) s_block = 1;
-          else if (stt == 1) push_pair(p.amb, p.amb_cnt, p.amb_cap, make_int2((int)slot, k));
+          int inc = len;
+#pragma unroll
+          for (int sh = 1; sh < 32; sh <<= 1) {
+            const int y = __shfl_up_sync(FULLMASK, inc, sh);
+            if (lane >= sh) inc += y;
+          }
+          if (lane == 31) s_wsum[warp] = inc;
+          __syncthreads();
+          int woff = 0;
+          for (int w = 0; w < warp; ++w) woff += s_wsum[w];
+          s_pre[tid + 1] = woff + inc;
+          if (tid == 0) s_pre[0] = 0;
+          __syncthreads();
+          const int total = s_pre[256];
+          const int nrg = ncur - cb < 256 ? ncur - cb : 256;
+          for (int j0 = 0; j0 < total; j0 += 256) {
+            const int j = j0 + tid;
+            bool keep = false;
+            int c = -1;
+            Front par;
+            if (j < total) {
+              int lo = 0, hi = nrg - 1;  // the last range q with s_pre[q] <= j
+              while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (s_pre[mid] <= j) lo = mid; else hi = mid - 1;
+              }
+              par = s_rg[lo];
+              c = par.s + (j - s_pre[lo]);
+              if (leaf) {
+                keep = c != g && c != o;
+                if (keep && p.pdist_hi && (par.dg > 0.0f || par.dq > 0.0f || par.dcs > 0.0f)) {
+                  // Prop. 5 / GRNG_S6 (assisted): |c - g| >= d(parent,g) - d(c,parent), ...
+                  const float mk = p.pdist_hi[c];
+                  const float sl = u2 * (par.dg + par.dq + par.dcs + mk);
+                  keep = !(par.dg - mk - sl >= t1d || par.dq - mk - sl >= t2d ||
+                           (rho2 >= 0.0f && par.dcs - mk - sl >= rho));
+                }
+              } else {
+                float kg, kq;
+                if (p.atab) {
+                  kg = p.atab[g * p.tabw + p.anc.toff[a] + c];
+                  kq = p.atab[o * p.tabw + p.anc.toff[a] + c];
+                } else {
+                  const float* pc = p.anc.X[a] + (int64_t)c * p.Dp;
+                  kg = key32(pc, gs, p.Dp, p.metric);
+                  kq = key32(pc, os, p.Dp, p.metric);
+                }
+                keep = test_node(a, c, kg, kq, par);
+              }
+            }
+            const unsigned bm = __ballot_sync(FULLMASK, keep);
+            if (leaf) {
+              int base = 0;
+              if (lane == 0 && bm) base = atomicAdd(&s_nl, __popc(bm));
+              base = __shfl_sync(FULLMASK, base, 0);
+              if (keep) s_list[base + __popc(bm & ((1u << lane) - 1u))] = c;
+              __syncthreads();
+              const int nl = s_nl;
+              // ---- distance tests once the list is nearly full, or at the end ----
+              if (nl > T3_LIST - 256 || (nl > 0 && j0 + 256 >= total && cb + 256 >= ncur)) {
+                test_nodes(s_list, nl);
+                __syncthreads();
+                if (tid == 0) s_nl = 0;
+              }
+              __syncthreads();
+              if (s_block) break;
+            } else {
+              int base = 0;
+              if (lane == 0 && bm) base = atomicAdd(&s_nxt_n, __popc(bm));
+              base = __shfl_sync(FULLMASK, base, 0);
+              const int pos = base + __popc(bm & ((1u << lane) - 1u));
+              if (keep && pos < p.fcap) nxt[pos] = par;
+            }
+          }
+          if (leaf && s_block) break;  // s_block was read after a barrier: uniform
+        }
+        if (leaf) break;
+        __syncthreads();
+        if (s_nxt_n > p.fcap) {
+          all = true;
+          n_over += tid == 0;
+        } else {
+          ncur = s_nxt_n;
+          Front* tmp = cur; cur = nxt; nxt = tmp;
+        }
+      }
+      if (all) {  // frontier too large: test every node (still exact)
+        for (int i = gid; i < (int)p.n; i += 32) {
+          if (__shfl_sync(gmask, *(volatile int*)&s_block, 0, 8)) break;
+          if (i == g || i == o) continue;
+          float ka, kb;
+          group_keys(p.X + (int64_t)i * p.Dp, gs, os, p.Dp, p.metric, l8, gmask, ka, kb);
+          if (l8 == 0) {
+            ++n_tested;
+            const int stt = block_state(ka, kb, P, e);
+            if (stt == 2) s_block = 1;
+            else if (stt == 1) push_pair(p.amb, p.amb_cnt, p.amb_cap, make_int2((int)slot, i));
+          }
         }
       }
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (tid == 0) {
       p.pend[slot] = make_int2((int)g, (int)o);
       p.pflag[slot] = s_block ? 3 : 0;
+      n_blk += s_block != 0;
     }
   }
   for (int sh = 16; sh > 0; sh >>= 1) n_tested += __shfl_down_sync(FULLMASK, n_tested, sh);
-  if (lane == 0) atomicAdd(p.stats + 1, n_tested);
-  if (threadIdx.x == 0 && n_over) atomicAdd(p.stats + 0, n_over);
+  if (lane == 0 && n_tested) atomicAdd(p.stats + 1, n_tested);
+  if (tid == 0 && n_over) atomicAdd(p.stats + 0, n_over);
+  if (tid == 0 && n_blk) atomicAdd(p.stats + 2, n_blk);
+  if (tid == 0 && n_probe) atomicAdd(p.stats + 3, n_probe);
 }
 
 // node x ancestor keys: out[r * ld + c] = key(Xr[r], Xc[c]) for a 128 x 128 tile per CTA
@@ -1176,7 +1430,8 @@ void run_level(const LevelIn& in, LevelOut& out, LevelStats& st, cudaStream_t s,
   GRNG_CUDA(ctr.alloc(64 * sizeof(unsigned long long)));
   unsigned long long* dc = ctr.as<unsigned long long>();
   // counters: 0 strip, 1 surv, 2..5 tile stats, 8.. tier2a, 12.. tier2b, 16 links, 17 pend,
-  // 18 unres, 19 amb, 20 unres2, 21 edges, 22 recheck blocked
+  // 18 unres, 19 amb, 20 unres2, 21 edges, 22 recheck blocked, 26..33 range lists,
+  // 34..37 tier 3, 40 tensor-core status
   if (KC == 32) launch_prep<32>(in, A.as<__half>(), nbi.as<uint8_t>(), nbk.as<float>(), s);
   else if (KC == 16) launch_prep<16>(in, A.as<__half>(), nbi.as<uint8_t>(), nbk.as<float>(), s);
   else launch_prep<8>(in, A.as<__half>(), nbi.as<uint8_t>(), nbk.as<float>(), s);
@@ -1388,25 +1643,28 @@ void run_level(const LevelIn& in, LevelOut& out, LevelStats& st, cudaStream_t s,
       t3.pend = pend.as<int2>(); t3.pflag = pflag.as<int>(); t3.slot0 = (int64_t)npend;
       t3.amb = amb.as<int2>(); t3.amb_cnt = dc + 19; t3.amb_cap = amb_cap;
       t3.anc = in.anc;
-      int grid3 = (int)std::min<unsigned long long>(nun2, 8ull * num_sms());
+      int grid3 = (int)std::min<unsigned long long>(nun2, 4ull * num_sms());
       t3.fcap = 1 << 15;
       GRNG_CUDA(fbuf.alloc((size_t)grid3 * 2 * t3.fcap * sizeof(Front)));
       t3.fbuf = fbuf.as<Front>();
       t3.pdist_hi = in.pdist_hi;
       t3.atab = nullptr;
       t3.tabw = 0;
+      t3.dense = 0;
       if (in.grng && in.anc.n > 0) {
         // pivot layers: node x ancestor keys once, instead of per pair
-        int64_t w = 0;
-        for (int a = 0; a < in.anc.n; ++a) { t3.anc.toff[a] = w; w += in.anc.m[a]; }
+        int64_t w = 0;  // each level's columns start on a 16-byte boundary
+        for (int a = 0; a < in.anc.n; ++a) { t3.anc.toff[a] = w; w += (in.anc.m[a] + 3) & ~(int64_t)3; }
         GRNG_CUDA(atab.alloc((size_t)n * w * 4));
         for (int a = 0; a < in.anc.n; ++a)
           launch_cross(in.X, n, in.anc.X[a], in.anc.m[a], in.Dp, in.metric, atab.as<float>() + t3.anc.toff[a], w, s);
         t3.atab = atab.as<float>();
         t3.tabw = w;
+        t3.dense = 1;
+        for (int a = 1; a < in.anc.n; ++a) t3.dense &= in.anc.m[a] <= 32 * T3_MKW;
       }
-      t3.stats = dc + 24;
-      GRNG_CUDA(cudaMemsetAsync(dc + 24, 0, 2 * sizeof(unsigned long long), s));
+      t3.stats = dc + 34;
+      GRNG_CUDA(cudaMemsetAsync(dc + 34, 0, 4 * sizeof(unsigned long long), s));
       tier3_kernel<<<grid3, 256, 2 * in.Dp * 4, s>>>(t3); note_launch();
       GRNG_CUDA(cudaGetLastError());
     }
@@ -1438,11 +1696,13 @@ void run_level(const LevelIn& in, LevelOut& out, LevelStats& st, cudaStream_t s,
           pend.as<int2>(), pflag.as<int>(), (int64_t)npp, in.grng, out.gx, out.gg, out.words,
           in.orig, dc + 21, ecap, in.grng ? nullptr : out.edges->as<uint64_t>()); note_launch();
     GRNG_CUDA(cudaGetLastError());
-    unsigned long long h[26];
+    unsigned long long h[40];
     GRNG_CUDA(cudaMemcpyAsync(h, dc, sizeof(h), cudaMemcpyDeviceToHost, s));
-    st.c[15] = nun2 ? h[24] : 0;  // tier-3 frontier overflows
-    st.c[16] = nun2 ? h[25] : 0;  // tier-3 nodes tested
     GRNG_CUDA(cudaStreamSynchronize(s));
+    st.c[15] = nun2 ? h[34] : 0;  // tier-3 frontier overflows
+    st.c[16] = nun2 ? h[35] : 0;  // tier-3 nodes tested
+    st.c[23] = nun2 ? h[36] : 0;  // tier-3 pairs blocked
+    st.c[24] = nun2 ? h[37] : 0;  // of which by the greedy descent
     out.n_edges = (int64_t)h[21];
     st.c[3] = h[8];  st.c[4] = h[9];  st.c[5] = h[10]; st.c[6] = h[11];   // tier 2a
     st.c[7] = h[12]; st.c[8] = h[13]; st.c[9] = h[14]; st.c[10] = h[15];  // tier 2b
