@@ -79,11 +79,55 @@ struct TcParams {
 static __host__ __device__ constexpr size_t tc_img_bytes(int Dp) { return (size_t)128 * Dp * 4; }  // hi + lo
 static __host__ __device__ constexpr size_t tc_t16_bytes() { return (size_t)128 * 130 * 2; }
 static __host__ __device__ constexpr size_t tc_smem_bytes(int Dp, int K) {
-  return 2 * tc_img_bytes(Dp) + (tc_img_bytes(Dp) >= tc_t16_bytes() ? 0 : tc_t16_bytes()) + 33280 + 32768 +
-         (size_t)128 * (K + 1) * 8 + 128 * GRNG_KIN * 10 + 8 * 512 + 128;
+  return (void)K, 2 * tc_img_bytes(Dp) + (tc_img_bytes(Dp) >= tc_t16_bytes() ? 0 : tc_t16_bytes()) + 33280 + 34816 +
+                      128 * GRNG_KIN * 10 + 8 * 512 + 2 * 4096 + 128;
 }
 
-__global__ void __launch_bounds__(128, 1) tc_sweep_kernel(TcParams p) {
+// Insert (v, id) into the ascending register list kk/ki (32 slots, the first K in use)
+// and return the new K-th key.  Fully unrolled so that the list stays in registers.
+__device__ __forceinline__ float knn_insert_reg(float (&kk)[GRNG_KMAX], int (&ki)[GRNG_KMAX], float v, int id,
+                                                int K) {
+#pragma unroll
+  for (int i = GRNG_KMAX - 1; i > 0; --i) {
+    if (kk[i - 1] > v) {
+      kk[i] = kk[i - 1];
+      ki[i] = ki[i - 1];
+    } else if (kk[i] > v) {
+      kk[i] = v;
+      ki[i] = id;
+    }
+  }
+  if (kk[0] > v) {
+    kk[0] = v;
+    ki[0] = id;
+  }
+  float t = kk[0];
+#pragma unroll
+  for (int i = 1; i < GRNG_KMAX; ++i)
+    if (i == K - 1) t = kk[i];
+  return t;
+}
+
+// top-2 of (m1, a1), (m2, a2) merged with (b1, i1), (b2, i2)
+__device__ __forceinline__ void top2_merge(float& m1, int& a1, float& m2, int& a2, float b1, int i1, float b2,
+                                           int i2) {
+  if (b1 < m1) {
+    if (b2 < m1) { m2 = b2; a2 = i2; }
+    else { m2 = m1; a2 = a1; }
+    m1 = b1; a1 = i1;
+  } else if (b1 < m2) {
+    m2 = b1; a2 = i1;
+  }
+}
+
+// One CTA of 256 threads per SM, persistent over row strips.  Per 128 x 128 tile: one
+// thread issues the 3*Dp/16 MMAs into TMEM; then warp w reads the TMEM lanes of rows
+// 32*(w%4).. and the 64 columns of half w/4.  Pass 1: keys to a rounded-up FP16 copy,
+// row minima and the K-nearest lists (registers, one per half, merged at the end of
+// the strip).  Upper tiles (y block >= x block) also run the tier-1 filter: column
+// minima over the FP16 copy, then pass 2 over TMEM again.  The y block's in-block key
+// matrix arrives by a bulk copy while pass 1 runs.
+__global__ void __launch_bounds__(256, 1) tc_sweep_kernel(TcParams p) {
   extern __shared__ __align__(1024) unsigned char sm[];
   const int Dp = p.Dp, K = p.K;
   const uint32_t IMG = (uint32_t)tc_img_bytes(Dp);
@@ -98,11 +142,9 @@ __global__ void __launch_bounds__(128, 1) tc_sweep_kernel(TcParams p) {
     o += tc_t16_bytes();
   }
   __half* AX = reinterpret_cast<__half*>(sm + o); o += 33280;   // [128][130]
-  __half* AY = reinterpret_cast<__half*>(sm + o); o += 32768;   // [128][128]
-  float* knnK = reinterpret_cast<float*>(sm + o); o += (size_t)128 * (K + 1) * 4;
-  int* knnI = reinterpret_cast<int*>(sm + o); o += (size_t)128 * (K + 1) * 4;
-  float* nbrXk = reinterpret_cast<float*>(sm + o); o += 128 * GRNG_KIN * 4;
-  float* nbrYk = reinterpret_cast<float*>(sm + o); o += 128 * GRNG_KIN * 4;
+  __half* AY = reinterpret_cast<__half*>(sm + o); o += 34816;   // [128][136]: rows 16-byte aligned
+  float* nbrXk = reinterpret_cast<float*>(sm + o); o += 128 * GRNG_KIN * 4;  // [t][row]
+  float* nbrYk = reinterpret_cast<float*>(sm + o); o += 128 * GRNG_KIN * 4;  // [row][t]
   uint8_t* nbrXi = sm + o; o += 128 * GRNG_KIN;
   uint8_t* nbrYi = sm + o; o += 128 * GRNG_KIN;
   float* nx = reinterpret_cast<float*>(sm + o); o += 512;
@@ -113,12 +155,17 @@ __global__ void __launch_bounds__(128, 1) tc_sweep_kernel(TcParams p) {
   int* carg2 = reinterpret_cast<int*>(sm + o); o += 512;
   int* parX = reinterpret_cast<int*>(sm + o); o += 512;
   int* parY = reinterpret_cast<int*>(sm + o); o += 512;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(sm + o);           // A image, B image, MMA done
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + o + 24);
-  int* s_strip = reinterpret_cast<int*>(sm + o + 28);
-  int* s_abort = reinterpret_cast<int*>(sm + o + 32);
+  float4* colx = reinterpret_cast<float4*>(sm + o); o += 4096;  // [2][128] partial column top-2
+  float4* rowx = reinterpret_cast<float4*>(sm + o); o += 4096;  // [2][128] partial row top-2
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sm + o);           // A image, B image, MMA done, AY
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + o + 32);
+  int* s_strip = reinterpret_cast<int*>(sm + o + 36);
+  int* s_abort = reinterpret_cast<int*>(sm + o + 40);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int lq = warp & 3, h = warp >> 2;
+  const int r = lq * 32 + lane;  // this thread's row (its TMEM lane)
+  const int cb = h * 64;         // first column of this thread's half
   const int64_t n = p.n;
   const int64_t nb = (n + 127) / 128;
   const Err e = err_fp32(Dp);
@@ -130,9 +177,7 @@ __global__ void __launch_bounds__(128, 1) tc_sweep_kernel(TcParams p) {
     tmem_relinquish();
   }
   if (tid == 0) {
-    mbar_init(&bars[0], 1);
-    mbar_init(&bars[1], 1);
-    mbar_init(&bars[2], 1);
+    for (int i = 0; i < 4; ++i) mbar_init(&bars[i], 1);
     *s_abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -140,8 +185,8 @@ __global__ void __launch_bounds__(128, 1) tc_sweep_kernel(TcParams p) {
   __syncthreads();
   tc_fence_after();
   const uint32_t tbase = *tslot;
-  const uint32_t trow = tbase + ((uint32_t)(warp * 32) << 16);  // this warp's 32 lanes
-  uint32_t phA = 0, phB = 0, phM = 0;
+  const uint32_t trow = tbase + ((uint32_t)(lq * 32) << 16) + (uint32_t)cb;
+  uint32_t phA = 0, phB = 0, phM = 0, phY = 0;
 
   for (;;) {
     __syncthreads();
@@ -156,25 +201,33 @@ __global__ void __launch_bounds__(128, 1) tc_sweep_kernel(TcParams p) {
       mbar_expect_tx(&bars[0], IMG);
       bulk_g2s(sA, p.img + (size_t)bx * IMG, IMG, &bars[0]);
     }
-    for (int i = tid; i < 128 * 128; i += 128) AX[(i >> 7) * 130 + (i & 127)] = p.A[bx * 16384 + i];
-    for (int i = tid; i < 128 * GRNG_KIN; i += 128) {
-      const bool ok = i / GRNG_KIN < nr;
+    {
+      const uint32_t* srcA = reinterpret_cast<const uint32_t*>(p.A + bx * 16384);
+      for (int w = tid; w < 8192; w += 256)
+        *reinterpret_cast<uint32_t*>(AX + (w >> 6) * 130 + (w & 63) * 2) = srcA[w];
+    }
+    for (int i = tid; i < 128 * GRNG_KIN; i += 256) {
       const int rr = i / GRNG_KIN, tt = i % GRNG_KIN;  // stored [t][row]: lanes = rows
+      const bool ok = rr < nr;
       nbrXi[tt * 128 + rr] = ok ? p.nbr_idx[xb * GRNG_KIN + i] : (uint8_t)255;
       nbrXk[tt * 128 + rr] = ok ? p.nbr_key[xb * GRNG_KIN + i] : INF;
     }
-    nx[tid] = tid < nr ? p.nrm[xb + tid] : 0.0f;
-    parX[tid] = (p.parent && tid < nr) ? p.parent[xb + tid] : 0;
-    for (int j = 0; j <= K; ++j) {
-      knnK[tid * (K + 1) + j] = INF;
-      knnI[tid * (K + 1) + j] = -1;
+    if (tid < 128) {
+      nx[tid] = tid < nr ? p.nrm[xb + tid] : 0.0f;
+      parX[tid] = (p.parent && tid < nr) ? p.parent[xb + tid] : 0;
     }
+    float kk[GRNG_KMAX];
+    int ki[GRNG_KMAX];
+#pragma unroll
+    for (int j = 0; j < GRNG_KMAX; ++j) { kk[j] = INF; ki[j] = -1; }
+    float thr = INF;
     if (tid == 0 && !mbar_wait(&bars[0], phA, p.spin)) {
       *s_abort = 1;
       atomicOr(p.status, 1);
     }
     phA ^= 1;
     const float bmx = __uint_as_float(p.bmax[bx]);
+    const bool vr = r < nr;
     int done = 0;
     for (int s = 0; done < nb; ++s) {
       const int64_t off = (s & 1) ? (int64_t)((s + 1) >> 1) : -(int64_t)(s >> 1);
@@ -185,27 +238,33 @@ __global__ void __launch_bounds__(128, 1) tc_sweep_kernel(TcParams p) {
       const int nc = (int)(n - yb < 128 ? n - yb : 128);
       const bool filt = by >= bx;
       const bool diag = by == bx;
-      // the previous tile's generic accesses to T16 (which may alias sB) are ordered
-      // before the bulk copy that overwrites it: each thread fences, then all meet
+      // the previous tile's generic accesses to T16 (which may alias sB) and AY are
+      // ordered before the bulk copies that overwrite them: each thread fences, then all meet
       fence_proxy_async();
       __syncthreads();
       if (*s_abort) break;
       if (tid == 0) {
         mbar_expect_tx(&bars[1], IMG);
         bulk_g2s(sB, p.img + (size_t)by * IMG, IMG, &bars[1]);
+        if (filt) mbar_expect_tx(&bars[3], 32768);
       }
-      ny[tid] = tid < nc ? p.nrm[yb + tid] : 0.0f;
-      if (filt) {
-        const uint4* src = reinterpret_cast<const uint4*>(p.A + by * 16384);
-        uint4* dst = reinterpret_cast<uint4*>(AY);
-        for (int i = tid; i < 16384 / 8; i += 128) dst[i] = src[i];
-        for (int i = tid; i < 128 * GRNG_KIN; i += 128) {
+      if (filt && warp == 0) {
+        // one 256-byte copy per row into rows of 272 bytes: lanes reading one column of
+        // different rows then meet at most 4 to a bank, not 32
+        __syncwarp();
+        for (int rr = lane; rr < 128; rr += 32)
+          bulk_g2s(AY + rr * 136, p.A + by * 16384 + rr * 128, 256, &bars[3]);
+      }
+      if (tid < 128) {
+        ny[tid] = tid < nc ? p.nrm[yb + tid] : 0.0f;
+        if (filt) parY[tid] = (p.parent && tid < nc) ? p.parent[yb + tid] : 0;
+      }
+      if (filt)
+        for (int i = tid; i < 128 * GRNG_KIN; i += 256) {
           const bool ok = i / GRNG_KIN < nc;
           nbrYi[i] = ok ? p.nbr_idx[yb * GRNG_KIN + i] : (uint8_t)255;
           nbrYk[i] = ok ? p.nbr_key[yb * GRNG_KIN + i] : INF;
         }
-        parY[tid] = (p.parent && tid < nc) ? p.parent[yb + tid] : 0;
-      }
       if (tid == 0) {
         if (mbar_wait(&bars[1], phB, p.spin)) {
           tc_fence_after();
@@ -227,71 +286,114 @@ __global__ void __launch_bounds__(128, 1) tc_sweep_kernel(TcParams p) {
       tc_fence_after();
       __syncthreads();
       if (*s_abort) break;
-      // ---- keys -> T16, neighbour lists and row minima (thread = row) --------------------
-      const int r = tid;
-      const bool vr = r < nr;
+      // ---- pass 1: keys -> T16, row minima, neighbour lists (thread = row, half) ----------
+      // 8 columns per TMEM load; list insertions, rare once the lists fill, are taken out
+      // of the unrolled part so that the loop stays small
+      const float nxr = nx[r];
       float m1 = INF, m2 = INF;
       int a1 = -1, a2 = -1;
-      float* kk = knnK + r * (K + 1);
-      int* ki = knnI + r * (K + 1);
-      float thr = kk[K - 1];
-      const float nxr = nx[r];
-      for (int q = 0; q < 4; ++q) {
-        float g[32];
-        tmem_ld32(trow + (uint32_t)(q * 32), g);
+#pragma unroll 1
+      for (int q = 0; q < 8; ++q) {
+        float g[8], vv[8];
+        tmem_ld8(trow + (uint32_t)(q * 8), g);
+        unsigned pm = 0;
 #pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          const int c = q * 32 + j;
+        for (int j = 0; j < 8; ++j) {
+          const int c = cb + q * 8 + j;
           float v = nxr + ny[c] - 2.0f * g[j];
           if (!vr || c >= nc || (diag && c == r)) v = INF;
+          vv[j] = v;
           T16[r * 130 + c] = __float2half_ru(v);
           if (v < m2) {
             if (v < m1) { m2 = m1; a2 = a1; m1 = v; a1 = c; }
             else { m2 = v; a2 = c; }
           }
-          if (v < thr) {
-            int pos = K - 1;
-            while (pos > 0 && kk[pos - 1] > v) { kk[pos] = kk[pos - 1]; ki[pos] = ki[pos - 1]; --pos; }
-            kk[pos] = v;
-            ki[pos] = (int)(yb + c);
-            thr = kk[K - 1];
-          }
+          if (v < thr) pm |= 1u << j;
+        }
+        while (pm) {
+          const int j = __ffs(pm) - 1;
+          pm &= pm - 1u;
+          float v = vv[0];
+#pragma unroll
+          for (int k = 1; k < 8; ++k)
+            if (j == k) v = vv[k];
+          if (v < thr) thr = knn_insert_reg(kk, ki, v, (int)(yb + cb + q * 8 + j), K);
         }
       }
       tc_fence_before();
+      if (filt) rowx[h * 128 + r] = make_float4(m1, m2, __int_as_float(a1), __int_as_float(a2));
       __syncthreads();
       if (filt) {
-        // ---- column minima over the row block (thread = column) -----------------------
+        // ---- column minima over the row block: thread = column, half of the rows -------
         {
-          const int c = tid;
+          const int c = tid & 127, hr = tid >> 7;
           float c1 = INF, c2 = INF;
           int b1 = -1, b2 = -1;
-          for (int rr = 0; rr < 128; ++rr) {
+          for (int rr = hr * 64; rr < hr * 64 + 64; ++rr) {
             const float v = __half2float(T16[rr * 130 + c]);
             if (v < c2) {
               if (v < c1) { c2 = c1; b2 = b1; c1 = v; b1 = rr; }
               else { c2 = v; b2 = rr; }
             }
           }
-          cmin1[c] = c1; cmin2[c] = c2; carg1[c] = b1; carg2[c] = b2;
+          colx[hr * 128 + c] = make_float4(c1, c2, __int_as_float(b1), __int_as_float(b2));
+        }
+        {  // the other half's row minima
+          const float4 w4 = rowx[(1 - h) * 128 + r];
+          top2_merge(m1, a1, m2, a2, w4.x, __float_as_int(w4.z), w4.y, __float_as_int(w4.w));
         }
         __syncthreads();
+        if (tid < 128) {
+          const float4 u0 = colx[tid], u1 = colx[128 + tid];
+          float c1 = u0.x, c2 = u0.y;
+          int b1 = __float_as_int(u0.z), b2 = __float_as_int(u0.w);
+          top2_merge(c1, b1, c2, b2, u1.x, __float_as_int(u1.z), u1.y, __float_as_int(u1.w));
+          cmin1[tid] = c1; cmin2[tid] = c2; carg1[tid] = b1; carg2[tid] = b2;
+        }
+        if (!mbar_wait(&bars[3], phY, p.spin)) {
+          *s_abort = 1;
+          atomicOr(p.status, 1);
+        }
+        phY ^= 1;
+        __syncthreads();
         tc_fence_after();
-        // ---- tier-1 filter: thread = row x, one column y at a time ------------------------
+        // ---- tier-1 filter: thread = row x, one column y of its half at a time ----------
         const float E = p.gam * (bmx + __uint_as_float(p.bmax[by]));
         const int px = parX[r];
-        for (int q = 0; q < 4; ++q) {
-          float g[32];
-          tmem_ld32(trow + (uint32_t)(q * 32), g);
+        // link bits of px's row of the parents' GRNG: y parents lie in [parY[0], parY[nc-1]]
+        // and are >= px in every upper tile (nodes are sorted by parent)
+        uint32_t gw[5] = {0u, 0u, 0u, 0u, 0u};
+        int wlo = 0, nw = 0;
+        if (p.gpar && vr) {
+          wlo = parY[0] >> 5;
+          nw = (parY[nc - 1] >> 5) - wlo + 1;
 #pragma unroll
-          for (int j = 0; j < 32; ++j) {
-            const int c = q * 32 + j;
+          for (int k = 0; k < 5; ++k)
+            if (k < nw) gw[k] = __ldg(p.gpar + (int64_t)px * p.gpar_words + wlo + k);
+        }
+#pragma unroll 1
+        for (int q = 0; q < 8; ++q) {
+          float g[8];
+          tmem_ld8(trow + (uint32_t)(q * 8), g);
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            const int c = cb + q * 8 + j;
             bool cand = vr && c < nc && (!diag || c > r);
             if (cand && p.gpar) {
               const int qy = parY[c];
               if (qy != px) {
-                const int lo = min(px, qy), hi = max(px, qy);
-                cand = (__ldg(p.gpar + (int64_t)lo * p.gpar_words + (hi >> 5)) >> (hi & 31)) & 1u;
+                const int b = qy - (wlo << 5);
+                if (qy > px && b >= 0 && (b >> 5) < nw && nw <= 5) {
+                  const int wi = b >> 5;
+                  uint32_t w = gw[0];
+#pragma unroll
+                  for (int k = 1; k < 5; ++k)
+                    if (wi == k) w = gw[k];
+                  cand = (w >> (b & 31)) & 1u;
+                } else {
+                  const int lo = min(px, qy), hi = max(px, qy);
+                  cand = (__ldg(p.gpar + (int64_t)lo * p.gpar_words + (hi >> 5)) >> (hi & 31)) & 1u;
+                }
               }
             }
             bool surv = false;
@@ -304,7 +406,7 @@ __global__ void __launch_bounds__(128, 1) tc_sweep_kernel(TcParams p) {
                 const int z = (a1 != c) ? a1 : a2;
                 if (z >= 0) {
                   const float a = (a1 != c) ? m1 : m2;
-                  blocked = hi_b(a + E, e) < vlo && hi_b(__half2float(AY[z * 128 + c]), e) < vlo;
+                  blocked = hi_b(a + E, e) < vlo && hi_b(__half2float(AY[z * 136 + c]), e) < vlo;
                 }
               }
               if (!blocked) {  // column minimum of y over the row block
@@ -345,16 +447,40 @@ __global__ void __launch_bounds__(128, 1) tc_sweep_kernel(TcParams p) {
         tc_fence_before();
       }
     }
+    // ---- the two halves' neighbour lists, merged (T16 and AY are free now) -------------
     __syncthreads();
-    if (tid < nr) {
-      const float* kkr = knnK + tid * (K + 1);
-      const int* kir = knnI + tid * (K + 1);
-      for (int j = 0; j < K; ++j) {
-        p.knn_idx[(xb + tid) * K + j] = kir[j];
-        p.knn_key[(xb + tid) * K + j] = kkr[j];
+    {
+      float* LK = reinterpret_cast<float*>(h ? static_cast<void*>(AY) : static_cast<void*>(T16));  // [t][row]
+      int* LI = reinterpret_cast<int*>(LK + GRNG_KMAX * 128);
+#pragma unroll
+      for (int t = 0; t < GRNG_KMAX; ++t) {
+        LK[t * 128 + r] = kk[t];
+        LI[t * 128 + r] = ki[t];
       }
-      // every unlisted node z has tile key >= kkr[K-1], hence exact key >= that - E(x, z)
-      p.knn_rb[xb + tid] = kir[K - 1] >= 0 ? kkr[K - 1] - p.gam * (nx[tid] + p.nmax_all) : INF;
+    }
+    __syncthreads();
+    if (h == 0 && vr) {
+      const float* K0 = reinterpret_cast<const float*>(T16);
+      const int* I0 = reinterpret_cast<const int*>(K0 + GRNG_KMAX * 128);
+      const float* K1 = reinterpret_cast<const float*>(AY);
+      const int* I1 = reinterpret_cast<const int*>(K1 + GRNG_KMAX * 128);
+      int i0 = 0, i1 = 0;
+      float lastk = INF;
+      int lasti = -1;
+      for (int j = 0; j < K; ++j) {
+        const float k0 = i0 < K ? K0[i0 * 128 + r] : INF;
+        const float k1 = i1 < K ? K1[i1 * 128 + r] : INF;
+        float kv;
+        int iv;
+        if (k0 <= k1) { kv = k0; iv = i0 < K ? I0[i0 * 128 + r] : -1; ++i0; }
+        else { kv = k1; iv = I1[i1 * 128 + r]; ++i1; }
+        p.knn_idx[(xb + r) * K + j] = iv;
+        p.knn_key[(xb + r) * K + j] = kv;
+        lastk = kv;
+        lasti = iv;
+      }
+      // every unlisted node z has tile key >= the K-th listed, hence exact key >= that - E(x, z)
+      p.knn_rb[xb + r] = lasti >= 0 ? lastk - p.gam * (nx[r] + p.nmax_all) : INF;
     }
   }
   for (int o2 = 16; o2 > 0; o2 >>= 1) st_cand += __shfl_down_sync(FULLMASK, st_cand, o2);
@@ -494,7 +620,7 @@ void tc_sweep(const TcLaunch& L, cudaStream_t s) {
   GRNG_CUDA(cudaFuncSetAttribute(tc_sweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   const int64_t nb = (L.n + 127) / 128;
   const int grid = (int)std::min<int64_t>(nb, sm_count());
-  tc_sweep_kernel<<<grid, 128, smem, s>>>(p); note_launch();
+  tc_sweep_kernel<<<grid, 256, smem, s>>>(p); note_launch();
   GRNG_CUDA(cudaGetLastError());
 }
 
