@@ -166,6 +166,7 @@ struct LevelOut {
 struct LevelStats {
   unsigned long long c[32];
   double ms[8];  // prep, tile sweeps, tier-2 grouping + 2a, tier 2b, range lists, tier 3, recheck + emit
+  double kms[2];  // CUDA-event time of the tile sweep kernel(s) and of the tier-3 kernel
 };
 void run_level(const LevelIn& in, LevelOut& out, LevelStats& st, cudaStream_t s,
                float* tile_ms = nullptr);

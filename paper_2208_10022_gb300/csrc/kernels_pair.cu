@@ -1465,11 +1465,9 @@ void run_level(const LevelIn& in, LevelOut& out, LevelStats& st, cudaStream_t s,
     tp.strip_ctr = reinterpret_cast<int*>(dc + 0); tp.stats = dc + 2;
     int grid = (int)std::min<int64_t>(nb, num_sms());
     cudaEvent_t e0, e1;
-    if (tile_ms) {
-      GRNG_CUDA(cudaEventCreate(&e0));
-      GRNG_CUDA(cudaEventCreate(&e1));
-      GRNG_CUDA(cudaEventRecord(e0, s));
-    }
+    GRNG_CUDA(cudaEventCreate(&e0));
+    GRNG_CUDA(cudaEventCreate(&e1));
+    GRNG_CUDA(cudaEventRecord(e0, s));
     // pivot layers: a first sweep for the neighbour lists, then the filter, which can
     // certify links from the final lists; exemplars: one sweep doing both
     tp.mode = in.grng ? 1 : 0;
@@ -1496,12 +1494,15 @@ void run_level(const LevelIn& in, LevelOut& out, LevelStats& st, cudaStream_t s,
         else launch_tile<8>(in, tp, grid, s);
       }
     }
-    if (tile_ms) {
+    {
       GRNG_CUDA(cudaEventRecord(e1, s));
       GRNG_CUDA(cudaEventSynchronize(e1));
-      GRNG_CUDA(cudaEventElapsedTime(tile_ms, e0, e1));
+      float ems = 0.0f;
+      GRNG_CUDA(cudaEventElapsedTime(&ems, e0, e1));
       cudaEventDestroy(e0);
       cudaEventDestroy(e1);
+      if (tile_ms) *tile_ms = ems;
+      st.kms[0] = ems;
     }
     nsurv = read_u64(dc + 1, s);
     if (use_tc) {
@@ -1665,8 +1666,19 @@ void run_level(const LevelIn& in, LevelOut& out, LevelStats& st, cudaStream_t s,
       }
       t3.stats = dc + 34;
       GRNG_CUDA(cudaMemsetAsync(dc + 34, 0, 4 * sizeof(unsigned long long), s));
+      cudaEvent_t f0, f1;
+      GRNG_CUDA(cudaEventCreate(&f0));
+      GRNG_CUDA(cudaEventCreate(&f1));
+      GRNG_CUDA(cudaEventRecord(f0, s));
       tier3_kernel<<<grid3, 256, 2 * in.Dp * 4, s>>>(t3); note_launch();
       GRNG_CUDA(cudaGetLastError());
+      GRNG_CUDA(cudaEventRecord(f1, s));
+      GRNG_CUDA(cudaEventSynchronize(f1));
+      float fms = 0.0f;
+      GRNG_CUDA(cudaEventElapsedTime(&fms, f0, f1));
+      cudaEventDestroy(f0);
+      cudaEventDestroy(f1);
+      st.kms[1] += fms;
     }
     unsigned long long namb = read_u64(dc + 19, s);
     tick(5);
