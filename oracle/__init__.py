@@ -47,10 +47,12 @@ def lib():
         _lib.orc_assign.restype = i32
         _lib.orc_assign.argtypes = [P, i32, i32, P, i64, P, P, i32, P, P, P, P]
         if hasattr(_lib, "orc_mlp_forward"):
+            _lib.orc_mlp_nparams.restype = i64
+            _lib.orc_mlp_nparams.argtypes = []
             _lib.orc_mlp_forward.restype = None
             _lib.orc_mlp_forward.argtypes = [P, P, i64, P]
             _lib.orc_mlp_backward.restype = f64
-            _lib.orc_mlp_backward.argtypes = [P, P, P, i64, P]
+            _lib.orc_mlp_backward.argtypes = [P, P, P, P, i64, P]
     return _lib
 
 
@@ -160,3 +162,31 @@ def build_layers(X, layers, metric=L2):
         out[li] = dict(pivots=piv, assign=a, dist=d, radius=r, delta_max=dm)
         members, member_r = piv, r
     return out
+
+
+# ---- interceptor-ranking network (extension of Stage V) ---------------------------------
+MLP_IN, MLP_H = 32, 128
+
+
+def mlp_nparams():
+    return int(lib().orc_mlp_nparams())
+
+
+def mlp_forward(params, X):
+    """FP64 logits of the samples X[N][32] under the parameter vector `params`."""
+    P = np.ascontiguousarray(params, dtype=np.float64)
+    X = np.ascontiguousarray(X, dtype=np.float64).reshape(-1, MLP_IN)
+    out = np.zeros(X.shape[0], np.float64)
+    lib().orc_mlp_forward(_p(P), _p(X), X.shape[0], _p(out))
+    return out
+
+
+def mlp_loss_grad(params, X, y, w=None):
+    """(loss, gradient) of the weighted mean logistic loss, FP64."""
+    P = np.ascontiguousarray(params, dtype=np.float64)
+    X = np.ascontiguousarray(X, dtype=np.float64).reshape(-1, MLP_IN)
+    y = np.ascontiguousarray(y, dtype=np.float64)
+    wv = None if w is None else np.ascontiguousarray(w, dtype=np.float64)
+    g = np.zeros(P.shape[0], np.float64)
+    loss = lib().orc_mlp_backward(_p(P), _p(X), _p(y), None if wv is None else _p(wv), X.shape[0], _p(g))
+    return float(loss), g
