@@ -75,6 +75,10 @@ typedef struct grng_opts {
 /* Testing aid: cap the pivot layers' range lists at 16 nodes so that more pairs take
  * the hierarchical exhaustive tier.  Results are identical; only the work changes. */
 #define GRNG_FLAG_SHORT_LISTS 1ull
+/* Record, during rng_build_exact, one training sample per candidate of the learned
+ * shortlist's pool for every pair that reaches the exhaustive tier (see
+ * grng_mlp_dataset).  Results are unchanged. */
+#define GRNG_FLAG_RECORD_MLP 2ull
 
 typedef struct grng_index grng_index; /* opaque; owns all device state */
 
@@ -134,6 +138,54 @@ grng_status rng_insert_batch(grng_index* idx, const float* pts, int64_t m);
  * sorted (host or device).  *n_edges receives the edge count; if cap < count the
  * call returns GRNG_ETRUNC after writing nothing. ij may be NULL to query. */
 grng_status rng_edges(const grng_index* idx, int32_t* ij, int64_t cap, int64_t* n_edges);
+
+/* ---- Learned shortlist (an extension of Stage V, Sec. 2: the "select group" of likely
+ * interceptors tried before the exhaustive Stage VI search) ---------------------------
+ * A ranking network scores candidate interceptors of the exemplar pairs that the exact
+ * tiers leave to the exhaustive search; each such pair first tests its k best-scored
+ * candidates exactly (Eq. 1) and, if none blocks it, goes on to the exhaustive search
+ * as without the network.  The network never decides an edge: it only changes which
+ * interceptors are tried first, so the edge set is identical with or without it.
+ *
+ * Network: 32 features -> 128 ReLU -> 128 ReLU -> 1 logit.  Parameter vector (FP32,
+ * grng_mlp_nparams() values, in this order): W1[128][32] (row = hidden unit), b1[128],
+ * W2[128][128], b2[128], w3[128], b3.  Inference inside the build (opts.mlp_weights with
+ * opts.mlp_bytes = 4 * grng_mlp_nparams() and opts.k_shortlist in 1..16) and in
+ * grng_mlp_score rounds the weights to BF16 and accumulates in FP32.
+ *
+ * Candidate pool of a pair (g, o): the K listed neighbours of each of the first 8
+ * listed neighbours of g and of o.  Features (all distances divided by d(g,o) and
+ * clamped to [0, 8]): side, neighbour rank, rank within its list, the two list
+ * distances and the triangle bounds they give, distances of z, g, o to their pivots,
+ * pivot equalities, pivot radii, the K-th list distance of g, o and the neighbour,
+ * log2 d(g,o) / 8, and 8 hashed bits of the pivot ids (+-1).
+ *
+ * All pointers may be host or device memory; these calls use the legacy default
+ * stream and return when their work is done. */
+int64_t grng_mlp_nparams(void);
+
+/* Logits scores[n] of the samples feats[n][32] under params (BF16 weights, FP32 sums). */
+grng_status grng_mlp_score(const float* params, const float* feats, int64_t n, float* scores);
+
+/* FP32 loss L = (1/n) sum_b w_b [log(1 + e^{s_b}) - y_b s_b] (w = 1 when weights is NULL)
+ * and its gradient grad[nparams] with respect to params (FP32 weights, no rounding);
+ * 1 <= n <= 2^20.  loss and grad may be NULL. */
+grng_status grng_mlp_loss_grad(const float* params, const float* feats, const float* labels,
+                               const float* weights, int64_t n, float* loss, float* grad);
+
+/* Train params (in/out) with Adam (lr, betas 0.9 / 0.999) on mini-batches of `batch`
+ * consecutive samples for `epochs` passes, on the GPU.  *loss_out (may be NULL) gets the
+ * mean loss of the last pass.  The caller shuffles the samples and draws the initial
+ * parameters. */
+grng_status grng_mlp_train(const float* feats, const float* labels, const float* weights, int64_t n,
+                           int32_t epochs, int32_t batch, float lr, float* params, float* loss_out);
+
+/* Samples recorded by the last rng_build_exact of an index created with
+ * GRNG_FLAG_RECORD_MLP: feats[count][32] and labels[count] (1 when the candidate blocks
+ * the pair by FP32 keys, else 0).  *count receives the number of samples (at most
+ * 4,194,304); with feats and labels NULL only the count is returned.  cap < count
+ * returns GRNG_ETRUNC. */
+grng_status grng_mlp_dataset(const grng_index* idx, float* feats, float* labels, int64_t cap, int64_t* count);
 
 /* Counters and timings of the last calls as one JSON object (NUL-terminated).
  * If cap is too small, returns GRNG_ETRUNC and writes nothing. */

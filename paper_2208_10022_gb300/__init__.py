@@ -74,8 +74,16 @@ def lib():
         L.grng_destroy.restype = None
         L.grng_last_error.argtypes = []
         L.grng_last_error.restype = ctypes.c_char_p
+        f32p = ctypes.POINTER(ctypes.c_float)
+        L.grng_mlp_nparams.argtypes = []
+        L.grng_mlp_nparams.restype = i64
+        L.grng_mlp_score.argtypes = [P, P, i64, P]
+        L.grng_mlp_loss_grad.argtypes = [P, P, P, P, i64, f32p, P]
+        L.grng_mlp_train.argtypes = [P, P, P, i64, i32, i32, ctypes.c_float, P, f32p]
+        L.grng_mlp_dataset.argtypes = [P, P, P, i64, ctypes.POINTER(i64)]
         for f in ("grng_create", "grng_build_layer", "grng_link_pivots", "grng_adjacency_rows",
-                  "rng_build_exact", "rng_insert_batch", "rng_edges", "grng_stats"):
+                  "rng_build_exact", "rng_insert_batch", "rng_edges", "grng_stats", "grng_mlp_score",
+                  "grng_mlp_loss_grad", "grng_mlp_train", "grng_mlp_dataset"):
             getattr(L, f).restype = i32
         _lib = L
     return _lib
@@ -106,13 +114,17 @@ def _contig(a, dtype):
 class Index:
     """An index over a point set (owns the library's grng_index)."""
 
-    def __init__(self, points, n_layers=1, metric=L2, precision=FP32, knn_k=32, stream=None, flags=0):
+    def __init__(self, points, n_layers=1, metric=L2, precision=FP32, knn_k=32, stream=None, flags=0,
+                 mlp_params=None, k_shortlist=0):
         self._h = ctypes.c_void_p()
         pts = _contig(points, np.float32)
         n, dim = int(pts.shape[0]), int(pts.shape[1])
         o = Opts()
         lib().grng_default_opts(ctypes.byref(o))
         o.metric, o.precision, o.n_layers, o.knn_k, o.flags = metric, precision, n_layers, knn_k, flags
+        if mlp_params is not None:
+            w = _contig(mlp_params, np.float32)
+            o.mlp_weights, o.mlp_bytes, o.k_shortlist = _ptr(w), 4 * int(w.shape[0]), k_shortlist
         if stream is not None:
             o.cuda_stream = stream if isinstance(stream, int) else stream.cuda_stream
         _check(lib().grng_create(ctypes.byref(self._h), _ptr(pts), n, dim, ctypes.byref(o)))
@@ -196,6 +208,16 @@ class Index:
         _check(lib().rng_edges(self._h, _ptr(out), ne, None))
         return out[:ne]
 
+    def mlp_dataset(self):
+        """(features [N, 32], labels [N]) recorded by the last RNG build (GRNG_FLAG_RECORD_MLP)."""
+        cnt = ctypes.c_int64(0)
+        _check(lib().grng_mlp_dataset(self._h, None, None, 0, ctypes.byref(cnt)))
+        n = cnt.value
+        F = np.zeros((max(n, 1), MLP_IN), np.float32)
+        y = np.zeros(max(n, 1), np.float32)
+        _check(lib().grng_mlp_dataset(self._h, F.ctypes.data, y.ctypes.data, n, ctypes.byref(cnt)))
+        return F[:n], y[:n]
+
     def stats(self):
         buf = ctypes.create_string_buffer(1 << 16)
         _check(lib().grng_stats(self._h, buf, len(buf)))
@@ -203,12 +225,66 @@ class Index:
 
 
 GRNG_FLAG_SHORT_LISTS = 1
+GRNG_FLAG_RECORD_MLP = 2
+MLP_IN = 32
 
 
-def build_all(X, layers, metric=L2, knn_k=32, want_adjacency=False, stream=None, flags=0, precision=FP32):
+def mlp_nparams():
+    return int(lib().grng_mlp_nparams())
+
+
+def mlp_score(params, feats):
+    """Logits of feats [N, 32] (BF16 weights, FP32 accumulation), numpy float32."""
+    P = np.ascontiguousarray(params, np.float32)
+    F = np.ascontiguousarray(feats, np.float32).reshape(-1, MLP_IN)
+    out = np.zeros(F.shape[0], np.float32)
+    _check(lib().grng_mlp_score(P.ctypes.data, F.ctypes.data, F.shape[0], out.ctypes.data))
+    return out
+
+
+def mlp_loss_grad(params, feats, labels, weights=None):
+    """(loss, gradient) of the weighted mean logistic loss, FP32 on the GPU."""
+    P = np.ascontiguousarray(params, np.float32)
+    F = np.ascontiguousarray(feats, np.float32).reshape(-1, MLP_IN)
+    y = np.ascontiguousarray(labels, np.float32)
+    w = None if weights is None else np.ascontiguousarray(weights, np.float32)
+    g = np.zeros(P.shape[0], np.float32)
+    loss = ctypes.c_float(0.0)
+    _check(lib().grng_mlp_loss_grad(P.ctypes.data, F.ctypes.data, y.ctypes.data, None if w is None else w.ctypes.data,
+                                    F.shape[0], ctypes.byref(loss), g.ctypes.data))
+    return float(loss.value), g
+
+
+def mlp_train(params, feats, labels, weights=None, epochs=10, batch=4096, lr=1e-3):
+    """Adam on the GPU; returns (trained parameters, mean loss of the last pass)."""
+    P = np.array(params, np.float32, copy=True)
+    F = np.ascontiguousarray(feats, np.float32).reshape(-1, MLP_IN)
+    y = np.ascontiguousarray(labels, np.float32)
+    w = None if weights is None else np.ascontiguousarray(weights, np.float32)
+    loss = ctypes.c_float(0.0)
+    _check(lib().grng_mlp_train(F.ctypes.data, y.ctypes.data, None if w is None else w.ctypes.data, F.shape[0],
+                                epochs, batch, lr, P.ctypes.data, ctypes.byref(loss)))
+    return P, float(loss.value)
+
+
+def mlp_init(seed=0):
+    """He-normal initial parameters (numpy, seeded), biases zero."""
+    rng = np.random.default_rng(seed)
+    P = np.zeros(mlp_nparams(), np.float32)
+    H, I = 128, MLP_IN
+    P[:H * I] = rng.normal(0.0, np.sqrt(2.0 / I), H * I)
+    o = H * I + H
+    P[o:o + H * H] = rng.normal(0.0, np.sqrt(2.0 / H), H * H)
+    o += H * H + H
+    P[o:o + H] = rng.normal(0.0, np.sqrt(1.0 / H), H)
+    return P
+
+
+def build_all(X, layers, metric=L2, knn_k=32, want_adjacency=False, stream=None, flags=0, precision=FP32,
+              mlp_params=None, k_shortlist=0):
     """Build every layer (finest first), link every layer (coarsest first) and the RNG."""
     ix = Index(X, n_layers=len(layers), metric=metric, knn_k=knn_k, stream=stream, flags=flags,
-               precision=precision)
+               precision=precision, mlp_params=mlp_params, k_shortlist=k_shortlist)
     out = {"layers": [None] * len(layers), "grng": [None] * len(layers)}
     for li in range(len(layers) - 1, -1, -1):
         out["layers"][li] = ix.build_layer(li, layers[li])

@@ -130,6 +130,9 @@ struct grng_index {
   bool rng_built = false;
   LevelStats rng_st{};
   double rng_ms = 0, rng_tile_ms = 0, sort_ms = 0;
+  DevBuf mlp;            // ranking network parameters (learned shortlist), or empty
+  DevBuf rec_f, rec_y;   // recorded training samples of the last RNG build
+  int64_t rec_n = 0;
 };
 
 namespace {
@@ -287,12 +290,13 @@ void level_json(std::string& js, const char* name, const LevelStats& st) {
                              "fp64_blocking", "edges", "tier3_overflows", "tier3_nodes_tested",
                              "list_certified", "range_pairs", "range_lists_cut", "range_listed_nodes",
                              "range_links", "range_nodes_tested", "tier3_blocked",
-                             "tier3_descent_blocked"};
+                             "tier3_descent_blocked", "learned_pairs", "learned_candidates", "learned_tests",
+                             "learned_blocked"};
   char buf[1024];
   js += "\"";
   js += name;
   js += "\":{";
-  for (int i = 0; i < 25; ++i) {
+  for (int i = 0; i < 29; ++i) {
     snprintf(buf, sizeof(buf), "%s\"%s\":%llu", i ? "," : "", nm[i], (unsigned long long)st.c[i]);
     js += buf;
   }
@@ -335,8 +339,12 @@ grng_status grng_create(grng_index** out, const float* pts, int64_t n, int32_t d
     if (opts->knn_k < 0 || opts->knn_k > GRNG_KMAX) fail(GRNG_EINVAL, "knn_k must be in [0, 32]");
     if (opts->precision != GRNG_FP32 && opts->precision != GRNG_BF16)
       fail(GRNG_ENOTIMPL, "FP32 and BF16 tile precisions are built");
-    if (opts->k_shortlist != 0 || opts->mlp_weights) fail(GRNG_ENOTIMPL, "learned shortlist not built");
-    if (opts->reserved != 0 || (opts->flags & ~(uint64_t)GRNG_FLAG_SHORT_LISTS) != 0)
+    if (opts->k_shortlist < 0 || opts->k_shortlist > GRNG_MLP_KMAX)
+      fail(GRNG_EINVAL, "k_shortlist must be in [0, 16]");
+    if (opts->k_shortlist > 0 && (!opts->mlp_weights || opts->mlp_bytes != (size_t)GRNG_MLP_NPARAM * 4))
+      fail(GRNG_EINVAL, "a shortlist needs mlp_weights of grng_mlp_nparams() floats (mlp_bytes)");
+    if (opts->reserved != 0 ||
+        (opts->flags & ~(uint64_t)(GRNG_FLAG_SHORT_LISTS | GRNG_FLAG_RECORD_MLP)) != 0)
       fail(GRNG_EINVAL, "reserved fields must be 0");
     ix = new grng_index();
     GRNG_CUDA(cudaGetDevice(&ix->device));
@@ -349,6 +357,11 @@ grng_status grng_create(grng_index** out, const float* pts, int64_t n, int32_t d
     ix->K = opts->knn_k ? opts->knn_k : 32;
     ix->layers.resize(opts->n_layers);
     cudaStream_t s = ix->stream;
+    if (opts->k_shortlist > 0) {
+      GRNG_CUDA(ix->mlp.alloc((size_t)GRNG_MLP_NPARAM * 4));
+      GRNG_CUDA(cudaMemcpyAsync(ix->mlp.p, opts->mlp_weights, (size_t)GRNG_MLP_NPARAM * 4, cudaMemcpyDefault, s));
+    }
+    ix->opts.mlp_weights = nullptr;  // the caller's pointer is not kept
     GRNG_CUDA(ix->X.alloc((size_t)n * ix->Dp * 4));
     GRNG_CUDA(cudaMemsetAsync(ix->X.p, 0, (size_t)n * ix->Dp * 4, s));
     GRNG_CUDA(cudaMemcpy2DAsync(ix->X.p, (size_t)ix->Dp * 4, pts, (size_t)dim * 4, (size_t)dim * 4, (size_t)n,
@@ -570,16 +583,44 @@ grng_status rng_build_exact(grng_index* ix) {
     in.pdist_hi = ix->xpdh.as<float>();
     in.precision = ix->opts.precision == GRNG_BF16 ? 1 : 0;
     if (ix->opts.spin_limit > 0) in.spin = ix->opts.spin_limit;
+    in.mlp_params = ix->mlp.p ? ix->mlp.as<float>() : nullptr;
+    in.kshort = ix->mlp.p ? ix->opts.k_shortlist : 0;
+    in.mlp_record = (ix->opts.flags & GRNG_FLAG_RECORD_MLP) ? 1 : 0;
     LevelOut lo;
     lo.edges = &ix->edges;
+    lo.rec_f = &ix->rec_f;
+    lo.rec_y = &ix->rec_y;
     float tile_ms = 0;
     run_level(in, lo, ix->rng_st, s, &tile_ms);
     ix->n_edges = lo.n_edges;
+    ix->rec_n = lo.rec_n;
     DevBuf tmp;
     if (ix->n_edges > 1) sort_u64(ix->edges.as<uint64_t>(), ix->n_edges, tmp, s);
     ix->rng_tile_ms = tile_ms;
     ix->rng_ms = tm.stop();
     ix->rng_built = true;
+  });
+}
+
+grng_status grng_mlp_dataset(const grng_index* cix, float* feats, float* labels, int64_t cap, int64_t* count) {
+  grng_index* ix = const_cast<grng_index*>(cix);
+  if (!ix) {
+    g_last_error = "index is NULL";
+    return GRNG_EINVAL;
+  }
+  return guarded(ix, [&] {
+    if (!ix->rng_built) fail(GRNG_ESTATE, "the RNG is not built");
+    if (!(ix->opts.flags & GRNG_FLAG_RECORD_MLP)) fail(GRNG_ESTATE, "the index was created without GRNG_FLAG_RECORD_MLP");
+    if (count) *count = ix->rec_n;
+    if (!feats && !labels) return;
+    if (cap < ix->rec_n) fail(GRNG_ETRUNC, "buffer smaller than the recorded sample count");
+    cudaStream_t s = ix->stream;
+    if (ix->rec_n > 0) {
+      if (feats)
+        GRNG_CUDA(cudaMemcpyAsync(feats, ix->rec_f.p, (size_t)ix->rec_n * GRNG_MLP_IN * 4, cudaMemcpyDefault, s));
+      if (labels) GRNG_CUDA(cudaMemcpyAsync(labels, ix->rec_y.p, (size_t)ix->rec_n * 4, cudaMemcpyDefault, s));
+    }
+    GRNG_CUDA(cudaStreamSynchronize(s));
   });
 }
 

@@ -118,6 +118,9 @@ struct LevelIn {
   const float* pdist_hi = nullptr;  // [n] FP32 upper bound of d(node, parent), or null
   int precision = 0;                // 1: tensor-core (split BF16) distance tiles for the RNG level
   long long spin = 1ll << 24;       // poll limit of every bounded device wait
+  const float* mlp_params = nullptr;  // RNG level: ranking network (GRNG_MLP_NPARAM floats, device)
+  int kshort = 0;                     // shortlist length tried before tier 3 (0: off)
+  int mlp_record = 0;                 // RNG level: record features and labels of the tier-3 pairs' pools
 };
 
 // ---- tensor-core tiles (kernels_tc.cu) ------------------------------------------------------
@@ -162,12 +165,43 @@ struct LevelOut {
   // RNG level: edges as (i << 32 | j), i < j original ids, unsorted
   DevBuf* edges = nullptr;
   int64_t n_edges = 0;
+  // RNG level with mlp_record: samples [rec_n][GRNG_MLP_IN] features and [rec_n] labels
+  DevBuf* rec_f = nullptr;
+  DevBuf* rec_y = nullptr;
+  int64_t rec_n = 0;
 };
 struct LevelStats {
   unsigned long long c[32];
   double ms[8];  // prep, tile sweeps, tier-2 grouping + 2a, tier 2b, range lists, tier 3, recheck + emit
   double kms[2];  // CUDA-event time of the tile sweep kernel(s) and of the tier-3 kernel
 };
+// ---- learned shortlist (kernels_mlp.cu) -------------------------------------------------------
+#define GRNG_MLP_IN 32
+#define GRNG_MLP_H 128
+#define GRNG_MLP_NPARAM (GRNG_MLP_H * GRNG_MLP_IN + GRNG_MLP_H + GRNG_MLP_H * GRNG_MLP_H + 2 * GRNG_MLP_H + 1)
+#define GRNG_MLP_KMAX 16
+#define GRNG_MLP_PW 8  // neighbours of each endpoint whose lists form the candidate pool
+struct MlpStage {
+  const float* X;
+  int64_t n;
+  int Dp, metric, K;
+  const int32_t* knn_idx;
+  const float* knn_key;
+  const int32_t* parent;
+  const float* pdist_hi;
+  const float* prad;     // radius upper bound of each parent, or null
+  const int2* pairs;     // pairs entering tier 3
+  int64_t m;
+  int64_t slot0;         // pending slot of pairs[0]
+  int* pflag;            // set to 3 for pairs the shortlist blocks
+  int2* amb; unsigned long long* amb_cnt; unsigned long long amb_cap;
+  const float* params;   // or null (record only)
+  int kshort;
+  float* rec_f; float* rec_y; unsigned long long* rec_cnt; unsigned long long rec_cap;  // or null
+  unsigned long long* stats;  // [0] candidates scored, [1] shortlist tests, [2] pairs blocked
+};
+void mlp_stage(const MlpStage& P, cudaStream_t s);
+
 void run_level(const LevelIn& in, LevelOut& out, LevelStats& st, cudaStream_t s,
                float* tile_ms = nullptr);
 

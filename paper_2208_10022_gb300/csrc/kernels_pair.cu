@@ -686,7 +686,9 @@ __global__ void __launch_bounds__(256, 4) tier3_kernel(Tier3Params p) {
                                 p.rlo ? p.rlo[o] : 0.0f, p.rhi ? p.rhi[o] : 0.0f, p.metric, e,
                                 p.guide);
     const int64_t slot = p.slot0 + t;
-    if (!P.quick) {
+    // a pair the learned shortlist has already blocked needs no exhaustive scan
+    const bool pre = p.pflag[slot] == 3;
+    if (!P.quick && !pre) {
       // thresholds as upper bounds in distance units
       const float t1d = p.metric == L2 ? sqrtf(fmaxf(P.t1hi, 0.0f)) * (1.0f + u2) : P.t1hi;
       const float t2d = p.metric == L2 ? sqrtf(fmaxf(P.t2hi, 0.0f)) * (1.0f + u2) : P.t2hi;
@@ -991,7 +993,7 @@ __global__ void __launch_bounds__(256, 4) tier3_kernel(Tier3Params p) {
     __syncthreads();
     if (tid == 0) {
       p.pend[slot] = make_int2((int)g, (int)o);
-      p.pflag[slot] = s_block ? 3 : 0;
+      if (s_block) p.pflag[slot] = 3;
       n_blk += s_block != 0;
     }
   }
@@ -1431,7 +1433,7 @@ void run_level(const LevelIn& in, LevelOut& out, LevelStats& st, cudaStream_t s,
   unsigned long long* dc = ctr.as<unsigned long long>();
   // counters: 0 strip, 1 surv, 2..5 tile stats, 8.. tier2a, 12.. tier2b, 16 links, 17 pend,
   // 18 unres, 19 amb, 20 unres2, 21 edges, 22 recheck blocked, 26..33 range lists,
-  // 34..37 tier 3, 40 tensor-core status
+  // 34..37 tier 3, 40 tensor-core status, 44..47 learned shortlist
   if (KC == 32) launch_prep<32>(in, A.as<__half>(), nbi.as<uint8_t>(), nbk.as<float>(), s);
   else if (KC == 16) launch_prep<16>(in, A.as<__half>(), nbi.as<uint8_t>(), nbk.as<float>(), s);
   else launch_prep<8>(in, A.as<__half>(), nbi.as<uint8_t>(), nbk.as<float>(), s);
@@ -1666,6 +1668,37 @@ void run_level(const LevelIn& in, LevelOut& out, LevelStats& st, cudaStream_t s,
       }
       t3.stats = dc + 34;
       GRNG_CUDA(cudaMemsetAsync(dc + 34, 0, 4 * sizeof(unsigned long long), s));
+      if (!in.grng && ((in.mlp_params && in.kshort > 0) || (in.mlp_record && out.rec_f))) {
+        // learned shortlist (extension of Stage V): k scored candidates per pair first
+        MlpStage ms;
+        ms.X = in.X; ms.n = n; ms.Dp = in.Dp; ms.metric = in.metric; ms.K = in.K;
+        ms.knn_idx = knni.as<int32_t>(); ms.knn_key = knnk.as<float>();
+        ms.parent = in.parent; ms.pdist_hi = in.pdist_hi;
+        ms.prad = in.anc.n ? in.anc.Rhi[in.anc.n - 1] : nullptr;
+        ms.pairs = t3pairs; ms.m = (int64_t)nun2; ms.slot0 = (int64_t)npend; ms.pflag = pflag.as<int>();
+        ms.amb = amb.as<int2>(); ms.amb_cnt = dc + 19; ms.amb_cap = amb_cap;
+        ms.params = in.kshort > 0 ? in.mlp_params : nullptr;
+        ms.kshort = in.kshort;
+        ms.rec_f = nullptr; ms.rec_y = nullptr; ms.rec_cnt = dc + 47; ms.rec_cap = 0;
+        if (in.mlp_record && out.rec_f) {
+          const unsigned long long rc = std::min<unsigned long long>(
+              nun2 * 2ull * GRNG_MLP_PW * in.K, 4ull << 20);
+          GRNG_CUDA(out.rec_f->alloc((size_t)rc * GRNG_MLP_IN * 4));
+          GRNG_CUDA(out.rec_y->alloc((size_t)rc * 4));
+          ms.rec_f = out.rec_f->as<float>(); ms.rec_y = out.rec_y->as<float>(); ms.rec_cap = rc;
+        }
+        ms.stats = dc + 44;
+        GRNG_CUDA(cudaMemsetAsync(dc + 44, 0, 4 * sizeof(unsigned long long), s));
+        mlp_stage(ms, s);
+        unsigned long long hm[4];
+        GRNG_CUDA(cudaMemcpyAsync(hm, dc + 44, sizeof(hm), cudaMemcpyDeviceToHost, s));
+        GRNG_CUDA(cudaStreamSynchronize(s));
+        st.c[25] = ms.params ? nun2 : 0;  // pairs given a shortlist
+        st.c[26] = hm[0];                 // candidates scored
+        st.c[27] = hm[1];                 // shortlist tests
+        st.c[28] = hm[2];                 // pairs blocked by the shortlist
+        if (ms.rec_f) out.rec_n = (int64_t)std::min<unsigned long long>(hm[3], ms.rec_cap);
+      }
       cudaEvent_t f0, f1;
       GRNG_CUDA(cudaEventCreate(&f0));
       GRNG_CUDA(cudaEventCreate(&f1));
