@@ -291,12 +291,12 @@ void level_json(std::string& js, const char* name, const LevelStats& st) {
                              "list_certified", "range_pairs", "range_lists_cut", "range_listed_nodes",
                              "range_links", "range_nodes_tested", "tier3_blocked",
                              "tier3_descent_blocked", "learned_pairs", "learned_candidates", "learned_tests",
-                             "learned_blocked"};
+                             "learned_blocked", "learned_pool_hits"};
   char buf[1024];
   js += "\"";
   js += name;
   js += "\":{";
-  for (int i = 0; i < 29; ++i) {
+  for (int i = 0; i < 30; ++i) {
     snprintf(buf, sizeof(buf), "%s\"%s\":%llu", i ? "," : "", nm[i], (unsigned long long)st.c[i]);
     js += buf;
   }

@@ -198,7 +198,8 @@ struct MlpStage {
   const float* params;   // or null (record only)
   int kshort;
   float* rec_f; float* rec_y; unsigned long long* rec_cnt; unsigned long long rec_cap;  // or null
-  unsigned long long* stats;  // [0] candidates scored, [1] shortlist tests, [2] pairs blocked
+  unsigned long long* stats;  // [0] candidates scored, [1] shortlist tests, [2] pairs blocked,
+                              // [3] samples recorded, [4] pairs with a blocker in the pool (recording)
 };
 void mlp_stage(const MlpStage& P, cudaStream_t s);
 

@@ -263,7 +263,21 @@ __device__ __forceinline__ uint32_t mix32(uint32_t h) {  // integer finaliser (x
 
 // Candidate q of pair (g, o) (q < 2 * GRNG_MLP_PW * K): returns the node z, or -1, and
 // its features f.  Distances are divided by d(g, o) and clamped to [0, 8].
-__device__ int mlp_candidate(const PoolCtx& c, int g, int o, float dxy, int q, float (&f)[GRNG_MLP_IN]) {
+// node z of candidate q of pair (g, o), or -1
+__device__ __forceinline__ int mlp_pool_z(const PoolCtx& c, int g, int o, int q) {
+  const int K = c.K;
+  const int side = q / (GRNG_MLP_PW * K);
+  const int j = (q / K) % GRNG_MLP_PW;
+  if (j >= K) return -1;
+  const int w = c.knn_idx[(int64_t)(side ? o : g) * K + j];
+  if (w < 0) return -1;
+  const int z = c.knn_idx[(int64_t)w * K + q % K];
+  return (z < 0 || z == g || z == o) ? -1 : z;
+}
+
+// c_other / c_same: how often z occurs in the pool of the other endpoint / again in its own
+__device__ int mlp_candidate(const PoolCtx& c, int g, int o, float dxy, int q, int c_other, int c_same,
+                             float (&f)[GRNG_MLP_IN]) {
   const int K = c.K;
   const int side = q / (GRNG_MLP_PW * K);
   const int j = (q / K) % GRNG_MLP_PW;
@@ -306,9 +320,9 @@ __device__ int mlp_candidate(const PoolCtx& c, int g, int o, float dxy, int q, f
   const uint32_t h = mix32((uint32_t)az * 0x9E3779B1u ^ mix32((uint32_t)(side ? ao : ag)));
 #pragma unroll
   for (int b = 0; b < 8; ++b) f[21 + b] = ((h >> b) & 1u) ? 1.0f : -1.0f;
-  f[29] = 0.0f;
-  f[30] = 0.0f;
-  f[31] = 0.0f;
+  f[29] = c_other > 0 ? 1.0f : 0.0f;  // reached from both endpoints: near both
+  f[30] = (float)min(c_other, 8) * 0.125f;
+  f[31] = (float)min(c_same, 8) * 0.125f;
   return z;
 }
 
@@ -325,7 +339,7 @@ __global__ void __launch_bounds__(256, 1) mlp_stage_kernel(MlpStage p) {
   __shared__ int s_sel[GRNG_MLP_KMAX];
   __shared__ unsigned long long s_best;
   __shared__ float s_v;
-  __shared__ int s_block, s_nsel;
+  __shared__ int s_block, s_nsel, s_pos;
   const int tid = threadIdx.x, lane = tid & 31;
   const Err e = err_fp32(p.Dp);
   const PoolCtx pc{p.knn_idx, p.knn_key, p.K, p.metric, p.parent, p.pdist_hi, p.prad};
@@ -347,9 +361,22 @@ __global__ void __launch_bounds__(256, 1) mlp_stage_kernel(MlpStage p) {
     const float v = s_v;
     const float dxy = p.metric == L2 ? sqrtf(fmaxf(v, 0.0f)) : v;
     const PairThr P = pair_thresholds(v, 0.0f, 0.0f, 0.0f, 0.0f, p.metric, e, 0);
+    for (int q = tid; q < MLP_POOL_MAX; q += blockDim.x) s_z[q] = q < Q ? mlp_pool_z(pc, g, o, q) : -1;
+    if (tid == 0) s_pos = 0;
+    __syncthreads();
+    const int half = GRNG_MLP_PW * p.K;
     for (int q = tid; q < MLP_POOL_MAX; q += blockDim.x) {
       float f[GRNG_MLP_IN];
-      const int z = q < Q ? mlp_candidate(pc, g, o, dxy, q, f) : -1;
+      int z = s_z[q];
+      if (z >= 0) {
+        const int mine = q < half ? 0 : half, other = q < half ? half : 0;
+        int c_other = 0, c_same = 0;
+        for (int r = 0; r < half; ++r) {
+          c_other += s_z[other + r] == z;
+          c_same += s_z[mine + r] == z;
+        }
+        z = mlp_candidate(pc, g, o, dxy, q, c_other, c_same - 1, f);
+      }
       if (p.rec_f && z >= 0) {
         // training sample: does z block (g, o)?  (FP32 keys; a label, not a decision)
         const float* pz = p.X + (int64_t)z * p.Dp;
@@ -359,13 +386,15 @@ __global__ void __launch_bounds__(256, 1) mlp_stage_kernel(MlpStage p) {
           for (int k = 0; k < GRNG_MLP_IN; ++k) p.rec_f[r * GRNG_MLP_IN + k] = f[k];
           p.rec_y[r] = fmaxf(a, b) < v ? 1.0f : 0.0f;
         }
+        if (fmaxf(a, b) < v) s_pos = 1;
       }
       if (p.params) {
-        s_z[q] = z;
         s_score[q] = z >= 0 ? mlp_score(W, f) : minf_();
         n_scored += z >= 0;
       }
     }
+    __syncthreads();
+    if (tid == 0 && s_pos) atomicAdd(p.stats + 4, 1ull);  // pairs with a blocker in the pool
     if (!p.params || P.quick) continue;
     // ---- the k best distinct candidates ----
     for (int r = 0; r < p.kshort; ++r) {

@@ -1688,15 +1688,16 @@ void run_level(const LevelIn& in, LevelOut& out, LevelStats& st, cudaStream_t s,
           ms.rec_f = out.rec_f->as<float>(); ms.rec_y = out.rec_y->as<float>(); ms.rec_cap = rc;
         }
         ms.stats = dc + 44;
-        GRNG_CUDA(cudaMemsetAsync(dc + 44, 0, 4 * sizeof(unsigned long long), s));
+        GRNG_CUDA(cudaMemsetAsync(dc + 44, 0, 5 * sizeof(unsigned long long), s));
         mlp_stage(ms, s);
-        unsigned long long hm[4];
+        unsigned long long hm[5];
         GRNG_CUDA(cudaMemcpyAsync(hm, dc + 44, sizeof(hm), cudaMemcpyDeviceToHost, s));
         GRNG_CUDA(cudaStreamSynchronize(s));
         st.c[25] = ms.params ? nun2 : 0;  // pairs given a shortlist
         st.c[26] = hm[0];                 // candidates scored
         st.c[27] = hm[1];                 // shortlist tests
         st.c[28] = hm[2];                 // pairs blocked by the shortlist
+        st.c[29] = hm[4];                 // recording: pairs with a blocker among the candidates
         if (ms.rec_f) out.rec_n = (int64_t)std::min<unsigned long long>(hm[3], ms.rec_cap);
       }
       cudaEvent_t f0, f1;
