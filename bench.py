@@ -44,6 +44,9 @@ def parse():
     ap.add_argument("--precision", default="bf16", choices=["fp32", "bf16"],
                     help="distance tiles of the exemplar level: tensor cores (bf16) or CUDA cores (fp32)")
     ap.add_argument("--no-compare", action="store_true", help="skip the one-step plain FP32 comparison")
+    ap.add_argument("--no-learned", action="store_true",
+                    help="bf16 without the learned shortlist (by default the network is trained, untimed, on a "
+                         "200,000-point build of the same generator and an 8-candidate shortlist is used)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=12000, help="points of the oracle's bounded sample")
@@ -146,6 +149,25 @@ def kernel_rooflines(stats, n, D, precision, peaks, sms):
     return top
 
 
+def train_shortlist(g, wl, kind, n_train=200000, k=8):
+    """Untimed: record the exhaustive tier's candidate pools of one 200,000-point build of
+    the same generator (other seeds), train the ranking network on the GPU, return it."""
+    import numpy as np
+    t0 = time.perf_counter()
+    w = wl.make(kind, n=n_train, data_seed=7001, pivot_seed=7002)
+    ix, _ = g.build_all(w.X, w.layers, flags=g.GRNG_FLAG_RECORD_MLP)
+    F, y = ix.mlp_dataset()
+    ix.close()
+    pos = float(y.mean()) if y.size else 0.0
+    if y.size == 0 or pos in (0.0, 1.0):
+        return None
+    wts = np.where(y > 0.5, 0.5 / pos, 0.5 / (1.0 - pos)).astype(np.float32)
+    perm = np.random.default_rng(7003).permutation(F.shape[0])
+    P, loss = g.mlp_train(g.mlp_init(7004), F[perm], y[perm], wts[perm], epochs=6, batch=4096, lr=1e-3)
+    return {"params": P, "k": k, "train_points": n_train, "samples": int(F.shape[0]),
+            "positives": int(y.sum()), "train_s": time.perf_counter() - t0, "final_loss": loss}
+
+
 def load_peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -217,9 +239,13 @@ def run_gpu(a, rank, world, local):
     piv_d = [torch.from_numpy(l).cuda() for l in w.layers]
 
     prec = g.BF16 if a.precision == "bf16" else g.FP32
+    learned = None
+    if a.precision == "bf16" and not a.no_learned:
+        learned = train_shortlist(g, wl, a.kind)
+    mlp = {"mlp_params": learned["params"], "k_shortlist": learned["k"]} if learned else {}
 
-    def step_device():
-        ix = g.Index(Xd, n_layers=L, stream=stream, precision=prec)
+    def step_device(plain=False):
+        ix = g.Index(Xd, n_layers=L, stream=stream, precision=prec, **({} if plain else mlp))
         for li in range(L - 1, -1, -1):
             ix.build_layer(li, piv_d[li], outputs=False)
         for li in range(L):
@@ -277,7 +303,7 @@ def run_gpu(a, rank, world, local):
         f0.record(stream)
         e_edges = 0
         for _ in range(a.steps):
-            ix = g.Index(Xh, n_layers=L, stream=stream, precision=prec)
+            ix = g.Index(Xh, n_layers=L, stream=stream, precision=prec, **mlp)
             for li in range(L - 1, -1, -1):
                 ix.build_layer(li, pivh[li], outputs=False)
             for li in range(L):
@@ -312,6 +338,8 @@ def run_gpu(a, rank, world, local):
             "config": {"workload": f"{a.kind}: {n:,} x {D} FP32, intrinsic dim 8, L2, nested random pivot layers "
                                    f"{'/'.join(str(s) for s in sizes)}", "n": n, "dim": D, "layers": sizes,
                        "metric": "L2", "precision": ("split-bf16 tcgen05 exemplar tiles" if a.precision == "bf16" else "fp32 tiles") + "; fp32 exact tiers; fp64 near-tie recheck",
+                       "learned": ({k: learned[k] for k in ("k", "train_points", "samples", "positives", "train_s",
+                                                            "final_loss")} if learned else None),
                        "l2_flush": "inputs larger than L2 (points alone are %d MB)" % (w.X.nbytes >> 20),
                        "parallelism": f"replicas x{world}"},
             "edges_per_step": edges // max(a.steps, 1), "roofline": roof, "clocks": clocks,
@@ -325,7 +353,7 @@ def run_gpu(a, rank, world, local):
         barrier()
         c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         c0.record(stream)
-        ne32, st32 = step_device()
+        ne32, st32 = step_device(plain=True)
         c1.record(stream)
         torch.cuda.synchronize()
         ms32 = c0.elapsed_time(c1)

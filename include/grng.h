@@ -131,7 +131,11 @@ grng_status rng_build_exact(grng_index* idx);
 
 /* Insert m new points pts[m][dim] (host or device) so that the stored RNG becomes
  * the RNG of the enlarged set (Algorithm 1 and Stage VII, Sec. 2).  Requires a
- * built RNG. */
+ * built RNG.  The new points get ids n .. n+m-1 and join the finest layer's domains;
+ * every layer keeps its pivots.  Radii, delta_max, every GRNG and the RNG are then
+ * those of a build from scratch on the enlarged set with the same pivots (this
+ * version recomputes them; results are exact, the cost is that of a rebuild).
+ * On failure the index must be destroyed. */
 grng_status rng_insert_batch(grng_index* idx, const float* pts, int64_t m);
 
 /* Copy the RNG edges: ij[cap][2] int32 point indices with i < j, lexicographically

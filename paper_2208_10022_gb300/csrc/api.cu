@@ -130,6 +130,8 @@ struct grng_index {
   bool rng_built = false;
   LevelStats rng_st{};
   double rng_ms = 0, rng_tile_ms = 0, sort_ms = 0;
+  double insert_ms = 0;  // batched insertion totals
+  int64_t insert_batches = 0, inserted = 0;
   DevBuf mlp;            // ranking network parameters (learned shortlist), or empty
   DevBuf rec_f, rec_y;   // recorded training samples of the last RNG build
   int64_t rec_n = 0;
@@ -625,14 +627,49 @@ grng_status grng_mlp_dataset(const grng_index* cix, float* feats, float* labels,
 }
 
 grng_status rng_insert_batch(grng_index* ix, const float* pts, int64_t m) {
-  (void)pts;
-  (void)m;
   if (!ix) {
     g_last_error = "index is NULL";
     return GRNG_EINVAL;
   }
-  g_last_error = "incremental insertion is not built yet";
-  return GRNG_ENOTIMPL;
+  return guarded(ix, [&] {
+    if (!pts || m < 1) fail(GRNG_EINVAL, "need pts and m >= 1");
+    if (!ix->rng_built) fail(GRNG_ESTATE, "the RNG is not built");
+    if (ix->n + m >= (int64_t)1 << 31) fail(GRNG_EINVAL, "n + m must stay below 2^31");
+    cudaStream_t s = ix->stream;
+    Timer tm(s);
+    // the enlarged point set: old rows, then the batch (ids n .. n+m-1)
+    const int64_t n0 = ix->n, n1 = n0 + m;
+    DevBuf X2, ids2;
+    GRNG_CUDA(X2.alloc((size_t)n1 * ix->Dp * 4));
+    GRNG_CUDA(cudaMemcpyAsync(X2.p, ix->X.p, (size_t)n0 * ix->Dp * 4, cudaMemcpyDeviceToDevice, s));
+    float* Xnew = X2.as<float>() + n0 * ix->Dp;
+    GRNG_CUDA(cudaMemsetAsync(Xnew, 0, (size_t)m * ix->Dp * 4, s));
+    GRNG_CUDA(cudaMemcpy2DAsync(Xnew, (size_t)ix->Dp * 4, pts, (size_t)ix->D * 4, (size_t)ix->D * 4, (size_t)m,
+                                cudaMemcpyDefault, s));
+    GRNG_CUDA(ids2.alloc((size_t)n1 * 4));
+    iota_kernel<<<nblk(n1), 256, 0, s>>>(ids2.as<int32_t>(), n1); note_launch();
+    GRNG_CUDA(cudaGetLastError());
+    GRNG_CUDA(cudaStreamSynchronize(s));
+    ix->X = std::move(X2);
+    ix->ids = std::move(ids2);
+    ix->n = n1;
+    // Every layer keeps its pivots; the batch joins the finest domains, radii and
+    // delta_max follow (Eq. 2), every GRNG and the RNG are recomputed over the enlarged
+    // set, so the stored graphs are those of a build from scratch on it.
+    const int L = (int)ix->layers.size();
+    std::vector<std::vector<int32_t>> piv(L);
+    for (int l = 0; l < L; ++l) piv[l] = ix->layers[l].piv_h;
+    auto call = [&](grng_status st) {
+      if (st != GRNG_OK) fail(st, g_last_error);
+    };
+    for (int l = L - 1; l >= 0; --l)
+      call(grng_build_layer(ix, l, piv[l].data(), (int32_t)piv[l].size(), nullptr, nullptr, nullptr));
+    for (int l = 0; l < L; ++l) call(grng_link_pivots(ix, l, nullptr, nullptr, nullptr, 0, nullptr));
+    call(rng_build_exact(ix));
+    ix->insert_ms += tm.stop();
+    ix->insert_batches += 1;
+    ix->inserted += m;
+  });
 }
 
 grng_status rng_edges(const grng_index* cix, int32_t* ij, int64_t cap, int64_t* n_edges) {
@@ -682,8 +719,11 @@ grng_status grng_stats(const grng_index* cix, char* json, size_t cap) {
     level_json(js, "grng", ly.st);
     js += "}";
   }
-  snprintf(buf, sizeof(buf), "],\"rng_built\":%d,\"n_edges\":%lld,\"rng_ms\":%.4f,\"rng_tile_ms\":%.4f,",
-           (int)ix->rng_built, (long long)ix->n_edges, ix->rng_ms, ix->rng_tile_ms);
+  snprintf(buf, sizeof(buf),
+           "],\"rng_built\":%d,\"n_edges\":%lld,\"rng_ms\":%.4f,\"rng_tile_ms\":%.4f,"
+           "\"insert\":{\"batches\":%lld,\"points\":%lld,\"ms\":%.4f},",
+           (int)ix->rng_built, (long long)ix->n_edges, ix->rng_ms, ix->rng_tile_ms, (long long)ix->insert_batches,
+           (long long)ix->inserted, ix->insert_ms);
   js += buf;
   level_json(js, "rng", ix->rng_st);
   js += "}";
