@@ -709,9 +709,17 @@ __global__ void __launch_bounds__(256, 4) tier3_kernel(Tier3Params p) {
       // test of one ancestor node c of level a from its keys; on survival, par = the
       // range of its children with its bounds
       auto test_node = [&](int a, int c, float kg, float kq, Front& par) -> bool {
+        const float R = p.anc.Rhi[a][c];
+        if (p.metric == L2) {
+          // the same pruning in key units, without square roots: d(c,g) >= T1 >= t1d + R
+          // (T1 carries 8 rounding units of margin, its square 4 more), so no node of
+          // the domain satisfies the first condition; likewise for o
+          const float T1 = (t1d + R) * (1.0f + 8.0f * u2), T2 = (t2d + R) * (1.0f + 8.0f * u2);
+          if (lo_b(kg, e) >= T1 * T1 * (1.0f + 4.0f * u2) || lo_b(kq, e) >= T2 * T2 * (1.0f + 4.0f * u2))
+            return false;
+        }
         const float dg = dist_lo(kg, p.metric, e);
         const float dq = dist_lo(kq, p.metric, e);
-        const float R = p.anc.Rhi[a][c];
         bool skip = (dg - R - u2 * (dg + R) >= t1d) || (dq - R - u2 * (dq + R) >= t2d);
         if (!skip) {  // the whole domain lies within the exclusion ball of g or of o
           const float dgh = dist_hi(kg, p.metric, e), dqh = dist_hi(kq, p.metric, e);
@@ -819,9 +827,11 @@ __global__ void __launch_bounds__(256, 4) tier3_kernel(Tier3Params p) {
           }
           __syncthreads();
           if (a == 0 && probe && s_best != ~0ull) {
-            // ---- greedy descent to the domain nearest c*, whose nodes are tested now ----
-            if (warp == 0) {
-              int cn = (int)(s_best & 0xffffffffu);
+            // ---- greedy descents towards c*, whose final domains' nodes are tested now:
+            // warp w starts from the top-level node nearest c* among those its lanes
+            // scanned (the nearest overall is one of them) ----
+            if (best != ~0ull) {
+              int cn = (int)(best & 0xffffffffu);
               int lvl = 0;
               bool ok = true;
               while (lvl < p.anc.n - 1) {
