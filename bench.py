@@ -53,6 +53,22 @@ def parse():
     return ap.parse_args()
 
 
+def max_over_ranks(ms, pg, device):
+    """The slowest rank's time (all ranks get it); `pg` is torch.distributed or None."""
+    if pg is None:
+        return float(ms)
+    import torch
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_rate(edges_per_rank, world, ms):
+    """Whole-job throughput of replicas: every rank builds the same workload, so the job
+    produced edges_per_rank x world edges in the slowest rank's time."""
+    return edges_per_rank * world / (ms / 1000.0)
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -285,12 +301,8 @@ def run_gpu(a, rank, world, local):
     torch.cuda.synchronize()
     clocks = clk.stop()
     launches1 = stats["kernel_launches"]  # counter after the last timed step
-    ms = e0.elapsed_time(e1)
-    if pg:
-        t = torch.tensor([ms], device="cuda")
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        ms = float(t.item())
-    value = edges * world / (ms / 1000.0)
+    ms = max_over_ranks(e0.elapsed_time(e1), pg, "cuda")
+    value = aggregate_rate(edges, world, ms)
 
     # end to end through the C ABI with host buffers: H2D of points and pivots, D2H of edges
     e2e = None
@@ -317,12 +329,8 @@ def run_gpu(a, rank, world, local):
             ix.close()
         f1.record(stream)
         torch.cuda.synchronize()
-        ems = f0.elapsed_time(f1)
-        if pg:
-            t = torch.tensor([ems], device="cuda")
-            pg.all_reduce(t, op=pg.ReduceOp.MAX)
-            ems = float(t.item())
-        e2e = {"value": e_edges * world / (ems / 1000.0), "unit": UNIT,
+        ems = max_over_ranks(f0.elapsed_time(f1), pg, "cuda")
+        e2e = {"value": aggregate_rate(e_edges, world, ems), "unit": UNIT,
                "h2d_bytes_per_step": int(w.X.nbytes + sum(l.nbytes for l in w.layers)),
                "d2h_bytes_per_step": int(8 * (e_edges // max(a.steps, 1)))}
 
