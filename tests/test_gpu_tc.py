@@ -69,3 +69,14 @@ def test_bf16_build_subsample_mixture():
     got = {tuple(e) for e in out["edges"].tolist()}
     want = {tuple(e) for e in oracle.rng_brute(s.X).tolist()}
     assert got == want, len(got ^ want)
+
+
+def test_bf16_build_equals_fp32_build_many_tiles():
+    # 20,000 points: 157 blocks, 24,649 tiles per sweep, a ragged last block; every tile of
+    # the pipelined tensor-core sweep against the FP32 CUDA-core build (itself oracle-checked)
+    w = wl.make("lin96", n=20000)
+    _, o32 = g.build_all(w.X, w.layers, precision=g.FP32)
+    ix, o16 = g.build_all(w.X, w.layers, precision=g.BF16)
+    assert np.array_equal(o16["edges"], o32["edges"])
+    st = ix.stats()["rng"]
+    assert st["kernel_ms"]["tiles"] > 0
