@@ -629,6 +629,8 @@ __device__ __forceinline__ void group_keys(const float* __restrict__ pk, const f
   b = sb;
 }
 
+#define T3_T 256        // threads per CTA (one pair per CTA)
+#define T3_MINB 4      // CTAs per SM (64 registers a thread)
 #define T3_LIST 1024   // nodes gathered for one round of distance tests
 #define T3_MKW 2048    // words of a level's candidate bitmask (levels of at most 65,536 nodes)
 
@@ -645,13 +647,13 @@ __device__ __forceinline__ void group_keys(const float* __restrict__ pk, const f
 // coordinates as whole 128-byte lines.  For L2, after the top level one greedy descent
 // towards the centre c* of the ball around the G-lune tests the nodes of a single
 // domain first: a blocker found there ends the pair early.
-__global__ void __launch_bounds__(256, 4) tier3_kernel(Tier3Params p) {
+__global__ void __launch_bounds__(T3_T, T3_MINB) tier3_kernel(Tier3Params p) {
   extern __shared__ __align__(16) float sm3[];
   float* gs = sm3;
   float* os = gs + p.Dp;
-  __shared__ Front s_rg[256];
-  __shared__ int s_pre[257];
-  __shared__ int s_wsum[8];
+  __shared__ Front s_rg[T3_T];
+  __shared__ int s_pre[T3_T + 1];
+  __shared__ int s_wsum[T3_T / 32];
   __shared__ int s_list[T3_LIST];
   __shared__ unsigned s_mk[2][T3_MKW];
   __shared__ unsigned long long s_best;
@@ -743,7 +745,7 @@ __global__ void __launch_bounds__(256, 4) tier3_kernel(Tier3Params p) {
       };
       // distance tests of nodes list[0..nl) (all threads; uniform call)
       auto test_nodes = [&](const int* list, int nl) {
-        for (int i = gid; i < nl; i += 32) {
+        for (int i = gid; i < nl; i += T3_T / 8) {
           // one decision per group: its lanes must all reach the shuffles
           if (__shfl_sync(gmask, *(volatile int*)&s_block, 0, 8)) break;
           const int k = list[i];
@@ -779,7 +781,7 @@ __global__ void __launch_bounds__(256, 4) tier3_kernel(Tier3Params p) {
           const float* rg_ = p.atab + g * p.tabw + p.anc.toff[a];
           const float* ro_ = p.atab + o * p.tabw + p.anc.toff[a];
           unsigned long long best = ~0ull;
-          for (int c0 = 0; c0 < ma; c0 += 4 * 256) {
+          for (int c0 = 0; c0 < ma; c0 += 4 * T3_T) {
             const int c = c0 + 4 * tid;
             unsigned vm = 0;  // candidate nodes among c .. c+3
 #pragma unroll
@@ -890,8 +892,8 @@ __global__ void __launch_bounds__(256, 4) tier3_kernel(Tier3Params p) {
         const bool leaf = a == p.anc.n;
         __syncthreads();  // every thread has read the previous level's count
         if (tid == 0) { s_nxt_n = 0; s_nl = 0; }
-        for (int cb = 0; cb < ncur; cb += 256) {
-          // ---- flatten 256 ranges: s_pre = exclusive prefix of their lengths ----
+        for (int cb = 0; cb < ncur; cb += T3_T) {
+          // ---- flatten T3_T ranges: s_pre = exclusive prefix of their lengths ----
           __syncthreads();
           int len = 0;
           if (cb + tid < ncur) {
@@ -912,9 +914,9 @@ __global__ void __launch_bounds__(256, 4) tier3_kernel(Tier3Params p) {
           s_pre[tid + 1] = woff + inc;
           if (tid == 0) s_pre[0] = 0;
           __syncthreads();
-          const int total = s_pre[256];
-          const int nrg = ncur - cb < 256 ? ncur - cb : 256;
-          for (int j0 = 0; j0 < total; j0 += 256) {
+          const int total = s_pre[T3_T];
+          const int nrg = ncur - cb < T3_T ? ncur - cb : T3_T;
+          for (int j0 = 0; j0 < total; j0 += T3_T) {
             const int j = j0 + tid;
             bool keep = false;
             int c = -1;
@@ -958,7 +960,7 @@ __global__ void __launch_bounds__(256, 4) tier3_kernel(Tier3Params p) {
               __syncthreads();
               const int nl = s_nl;
               // ---- distance tests once the list is nearly full, or at the end ----
-              if (nl > T3_LIST - 256 || (nl > 0 && j0 + 256 >= total && cb + 256 >= ncur)) {
+              if (nl > T3_LIST - T3_T || (nl > 0 && j0 + T3_T >= total && cb + T3_T >= ncur)) {
                 test_nodes(s_list, nl);
                 __syncthreads();
                 if (tid == 0) s_nl = 0;
@@ -986,7 +988,7 @@ __global__ void __launch_bounds__(256, 4) tier3_kernel(Tier3Params p) {
         }
       }
       if (all) {  // frontier too large: test every node (still exact)
-        for (int i = gid; i < (int)p.n; i += 32) {
+        for (int i = gid; i < (int)p.n; i += T3_T / 8) {
           if (__shfl_sync(gmask, *(volatile int*)&s_block, 0, 8)) break;
           if (i == g || i == o) continue;
           float ka, kb;
@@ -1656,7 +1658,7 @@ void run_level(const LevelIn& in, LevelOut& out, LevelStats& st, cudaStream_t s,
       t3.pend = pend.as<int2>(); t3.pflag = pflag.as<int>(); t3.slot0 = (int64_t)npend;
       t3.amb = amb.as<int2>(); t3.amb_cnt = dc + 19; t3.amb_cap = amb_cap;
       t3.anc = in.anc;
-      int grid3 = (int)std::min<unsigned long long>(nun2, 4ull * num_sms());
+      int grid3 = (int)std::min<unsigned long long>(nun2, (unsigned long long)T3_MINB * num_sms());
       t3.fcap = 1 << 15;
       GRNG_CUDA(fbuf.alloc((size_t)grid3 * 2 * t3.fcap * sizeof(Front)));
       t3.fbuf = fbuf.as<Front>();
@@ -1714,7 +1716,7 @@ void run_level(const LevelIn& in, LevelOut& out, LevelStats& st, cudaStream_t s,
       GRNG_CUDA(cudaEventCreate(&f0));
       GRNG_CUDA(cudaEventCreate(&f1));
       GRNG_CUDA(cudaEventRecord(f0, s));
-      tier3_kernel<<<grid3, 256, 2 * in.Dp * 4, s>>>(t3); note_launch();
+      tier3_kernel<<<grid3, T3_T, 2 * in.Dp * 4, s>>>(t3); note_launch();
       GRNG_CUDA(cudaGetLastError());
       GRNG_CUDA(cudaEventRecord(f1, s));
       GRNG_CUDA(cudaEventSynchronize(f1));
