@@ -585,8 +585,19 @@ struct Tier3Params {
   int64_t tabw;
   int fcap;
   int dense;              // ancestor levels scanned densely (needs atab, levels <= 65,536 nodes)
+  int mkw;                // words of one candidate bitmask (dynamic shared memory, dense scans)
   unsigned long long* stats;  // [0] frontier overflows, [1] nodes tested, [2] pairs blocked, [3] by the descent
 };
+
+// asynchronous 16-byte copy global -> shared (src_bytes < 16: the rest is zero-filled, 0: no read)
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, int src_bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+               "l"(src), "r"(src_bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+// wait until at most one committed group of this thread is still in flight
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 
 // lower / upper bound of the distance whose FP32 key is k
 __device__ __forceinline__ float dist_lo(float k, int metric, Err e) {
@@ -651,11 +662,13 @@ __global__ void __launch_bounds__(T3_T, T3_MINB) tier3_kernel(Tier3Params p) {
   extern __shared__ __align__(16) float sm3[];
   float* gs = sm3;
   float* os = gs + p.Dp;
+  unsigned* mk0 = reinterpret_cast<unsigned*>(os + p.Dp);  // two bitmasks of p.mkw words
+  unsigned* mk1 = mk0 + p.mkw;
   __shared__ Front s_rg[T3_T];
   __shared__ int s_pre[T3_T + 1];
   __shared__ int s_wsum[T3_T / 32];
   __shared__ int s_list[T3_LIST];
-  __shared__ unsigned s_mk[2][T3_MKW];
+  __shared__ float4 s_pf[2][2][T3_T];  // keys of the next 4 nodes per thread, copied ahead (cp.async)
   __shared__ unsigned long long s_best;
   __shared__ int s_block, s_nxt_n, s_nl;
   __shared__ float s_v;
@@ -710,8 +723,7 @@ __global__ void __launch_bounds__(T3_T, T3_MINB) tier3_kernel(Tier3Params p) {
 
       // test of one ancestor node c of level a from its keys; on survival, par = the
       // range of its children with its bounds
-      auto test_node = [&](int a, int c, float kg, float kq, Front& par) -> bool {
-        const float R = p.anc.Rhi[a][c];
+      auto test_node = [&](int a, int c, float kg, float kq, float R, Front& par) -> bool {
         if (p.metric == L2) {
           // the same pruning in key units, without square roots: d(c,g) >= T1 >= t1d + R
           // (T1 carries 8 rounding units of margin, its square 4 more), so no node of
@@ -771,8 +783,8 @@ __global__ void __launch_bounds__(T3_T, T3_MINB) tier3_kernel(Tier3Params p) {
         for (int a = 0; a < p.anc.n; ++a) {
           const bool last = a == p.anc.n - 1;
           const int ma = (int)p.anc.m[a];
-          const unsigned* mk_in = s_mk[a & 1];
-          unsigned* mk_out = s_mk[(a + 1) & 1];
+          const unsigned* mk_in = (a & 1) ? mk1 : mk0;
+          unsigned* mk_out = (a & 1) ? mk0 : mk1;
           __syncthreads();
           if (!last)
             for (int w = tid; w < (int)((p.anc.m[a + 1] + 31) >> 5); w += blockDim.x) mk_out[w] = 0u;
@@ -781,23 +793,43 @@ __global__ void __launch_bounds__(T3_T, T3_MINB) tier3_kernel(Tier3Params p) {
           const float* rg_ = p.atab + g * p.tabw + p.anc.toff[a];
           const float* ro_ = p.atab + o * p.tabw + p.anc.toff[a];
           unsigned long long best = ~0ull;
-          for (int c0 = 0; c0 < ma; c0 += 4 * T3_T) {
-            const int c = c0 + 4 * tid;
+          // the keys of a thread's 4 nodes arrive by asynchronous copies one round ahead
+          const int nch = (ma + 4 * T3_T - 1) / (4 * T3_T);
+          const float* Ra = p.anc.Rhi[a];
+          auto issue = [&](int it) {
+            const int c = it * 4 * T3_T + 4 * tid;
+            const bool in = c < ma;  // the table's rows are padded to 4 columns per level
+            cp_async16(&s_pf[it & 1][0][tid], rg_ + (in ? c : 0), in ? 16 : 0);
+            cp_async16(&s_pf[it & 1][1][tid], ro_ + (in ? c : 0), in ? 16 : 0);
+            cp_async_commit();
+          };
+          issue(0);
+          for (int it = 0; it < nch; ++it) {
+            if (it + 1 < nch) issue(it + 1);
+            else cp_async_commit();  // an empty group keeps the count uniform
+            cp_async_wait1();
+            const int c = it * 4 * T3_T + 4 * tid;
             unsigned vm = 0;  // candidate nodes among c .. c+3
 #pragma unroll
             for (int u = 0; u < 4; ++u)
               if (c + u < ma && (a == 0 || ((mk_in[(c + u) >> 5] >> ((c + u) & 31)) & 1u))) vm |= 1u << u;
-            float kgv[4], kqv[4];
+            const float4 G4 = s_pf[it & 1][0][tid], O4 = s_pf[it & 1][1][tid];
+            const float kgv[4] = {G4.x, G4.y, G4.z, G4.w}, kqv[4] = {O4.x, O4.y, O4.z, O4.w};
+            float Rv[4] = {0.0f, 0.0f, 0.0f, 0.0f};
             if (vm) {
-              const float4 G4 = __ldg(reinterpret_cast<const float4*>(rg_ + c));
-              const float4 O4 = __ldg(reinterpret_cast<const float4*>(ro_ + c));
-              kgv[0] = G4.x; kgv[1] = G4.y; kgv[2] = G4.z; kgv[3] = G4.w;
-              kqv[0] = O4.x; kqv[1] = O4.y; kqv[2] = O4.z; kqv[3] = O4.w;
+              if (c + 3 < ma) {
+                const float4 R4 = __ldg(reinterpret_cast<const float4*>(Ra + c));
+                Rv[0] = R4.x; Rv[1] = R4.y; Rv[2] = R4.z; Rv[3] = R4.w;
+              } else {
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                  if (c + u < ma) Rv[u] = Ra[c + u];
+              }
             }
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
               Front par;
-              const bool keep = ((vm >> u) & 1u) && test_node(a, c + u, kgv[u], kqv[u], par);
+              const bool keep = ((vm >> u) & 1u) && test_node(a, c + u, kgv[u], kqv[u], Rv[u], par);
               if (keep && a == 0 && probe) {  // Stewart estimate of |c - c*|^2
                 const float s2 = fmaxf((1.0f - lam) * kgv[u] + lam * kqv[u] - lam * (1.0f - lam) * v, 0.0f);
                 const unsigned long long key = ((unsigned long long)__float_as_uint(s2) << 32) | (unsigned)(c + u);
@@ -948,7 +980,7 @@ __global__ void __launch_bounds__(T3_T, T3_MINB) tier3_kernel(Tier3Params p) {
                   kg = key32(pc, gs, p.Dp, p.metric);
                   kq = key32(pc, os, p.Dp, p.metric);
                 }
-                keep = test_node(a, c, kg, kq, par);
+                keep = test_node(a, c, kg, kq, p.anc.Rhi[a][c], par);
               }
             }
             const unsigned bm = __ballot_sync(FULLMASK, keep);
@@ -1666,6 +1698,7 @@ void run_level(const LevelIn& in, LevelOut& out, LevelStats& st, cudaStream_t s,
       t3.atab = nullptr;
       t3.tabw = 0;
       t3.dense = 0;
+      t3.mkw = 0;
       if (in.grng && in.anc.n > 0) {
         // pivot layers: node x ancestor keys once, instead of per pair
         int64_t w = 0;  // each level's columns start on a 16-byte boundary
@@ -1676,7 +1709,11 @@ void run_level(const LevelIn& in, LevelOut& out, LevelStats& st, cudaStream_t s,
         t3.atab = atab.as<float>();
         t3.tabw = w;
         t3.dense = 1;
-        for (int a = 1; a < in.anc.n; ++a) t3.dense &= in.anc.m[a] <= 32 * T3_MKW;
+        for (int a = 1; a < in.anc.n; ++a) {
+          t3.dense &= in.anc.m[a] <= 32 * T3_MKW;
+          t3.mkw = std::max<int>(t3.mkw, (int)((in.anc.m[a] + 31) / 32));
+        }
+        if (!t3.dense) t3.mkw = 0;
       }
       t3.stats = dc + 34;
       GRNG_CUDA(cudaMemsetAsync(dc + 34, 0, 4 * sizeof(unsigned long long), s));
@@ -1716,7 +1753,7 @@ void run_level(const LevelIn& in, LevelOut& out, LevelStats& st, cudaStream_t s,
       GRNG_CUDA(cudaEventCreate(&f0));
       GRNG_CUDA(cudaEventCreate(&f1));
       GRNG_CUDA(cudaEventRecord(f0, s));
-      tier3_kernel<<<grid3, T3_T, 2 * in.Dp * 4, s>>>(t3); note_launch();
+      tier3_kernel<<<grid3, T3_T, 2 * in.Dp * 4 + 2 * (size_t)t3.mkw * 4, s>>>(t3); note_launch();
       GRNG_CUDA(cudaGetLastError());
       GRNG_CUDA(cudaEventRecord(f1, s));
       GRNG_CUDA(cudaEventSynchronize(f1));
