@@ -292,23 +292,36 @@ __global__ void __launch_bounds__(256, 1) tc_sweep_kernel(TcParams p) {
       const float nxr = nx[r];
       float m1 = INF, m2 = INF;
       int a1 = -1, a2 = -1;
+      // lower tiles feed only the neighbour lists; full tiles need no per-key mask
+      const bool full = vr && nc == 128 && !diag;
 #pragma unroll 1
       for (int q = 0; q < 8; ++q) {
         float g[8], vv[8];
         tmem_ld8(trow + (uint32_t)(q * 8), g);
         unsigned pm = 0;
+        if (!filt) {
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          const int c = cb + q * 8 + j;
-          float v = nxr + ny[c] - 2.0f * g[j];
-          if (!vr || c >= nc || (diag && c == r)) v = INF;
-          vv[j] = v;
-          T16[r * 130 + c] = __float2half_ru(v);
-          if (v < m2) {
-            if (v < m1) { m2 = m1; a2 = a1; m1 = v; a1 = c; }
-            else { m2 = v; a2 = c; }
+          for (int j = 0; j < 8; ++j) {
+            const int c = cb + q * 8 + j;
+            float v = nxr + ny[c] - 2.0f * g[j];
+            if (!full && (!vr || c >= nc)) v = INF;
+            vv[j] = v;
+            if (v < thr) pm |= 1u << j;
           }
-          if (v < thr) pm |= 1u << j;
+        } else {
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            const int c = cb + q * 8 + j;
+            float v = nxr + ny[c] - 2.0f * g[j];
+            if (!full && (!vr || c >= nc || (diag && c == r))) v = INF;
+            vv[j] = v;
+            T16[r * 130 + c] = __float2half_ru(v);
+            if (v < m2) {
+              if (v < m1) { m2 = m1; a2 = a1; m1 = v; a1 = c; }
+              else { m2 = v; a2 = c; }
+            }
+            if (v < thr) pm |= 1u << j;
+          }
         }
         while (pm) {
           const int j = __ffs(pm) - 1;
@@ -364,12 +377,26 @@ __global__ void __launch_bounds__(256, 1) tc_sweep_kernel(TcParams p) {
         // and are >= px in every upper tile (nodes are sorted by parent)
         uint32_t gw[5] = {0u, 0u, 0u, 0u, 0u};
         int wlo = 0, nw = 0;
+        bool all_linked = !p.gpar;  // every y parent equal to or linked with px: no per-pair test
         if (p.gpar && vr) {
           wlo = parY[0] >> 5;
           nw = (parY[nc - 1] >> 5) - wlo + 1;
 #pragma unroll
           for (int k = 0; k < 5; ++k)
             if (k < nw) gw[k] = __ldg(p.gpar + (int64_t)px * p.gpar_words + wlo + k);
+          if (nw <= 5 && parY[0] > px) {
+            // bits parY[0] .. parY[nc-1] of px's row, relative to word wlo
+            const int b0 = parY[0] - (wlo << 5), b1 = parY[nc - 1] - (wlo << 5);
+            all_linked = true;
+#pragma unroll
+            for (int k = 0; k < 5; ++k) {
+              if (k >= nw) break;
+              const int lo = max(b0 - 32 * k, 0), hi = min(b1 - 32 * k, 31);
+              if (lo > hi) continue;
+              const uint32_t msk = (hi - lo == 31) ? ~0u : (((1u << (hi - lo + 1)) - 1u) << lo);
+              all_linked = all_linked && ((gw[k] & msk) == msk);
+            }
+          }
         }
 #pragma unroll 1
         for (int q = 0; q < 8; ++q) {
@@ -379,7 +406,7 @@ __global__ void __launch_bounds__(256, 1) tc_sweep_kernel(TcParams p) {
           for (int j = 0; j < 8; ++j) {
             const int c = cb + q * 8 + j;
             bool cand = vr && c < nc && (!diag || c > r);
-            if (cand && p.gpar) {
+            if (cand && !all_linked) {
               const int qy = parY[c];
               if (qy != px) {
                 const int b = qy - (wlo << 5);
