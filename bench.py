@@ -50,6 +50,10 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=12000, help="points of the oracle's bounded sample")
+    ap.add_argument("--insert", type=int, default=0, metavar="B",
+                    help="instead of the build benchmark: insert B batches of uneven size (log-uniform in "
+                         "[1,000, 65,536] points, scaled to --n) into an index built on the rest, and print "
+                         "points/s and per-batch latency")
     return ap.parse_args()
 
 
@@ -380,11 +384,57 @@ def run_gpu(a, rank, world, local):
     return 0
 
 
+def run_insert(a, rank):
+    """Batched insertion (rng_insert_batch): the index is built on the first points of the
+    workload, then the batches arrive in order; every batch is timed with CUDA events."""
+    import numpy as np
+    import torch
+
+    import paper_2208_10022_gb300 as g
+    from paper_2208_10022_gb300 import build as gb
+    from paper_2208_10022_gb300 import workloads as wl
+    gb.build()
+    w = wl.make(a.kind, n=a.n)
+    scale = w.n / 2_000_000
+    sizes = [max(1, int(b * scale)) for b in wl.insertion_batches(a.insert)]
+    n0 = w.n - sum(sizes)
+    rng = np.random.default_rng(4001)
+    layers = [np.sort(rng.choice(n0, len(l), replace=False)).astype(np.int32) for l in w.layers[-1:]]
+    sub = []
+    for l in reversed(w.layers[:-1]):  # nested coarser layers drawn from the finer one
+        sub.insert(0, np.sort(rng.choice(layers[0] if not sub else sub[0], len(l), replace=False)).astype(np.int32))
+    layers = sub + layers
+    prec = g.BF16 if a.precision == "bf16" else g.FP32
+    ix, _ = g.build_all(w.X[:n0], layers, precision=prec)
+    stream = torch.cuda.current_stream()
+    lat, at = [], n0
+    for b in sizes:
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ix.rng_insert_batch(w.X[at:at + b])
+        e1.record(stream)
+        torch.cuda.synchronize()
+        lat.append(e0.elapsed_time(e1))
+        at += b
+    tot = sum(lat)
+    line = {"metric": "batched insertion points/s", "value": sum(sizes) / (tot / 1000.0), "unit": "points/s",
+            "higher_is_better": True, "n_gpus": 1, "batches": len(sizes), "points": int(sum(sizes)),
+            "base_points": int(n0), "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "edges_after": int(ix.n_edges()), "method": "pivots kept; radii, GRNGs and RNG recomputed per batch",
+            "config": {"workload": a.kind, "n": int(w.n), "layers": [len(l) for l in layers],
+                       "batch_sizes": sizes, "precision": a.precision}}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     a = parse()
     rank, world, local = dist_env()
     if a.impl == "reference":
         return run_reference(a, rank, world)
+    if a.insert:
+        return run_insert(a, rank)
     return run_gpu(a, rank, world, local)
 
 
