@@ -165,6 +165,7 @@ def kernel_rooflines(stats, n, D, precision, peaks, sms):
             G["tier3_nodes_tested"] * 2 * 2 * D, "Gop/s", alu, alu_src)
     out.sort(key=lambda r: -r["launch_ms"])
     top = dict(out[0])
+    top["traffic"] = measured_traffic(top["kernel"], n)
     top["others"] = [{k: r[k] for k in ("kernel", "bound", "achieved", "unit", "frac", "launch_ms")} for r in out[1:6]]
     return top
 
@@ -186,6 +187,25 @@ def train_shortlist(g, wl, kind, n_train=200000, k=8):
     P, loss = g.mlp_train(g.mlp_init(7004), F[perm], y[perm], wts[perm], epochs=6, batch=4096, lr=1e-3)
     return {"params": P, "k": k, "train_points": n_train, "samples": int(F.shape[0]),
             "positives": int(y.sum()), "train_s": time.perf_counter() - t0, "final_loss": loss}
+
+
+# Revision tags of the kernels whose DRAM traffic was captured with ncu (profiles/*traffic*.json);
+# a kernel changed since its capture gets a new tag here, and its traffic reads as null.
+KERNEL_REVS = {"tier3_kernel": "tier3-r6"}
+
+
+def measured_traffic(kernel, n):
+    """DRAM bytes per launch of `kernel` at n points from a committed ncu capture, or None."""
+    import glob
+    for f in glob.glob(os.path.join(ROOT, "profiles", "*traffic*.json")):
+        try:
+            t = json.load(open(f))
+        except ValueError:
+            continue
+        base = t.get("kernel", "").split(" ")[0]
+        if t.get("kernel") == kernel and t.get("n") == n and KERNEL_REVS.get(base) == t.get("rev"):
+            return t.get("dram_bytes_per_launch")
+    return None
 
 
 def load_peaks():
