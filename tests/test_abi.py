@@ -13,7 +13,7 @@ def _declared():
         if h.endswith(".h"):
             src = open(os.path.join(ROOT, "include", h)).read()
             src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-            names |= set(re.findall(r"^\s*(?:grng_status|void|const char\*)\s+(\w+)\s*\(", src, flags=re.M))
+            names |= set(re.findall(r"^\s*(?:grng_status|void|const char\*|int64_t)\s+(\w+)\s*\(", src, flags=re.M))
     return names
 
 
@@ -35,3 +35,23 @@ def test_binding_raises_without_library(monkeypatch, tmp_path):
     monkeypatch.setattr(g, "_lib", None)
     with pytest.raises(ImportError):
         g.lib()
+
+
+def test_learned_entry_points_host_checks():
+    """Parameter count agrees with the oracle; invalid arguments are refused on the host
+    (no device work is started, so this runs without a GPU)."""
+    import ctypes
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import oracle
+    import paper_2208_10022_gb300 as g
+    L = g.lib()
+    assert "grng_mlp_nparams" in _declared()
+    assert g.mlp_nparams() == oracle.mlp_nparams() == 20865
+    assert L.grng_mlp_score(None, None, 0, None) == g.GRNG_EINVAL
+    loss = ctypes.c_float(0.0)
+    assert L.grng_mlp_loss_grad(None, None, None, None, 0, ctypes.byref(loss), None) == g.GRNG_EINVAL
+    assert L.grng_mlp_train(None, None, None, 0, 1, 1, ctypes.c_float(1e-3), None, None) == g.GRNG_EINVAL
+    assert L.grng_mlp_dataset(None, None, None, 0, None) == g.GRNG_EINVAL
+    assert b"must" in L.grng_last_error() or b"NULL" in L.grng_last_error()
