@@ -229,6 +229,11 @@ def cpu_baseline(kind, n_sample, seed=3002):
                       f"({len(E)} edges in {dt:.2f} s)", "seconds": dt, "edges": int(len(E))}
 
 
+def workload_name(kind, n, D, sizes):
+    return (f"{kind}: {n:,} x {D} FP32, intrinsic dim 8, L2, nested random pivot layers "
+            f"{'/'.join(str(s) for s in sizes)}")
+
+
 def run_reference(a, rank, world):
     if rank != 0:
         return 0
@@ -248,7 +253,11 @@ def run_reference(a, rank, world):
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": a.gpus, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": 1000 * tot / max(a.steps, 1), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"{a.kind}: {n} x {D}, layers {sizes}", "oracle_sample_points": a.cpu_sample},
+            "config": {"workload": workload_name(a.kind, n, D, wl.scaled_layer_sizes(a.kind, n)),
+                       "n": n, "dim": D, "metric": "L2",
+                       "oracle_sample_points": a.cpu_sample,
+                       "note": "each step times the FP64 oracle (brute force over all triples) on a seeded "
+                               "sample of this workload's generator"},
             "cpu_baseline": {k: last[k] for k in ("kind", "cores", "sample")} | {"value": v, "unit": UNIT},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -367,8 +376,7 @@ def run_gpu(a, rank, world, local):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
             "ms_per_step": ms / a.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "bf16+f32" if a.precision == "bf16" else "f32", "data": "synthetic",
-            "config": {"workload": f"{a.kind}: {n:,} x {D} FP32, intrinsic dim 8, L2, nested random pivot layers "
-                                   f"{'/'.join(str(s) for s in sizes)}", "n": n, "dim": D, "layers": sizes,
+            "config": {"workload": workload_name(a.kind, n, D, sizes), "n": n, "dim": D, "layers": sizes,
                        "metric": "L2", "precision": ("split-bf16 tcgen05 exemplar tiles" if a.precision == "bf16" else "fp32 tiles") + "; fp32 exact tiers; fp64 near-tie recheck",
                        "learned": ({k: learned[k] for k in ("k", "train_points", "samples", "positives", "train_s",
                                                             "final_loss")} if learned else None),

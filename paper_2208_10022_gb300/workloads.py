@@ -91,6 +91,12 @@ def nested_pivots(n: int, sizes, seed: int):
     return layers
 
 
+def scaled_layer_sizes(kind: str, n: int):
+    """Layer sizes of generator `kind` at n points: the full sizes scaled by n / N (at least 2)."""
+    N0, _, sizes0, _, _ = SPECS[kind]
+    return [max(2, int(round(s * n / N0))) for s in sizes0]
+
+
 def make(kind: str, n: int | None = None, metric: int = L2, layer_sizes=None,
          data_seed: int | None = None, pivot_seed: int | None = None) -> Workload:
     """A workload of generator `kind`; with n smaller than the full size, the layer
@@ -98,7 +104,7 @@ def make(kind: str, n: int | None = None, metric: int = L2, layer_sizes=None,
     N0, _, sizes0, ds, ps = SPECS[kind]
     n = N0 if n is None else int(n)
     if layer_sizes is None:
-        layer_sizes = [max(2, int(round(s * n / N0))) for s in sizes0]
+        layer_sizes = scaled_layer_sizes(kind, n)
     X = gen_points(kind, n, ds if data_seed is None else data_seed)
     layers = nested_pivots(n, layer_sizes, ps if pivot_seed is None else pivot_seed)
     return Workload(name=f"{kind}-{n}", X=X, layers=layers, metric=metric)
