@@ -325,11 +325,10 @@ def run_gpu(a, rank, world, local):
     clk = Clocks(local)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    tile_ms, edges, stats = [], 0, None
+    edges, stats = 0, None
     for _ in range(a.steps):
         ne, stats = step_device()
         edges += ne
-        tile_ms.append(stats["rng_tile_ms"])
     e1.record(stream)
     torch.cuda.synchronize()
     clocks = clk.stop()

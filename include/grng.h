@@ -63,13 +63,14 @@ typedef struct grng_opts {
   int32_t precision;       /* grng_precision of the distance tiles (FP32: CUDA cores) */
   int32_t n_layers;        /* number of pivot layers L >= 1 */
   int32_t knn_k;           /* neighbour-list length of the exact tier, 1..32 (0: 32) */
-  int32_t k_shortlist;     /* learned interceptor shortlist length (0: off) */
+  int32_t k_shortlist;     /* learned interceptor shortlist length, 0 (off) or 1..16 */
   int32_t reserved;        /* must be 0 */
-  const void* mlp_weights; /* learned ranker weights (see grng_mlp_*), or NULL */
-  size_t mlp_bytes;
+  const void* mlp_weights; /* ranking network parameters, grng_mlp_nparams() FP32 values (host or
+                              device; copied at grng_create), required when k_shortlist > 0 */
+  size_t mlp_bytes;        /* 4 * grng_mlp_nparams() when mlp_weights is given */
   int64_t spin_limit;      /* iteration cap of bounded device waits (0: default) */
   void* cuda_stream;       /* cudaStream_t, or NULL */
-  uint64_t flags;          /* 0, or GRNG_FLAG_SHORT_LISTS (testing) */
+  uint64_t flags;          /* 0, or GRNG_FLAG_SHORT_LISTS (testing) | GRNG_FLAG_RECORD_MLP */
 } grng_opts;
 
 /* Testing aid: cap the pivot layers' range lists at 16 nodes so that more pairs take
