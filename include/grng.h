@@ -53,7 +53,7 @@ typedef int32_t grng_status;
 #define GRNG_ETRUNC 5    /* output buffer too small; the needed size is reported */
 #define GRNG_EINTERNAL 6 /* internal consistency check failed */
 #define GRNG_ESTATE 7    /* call order violated (e.g. a layer not built or not linked) */
-#define GRNG_ENOTIMPL 8  /* option not supported by this build */
+#define GRNG_ENOTIMPL 8  /* option the library does not support */
 
 typedef enum { GRNG_L2 = 0, GRNG_L1 = 1 } grng_metric;
 typedef enum { GRNG_FP32 = 0, GRNG_BF16 = 1, GRNG_FP8 = 2 } grng_precision;
