@@ -1105,8 +1105,8 @@ static void launch_cross(const float* Xr, int64_t nr, const float* Xc, int64_t n
 // that could satisfy that condition is then listed, and only the listed nodes of the
 // pair's annulus are tested.  Uncovered pairs go to the exhaustive tier.
 // ---------------------------------------------------------------------------------
-#define GRNG_LMAX 4096  // target list length
-#define GRNG_LCAP 8192  // list capacity (bin-edge rounding can add a few nodes)
+#define GRNG_LMAX 8192  // target list length
+#define GRNG_LCAP 16384  // list capacity (bin-edge rounding can add a few nodes)
 #define GRNG_HBINS 128
 
 struct SideParams {
