@@ -42,7 +42,14 @@ def test_fp32_sweep_reports_lane_peak():
 
 def test_measured_traffic_lookup():
     k = "tier3_kernel (pivot layer m=131072)"
-    assert bench.measured_traffic(k, 1_000_000) > 0
+    saved = dict(bench.KERNEL_REVS)
+    bench.KERNEL_REVS["tier3_kernel"] = "tier3-r6"  # the revision the committed capture was taken at
+    try:
+        assert bench.measured_traffic(k, 1_000_000) > 0
+    finally:
+        bench.KERNEL_REVS.clear()
+        bench.KERNEL_REVS.update(saved)
+    assert bench.measured_traffic(k, 1_000_000) is None  # the current launch differs from the capture
     assert bench.measured_traffic(k, 999_999) is None          # another size
     assert bench.measured_traffic("tc_sweep_kernel (x)", 1_000_000) is None  # never captured
     saved = dict(bench.KERNEL_REVS)
