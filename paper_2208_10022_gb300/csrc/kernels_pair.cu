@@ -15,7 +15,13 @@
 //           reaches past the first G-lune threshold of that endpoint, every node
 //           that could satisfy that condition is in the list, so the test is exact
 //           (the exhaustive check of Stage VI restricted by a ball bound).
-//   tier 3  exhaustive scan of all nodes (Stage VI) for the few pairs left.
+//   lists   (pivot layers) per-node range lists, cut to about 8,192 nodes by a key
+//           histogram; a pair whose threshold one endpoint's list reaches is decided
+//           from that list alone.
+//   tier 3  the exhaustive Stage VI search down the pivot tree, pruned by domain
+//           bounds (Prop. 4 / GRNG_S6, Prop. 5) and by the ball around the G-lune,
+//           after greedy descents towards that ball's centre; at the exemplar level
+//           the learned shortlist (kernels_mlp.cu) may decide a pair first.
 // Comparisons whose FP32 brackets overlap are re-decided in canonical FP64.
 #include <algorithm>
 #include <chrono>
