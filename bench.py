@@ -126,7 +126,8 @@ def kernel_rooflines(stats, n, D, precision, peaks, sms):
     tier-3 kernel.  Algorithmic work per unit:
       exemplar Gram tiles (tcgen05): 2*D flops per unordered pair of points;
       FP32 tiles (CUDA cores): 2*D lane instructions (subtract + FMA) per unordered pair;
-      tier 3: 2 distances (to both endpoints) x 2*D lane instructions per node tested.
+      tier 3: 2 distances (to both endpoints) x 2*D lane instructions per node tested;
+      range-list tier: one distance (to the other endpoint) x 2*D per listed node tested.
     Peaks: bf16 sustained tensor rate from MEASURED_PEAKS.json (the kernels run inside a
     long step); FP32 lanes: SMs x 128 x the maximum SM clock (derived)."""
     sm_max = peaks.get("sm_max_mhz", 2070.0)
@@ -163,6 +164,8 @@ def kernel_rooflines(stats, n, D, precision, peaks, sms):
             m * (m - 1) / 2 * 2 * D, "Gop/s", alu, alu_src)
         add(f"tier3_kernel (pivot layer m={m})", "alu", k.get("tier3", 0),
             G["tier3_nodes_tested"] * 2 * 2 * D, "Gop/s", alu, alu_src)
+        add(f"list_tier_kernel (pivot layer m={m})", "alu", k.get("lists", 0),
+            G.get("range_nodes_tested", 0) * 2 * D, "Gop/s", alu, alu_src)
     out.sort(key=lambda r: -r["launch_ms"])
     top = dict(out[0])
     top["traffic"] = measured_traffic(top["kernel"], n)

@@ -304,8 +304,8 @@ void level_json(std::string& js, const char* name, const LevelStats& st) {
   }
   snprintf(buf, sizeof(buf),
            ",\"phase_ms\":{\"prep\":%.3f,\"tiles\":%.3f,\"tier2a\":%.3f,\"tier2b\":%.3f,\"range\":%.3f,"
-           "\"tier3\":%.3f,\"recheck_emit\":%.3f},\"kernel_ms\":{\"tiles\":%.4f,\"tier3\":%.4f}",
-           st.ms[0], st.ms[1], st.ms[2], st.ms[3], st.ms[4], st.ms[5], st.ms[6], st.kms[0], st.kms[1]);
+           "\"tier3\":%.3f,\"recheck_emit\":%.3f},\"kernel_ms\":{\"tiles\":%.4f,\"tier3\":%.4f,\"lists\":%.4f}",
+           st.ms[0], st.ms[1], st.ms[2], st.ms[3], st.ms[4], st.ms[5], st.ms[6], st.kms[0], st.kms[1], st.kms[2]);
   js += buf;
   js += "}";
 }

@@ -173,7 +173,7 @@ struct LevelOut {
 struct LevelStats {
   unsigned long long c[32];
   double ms[8];  // prep, tile sweeps, tier-2 grouping + 2a, tier 2b, range lists, tier 3, recheck + emit
-  double kms[2];  // CUDA-event time of the tile sweep kernel(s) and of the tier-3 kernel
+  double kms[3];  // CUDA-event time of the tile sweep kernel(s), the tier-3 kernel and the range-list tier
 };
 // ---- learned shortlist (kernels_mlp.cu) -------------------------------------------------------
 #define GRNG_MLP_IN 32

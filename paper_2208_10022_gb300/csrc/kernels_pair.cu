@@ -1659,8 +1659,19 @@ void run_level(const LevelIn& in, LevelOut& out, LevelStats& st, cudaStream_t s,
       lp.pend = pend.as<int2>(); lp.pend_cnt = dc + 17; lp.pend_cap = 2 * cap;
       lp.amb = amb.as<int2>(); lp.amb_cnt = dc + 19; lp.amb_cap = amb_cap;
       lp.stats = dc + 28;
+      cudaEvent_t l0, l1;
+      GRNG_CUDA(cudaEventCreate(&l0));
+      GRNG_CUDA(cudaEventCreate(&l1));
+      GRNG_CUDA(cudaEventRecord(l0, s));
       list_tier_kernel<<<(unsigned)std::min<unsigned long long>((nun2 + 7) / 8, 64ull * num_sms()), 256, 0, s>>>(lp); note_launch();
       GRNG_CUDA(cudaGetLastError());
+      GRNG_CUDA(cudaEventRecord(l1, s));
+      GRNG_CUDA(cudaEventSynchronize(l1));
+      float lms = 0.0f;
+      GRNG_CUDA(cudaEventElapsedTime(&lms, l0, l1));
+      cudaEventDestroy(l0);
+      cudaEventDestroy(l1);
+      st.kms[2] += lms;
       unsigned long long h8[8];  // -, to tier 3, links, pending, (to tier 3), blocked, tested
       GRNG_CUDA(cudaMemcpyAsync(h8, dc + 26, sizeof(h8), cudaMemcpyDeviceToHost, s));
       std::vector<int> hl((size_t)n);
