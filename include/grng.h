@@ -218,11 +218,16 @@ grng_status grng_tc_keys(const float* pts, int64_t n, int32_t dim, float* keys);
  * (nearest pivot by canonical key, ties to the lowest position, a pivot owns itself),
  * without an index and without cudaMalloc/cudaFree or any allocating library call.
  *
- * pts[n][dim]       DEVICE pointer, FP32 row-major; dim a positive multiple of 8
- * pivot_idx[m]      DEVICE pointer, distinct point indices in [0, n)
- * assign[n]         DEVICE output: pivot position of every point
- * dist[n]           DEVICE output: FP64 canonical distance to that pivot (the layer's
- *                   radius of pivot p is the maximum of dist over the points assigned to p)
+ * pts[n][dim]       DEVICE pointer, FP32 row-major, 16-byte aligned; dim a positive
+ *                   multiple of 8
+ * pivot_idx[m]      DEVICE pointer, 4-byte aligned, distinct point indices in [0, n)
+ * assign[n]         DEVICE output, 4-byte aligned: pivot position of every point
+ * dist[n]           DEVICE output, 8-byte aligned: FP64 canonical distance to that pivot
+ *                   (the layer's radius of pivot p is the maximum of dist over the points
+ *                   assigned to p)
+ * Every pointer must be device (or managed) memory of the current device, checked with
+ * cudaPointerGetAttributes before any work is queued: a host pointer, a pointer of another
+ * device or a misaligned one returns GRNG_EINVAL.
  * cuda_stream       cudaStream_t the work is queued on (NULL = legacy default stream);
  *                   the call returns after that stream has finished it.
  * Limits: 1 <= n <= 262,144; 1 <= m <= min(n, 65,536); m * dim <= 2,097,152; larger

@@ -38,8 +38,12 @@ def lib():
         _lib.orc_rng_brute.argtypes = [P, i64, i32, i32, P, i64]
         _lib.orc_rng_row.restype = i64
         _lib.orc_rng_row.argtypes = [P, i64, i32, i32, i64, P, i64]
-        _lib.orc_in_lune.restype = i32
-        _lib.orc_in_lune.argtypes = [P, i32, i32, i64, i64, i64]
+        _lib.orc_rng_rows.restype = i32
+        _lib.orc_rng_rows.argtypes = [P, i64, i32, i32, P, i64, P, i64, P]
+        _lib.orc_verify_witness.restype = i32
+        _lib.orc_verify_witness.argtypes = [P, i32, i32, i64, i64, i64]
+        _lib.orc_emst.restype = i64
+        _lib.orc_emst.argtypes = [P, i64, i32, i32, P]
         _lib.orc_grng_brute.restype = i64
         _lib.orc_grng_brute.argtypes = [P, P, i64, i32, i32, P, i64]
         _lib.orc_grng_row.restype = i64
@@ -105,9 +109,36 @@ def rng_row(X, x, metric=L2):
     return out[:cnt]
 
 
-def in_lune(X, x, y, z, metric=L2):
+def rng_rows(X, xs, metric=L2, row_cap=4096):
+    """Exact RNG neighbourhoods of the points xs (a list of ascending int32 arrays), the
+    rows spread over the host's cores."""
     X = _f32(X)
-    return bool(lib().orc_in_lune(_p(X), X.shape[1], metric, int(x), int(y), int(z)))
+    xs = np.ascontiguousarray(xs, dtype=np.int64)
+    nb = np.zeros((max(len(xs), 1), row_cap), np.int32)
+    cnt = np.zeros(max(len(xs), 1), np.int64)
+    rc = lib().orc_rng_rows(_p(X), X.shape[0], X.shape[1], metric, _p(xs), len(xs), _p(nb), row_cap, _p(cnt))
+    if rc != 0:
+        raise MemoryError("oracle allocation failed")
+    if len(xs) and cnt.max() > row_cap:
+        raise ValueError("a neighbourhood exceeds row_cap")
+    return [nb[t, :cnt[t]].copy() for t in range(len(xs))]
+
+
+def verify_witness(X, x, y, z, metric=L2):
+    """True when z (not x or y) lies strictly inside the lune of (x, y) (Eq. 1)."""
+    X = _f32(X)
+    return bool(lib().orc_verify_witness(_p(X), X.shape[1], metric, int(x), int(y), int(z)))
+
+
+def emst(X, metric=L2):
+    """A minimum spanning tree of the complete graph (Prim, canonical keys): int32 [n-1, 2]."""
+    X = _f32(X)
+    n = X.shape[0]
+    out = np.zeros((max(n - 1, 1), 2), np.int32)
+    cnt = lib().orc_emst(_p(X), n, X.shape[1], metric, _p(out))
+    if cnt < 0:
+        raise MemoryError("oracle allocation failed")
+    return out[:cnt]
 
 
 def grng_brute(P, r, metric=L2):

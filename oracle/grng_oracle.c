@@ -31,7 +31,7 @@
  *     except when r_i == r_j == 0, where they compare keys (so that the GRNG with
  *     zero radii is exactly the RNG, as the paper remarks after the definition).
  *
- * Readings of points the paper leaves open (each is also listed in the design notes):
+ * Readings of points the paper leaves open:
  *   - interceptors x3 in Eq. 1 range over S minus {x1, x2} (x1, x2 themselves can
  *     never be strictly inside their own lune);
  *   - nearest-pivot ties go to the lowest position in the layer's pivot list, and a
@@ -128,14 +128,14 @@ static int kv_cmp(const void *a, const void *b) {
     if (p->k > q->k) return 1;
     return (p->i > q->i) - (p->i < q->i);
 }
-int64_t orc_rng_row(const float *X, int64_t n, int32_t D, int32_t metric, int64_t x,
-                    int32_t *nbrs, int64_t cap) {
-    kv_t *o = (kv_t *)malloc(sizeof(kv_t) * (size_t)n);
-    unsigned char *is = (unsigned char *)calloc((size_t)n, 1);
-    if (!o || !is) { free(o); free(is); return -1; }
+/* Neighbours of x (ascending) into nbrs[cap]; o[n] and is[n] are caller scratch.
+ * parallel = 1 spreads the candidates y over the OpenMP threads.  Returns the count. */
+static int64_t rng_row_into(const float *X, int64_t n, int32_t D, int32_t metric, int64_t x,
+                            int32_t *nbrs, int64_t cap, kv_t *o, unsigned char *is, int parallel) {
     for (int64_t z = 0; z < n; ++z) { o[z].k = orc_key(X + x * D, X + z * D, D, metric); o[z].i = z; }
     qsort(o, (size_t)n, sizeof(kv_t), kv_cmp);
-#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t y = 0; y < n; ++y) is[y] = 0;
+#pragma omp parallel for schedule(dynamic, 64) if (parallel)
     for (int64_t p = 0; p < n; ++p) {
         int64_t y = o[p].i;
         if (y == x) continue;
@@ -153,18 +153,90 @@ int64_t orc_rng_row(const float *X, int64_t n, int32_t D, int32_t metric, int64_
     int64_t cnt = 0;
     for (int64_t y = 0; y < n; ++y)
         if (is[y]) { if (cnt < cap) nbrs[cnt] = (int32_t)y; ++cnt; }
+    return cnt;
+}
+
+int64_t orc_rng_row(const float *X, int64_t n, int32_t D, int32_t metric, int64_t x,
+                    int32_t *nbrs, int64_t cap) {
+    kv_t *o = (kv_t *)malloc(sizeof(kv_t) * (size_t)n);
+    unsigned char *is = (unsigned char *)malloc((size_t)n);
+    if (!o || !is) { free(o); free(is); return -1; }
+    int64_t cnt = rng_row_into(X, n, D, metric, x, nbrs, cap, o, is, 1);
     free(o);
     free(is);
     return cnt;
 }
 
-/* 1 if z lies strictly inside lune(x, y) (Eq. 1), else 0 */
-int32_t orc_in_lune(const float *X, int32_t D, int32_t metric, int64_t x, int64_t y, int64_t z) {
+/* The exact neighbourhoods of count points xs[] at once (rows spread over the OpenMP
+ * threads, each row computed as orc_rng_row computes it).  Row t's neighbours go to
+ * nbrs[t * row_cap ...], its count to cnt[t] (a count above row_cap means the row was
+ * cut).  Returns 0, or -1 on allocation failure. */
+int32_t orc_rng_rows(const float *X, int64_t n, int32_t D, int32_t metric, const int64_t *xs,
+                     int64_t count, int32_t *nbrs, int64_t row_cap, int64_t *cnt) {
+    int failed = 0;
+#pragma omp parallel
+    {
+        kv_t *o = (kv_t *)malloc(sizeof(kv_t) * (size_t)n);
+        unsigned char *is = (unsigned char *)malloc((size_t)n);
+        if (!o || !is) {
+#pragma omp atomic write
+            failed = 1;
+        }
+#pragma omp for schedule(dynamic, 1)
+        for (int64_t t = 0; t < count; ++t) {
+            if (o && is)
+                cnt[t] = rng_row_into(X, n, D, metric, xs[t], nbrs + t * row_cap, row_cap, o, is, 0);
+        }
+        free(o);
+        free(is);
+    }
+    return failed ? -1 : 0;
+}
+
+/* Witness check (Eq. 1): 1 if z is a point other than x and y lying strictly inside
+ * the open lune of (x, y), i.e. max(d(x,z), d(y,z)) < d(x,y), so that z proves the pair
+ * is not an RNG edge; else 0. */
+int32_t orc_verify_witness(const float *X, int32_t D, int32_t metric, int64_t x, int64_t y, int64_t z) {
+    if (z == x || z == y) return 0;
     double dxy = orc_key(X + x * D, X + y * D, D, metric);
     double a = orc_key(X + x * D, X + z * D, D, metric);
     double b = orc_key(X + y * D, X + z * D, D, metric);
     double m = a > b ? a : b;
     return m < dxy ? 1 : 0;
+}
+
+/* A minimum spanning tree of the complete graph on the n points under canonical keys
+ * (Prim's algorithm, O(n^2 D)).  Every minimum spanning tree lies in the RNG: an edge
+ * with a point strictly inside its lune could be swapped for a strictly lighter one
+ * (Sec. 1, the RNG contains the MST).  Writes the n-1 tree edges (parent, child) into
+ * edges[n-1][2]; returns n-1, or -1 on allocation failure. */
+int64_t orc_emst(const float *X, int64_t n, int32_t D, int32_t metric, int32_t *edges) {
+    if (n < 2) return 0;
+    double *best = (double *)malloc(sizeof(double) * (size_t)n);
+    int64_t *from = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
+    unsigned char *in = (unsigned char *)calloc((size_t)n, 1);
+    if (!best || !from || !in) { free(best); free(from); free(in); return -1; }
+    in[0] = 1;
+    for (int64_t v = 0; v < n; ++v) { best[v] = orc_key(X, X + v * D, D, metric); from[v] = 0; }
+    for (int64_t e = 0; e + 1 < n; ++e) {
+        int64_t u = -1;
+        double bu = 0.0;
+        for (int64_t v = 0; v < n; ++v)
+            if (!in[v] && (u < 0 || best[v] < bu)) { u = v; bu = best[v]; }
+        in[u] = 1;
+        edges[2 * e] = (int32_t)from[u];
+        edges[2 * e + 1] = (int32_t)u;
+#pragma omp parallel for schedule(static)
+        for (int64_t v = 0; v < n; ++v) {
+            if (in[v]) continue;
+            double k = orc_key(X + u * D, X + v * D, D, metric);
+            if (k < best[v]) { best[v] = k; from[v] = u; }
+        }
+    }
+    free(best);
+    free(from);
+    free(in);
+    return n - 1;
 }
 
 /* ---- GRNG by its definition (Sec. 2) ------------------------------------------ */
@@ -292,6 +364,10 @@ int32_t orc_assign(const float *X, int32_t D, int32_t metric, const int32_t *mem
         as[t] = best;
         ds[t] = orc_dist(x, X + (int64_t)piv[best] * D, D, metric);
     }
+    /* delta_max(p) is the largest d(p, member) over the members assigned to p, without
+     * the member radii (Sec. 2 Stage VI bounds d(p, z) for the exemplars below p by it);
+     * the radius adds each member's own radius (relative pivot domain, Sec. 3), so on a
+     * coarse layer the two differ. */
     if (radius || delta_max) {
         for (int32_t p = 0; p < m; ++p) {
             if (radius) radius[p] = 0.0;

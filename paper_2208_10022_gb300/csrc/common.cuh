@@ -44,10 +44,13 @@ __host__ __device__ inline Err err_fp32(int D) {
 __device__ __forceinline__ float hi_b(float a, Err e) { return fmaf(a, 1.0f + e.eps, e.eta); }
 __device__ __forceinline__ float lo_b(float a, Err e) { return fmaf(a, 1.0f - e.eps, -e.eta); }
 
-// Guidance margin (see the design notes): a pair counts as "safely" non-linked -- so
-// that Theorem 1 / Theorem 2 may prune its descendants -- only when some blocker
-// clears both G-lune thresholds by more than TAU_REL times the magnitude of the
-// quantities involved; the FP64 rounding of those quantities is ~2^-46 relative.
+// Guidance margin.  Theorems 1 and 2 prune the pairs below a non-linked pivot pair, and
+// that pruning is exact in the reals; near a threshold, the FP64 rounding of the
+// definition's distances could call a pair non-linked that exact arithmetic links.  So
+// a pair counts as "safely" non-linked -- and may prune its descendants -- only when
+// some blocker clears both G-lune thresholds by more than TAU_REL times the magnitude
+// of the quantities involved; the FP64 rounding of those quantities is ~2^-46 relative,
+// 64 times smaller than the margin for sums of up to 128 terms.
 #define GRNG_TAU_REL 9.094947017729282e-13  // 2^-40
 
 // ---- canonical FP64 key, the only FP64 arithmetic of the fast path --------------

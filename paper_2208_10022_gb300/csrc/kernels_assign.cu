@@ -275,9 +275,33 @@ static void* static_scratch_address(int dev) {
   return addr[dev];
 }
 
+// The kernels of the allocation-free call read and write the caller's buffers directly
+// (float4 loads of the points, FP64 stores of the distances), so every buffer must be
+// memory the device can address and must start on the boundary of its widest access.
+static void check_device_buffer(const void* p, size_t align, const char* name) {
+  if (reinterpret_cast<uintptr_t>(p) % align != 0)
+    fail(1, std::string(name) + " must be aligned to " + std::to_string(align) + " bytes");
+  cudaPointerAttributes at{};
+  cudaError_t e = cudaPointerGetAttributes(&at, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    fail(1, std::string(name) + " is not a pointer the CUDA runtime knows");
+  }
+  if (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged)
+    fail(1, std::string(name) + " must be device (or managed) memory");
+  int dev = 0;
+  GRNG_CUDA(cudaGetDevice(&dev));
+  if (at.type == cudaMemoryTypeDevice && at.device != dev)
+    fail(1, std::string(name) + " lives on another device than the current one");
+}
+
 void assign_static(const float* X, int64_t n, int dim, const int32_t* piv, int64_t m, int metric,
                    int32_t* assign, double* dist, cudaStream_t s) {
   if (!X || !piv || !assign || !dist) fail(1, "pointers must not be NULL");
+  check_device_buffer(X, 16, "pts");
+  check_device_buffer(piv, 4, "pivot_idx");
+  check_device_buffer(assign, 4, "assign");
+  check_device_buffer(dist, 8, "dist");
   if (metric != L2 && metric != L1) fail(1, "unknown metric");
   if (dim < 8 || dim % 8 != 0) fail(1, "dim must be a positive multiple of 8");
   if (n < 1 || n > GRNG_STATIC_MAX_POINTS) fail(1, "n must be in [1, 262144] for the allocation-free call");

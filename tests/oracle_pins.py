@@ -14,6 +14,12 @@ What pins what:
                               properties of the oracle's outputs
   cross_checks             -- rng_row vs rng_brute and grng_row vs grng_brute (two
                               different loops), assignment vs a Python restatement
+  layer_examples           -- a hand-derived two-layer hierarchy whose coarse radius
+                              and delta_max differ (tests/golden)
+  witnesses                -- the witness check against the exact lune test, and
+                              every non-edge of Eq. 1 has a witness
+  spanning_trees           -- Prim's tree has the weight of an exact Kruskal over all
+                              pairs and lies in the RNG
 """
 import json
 import os
@@ -23,6 +29,7 @@ import numpy as np
 from . import exact
 
 GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "worked_examples.json")
+LAYERS = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "layers_delta_max.json")
 
 
 def _as_set(E):
@@ -232,4 +239,58 @@ def degree_arithmetic():
         assert round(2.0 * ex["edges"] / ex["n"], 4) == ex["avg_degree"], ex["name"]
 
 
-ALL = [exact_rng, exact_grng, worked_examples, invariants, theorems, cross_checks]
+def layer_examples(orc):
+    """Assignment, radius and delta_max of both layers equal the hand-derived values."""
+    g = json.load(open(LAYERS))
+    X = np.asarray(g["points"], np.float32)
+    for case in g["cases"]:
+        lay = orc.build_layers(X, [np.asarray(l, np.int32) for l in g["layers"]], case["metric"])
+        for li in range(len(g["layers"])):
+            assert list(lay[li]["assign"]) == case["assign"][li], ("assign", case["metric"], li)
+            assert list(lay[li]["radius"]) == case["radius"][li], ("radius", case["metric"], li)
+            assert list(lay[li]["delta_max"]) == case["delta_max"][li], ("delta_max", case["metric"], li)
+
+
+def witnesses(orc, trials=25, seed=16):
+    """verify_witness(x, y, z) is the exact rational lune test; a pair is a non-edge of
+    Eq. 1 exactly when some z is a witness."""
+    rng = np.random.default_rng(seed)
+    for t in range(trials):
+        n = int(rng.integers(3, 9))
+        d = int(rng.integers(1, 4))
+        X = _rand_int_points(rng, n, d, 4)
+        for metric in (exact.L2, exact.L1):
+            E = set(exact.rng(X.tolist(), metric))
+            for i in range(n):
+                for j in range(i + 1, n):
+                    any_w = False
+                    for k in range(n):
+                        kij = exact.key(X[i].tolist(), X[j].tolist(), metric)
+                        inside = k not in (i, j) and max(exact.key(X[k].tolist(), X[i].tolist(), metric),
+                                                         exact.key(X[k].tolist(), X[j].tolist(), metric)) < kij
+                        w = orc.verify_witness(X, i, j, k, metric)
+                        assert w == inside, (t, metric, i, j, k)
+                        any_w |= w
+                    assert any_w == ((i, j) not in E), (t, metric, i, j)
+
+
+def spanning_trees(orc, seed=17):
+    """Prim's tree (orc.emst) is a spanning tree with the weight of Kruskal's over the
+    exact key matrix, and every tree edge is an RNG edge (Sec. 1: MST within RNG)."""
+    rng = np.random.default_rng(seed)
+    for t in range(4):
+        n = int(rng.integers(30, 120))
+        X = rng.standard_normal((n, 3)).astype(np.float32)
+        for metric in (exact.L2, exact.L1):
+            T = orc.emst(X, metric)
+            assert T.shape == (n - 1, 2) and _connected(n, [tuple(map(int, e)) for e in T])
+            K = _key_matrix(orc, X, metric)
+            w_prim = sum(K[int(a), int(b)] for a, b in T)
+            w_kruskal = sum(K[i, j] for i, j in _mst_edges(K))
+            assert abs(w_prim - w_kruskal) <= 1e-9 * max(1.0, w_kruskal), (t, metric)
+            E = _as_set(orc.rng_brute(X, metric))
+            assert {(min(int(a), int(b)), max(int(a), int(b))) for a, b in T} <= E
+
+
+ALL = [exact_rng, exact_grng, worked_examples, invariants, theorems, cross_checks, layer_examples, witnesses,
+       spanning_trees]

@@ -29,6 +29,10 @@ MUTANTS = {
     "radius_without_member_radius": ("double rr = ds[t] + (member_r ? member_r[t] : 0.0);", "double rr = ds[t];"),
     "no_self_assign": ("if (piv[p] == members[t]) { best = p; break; }", ""),
     "row_scan_stops_early": ("if (!(o[q].k < dxy)) break;", "if (!(o[q].k < 0.5 * dxy)) break;"),
+    "delta_max_with_member_radius": ("if (delta_max && ds[t] > delta_max[as[t]]) delta_max[as[t]] = ds[t];",
+                                     "if (delta_max && rr > delta_max[as[t]]) delta_max[as[t]] = rr;"),
+    "witness_closed_lune": ("return m < dxy ? 1 : 0;", "return m <= dxy ? 1 : 0;"),
+    "emst_wrong_endpoint": ("edges[2 * e] = (int32_t)from[u];", "edges[2 * e] = (int32_t)(u > 0 ? u - 1 : 1);"),
 }
 
 RUNNER = r"""

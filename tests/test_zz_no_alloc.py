@@ -59,3 +59,28 @@ def test_static_rejects_sizes_beyond_its_array():
     st, _, _ = _static(X, P, wl.L2)
     assert st == g.GRNG_EINVAL
     assert b"262144" in g.lib().grng_last_error()
+
+
+def test_static_rejects_host_and_misaligned_buffers():
+    """The call reads and writes the caller's buffers in place, so it checks on the host,
+    before queueing any work, that each one is device memory on its access boundary."""
+    n, dim = 512, 8
+    P = torch.arange(4, dtype=torch.int32, device="cuda")
+    Xh = np.zeros((n, dim), np.float32)                     # host memory
+    L = g.lib()
+    f = L.grng_assign_static
+    f.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_void_p, ctypes.c_int32,
+                  ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    f.restype = ctypes.c_int32
+    assign = torch.zeros(n, dtype=torch.int32, device="cuda")
+    dist = torch.zeros(n, dtype=torch.float64, device="cuda")
+    st = f(Xh.ctypes.data, n, dim, P.data_ptr(), 4, wl.L2, assign.data_ptr(), dist.data_ptr(), None)
+    assert st == g.GRNG_EINVAL and b"device" in L.grng_last_error()
+    buf = torch.zeros(n * dim + 4, dtype=torch.float32, device="cuda")
+    Xoff = buf[1:1 + n * dim].view(n, dim)                  # starts 4 bytes past a 16-byte boundary
+    st = f(Xoff.data_ptr(), n, dim, P.data_ptr(), 4, wl.L2, assign.data_ptr(), dist.data_ptr(), None)
+    assert st == g.GRNG_EINVAL and b"aligned" in L.grng_last_error()
+    # the index buffers keep working afterwards
+    X = buf[:n * dim].view(n, dim)
+    st = f(X.data_ptr(), n, dim, P.data_ptr(), 4, wl.L2, assign.data_ptr(), dist.data_ptr(), None)
+    assert st == g.GRNG_OK, L.grng_last_error()
