@@ -50,6 +50,12 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=12000, help="points of the oracle's bounded sample")
+    ap.add_argument("--check-rows", type=int, default=1000,
+                    help="after timing, compare this many seeded points' RNG neighbourhoods with the FP64 oracle's "
+                         "exact rows (0: skip)")
+    ap.add_argument("--plain-steps", type=int, default=3,
+                    help="timed steps of the plain FP32 comparison build (after one warm-up step)")
+    ap.add_argument("--e2e-steps", type=int, default=5, help="timed steps of the end-to-end measurement")
     ap.add_argument("--insert", type=int, default=0, metavar="B",
                     help="instead of the build benchmark: insert B batches of uneven size (log-uniform in "
                          "[1,000, 65,536] points, scaled to --n) into an index built on the rest, and print "
@@ -127,7 +133,8 @@ def kernel_rooflines(stats, n, D, precision, peaks, sms):
       exemplar Gram tiles (tcgen05): 2*D flops per unordered pair of points;
       FP32 tiles (CUDA cores): 2*D lane instructions (subtract + FMA) per unordered pair;
       tier 3: 2 distances (to both endpoints) x 2*D lane instructions per node tested;
-      range-list tier: one distance (to the other endpoint) x 2*D per listed node tested.
+      range-list tier: 8 bytes (node id and key) per list entry read, plus one padded row
+      (4*Dp bytes) per listed node tested by distance -- a streaming bound against HBM.
     Peaks: bf16 sustained tensor rate from MEASURED_PEAKS.json (the kernels run inside a
     long step); FP32 lanes: SMs x 128 x the maximum SM clock (derived)."""
     sm_max = peaks.get("sm_max_mhz", 2070.0)
@@ -136,6 +143,9 @@ def kernel_rooflines(stats, n, D, precision, peaks, sms):
     bf_src = "MEASURED_PEAKS bf16_tflops_sustained (of measured)" if bf else "fallback 1700 TFLOP/s sustained"
     bf = bf or 1700.0
     alu_src = f"derived: {sms} SMs x 128 FP32 lanes x {sm_max:.0f} MHz (MEASURED_PEAKS sm_max_mhz)"
+    hbm = peaks.get("hbm_gbs") or 6800.0
+    hbm_src = "MEASURED_PEAKS hbm_gbs (of measured)" if peaks.get("hbm_gbs") else "fallback 6800 GB/s"
+    Dp = D if D <= 8 else (16 if D <= 16 else ((D + 31) // 32) * 32)
     out = []
 
     def add(kernel, bound, ms, work, unit, peak, src):
@@ -164,8 +174,8 @@ def kernel_rooflines(stats, n, D, precision, peaks, sms):
             m * (m - 1) / 2 * 2 * D, "Gop/s", alu, alu_src)
         add(f"tier3_kernel (pivot layer m={m})", "alu", k.get("tier3", 0),
             G["tier3_nodes_tested"] * 2 * 2 * D, "Gop/s", alu, alu_src)
-        add(f"list_tier_kernel (pivot layer m={m})", "alu", k.get("lists", 0),
-            G.get("range_nodes_tested", 0) * 2 * D, "Gop/s", alu, alu_src)
+        add(f"list_tier_kernel (pivot layer m={m})", "hbm", k.get("lists", 0),
+            G.get("range_entries_read", 0) * 8 + G.get("range_nodes_tested", 0) * 4 * Dp, "GB/s", hbm, hbm_src)
     out.sort(key=lambda r: -r["launch_ms"])
     top = dict(out[0])
     top["traffic"] = measured_traffic(top["kernel"], n)
@@ -218,18 +228,99 @@ def load_peaks():
         return {}
 
 
-def cpu_baseline(kind, n_sample, seed=3002):
-    """The FP64 oracle (brute force over all triples, Eq. 1) on a bounded sample."""
+def cpu_baseline(kind, n_sample, seed=3002, threads=None):
+    """The FP64 oracle (brute force over all triples, Eq. 1) on a bounded sample, on all
+    the host's cores or on `threads` of them."""
     import oracle
     from paper_2208_10022_gb300 import workloads as wl
     w = wl.make(kind, n=n_sample, data_seed=seed)
-    t0 = time.perf_counter()
-    E = oracle.rng_brute(w.X)
-    dt = time.perf_counter() - t0
-    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    prev = oracle.set_threads(threads) if threads else None
+    try:
+        t0 = time.perf_counter()
+        E = oracle.rng_brute(w.X)
+        dt = time.perf_counter() - t0
+    finally:
+        if prev:
+            oracle.set_threads(prev)
+    cores = threads or oracle.max_threads()
     return {"value": len(E) / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"rng_brute on a seeded {n_sample}-point sample of the {kind} generator "
                       f"({len(E)} edges in {dt:.2f} s)", "seconds": dt, "edges": int(len(E))}
+
+
+def cpu_model():
+    """The host CPU's model name (lscpu), or the architecture when lscpu is absent."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.split(":")[0].strip() in ("Model name", "Model"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    import platform
+    return platform.machine()
+
+
+def step_measures(stats, step_ms):
+    """Work counters of one step, from the library's statistics (grng_stats):
+    candidate lune tests are the candidate pairs every level decides (tier 1 to the FP64
+    recheck), interceptor evaluations the exact tests of one interceptor against one pair
+    outside the tile sweeps (tier 3, range-list distance tests and list intersections, the
+    learned shortlist), the recheck fraction the FP64 triples among those evaluations."""
+    levels = [L["grng"] for L in stats["layers"]] + [stats["rng"]]
+    cand = sum(L["candidate_pairs"] for L in levels)
+    ev = sum(L["tier3_nodes_tested"] + L["range_nodes_tested"] + L.get("range_probes", 0) + L["learned_tests"]
+             for L in levels)
+    fp64 = sum(L["fp64_triples"] for L in levels)
+    s = step_ms / 1000.0
+    n = stats["n"]
+    return {"candidate_pairs_per_step": cand, "candidate_lune_tests_per_s": cand / s,
+            "exemplar_candidate_pairs": stats["rng"]["candidate_pairs"],
+            "exemplar_pairs_of_all": stats["rng"]["candidate_pairs"] / max(1.0, n * (n - 1) / 2),
+            "interceptor_evaluations_per_step": ev, "interceptor_evaluations_per_s": ev / s,
+            "fp64_triples_per_step": fp64, "fp64_recheck_fraction": fp64 / max(1, ev)}
+
+
+def tc_key_error(g, X, n=256, seed=3003):
+    """Largest error of the tensor-core tile keys on a seeded 256-point sample of the
+    workload against the FP64 keys, absolute and as a fraction of the stated bound."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    S = X[rng.choice(X.shape[0], size=min(n, X.shape[0]), replace=False)]
+    got = g.tc_keys(S).astype(np.float64)
+    S64 = S.astype(np.float64)
+    nrm = (S64 ** 2).sum(1)
+    want = ((S64[:, None, :] - S64[None, :, :]) ** 2).sum(-1)
+    Dp = ((S.shape[1] + 15) // 16) * 16
+    bound = (2.0 ** -12 + (3 * Dp + 16) * 2.0 ** -24) * (nrm[:, None] + nrm[None, :])
+    err = np.abs(got - want)
+    return {"sample_points": int(S.shape[0]), "max_abs_err": float(err.max()),
+            "max_err_over_bound": float((err / np.maximum(bound, 1e-300)).max()),
+            "max_rel_err": float((err / np.maximum(want, 1e-30))[~np.eye(S.shape[0], dtype=bool)].max())}
+
+
+def check_rows(X, E, count, seed=3004):
+    """The RNG neighbourhoods of `count` seeded points of the GPU edge list E against the
+    FP64 oracle's exact rows (each row: every y tested against every z closer to x, Eq. 1),
+    computed on the host's cores after the timed region."""
+    import numpy as np
+    import oracle
+    n = X.shape[0]
+    xs = np.sort(np.random.default_rng(seed).choice(n, size=min(count, n), replace=False))
+    t0 = time.perf_counter()
+    want = oracle.rng_rows(X, xs)
+    dt = time.perf_counter() - t0
+    both = np.concatenate([E, E[:, ::-1]])
+    order = np.argsort(both[:, 0], kind="stable")
+    src, dst = both[order, 0], both[order, 1]
+    lo = np.searchsorted(src, xs, "left")
+    hi = np.searchsorted(src, xs, "right")
+    bad = 0
+    for t in range(len(xs)):
+        if not np.array_equal(np.sort(dst[lo[t]:hi[t]]), want[t]):
+            bad += 1
+    return {"rows_checked": int(len(xs)), "row_mismatches": int(bad), "oracle_seconds": dt,
+            "neighbours_checked": int(sum(len(r) for r in want))}
 
 
 def workload_name(kind, n, D, sizes):
@@ -297,7 +388,7 @@ def run_gpu(a, rank, world, local):
     mlp = {"mlp_params": learned["params"], "k_shortlist": learned["k"]} if learned else {}
 
     def step_device(plain=False):
-        ix = g.Index(Xd, n_layers=L, stream=stream, precision=prec, **({} if plain else mlp))
+        ix = g.Index(Xd, n_layers=L, stream=stream, precision=g.FP32 if plain else prec, **({} if plain else mlp))
         for li in range(L - 1, -1, -1):
             ix.build_layer(li, piv_d[li], outputs=False)
         for li in range(L):
@@ -308,7 +399,7 @@ def run_gpu(a, rank, world, local):
         ix.rng_edges(out=out)
         st = ix.stats()
         ix.close()
-        return ne, st
+        return ne, st, out[:ne]
 
     def barrier():
         if pg:
@@ -317,7 +408,7 @@ def run_gpu(a, rank, world, local):
 
     wst = None
     for _ in range(a.warmup):
-        _, wst = step_device()
+        _, wst, _ = step_device()
     barrier()
     if wst is not None:
         launches0 = wst["kernel_launches"]           # counter after the last warm-up step
@@ -328,9 +419,9 @@ def run_gpu(a, rank, world, local):
     clk = Clocks(local)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    edges, stats = 0, None
+    edges, stats, e_last = 0, None, None
     for _ in range(a.steps):
-        ne, stats = step_device()
+        ne, stats, e_last = step_device()
         edges += ne
     e1.record(stream)
     torch.cuda.synchronize()
@@ -349,7 +440,8 @@ def run_gpu(a, rank, world, local):
         f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         f0.record(stream)
         e_edges = 0
-        for _ in range(a.steps):
+        e2e_steps = max(1, min(a.steps, a.e2e_steps))
+        for _ in range(e2e_steps):
             ix = g.Index(Xh, n_layers=L, stream=stream, precision=prec, **mlp)
             for li in range(L - 1, -1, -1):
                 ix.build_layer(li, pivh[li], outputs=False)
@@ -367,7 +459,8 @@ def run_gpu(a, rank, world, local):
         ems = max_over_ranks(f0.elapsed_time(f1), pg, "cuda")
         e2e = {"value": aggregate_rate(e_edges, world, ems), "unit": UNIT,
                "h2d_bytes_per_step": int(w.X.nbytes + sum(l.nbytes for l in w.layers)),
-               "d2h_bytes_per_step": int(8 * (e_edges // max(a.steps, 1)))}
+               "d2h_bytes_per_step": int(8 * (e_edges // e2e_steps)), "steps": e2e_steps,
+               "ms_per_step": ems / e2e_steps}
 
     # rooflines of the main kernels, timed with CUDA events inside the library on the
     # launching stream; the line's "roofline" is the one with the largest time
@@ -388,25 +481,37 @@ def run_gpu(a, rank, world, local):
             "gpu_launches": launches1 - launches0, "e2e": e2e,
             "detail": {"rng": stats["rng"], "layers": stats["layers"],
                        "rng_ms": stats["rng_ms"], "rng_tile_ms": stats["rng_tile_ms"], "sort_ms": stats["sort_ms"]}}
+    line["measures"] = step_measures(stats, ms / a.steps)
     if prec == g.BF16 and not a.no_compare:
-        # the plain build: FP32 CUDA-core tiles everywhere (one timed step, same workload)
-        prec_saved = prec
-        prec = g.FP32
+        # the plain build: FP32 CUDA-core tiles everywhere, no learned shortlist, same workload;
+        # one untimed warm-up step, then the timed steps; its edge list is compared with the
+        # BF16 + learned build's element by element on the device
+        step_device(plain=True)
         barrier()
         c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        k32 = max(1, a.plain_steps)
         c0.record(stream)
-        ne32, st32 = step_device(plain=True)
+        for _ in range(k32):
+            ne32, st32, e32 = step_device(plain=True)
         c1.record(stream)
         torch.cuda.synchronize()
-        ms32 = c0.elapsed_time(c1)
-        prec = prec_saved
+        ms32 = c0.elapsed_time(c1) / k32
+        same = bool(ne32 == e_last.shape[0] and torch.equal(e32, e_last))
         line["compare"] = {"plain_fp32_value": ne32 / (ms32 / 1000.0), "plain_fp32_ms_per_step": ms32,
-                           "plain_fp32_edges": ne32, "same_edge_count": ne32 == line["edges_per_step"],
-                           "speedup_vs_plain_fp32": (ms32 / (ms / a.steps)),
+                           "plain_fp32_steps": k32, "plain_fp32_warmup": 1, "plain_fp32_edges": ne32,
+                           "edge_set_equal": same, "speedup_vs_plain_fp32": (ms32 / (ms / a.steps)),
                            "plain_fp32_tile_ms": st32["rng_tile_ms"]}
+        del e32
+    if prec == g.BF16:
+        line["tc_key_error"] = tc_key_error(g, w.X)
+    if rank == 0 and a.check_rows > 0:
+        line["rng_row_check"] = check_rows(w.X, e_last.cpu().numpy(), a.check_rows)
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         cb = cpu_baseline(a.kind, a.cpu_sample)
         line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
+        one = cpu_baseline(a.kind, max(1000, a.cpu_sample // 3), threads=1)
+        line["cpu_baseline"]["one_thread"] = {k: one[k] for k in ("value", "unit", "cores", "sample")}
+        line["cpu_baseline"]["cpu_model"] = cpu_model()
     if rank == 0:
         print(json.dumps(line), flush=True)
     if pg:

@@ -70,7 +70,8 @@ typedef struct grng_opts {
   size_t mlp_bytes;        /* 4 * grng_mlp_nparams() when mlp_weights is given */
   int64_t spin_limit;      /* iteration cap of bounded device waits (0: default) */
   void* cuda_stream;       /* cudaStream_t, or NULL */
-  uint64_t flags;          /* 0, or GRNG_FLAG_SHORT_LISTS (testing) | GRNG_FLAG_RECORD_MLP */
+  uint64_t flags;          /* 0, or GRNG_FLAG_SHORT_LISTS | GRNG_FLAG_SMALL_BUFFERS (testing) |
+                              GRNG_FLAG_RECORD_MLP */
 } grng_opts;
 
 /* Testing aid: cap the pivot layers' range lists at 16 nodes so that more pairs take
@@ -80,6 +81,11 @@ typedef struct grng_opts {
  * shortlist's pool for every pair that reaches the exhaustive tier (see
  * grng_mlp_dataset).  Results are unchanged. */
 #define GRNG_FLAG_RECORD_MLP 2ull
+/* Testing aid: start every internal work buffer (tier-1 survivors, ambiguous triples,
+ * the exhaustive tier's frontier) at a tiny capacity, so that the overflow paths run:
+ * a repeated sweep with a larger buffer, or the exhaustive scan of every node.  Results
+ * are identical; only the work changes. */
+#define GRNG_FLAG_SMALL_BUFFERS 4ull
 
 typedef struct grng_index grng_index; /* opaque; owns all device state */
 

@@ -42,6 +42,10 @@ def lib():
         _lib.orc_rng_rows.argtypes = [P, i64, i32, i32, P, i64, P, i64, P]
         _lib.orc_verify_witness.restype = i32
         _lib.orc_verify_witness.argtypes = [P, i32, i32, i64, i64, i64]
+        _lib.orc_set_threads.restype = i32
+        _lib.orc_set_threads.argtypes = [i32]
+        _lib.orc_max_threads.restype = i32
+        _lib.orc_max_threads.argtypes = []
         _lib.orc_emst.restype = i64
         _lib.orc_emst.argtypes = [P, i64, i32, i32, P]
         _lib.orc_grng_brute.restype = i64
@@ -68,6 +72,15 @@ def _f32(X):
 
 def _p(a):
     return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def set_threads(t):
+    """Use t OpenMP threads from now on; returns the previous count."""
+    return int(lib().orc_set_threads(int(t)))
+
+
+def max_threads():
+    return int(lib().orc_max_threads())
 
 
 def key(a, b, metric=L2):

@@ -40,12 +40,21 @@
  *     duplicate never blocks.
  */
 #include <math.h>
+#include <omp.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
 
 #define ORC_L2 0
 #define ORC_L1 1
+
+/* OpenMP threads of the parallel loops below: set, and the number in use */
+int32_t orc_set_threads(int32_t t) {
+    int32_t prev = (int32_t)omp_get_max_threads();
+    if (t > 0) omp_set_num_threads(t);
+    return prev;
+}
+int32_t orc_max_threads(void) { return (int32_t)omp_get_max_threads(); }
 
 /* ---- canonical FP64 distances (Eq. 1 metric; L2 or L1) ---------------------- */
 
@@ -212,30 +221,48 @@ int32_t orc_verify_witness(const float *X, int32_t D, int32_t metric, int64_t x,
  * edges[n-1][2]; returns n-1, or -1 on allocation failure. */
 int64_t orc_emst(const float *X, int64_t n, int32_t D, int32_t metric, int32_t *edges) {
     if (n < 2) return 0;
+    int nt = omp_get_max_threads();
     double *best = (double *)malloc(sizeof(double) * (size_t)n);
     int64_t *from = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
     unsigned char *in = (unsigned char *)calloc((size_t)n, 1);
-    if (!best || !from || !in) { free(best); free(from); free(in); return -1; }
-    in[0] = 1;
-    for (int64_t v = 0; v < n; ++v) { best[v] = orc_key(X, X + v * D, D, metric); from[v] = 0; }
-    for (int64_t e = 0; e + 1 < n; ++e) {
-        int64_t u = -1;
-        double bu = 0.0;
-        for (int64_t v = 0; v < n; ++v)
-            if (!in[v] && (u < 0 || best[v] < bu)) { u = v; bu = best[v]; }
-        in[u] = 1;
-        edges[2 * e] = (int32_t)from[u];
-        edges[2 * e + 1] = (int32_t)u;
-#pragma omp parallel for schedule(static)
-        for (int64_t v = 0; v < n; ++v) {
-            if (in[v]) continue;
-            double k = orc_key(X + u * D, X + v * D, D, metric);
-            if (k < best[v]) { best[v] = k; from[v] = u; }
-        }
+    double *tmin = (double *)malloc(sizeof(double) * (size_t)nt);
+    int64_t *targ = (int64_t *)malloc(sizeof(int64_t) * (size_t)nt);
+    if (!best || !from || !in || !tmin || !targ) {
+        free(best); free(from); free(in); free(tmin); free(targ);
+        return -1;
     }
-    free(best);
-    free(from);
-    free(in);
+    for (int64_t v = 0; v < n; ++v) { best[v] = INFINITY; from[v] = 0; }
+    int64_t u = 0;                                   /* the tree grows from point 0 */
+    for (int64_t e = 0; e < n; ++e) {
+        in[u] = 1;
+        if (e > 0) {
+            edges[2 * (e - 1)] = (int32_t)from[u];
+            edges[2 * (e - 1) + 1] = (int32_t)u;
+        }
+        if (e == n - 1) break;
+        /* relax every point outside the tree through u, and find the closest one */
+#pragma omp parallel num_threads(nt)
+        {
+            int t = omp_get_thread_num();
+            double lb = INFINITY;
+            int64_t la = -1;
+#pragma omp for schedule(static)
+            for (int64_t v = 0; v < n; ++v) {
+                if (in[v]) continue;
+                double k = orc_key(X + u * D, X + v * D, D, metric);
+                if (k < best[v]) { best[v] = k; from[v] = u; }
+                if (la < 0 || best[v] < lb) { lb = best[v]; la = v; }
+            }
+            tmin[t] = lb;
+            targ[t] = la;
+        }
+        int64_t nu = -1;
+        double bu = INFINITY;
+        for (int t = 0; t < nt; ++t)      /* threads own increasing ranges: ties keep the lowest */
+            if (targ[t] >= 0 && (nu < 0 || tmin[t] < bu)) { nu = targ[t]; bu = tmin[t]; }
+        u = nu;
+    }
+    free(best); free(from); free(in); free(tmin); free(targ);
     return n - 1;
 }
 

@@ -81,9 +81,10 @@ def lib():
         L.grng_mlp_loss_grad.argtypes = [P, P, P, P, i64, f32p, P]
         L.grng_mlp_train.argtypes = [P, P, P, i64, i32, i32, ctypes.c_float, P, f32p]
         L.grng_mlp_dataset.argtypes = [P, P, P, i64, ctypes.POINTER(i64)]
+        L.grng_tc_keys.argtypes = [P, i64, i32, P]
         for f in ("grng_create", "grng_build_layer", "grng_link_pivots", "grng_adjacency_rows",
                   "rng_build_exact", "rng_insert_batch", "rng_edges", "grng_stats", "grng_mlp_score",
-                  "grng_mlp_loss_grad", "grng_mlp_train", "grng_mlp_dataset"):
+                  "grng_mlp_loss_grad", "grng_mlp_train", "grng_mlp_dataset", "grng_tc_keys"):
             getattr(L, f).restype = i32
         _lib = L
     return _lib
@@ -226,7 +227,17 @@ class Index:
 
 GRNG_FLAG_SHORT_LISTS = 1
 GRNG_FLAG_RECORD_MLP = 2
+GRNG_FLAG_SMALL_BUFFERS = 4
 MLP_IN = 32
+
+
+def tc_keys(points):
+    """Tensor-core (split BF16) Gram keys of all pairs of at most 256 points, float32 [n, n]."""
+    X = np.ascontiguousarray(points, np.float32)
+    n, d = X.shape
+    out = np.zeros((n, n), np.float32)
+    _check(lib().grng_tc_keys(X.ctypes.data, n, d, out.ctypes.data))
+    return out
 
 
 def mlp_nparams():

@@ -293,19 +293,22 @@ void level_json(std::string& js, const char* name, const LevelStats& st) {
                              "list_certified", "range_pairs", "range_lists_cut", "range_listed_nodes",
                              "range_links", "range_nodes_tested", "tier3_blocked",
                              "tier3_descent_blocked", "learned_pairs", "learned_candidates", "learned_tests",
-                             "learned_blocked", "learned_pool_hits"};
+                             "learned_blocked", "learned_pool_hits", "tier1_attempts", "tier23_attempts",
+                             "range_intersected", "range_probes", "range_entries_read"};
   char buf[1024];
   js += "\"";
   js += name;
   js += "\":{";
-  for (int i = 0; i < 30; ++i) {
+  for (int i = 0; i < 35; ++i) {
     snprintf(buf, sizeof(buf), "%s\"%s\":%llu", i ? "," : "", nm[i], (unsigned long long)st.c[i]);
     js += buf;
   }
   snprintf(buf, sizeof(buf),
            ",\"phase_ms\":{\"prep\":%.3f,\"tiles\":%.3f,\"tier2a\":%.3f,\"tier2b\":%.3f,\"range\":%.3f,"
-           "\"tier3\":%.3f,\"recheck_emit\":%.3f},\"kernel_ms\":{\"tiles\":%.4f,\"tier3\":%.4f,\"lists\":%.4f}",
-           st.ms[0], st.ms[1], st.ms[2], st.ms[3], st.ms[4], st.ms[5], st.ms[6], st.kms[0], st.kms[1], st.kms[2]);
+           "\"tier3\":%.3f,\"recheck_emit\":%.3f},\"kernel_ms\":{\"tiles\":%.4f,\"tier3\":%.4f,\"lists\":%.4f,"
+           "\"range_phase\":%.4f}",
+           st.ms[0], st.ms[1], st.ms[2], st.ms[3], st.ms[4], st.ms[5], st.ms[6], st.kms[0], st.kms[1], st.kms[2],
+           st.kms[3]);
   js += buf;
   js += "}";
 }
@@ -346,7 +349,7 @@ grng_status grng_create(grng_index** out, const float* pts, int64_t n, int32_t d
     if (opts->k_shortlist > 0 && (!opts->mlp_weights || opts->mlp_bytes != (size_t)GRNG_MLP_NPARAM * 4))
       fail(GRNG_EINVAL, "a shortlist needs mlp_weights of grng_mlp_nparams() floats (mlp_bytes)");
     if (opts->reserved != 0 ||
-        (opts->flags & ~(uint64_t)(GRNG_FLAG_SHORT_LISTS | GRNG_FLAG_RECORD_MLP)) != 0)
+        (opts->flags & ~(uint64_t)(GRNG_FLAG_SHORT_LISTS | GRNG_FLAG_RECORD_MLP | GRNG_FLAG_SMALL_BUFFERS)) != 0)
       fail(GRNG_EINVAL, "reserved fields must be 0");
     ix = new grng_index();
     GRNG_CUDA(cudaGetDevice(&ix->device));
@@ -481,6 +484,7 @@ grng_status grng_link_pivots(grng_index* ix, int32_t layer, const double* radius
     in.orig = ly.order.as<int32_t>();
     in.anc = ancestors_of(ix, layer);
     in.lmax = (ix->opts.flags & GRNG_FLAG_SHORT_LISTS) ? 16 : 0;
+    in.small_buffers = (ix->opts.flags & GRNG_FLAG_SMALL_BUFFERS) ? 1 : 0;
     in.pdist_hi = layer > 0 ? ly.pdh.as<float>() : nullptr;
     DevBuf ovr, o64, olo, ohi, tgx, tgg;
     Timer tm(s);
@@ -588,6 +592,7 @@ grng_status rng_build_exact(grng_index* ix) {
     in.mlp_params = ix->mlp.p ? ix->mlp.as<float>() : nullptr;
     in.kshort = ix->mlp.p ? ix->opts.k_shortlist : 0;
     in.mlp_record = (ix->opts.flags & GRNG_FLAG_RECORD_MLP) ? 1 : 0;
+    in.small_buffers = (ix->opts.flags & GRNG_FLAG_SMALL_BUFFERS) ? 1 : 0;
     LevelOut lo;
     lo.edges = &ix->edges;
     lo.rec_f = &ix->rec_f;

@@ -121,6 +121,7 @@ struct LevelIn {
   const float* mlp_params = nullptr;  // RNG level: ranking network (GRNG_MLP_NPARAM floats, device)
   int kshort = 0;                     // shortlist length tried before tier 3 (0: off)
   int mlp_record = 0;                 // RNG level: record features and labels of the tier-3 pairs' pools
+  int small_buffers = 0;              // testing: tiny first capacities, so every retry and fallback runs
 };
 
 // ---- tensor-core tiles (kernels_tc.cu) ------------------------------------------------------
@@ -171,9 +172,10 @@ struct LevelOut {
   int64_t rec_n = 0;
 };
 struct LevelStats {
-  unsigned long long c[32];
+  unsigned long long c[40];
   double ms[8];  // prep, tile sweeps, tier-2 grouping + 2a, tier 2b, range lists, tier 3, recheck + emit
-  double kms[3];  // CUDA-event time of the tile sweep kernel(s), the tier-3 kernel and the range-list tier
+  double kms[4];  // CUDA-event time of the tile sweep kernel(s), the tier-3 kernel, the list tier kernel
+                  // and the whole range-list phase (thresholds, both sweeps, cut, sides, list tier)
 };
 // ---- learned shortlist (kernels_mlp.cu) -------------------------------------------------------
 #define GRNG_MLP_IN 32

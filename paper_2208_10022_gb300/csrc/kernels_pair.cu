@@ -1104,15 +1104,23 @@ static void launch_cross(const float* Xr, int64_t nr, const float* Xc, int64_t n
 // ---------------------------------------------------------------------------------
 // Range lists (pivot layers): pairs that neither endpoint's neighbour list covers.
 // Every endpoint s of such a pair gets T_s, the largest threshold among its pairs.
-// One sweep histograms, per node, the keys below T_s (16 bins per octave of key);
-// the list radius is then cut to the largest bin edge T'_s that keeps at most
-// GRNG_LMAX nodes, and a second sweep lists every node with key < T'_s.  A pair is
-// covered from a side whose T'_s reaches past its threshold on that side: every node
-// that could satisfy that condition is then listed, and only the listed nodes of the
-// pair's annulus are tested.  Uncovered pairs go to the exhaustive tier.
+// One sweep histograms, per node, the keys below T_s in buckets of 1/16 octave of
+// key (bucket = hist_bin(key, T_s)); the list keeps the lowest buckets whose total
+// stays within the list length, and a second sweep writes every such node into its
+// bucket's slots, so a list is ordered by bucket (unordered inside one).  T'_s, a
+// lower bound of every key the list leaves out, decides coverage: a pair is covered
+// from a side whose T'_s reaches past its threshold on that side, because every node
+// that could satisfy that condition is then listed (GRNG definition, Sec. 2).
+//   - covered from both sides: a blocker must appear in both lists (a node missing
+//     from a covering list certainly fails that side's condition), and both lists
+//     carry the node's keys to their endpoint, so the test is the intersection of the
+//     two lists' annuli, with no distance computed;
+//   - covered from one side: the annulus of that side's list is tested by distance to
+//     the other endpoint;
+//   - uncovered pairs go to the exhaustive tier.
 // ---------------------------------------------------------------------------------
-#define GRNG_LMAX 8192  // target list length
-#define GRNG_LCAP 16384  // list capacity (bin-edge rounding can add a few nodes)
+#define GRNG_LMAX 8192  // list length (a list never exceeds it: its buckets are counted first)
+#define GRNG_LCAP 8192  // list slots per node
 #define GRNG_HBINS 128
 
 struct SideParams {
@@ -1122,10 +1130,10 @@ struct SideParams {
   const float* rhi;
   const int2* pairs;
   int64_t m;
-  int8_t* side;               // 3: linked; otherwise set by pick_side_kernel
+  int8_t* side;               // 3: linked; 0 / 1: covered from x / y only; 4: both; 2: neither
   unsigned int* tkey;         // [n] float bits of T_s (key units)
   const unsigned int* tcut;   // [n] float bits of T'_s
-  const int* lcnt;            // [n] listed nodes (> GRNG_LCAP: incomplete)
+  const int* lcnt;            // [n] listed nodes
 };
 
 __device__ __forceinline__ PairThr thr_of(const SideParams& p, int a, int b, float v, Err e) {
@@ -1147,7 +1155,7 @@ __global__ void range_thresholds_kernel(SideParams p) {
   atomicMax(p.tkey + b, __float_as_uint(P.t2hi));
 }
 
-// a covered side with the shorter list, or 2 (exhaustive tier)
+// which sides cover the pair
 __global__ void pick_side_kernel(SideParams p) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= p.m || p.side[t] == 3) return;
@@ -1157,37 +1165,44 @@ __global__ void pick_side_kernel(SideParams p) {
   const PairThr P = thr_of(p, a, b, v, e);
   const bool ca = p.lcnt[a] <= GRNG_LCAP && lo_b(__uint_as_float(p.tcut[a]), e) >= P.t1hi;
   const bool cb = p.lcnt[b] <= GRNG_LCAP && lo_b(__uint_as_float(p.tcut[b]), e) >= P.t2hi;
-  p.side[t] = (int8_t)(ca && cb ? (p.lcnt[b] < p.lcnt[a] ? 1 : 0) : ca ? 0 : cb ? 1 : 2);
+  p.side[t] = (int8_t)(ca && cb ? 4 : ca ? 0 : cb ? 1 : 2);
 }
 
+// Bucket of a key below T: 16 buckets per octave of key, 0 for everything under
+// T / 2^(127/16).  The same function (same inputs, same code) places keys in the
+// histogram and in the lists, so the bucket counts are the list's.
 __device__ __forceinline__ int hist_bin(float v, float T) {
   const float l = log2f(fmaxf(v, 1e-37f) / T);  // < 0 for v < T
   return max(0, min(GRNG_HBINS - 1, (int)floorf(16.0f * l) + GRNG_HBINS));
 }
 
-// mode 0: per-row histogram of keys below T_s; mode 1: list every node with key < T'_s
+// mode 0: per-row histogram of keys below T_s; mode 1: every node with key < T_s whose
+// bucket is at most the row's last listed bucket, written at its bucket's cursor
 template <int KC, int METRIC>
 __global__ void __launch_bounds__(GRNG_THREADS) range_sweep_kernel(const float* __restrict__ X, int64_t n, int Dp,
                                                                    const unsigned int* __restrict__ tkey,
                                                                    int* __restrict__ hist,
-                                                                   int* __restrict__ lcnt,
+                                                                   const int* __restrict__ lastb,
+                                                                   const int* __restrict__ boff,
                                                                    int32_t* __restrict__ lidx,
                                                                    float* __restrict__ lkey, int fill) {
   extern __shared__ __align__(16) unsigned char sm_raw[];
   float* sA = reinterpret_cast<float*>(sm_raw);
   float* sB = sA + KC * GRNG_SSTRIDE;
   float* T = sB + KC * GRNG_SSTRIDE;
-  int* H = reinterpret_cast<int*>(T + 128 * 129);  // [GRNG_HBINS][128]: lanes = rows
+  int* H = reinterpret_cast<int*>(T + 128 * 129);  // [GRNG_HBINS][128]: lanes = rows (counts or cursors)
   const int64_t xb = (int64_t)blockIdx.x * GRNG_TILE;
   const int nr = (int)(n - xb < GRNG_TILE ? n - xb : GRNG_TILE);
   const int tid = threadIdx.x;
   const float Tr = tid < nr ? __uint_as_float(tkey[xb + tid]) : 0.0f;
-  const bool act = tid < nr && Tr > 0.0f;
+  const int lastr = (fill && tid < nr) ? lastb[xb + tid] : GRNG_HBINS - 1;
+  const bool act = tid < nr && Tr > 0.0f && lastr >= 0;
   if (!__syncthreads_or(act)) return;
-  if (!fill)
-    for (int i = tid; i < GRNG_HBINS * 128; i += GRNG_THREADS) H[i] = 0;
+  for (int i = tid; i < GRNG_HBINS * 128; i += GRNG_THREADS) {
+    const int b = i >> 7, r = i & 127;
+    H[i] = (fill && r < nr) ? boff[(xb + r) * (GRNG_HBINS + 1) + b] : 0;
+  }
   const int64_t nb = (n + GRNG_TILE - 1) / GRNG_TILE;
-  int c_row = 0;
   for (int64_t by = 0; by < nb; ++by) {
     const int64_t yb = by * GRNG_TILE;
     const int nc = (int)(n - yb < GRNG_TILE ? n - yb : GRNG_TILE);
@@ -1204,45 +1219,55 @@ __global__ void __launch_bounds__(GRNG_THREADS) range_sweep_kernel(const float* 
         if (k == xb + tid) continue;
         const float v = T[tid * 129 + c];
         if (v < Tr) {
-          if (fill) {
-            if (c_row < GRNG_LCAP) {
-              lidx[(xb + tid) * GRNG_LCAP + c_row] = (int32_t)k;
-              lkey[(xb + tid) * GRNG_LCAP + c_row] = v;
+          const int b = hist_bin(v, Tr);
+          if (!fill) {
+            ++H[b * 128 + tid];
+          } else if (b <= lastr) {
+            const int pos = H[b * 128 + tid]++;
+            if (pos < GRNG_LCAP) {  // always: the counts of both sweeps agree
+              lidx[(xb + tid) * GRNG_LCAP + pos] = (int32_t)k;
+              lkey[(xb + tid) * GRNG_LCAP + pos] = v;
             }
-            ++c_row;
-          } else {
-            ++H[hist_bin(v, Tr) * 128 + tid];
           }
         }
       }
     }
     __syncthreads();
   }
-  if (tid < nr) {
-    if (fill) lcnt[xb + tid] = act ? c_row : 0;
-    else
-      for (int b = 0; b < GRNG_HBINS; ++b) hist[(xb + tid) * GRNG_HBINS + b] = H[b * 128 + tid];
-  }
+  if (!fill && tid < nr)
+    for (int b = 0; b < GRNG_HBINS; ++b) hist[(xb + tid) * GRNG_HBINS + b] = H[b * 128 + tid];
 }
 
-// T'_s = upper edge of the last histogram bin that keeps the cumulative count <= lmax
+// The last bucket that keeps the cumulative count <= lmax, the bucket offsets of the
+// list, its length, and T'_s: T_s when every bucket is listed, otherwise the lower edge
+// of the first bucket left out, shrunk by 2^-16 relative -- far more than the error of
+// hist_bin (a float log2 of a quotient, a few 2^-24 in 16 log2 units against 16 * 2^-16
+// / ln 2), so every key below T'_s lies in a listed bucket.
 __global__ void range_cut_kernel(const unsigned int* __restrict__ tkey, const int* __restrict__ hist, int64_t n,
-                                 unsigned int* __restrict__ tcut, int lmax) {
+                                 unsigned int* __restrict__ tcut, int* __restrict__ lastb, int* __restrict__ boff,
+                                 int* __restrict__ lcnt, int lmax) {
   const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= n) return;
   const float T = __uint_as_float(tkey[s]);
-  float cut = 0.0f;
+  int last = -1, cum = 0;
+  int* bo = boff + s * (GRNG_HBINS + 1);
+  bo[0] = 0;
   if (T > 0.0f) {
-    int cum = 0, last = -1;
     for (int b = 0; b < GRNG_HBINS; ++b) {
-      cum += hist[s * GRNG_HBINS + b];
-      if (cum > lmax) break;
+      const int h = hist[s * GRNG_HBINS + b];
+      if (cum + h > lmax) break;
+      cum += h;
       last = b;
+      bo[b + 1] = cum;
     }
-    if (last == GRNG_HBINS - 1) cut = T;
-    else if (last >= 0) cut = T * exp2f((float)(last + 1 - GRNG_HBINS) / 16.0f);
   }
+  for (int b = last + 1; b < GRNG_HBINS; ++b) bo[b + 1] = cum;
+  float cut = 0.0f;
+  if (last == GRNG_HBINS - 1) cut = T;
+  else if (last >= 0) cut = T * exp2f((float)(last + 1 - GRNG_HBINS) / 16.0f) * (1.0f - 1.52587890625e-05f);
   tcut[s] = __float_as_uint(cut);
+  lastb[s] = last;
+  lcnt[s] = cum;
 }
 
 struct ListParams {
@@ -1253,23 +1278,61 @@ struct ListParams {
   const int2* pairs;
   int64_t m;
   const int8_t* side;
-  const int* lcnt;      // listed nodes of each node (slots of GRNG_LCAP)
+  const unsigned int* tkey;  // [n] T_s
+  const int* lastb;          // [n] last listed bucket (-1: empty list)
+  const int* boff;           // [n][GRNG_HBINS + 1] start of each bucket in the list
   const int32_t* lidx;
   const float* lkey;
+  // node x ancestor key table (or null): column toff + c holds key(node, parent-level node c);
+  // parent[k] is k's parent, pdh[k] an upper bound of d(k, parent[k])
+  const float* atab;
+  int64_t tabw, toff;
+  const int32_t* parent;
+  const float* pdh;
   int2* links; unsigned long long* link_cnt; unsigned long long link_cap;
   int2* unres; unsigned long long* unres_cnt; unsigned long long unres_cap;
   int2* pend; unsigned long long* pend_cnt; unsigned long long pend_cap;
   int2* amb; unsigned long long* amb_cnt; unsigned long long amb_cap;
-  unsigned long long* stats;  // [0] links [1] pending [2] to tier 3 [3] blocked [4] listed nodes tested
+  unsigned long long* stats;  // [0] links [1] pending [2] to tier 3 [3] blocked [4] listed nodes tested by
+                              // distance [5] pairs decided by intersection [6] intersection probes
+                              // [7] list entries read
 };
 
-// one warp per pair
-__global__ void __launch_bounds__(256) list_tier_kernel(ListParams p) {
-  const int lane = threadIdx.x & 31;
+// Entries [first, last) of s's list whose keys may lie in (klo, khi): the buckets from
+// one below klo's to one above khi's (hist_bin carries far less than a bucket of error,
+// the FP32 brackets of the filters less again; for bounds below 1e-30 the absolute term
+// of the bracket could span buckets, so the span then runs to the end of the list).
+__device__ __forceinline__ int2 bucket_span(const ListParams& p, int s, float klo, float khi) {
+  const int last = p.lastb[s];
+  if (last < 0 || !(khi > 0.0f)) return make_int2(0, 0);
+  const float T = __uint_as_float(p.tkey[s]);
+  const int b0 = klo > 1e-30f ? max(hist_bin(klo, T) - 1, 0) : 0;
+  const int b1 = khi > 1e-30f ? min(hist_bin(khi, T) + 1, last) : last;
+  if (b1 < b0) return make_int2(0, 0);
+  const int* bo = p.boff + (int64_t)s * (GRNG_HBINS + 1);
+  return make_int2(bo[b0], bo[b1 + 1]);
+}
+
+#define LT_WARPS 8
+#define LT_TAB 1024            // hash slots per warp (intersection of two list annuli)
+#define LT_CHUNK (LT_TAB / 2)  // entries hashed per round: load factor at most 1/2
+
+__device__ __forceinline__ unsigned lt_hash(int k) { return ((unsigned)k * 2654435761u) >> (32 - 10); }
+
+// One warp per pair.  G lanes share one listed node in the distance scan (G = 8 for
+// dimensions that are multiples of 32, fewer for 8 and 16); NQ = float4 columns per lane
+// (0: any dimension, the other endpoint's row read from memory).
+template <int G, int NQ>
+__global__ void __launch_bounds__(LT_WARPS * 32, 2) list_tier_kernel(ListParams p) {
+  extern __shared__ __align__(16) int lt_sm[];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  int* tab_i = lt_sm + wib * 2 * LT_TAB;                          // node ids (-1: empty)
+  float* tab_k = reinterpret_cast<float*>(tab_i + LT_TAB);       // their keys
   const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const Err e = err_fp32(p.Dp);
-  unsigned long long c_link = 0, c_pend = 0, c_un = 0, c_blk = 0, c_test = 0;
+  const int gl = lane % G, gi = lane / G;
+  unsigned long long c_link = 0, c_pend = 0, c_un = 0, c_blk = 0, c_test = 0, c_isect = 0, c_probe = 0, c_read = 0;
   for (int64_t t = wid; t < p.m; t += nw) {
     const int sd = p.side[t];
     const int2 pr = p.pairs[t];
@@ -1283,64 +1346,250 @@ __global__ void __launch_bounds__(256) list_tier_kernel(ListParams p) {
       c_un += lane == 0;
       continue;
     }
-    const int s = sd ? pr.y : pr.x, o = sd ? pr.x : pr.y;
-    const float* xs = p.X + (int64_t)s * p.Dp;
-    const float* xo = p.X + (int64_t)o * p.Dp;
-    const float v = key32(xs, xo, p.Dp, p.metric);
-    const PairThr P = pair_thresholds(v, p.rlo ? p.rlo[s] : 0.0f, p.rhi ? p.rhi[s] : 0.0f,
-                                      p.rlo ? p.rlo[o] : 0.0f, p.rhi ? p.rhi[o] : 0.0f, p.metric, e, p.guide);
+    const int x = pr.x, y = pr.y;
+    const float v = key32(p.X + (int64_t)x * p.Dp, p.X + (int64_t)y * p.Dp, p.Dp, p.metric);
+    const PairThr P = pair_thresholds(v, p.rlo ? p.rlo[x] : 0.0f, p.rhi ? p.rhi[x] : 0.0f,
+                                      p.rlo ? p.rlo[y] : 0.0f, p.rhi ? p.rhi[y] : 0.0f, p.metric, e, p.guide);
     if (P.quick) {
       if (lane == 0) push_pair(p.links, p.link_cnt, p.link_cap, pr);
       c_link += lane == 0;
       continue;
     }
-    const float ekey = excl_key(excl_dist(v, P.t2hi, p.metric, e), p.metric);
-    const int64_t j0 = (int64_t)s * GRNG_LCAP, j1 = j0 + p.lcnt[s];
+    // nodes within E of one endpoint cannot satisfy the other endpoint's condition
+    const float ekx = excl_key(excl_dist(v, P.t2hi, p.metric, e), p.metric);
+    const float eky = excl_key(excl_dist(v, P.t1hi, p.metric, e), p.metric);
     bool blocked = false, anyamb = false;
-    for (int64_t jb = j0; jb < j1 && !blocked; jb += 32) {
-      const int64_t j = jb + lane;
-      int stt = 0;
-      if (j < j1) {
-        const float kk = p.lkey[j];
-        const int k = p.lidx[j];
-        if (k != o && lo_b(kk, e) < P.t1hi && hi_b(kk, e) > ekey) {
-          stt = block_state(kk, key32(p.X + (int64_t)k * p.Dp, xo, p.Dp, p.metric), P, e);
-          ++c_test;
+    unsigned long long slot = 0;
+    if (sd == 4) {
+      // ---- both lists cover: a blocker is a node of both annuli ----------------------
+      const int2 ax = bucket_span(p, x, ekx, P.t1hi), ay = bucket_span(p, y, eky, P.t2hi);
+      const bool hy = (ay.y - ay.x) <= (ax.y - ax.x);  // hash the shorter annulus
+      const int hs = hy ? y : x, qs = hy ? x : y;
+      const int2 hspan = hy ? ay : ax, qspan = hy ? ax : ay;
+      const float hlo = hy ? eky : ekx, hhi = hy ? P.t2hi : P.t1hi;
+      const float qlo = hy ? ekx : eky, qhi = hy ? P.t1hi : P.t2hi;
+      const int64_t hb = (int64_t)hs * GRNG_LCAP, qb = (int64_t)qs * GRNG_LCAP;
+      for (int pass = 0; pass < 2; ++pass) {  // pass 1 records the ambiguous triples
+        if (pass == 1) {
+          if (blocked || !anyamb) break;
+          if (lane == 0) slot = atomicAdd(p.pend_cnt, 1ull);
+          slot = __shfl_sync(FULLMASK, slot, 0);
+          if (lane == 0 && slot < p.pend_cap) p.pend[slot] = pr;
+        }
+        for (int h0 = hspan.x; h0 < hspan.y && !blocked; h0 += LT_CHUNK) {
+          __syncwarp();
+          for (int i = lane; i < LT_TAB; i += 32) tab_i[i] = -1;
+          __syncwarp();
+          const int h1 = min(h0 + LT_CHUNK, hspan.y);
+          for (int j = h0 + lane; j < h1; j += 32) {
+            ++c_read;
+            const float kk = p.lkey[hb + j];
+            if (lo_b(kk, e) < hhi && hi_b(kk, e) > hlo) {
+              const int k = p.lidx[hb + j];
+              unsigned h = lt_hash(k);
+              for (int probe = 0; probe < LT_TAB; ++probe) {  // at most half the slots are taken
+                if (atomicCAS(tab_i + h, -1, k) == -1) { tab_k[h] = kk; break; }
+                h = (h + 1) & (LT_TAB - 1);
+              }
+            }
+          }
+          __syncwarp();
+          for (int jb = qspan.x; jb < qspan.y; jb += 32) {
+            const int j = jb + lane;
+            int stt = 0, k = -1;
+            if (j < qspan.y) {
+              c_read += pass == 0;
+              const float kk = p.lkey[qb + j];
+              if (lo_b(kk, e) < qhi && hi_b(kk, e) > qlo) {
+                k = p.lidx[qb + j];
+                unsigned h = lt_hash(k);
+                ++c_probe;
+                for (int probe = 0; probe < LT_TAB; ++probe) {
+                  const int w = tab_i[h];
+                  if (w == -1) break;
+                  if (w == k) {
+                    const float other = tab_k[h];
+                    const float a = hy ? kk : other, b = hy ? other : kk;  // keys to x and to y
+                    stt = block_state(a, b, P, e);
+                    break;
+                  }
+                  h = (h + 1) & (LT_TAB - 1);
+                }
+              }
+            }
+            if (pass == 0) {
+              blocked = __any_sync(FULLMASK, stt == 2);
+              anyamb |= __any_sync(FULLMASK, stt == 1);
+              if (blocked) break;
+            } else if (stt == 1) {
+              push_pair(p.amb, p.amb_cnt, p.amb_cap, make_int2((int)slot, k));
+            }
+          }
         }
       }
-      blocked = __any_sync(FULLMASK, stt == 2);
-      anyamb |= __any_sync(FULLMASK, stt == 1);
+      c_isect += lane == 0;
+    } else {
+      // ---- one list covers: its annulus, tested against the other endpoint o ----------------
+      // Each listed node k is first bounded through its parent c, whose keys to s and o the
+      // ancestor table holds: d(k,o) >= d(c,o) - d(k,c) settles "k fails the condition at o"
+      // (triangle inequality), and for L2 |k - c*| >= |c - c*| - d(k,c) >= rho puts k outside
+      // the ball around the G-lune (Stewart's identity, as in tier 3); d(k,o) <= d(c,o) + d(k,c)
+      // can settle "k blocks".  Only the nodes no bound settles get their distance to o.
+      const int s = sd ? y : x, o = sd ? x : y;
+      const float slo = sd ? eky : ekx, shi = sd ? P.t2hi : P.t1hi;
+      const float olo_k = sd ? P.t1lo : P.t2lo, ohi_k = sd ? P.t1hi : P.t2hi;  // thresholds at o (keys)
+      const float slo_k = sd ? P.t2lo : P.t1lo;                                // certain side at s
+      const int2 sp = bucket_span(p, s, slo, shi);
+      const int64_t sb = (int64_t)s * GRNG_LCAP;
+      const float* xo = p.X + (int64_t)o * p.Dp;
+      const float u2 = 1.1920928955078125e-07f;
+      // thresholds at o in distance units: above ohd no node satisfies it, below old every one does
+      const float ohd = p.metric == L2 ? sqrtf(fmaxf(ohi_k, 0.0f)) * (1.0f + u2) : ohi_k;
+      const float old_ = p.metric == L2 ? (olo_k > 0.0f ? sqrtf(olo_k) * (1.0f - u2) : -1.0f) : olo_k;
+      // ball around the G-lune (L2): centre c* = (1-lam) x + lam y, radius rho
+      const float vlo = fmaxf(lo_b(v, e), 0.0f), vhi = hi_b(v, e);
+      float lam = 0.5f, rho2 = -1.0f;
+      if (p.metric == L2) {
+        lam = fminf(fmaxf((vhi + P.t1hi - P.t2hi) / (2.0f * fmaxf(vhi, 1e-30f)), 0.0f), 1.0f);
+        const float m1 = (1.0f - lam) * P.t1hi + lam * P.t2hi;
+        rho2 = m1 - lam * (1.0f - lam) * vlo + 8.0f * u2 * (m1 + lam * (1.0f - lam) * vhi);
+      }
+      const float rho = rho2 >= 0.0f ? sqrtf(rho2) * (1.0f + u2) : -1.0f;
+      const float* tab_x = p.atab ? p.atab + (int64_t)x * p.tabw + p.toff : nullptr;
+      const float* tab_y = p.atab ? p.atab + (int64_t)y * p.tabw + p.toff : nullptr;
+      float4 orow[NQ > 0 ? NQ : 1];
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) orow[q] = __ldg(reinterpret_cast<const float4*>(xo) + gl + G * q);
+      for (int pass = 0; pass < 2; ++pass) {
+        if (pass == 1) {
+          if (blocked || !anyamb) break;
+          if (lane == 0) slot = atomicAdd(p.pend_cnt, 1ull);
+          slot = __shfl_sync(FULLMASK, slot, 0);
+          if (lane == 0 && slot < p.pend_cap) p.pend[slot] = pr;
+        }
+        for (int jb = sp.x; jb < sp.y; jb += 32) {
+          // ---- one entry per lane: filters and bounds ----
+          const int j = jb + lane;
+          bool need = false;
+          float kk = 0.0f;
+          int k = -1, stt = 0;
+          if (j < sp.y) {
+            c_read += pass == 0;
+            kk = p.lkey[sb + j];
+            const int kj = p.lidx[sb + j];
+            if (kj != o && lo_b(kk, e) < shi && hi_b(kk, e) > slo) {
+              k = kj;
+              need = true;
+              if (p.atab) {
+                const int c = p.parent[k];
+                const float dk = p.pdh[k];
+                const float kcx = tab_x[c], kcy = tab_y[c];
+                const float kco = sd ? kcx : kcy;
+                const float dlo_ = dist_lo(kco, p.metric, e), dhi_ = dist_hi(kco, p.metric, e);
+                if (dlo_ - dk - u2 * (dlo_ + dk) >= ohd) {
+                  need = false;  // k fails the condition at o
+                } else if (rho >= 0.0f) {
+                  const float Alo = fmaxf(lo_b(kcx, e), 0.0f), Blo = fmaxf(lo_b(kcy, e), 0.0f);
+                  const float Ahi = hi_b(kcx, e), Bhi = hi_b(kcy, e);
+                  const float mm = (1.0f - lam) * Ahi + lam * Bhi + lam * (1.0f - lam) * vhi;
+                  const float qq = (1.0f - lam) * Alo + lam * Blo - lam * (1.0f - lam) * vhi - 8.0f * u2 * mm;
+                  const float dcs = qq > 0.0f ? sqrtf(qq) * (1.0f - u2) : 0.0f;
+                  if (dcs - dk - u2 * (dcs + dk) >= rho) need = false;  // k outside the lune's ball
+                }
+                if (need && old_ > 0.0f && dhi_ + dk + u2 * (dhi_ + dk) < old_ && hi_b(kk, e) < slo_k) {
+                  need = false;  // d(k,o) < the certain threshold at o, and k certainly meets s's
+                  stt = 2;
+                }
+              }
+            }
+          }
+          if (pass == 0) {
+            blocked = __any_sync(FULLMASK, stt == 2);
+            if (blocked) break;
+          }
+          // ---- the unsettled entries, G lanes per distance ----
+          unsigned nm = __ballot_sync(FULLMASK, need);
+          while (nm) {
+            // group gi takes the gi-th remaining entry
+            unsigned mm_ = nm;
+            for (int t = 0; t < gi && mm_; ++t) mm_ &= mm_ - 1u;
+            const int src = mm_ ? __ffs(mm_) - 1 : -1;
+            for (int t = 0; t < 32 / G && nm; ++t) nm &= nm - 1u;
+            const int kq = __shfl_sync(FULLMASK, k, src < 0 ? 0 : src);
+            const float kkq = __shfl_sync(FULLMASK, kk, src < 0 ? 0 : src);
+            const int krow = src < 0 ? o : kq;  // a safe row to read when the group has no entry
+            const float4* xk = reinterpret_cast<const float4*>(p.X + (int64_t)krow * p.Dp);
+            float acc = 0.0f;
+            if (NQ > 0) {
+#pragma unroll
+              for (int q = 0; q < (NQ > 0 ? NQ : 1); ++q) {
+                const float4 a4 = __ldg(xk + gl + G * q), b4 = orow[q];
+                if (p.metric == L2) {
+                  float d;
+                  d = a4.x - b4.x; acc = fmaf(d, d, acc); d = a4.y - b4.y; acc = fmaf(d, d, acc);
+                  d = a4.z - b4.z; acc = fmaf(d, d, acc); d = a4.w - b4.w; acc = fmaf(d, d, acc);
+                } else {
+                  acc += fabsf(a4.x - b4.x); acc += fabsf(a4.y - b4.y); acc += fabsf(a4.z - b4.z);
+                  acc += fabsf(a4.w - b4.w);
+                }
+              }
+            } else {
+              const float4* x4 = reinterpret_cast<const float4*>(xo);
+              for (int q = gl; q < (p.Dp >> 2); q += G) {
+                const float4 a4 = __ldg(xk + q), b4 = __ldg(x4 + q);
+                if (p.metric == L2) {
+                  float d;
+                  d = a4.x - b4.x; acc = fmaf(d, d, acc); d = a4.y - b4.y; acc = fmaf(d, d, acc);
+                  d = a4.z - b4.z; acc = fmaf(d, d, acc); d = a4.w - b4.w; acc = fmaf(d, d, acc);
+                } else {
+                  acc += fabsf(a4.x - b4.x); acc += fabsf(a4.y - b4.y); acc += fabsf(a4.z - b4.z);
+                  acc += fabsf(a4.w - b4.w);
+                }
+              }
+            }
+#pragma unroll
+            for (int sh = G / 2; sh > 0; sh >>= 1) acc += __shfl_xor_sync(FULLMASK, acc, sh);
+            int st2 = 0;
+            if (src >= 0) {
+              // keys of kq to x and to y: the listed key is to s
+              const float a = sd ? acc : kkq, b = sd ? kkq : acc;
+              st2 = block_state(a, b, P, e);
+              c_test += (gl == 0 && pass == 0);
+            }
+            if (pass == 0) {
+              if (__any_sync(FULLMASK, st2 == 2)) { blocked = true; break; }
+              anyamb |= __any_sync(FULLMASK, st2 == 1);
+            } else if (st2 == 1 && gl == 0) {
+              push_pair(p.amb, p.amb_cnt, p.amb_cap, make_int2((int)slot, kq));
+            }
+          }
+          if (pass == 0 && blocked) break;
+        }
+      }
     }
     if (blocked) {
       c_blk += lane == 0;
     } else if (!anyamb) {
       if (lane == 0) push_pair(p.links, p.link_cnt, p.link_cap, pr);
       c_link += lane == 0;
-    } else {  // rare: record the ambiguous triples for the FP64 recheck
-      unsigned long long slot = 0;
-      if (lane == 0) slot = atomicAdd(p.pend_cnt, 1ull);
-      slot = __shfl_sync(FULLMASK, slot, 0);
-      if (lane == 0 && slot < p.pend_cap) p.pend[slot] = pr;
-      for (int64_t jb = j0; jb < j1; jb += 32) {
-        const int64_t j = jb + lane;
-        if (j < j1) {
-          const float kk = p.lkey[j];
-          const int k = p.lidx[j];
-          if (k != o && lo_b(kk, e) < P.t1hi && hi_b(kk, e) > ekey &&
-              block_state(kk, key32(p.X + (int64_t)k * p.Dp, xo, p.Dp, p.metric), P, e) == 1)
-            push_pair(p.amb, p.amb_cnt, p.amb_cap, make_int2((int)slot, k));
-        }
-      }
+    } else {
       c_pend += lane == 0;
     }
   }
-  for (int sh = 16; sh > 0; sh >>= 1) c_test += __shfl_down_sync(FULLMASK, c_test, sh);
+  for (int sh = 16; sh > 0; sh >>= 1) {
+    c_test += __shfl_down_sync(FULLMASK, c_test, sh);
+    c_probe += __shfl_down_sync(FULLMASK, c_probe, sh);
+    c_read += __shfl_down_sync(FULLMASK, c_read, sh);
+  }
   if (lane == 0) {
     atomicAdd(p.stats + 0, c_link);
     atomicAdd(p.stats + 1, c_pend);
     atomicAdd(p.stats + 2, c_un);
     atomicAdd(p.stats + 3, c_blk);
     atomicAdd(p.stats + 4, c_test);
+    atomicAdd(p.stats + 5, c_isect);
+    atomicAdd(p.stats + 6, c_probe);
+    atomicAdd(p.stats + 7, c_read);
   }
 }
 
@@ -1416,25 +1665,47 @@ static void launch_tile(const LevelIn& in, TileParams tp, int grid, cudaStream_t
 }
 
 template <int KC>
-static void launch_range_kc(const LevelIn& in, const unsigned int* tk, int* hist, int* lcnt, int32_t* li, float* lk,
-                            int fill, cudaStream_t s) {
+static void launch_range_kc(const LevelIn& in, const unsigned int* tk, int* hist, const int* lastb, const int* boff,
+                            int32_t* li, float* lk, int fill, cudaStream_t s) {
   const int64_t nb = (in.n + GRNG_TILE - 1) / GRNG_TILE;
   const size_t smem = (size_t)(2 * KC * GRNG_SSTRIDE + 128 * 129) * 4 + (size_t)GRNG_HBINS * 128 * 4;
   if (in.metric == L2) {
     GRNG_CUDA(cudaFuncSetAttribute(range_sweep_kernel<KC, L2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    range_sweep_kernel<KC, L2><<<(unsigned)nb, GRNG_THREADS, smem, s>>>(in.X, in.n, in.Dp, tk, hist, lcnt, li, lk, fill); note_launch();
+    range_sweep_kernel<KC, L2><<<(unsigned)nb, GRNG_THREADS, smem, s>>>(in.X, in.n, in.Dp, tk, hist, lastb, boff, li,
+                                                                         lk, fill); note_launch();
   } else {
     GRNG_CUDA(cudaFuncSetAttribute(range_sweep_kernel<KC, L1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    range_sweep_kernel<KC, L1><<<(unsigned)nb, GRNG_THREADS, smem, s>>>(in.X, in.n, in.Dp, tk, hist, lcnt, li, lk, fill); note_launch();
+    range_sweep_kernel<KC, L1><<<(unsigned)nb, GRNG_THREADS, smem, s>>>(in.X, in.n, in.Dp, tk, hist, lastb, boff, li,
+                                                                         lk, fill); note_launch();
   }
   GRNG_CUDA(cudaGetLastError());
 }
-static void launch_range(const LevelIn& in, const unsigned int* tk, int* hist, int* lcnt, int32_t* li, float* lk,
-                         int fill, cudaStream_t s) {
+static void launch_range(const LevelIn& in, const unsigned int* tk, int* hist, const int* lastb, const int* boff,
+                         int32_t* li, float* lk, int fill, cudaStream_t s) {
   const int KC = in.Dp % 32 == 0 ? 32 : (in.Dp % 16 == 0 ? 16 : 8);
-  if (KC == 32) launch_range_kc<32>(in, tk, hist, lcnt, li, lk, fill, s);
-  else if (KC == 16) launch_range_kc<16>(in, tk, hist, lcnt, li, lk, fill, s);
-  else launch_range_kc<8>(in, tk, hist, lcnt, li, lk, fill, s);
+  if (KC == 32) launch_range_kc<32>(in, tk, hist, lastb, boff, li, lk, fill, s);
+  else if (KC == 16) launch_range_kc<16>(in, tk, hist, lastb, boff, li, lk, fill, s);
+  else launch_range_kc<8>(in, tk, hist, lastb, boff, li, lk, fill, s);
+}
+
+template <int G, int NQ>
+static void launch_list_gq(const ListParams& lp, unsigned grid, cudaStream_t s) {
+  const size_t smem = (size_t)LT_WARPS * 2 * LT_TAB * 4;
+  GRNG_CUDA(cudaFuncSetAttribute(list_tier_kernel<G, NQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  list_tier_kernel<G, NQ><<<grid, LT_WARPS * 32, smem, s>>>(lp); note_launch();
+  GRNG_CUDA(cudaGetLastError());
+}
+// group width and float4 columns per lane for the padded dimension (8, 16 or a multiple of 32)
+static void launch_list(const ListParams& lp, unsigned grid, cudaStream_t s) {
+  switch (lp.Dp) {
+    case 8: launch_list_gq<2, 1>(lp, grid, s); break;
+    case 16: launch_list_gq<4, 1>(lp, grid, s); break;
+    case 32: launch_list_gq<8, 1>(lp, grid, s); break;
+    case 64: launch_list_gq<8, 2>(lp, grid, s); break;
+    case 96: launch_list_gq<8, 3>(lp, grid, s); break;
+    case 128: launch_list_gq<8, 4>(lp, grid, s); break;
+    default: launch_list_gq<8, 0>(lp, grid, s); break;
+  }
 }
 
 static unsigned long long read_u64(const unsigned long long* d, cudaStream_t s) {
@@ -1490,7 +1761,7 @@ void run_level(const LevelIn& in, LevelOut& out, LevelStats& st, cudaStream_t s,
 
   tick(0);
   // ---- tier 1 -------------------------------------------------------------------------
-  unsigned long long surv_cap = (unsigned long long)std::max<int64_t>(1 << 20, 256 * n);
+  unsigned long long surv_cap = in.small_buffers ? 64ull : (unsigned long long)std::max<int64_t>(1 << 20, 256 * n);
   const bool use_tc = !in.grng && in.precision == 1 && in.metric == L2 && tc_supported(in.Dp);
   DevBuf tcimg, tcnrm, tcbmax, knnrb;
   float nmax_all = 0.0f;
@@ -1557,6 +1828,7 @@ void run_level(const LevelIn& in, LevelOut& out, LevelStats& st, cudaStream_t s,
       st.kms[0] = ems;
     }
     nsurv = read_u64(dc + 1, s);
+    st.c[30] = attempt + 1;  // tier-1 sweeps run (a survivor buffer overflow repeats the sweep)
     if (use_tc) {
       if (read_u64(dc + 40, s) != 0) fail(4 /* GRNG_ETIMEOUT */, "a bounded tensor-core wait ran out");
       if (nsurv <= surv_cap) tc_knn_fix(in.X, n, in.Dp, in.K, in.metric, knni.as<int32_t>(), knnk.as<float>(), s);
@@ -1576,13 +1848,15 @@ void run_level(const LevelIn& in, LevelOut& out, LevelStats& st, cudaStream_t s,
   tick(1);
   // ---- tiers 2 and 3 ---------------------------------------------------------------------
   DevBuf off, oth, tmp, links, unres, pend, amb, pflag, unres2, off2, oth2, fbuf;
-  DevBuf side, tkey, tcut, hist, lcnt, lidx, lkey, unres3, atab;
+  DevBuf side, tkey, tcut, hist, lcnt, lastb, boff, lidx, lkey, unres3, atab;
+  int64_t toff[GRNG_MAXL] = {0}, tabw = 0;  // columns of the node x ancestor key table
   GRNG_CUDA(off.alloc((size_t)(n + 1) * 8));
   GRNG_CUDA(oth.alloc(std::max<size_t>(nsurv, 1) * 4));
   group_pairs(surv.as<int2>(), (int64_t)nsurv, 0, n, off.as<int64_t>(), oth.as<int32_t>(), tmp, s);
   unsigned long long cap = std::max<unsigned long long>(nsurv, 1024);
-  unsigned long long amb_cap = std::max<unsigned long long>(4 * nsurv, 1 << 20);
+  unsigned long long amb_cap = in.small_buffers ? 8ull : std::max<unsigned long long>(4 * nsurv, 1 << 20);
   for (int attempt = 0;; ++attempt) {
+    st.c[31] = attempt + 1;  // passes of tiers 2-3 (an ambiguity buffer overflow repeats them)
     GRNG_CUDA(links.alloc(cap * 8));
     GRNG_CUDA(unres.alloc(cap * 8));
     GRNG_CUDA(pend.alloc(cap * 8 * 2));
@@ -1623,6 +1897,15 @@ void run_level(const LevelIn& in, LevelOut& out, LevelStats& st, cudaStream_t s,
     tick(3);
     const int2* t3pairs = unres2.as<int2>();
     GRNG_CUDA(cudaMemsetAsync(dc + 26, 0, 8 * sizeof(unsigned long long), s));
+    GRNG_CUDA(cudaMemsetAsync(dc + 50, 0, 8 * sizeof(unsigned long long), s));
+    if (in.grng && in.anc.n > 0 && nun2 && !atab.p) {
+      // pivot layers: node x ancestor keys once (the list tier's bounds and tier 3)
+      tabw = 0;  // each level's columns start on a 16-byte boundary
+      for (int a = 0; a < in.anc.n; ++a) { toff[a] = tabw; tabw += (in.anc.m[a] + 3) & ~(int64_t)3; }
+      GRNG_CUDA(atab.alloc((size_t)n * tabw * 4));
+      for (int a = 0; a < in.anc.n; ++a)
+        launch_cross(in.X, n, in.anc.X[a], in.anc.m[a], in.Dp, in.metric, atab.as<float>() + toff[a], tabw, s);
+    }
     if (in.grng && nun2) {
       // range lists for the pairs no neighbour list covers
       GRNG_CUDA(side.alloc(nun2));
@@ -1630,67 +1913,88 @@ void run_level(const LevelIn& in, LevelOut& out, LevelStats& st, cudaStream_t s,
       GRNG_CUDA(tcut.alloc((size_t)n * 4));
       GRNG_CUDA(hist.alloc((size_t)n * GRNG_HBINS * 4));
       GRNG_CUDA(lcnt.alloc((size_t)n * 4));
+      GRNG_CUDA(lastb.alloc((size_t)n * 4));
+      GRNG_CUDA(boff.alloc((size_t)n * (GRNG_HBINS + 1) * 4));
       GRNG_CUDA(cudaMemsetAsync(tkey.p, 0, (size_t)n * 4, s));
-      GRNG_CUDA(cudaMemsetAsync(lcnt.p, 0, (size_t)n * 4, s));
       SideParams sp;
       sp.X = in.X; sp.Dp = in.Dp; sp.metric = in.metric; sp.guide = in.grng; sp.K = in.K;
       sp.rlo = in.rlo; sp.rhi = in.rhi; sp.pairs = unres2.as<int2>(); sp.m = (int64_t)nun2;
       sp.side = side.as<int8_t>(); sp.tkey = tkey.as<unsigned int>(); sp.tcut = tcut.as<unsigned int>();
       sp.lcnt = lcnt.as<int>();
+      cudaEvent_t l0, l1;
+      GRNG_CUDA(cudaEventCreate(&l0));
+      GRNG_CUDA(cudaEventCreate(&l1));
+      GRNG_CUDA(cudaEventRecord(l0, s));
       range_thresholds_kernel<<<(unsigned)((nun2 + 255) / 256), 256, 0, s>>>(sp); note_launch();
       GRNG_CUDA(cudaGetLastError());
-      launch_range(in, tkey.as<unsigned int>(), hist.as<int>(), nullptr, nullptr, nullptr, 0, s);
+      launch_range(in, tkey.as<unsigned int>(), hist.as<int>(), nullptr, nullptr, nullptr, nullptr, 0, s);
+      const int lmax = in.lmax > 0 ? (int)std::min<int64_t>(in.lmax, GRNG_LCAP) : GRNG_LMAX;
       range_cut_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(tkey.as<unsigned int>(), hist.as<int>(), n,
-                                                                  tcut.as<unsigned int>(),
-                                                                  in.lmax > 0 ? (int)in.lmax : GRNG_LMAX); note_launch();
+                                                                  tcut.as<unsigned int>(), lastb.as<int>(),
+                                                                  boff.as<int>(), lcnt.as<int>(), lmax); note_launch();
       GRNG_CUDA(cudaGetLastError());
       GRNG_CUDA(lidx.alloc((size_t)n * GRNG_LCAP * 4));
       GRNG_CUDA(lkey.alloc((size_t)n * GRNG_LCAP * 4));
-      launch_range(in, tcut.as<unsigned int>(), nullptr, lcnt.as<int>(), lidx.as<int32_t>(), lkey.as<float>(), 1, s);
+      launch_range(in, tkey.as<unsigned int>(), nullptr, lastb.as<int>(), boff.as<int>(), lidx.as<int32_t>(),
+                   lkey.as<float>(), 1, s);
       pick_side_kernel<<<(unsigned)((nun2 + 255) / 256), 256, 0, s>>>(sp); note_launch();
       GRNG_CUDA(cudaGetLastError());
       GRNG_CUDA(unres3.alloc(nun2 * 8));
       ListParams lp;
       lp.X = in.X; lp.Dp = in.Dp; lp.metric = in.metric; lp.guide = in.grng; lp.rlo = in.rlo; lp.rhi = in.rhi;
-      lp.pairs = unres2.as<int2>(); lp.m = (int64_t)nun2; lp.side = side.as<int8_t>(); lp.lcnt = lcnt.as<int>();
+      lp.pairs = unres2.as<int2>(); lp.m = (int64_t)nun2; lp.side = side.as<int8_t>();
+      lp.tkey = tkey.as<unsigned int>(); lp.lastb = lastb.as<int>(); lp.boff = boff.as<int>();
       lp.lidx = lidx.as<int32_t>(); lp.lkey = lkey.as<float>();
+      lp.atab = atab.p ? atab.as<float>() : nullptr;
+      lp.tabw = tabw;
+      lp.toff = in.anc.n > 0 ? toff[in.anc.n - 1] : 0;
+      lp.parent = in.parent;
+      lp.pdh = in.pdist_hi;
+      if (!in.parent || !in.pdist_hi) lp.atab = nullptr;
       lp.links = links.as<int2>(); lp.link_cnt = dc + 16; lp.link_cap = cap;
       lp.unres = unres3.as<int2>(); lp.unres_cnt = dc + 27; lp.unres_cap = nun2;
       lp.pend = pend.as<int2>(); lp.pend_cnt = dc + 17; lp.pend_cap = 2 * cap;
       lp.amb = amb.as<int2>(); lp.amb_cnt = dc + 19; lp.amb_cap = amb_cap;
-      lp.stats = dc + 28;
-      cudaEvent_t l0, l1;
-      GRNG_CUDA(cudaEventCreate(&l0));
-      GRNG_CUDA(cudaEventCreate(&l1));
-      GRNG_CUDA(cudaEventRecord(l0, s));
-      list_tier_kernel<<<(unsigned)std::min<unsigned long long>((nun2 + 7) / 8, 64ull * num_sms()), 256, 0, s>>>(lp); note_launch();
-      GRNG_CUDA(cudaGetLastError());
+      lp.stats = dc + 50;
+      cudaEvent_t k0;
+      GRNG_CUDA(cudaEventCreate(&k0));
+      GRNG_CUDA(cudaEventRecord(k0, s));
+      launch_list(lp, (unsigned)std::min<unsigned long long>((nun2 + LT_WARPS - 1) / LT_WARPS,
+                                                             (unsigned long long)2 * num_sms()), s);
       GRNG_CUDA(cudaEventRecord(l1, s));
       GRNG_CUDA(cudaEventSynchronize(l1));
-      float lms = 0.0f;
+      float lms = 0.0f, kms = 0.0f;
       GRNG_CUDA(cudaEventElapsedTime(&lms, l0, l1));
+      GRNG_CUDA(cudaEventElapsedTime(&kms, k0, l1));
       cudaEventDestroy(l0);
       cudaEventDestroy(l1);
-      st.kms[2] += lms;
-      unsigned long long h8[8];  // -, to tier 3, links, pending, (to tier 3), blocked, tested
-      GRNG_CUDA(cudaMemcpyAsync(h8, dc + 26, sizeof(h8), cudaMemcpyDeviceToHost, s));
-      std::vector<int> hl((size_t)n);
-      std::vector<unsigned int> htk((size_t)n), htc((size_t)n);
+      cudaEventDestroy(k0);
+      st.kms[2] += kms;   // the list tier kernel
+      st.kms[3] += lms;   // thresholds, both sweeps, cut, sides and the list tier
+      unsigned long long h8[8];  // links, pending, to tier 3, blocked, tested by distance, intersections, probes
+      GRNG_CUDA(cudaMemcpyAsync(h8, dc + 50, sizeof(h8), cudaMemcpyDeviceToHost, s));
+      unsigned long long n3 = 0;
+      GRNG_CUDA(cudaMemcpyAsync(&n3, dc + 27, sizeof(n3), cudaMemcpyDeviceToHost, s));
+      std::vector<int> hl((size_t)n), hlb((size_t)n);
+      std::vector<unsigned int> htk((size_t)n);
       GRNG_CUDA(cudaMemcpyAsync(hl.data(), lcnt.p, (size_t)n * 4, cudaMemcpyDeviceToHost, s));
+      GRNG_CUDA(cudaMemcpyAsync(hlb.data(), lastb.p, (size_t)n * 4, cudaMemcpyDeviceToHost, s));
       GRNG_CUDA(cudaMemcpyAsync(htk.data(), tkey.p, (size_t)n * 4, cudaMemcpyDeviceToHost, s));
-      GRNG_CUDA(cudaMemcpyAsync(htc.data(), tcut.p, (size_t)n * 4, cudaMemcpyDeviceToHost, s));
       GRNG_CUDA(cudaStreamSynchronize(s));
       unsigned long long ltot = 0, lcut = 0;
       for (size_t i = 0; i < hl.size(); ++i) {
-        ltot += (unsigned long long)std::min(hl[i], GRNG_LCAP);
-        lcut += htk[i] != 0 && (htc[i] < htk[i] || hl[i] > GRNG_LCAP);
+        ltot += (unsigned long long)hl[i];
+        lcut += htk[i] != 0 && hlb[i] < GRNG_HBINS - 1;
       }
       st.c[18] = nun2;    // pairs given range lists
-      st.c[19] = lcut;    // lists cut below their T_s or over the capacity
+      st.c[19] = lcut;    // lists cut below their T_s
       st.c[20] = ltot;    // listed nodes
-      st.c[21] = h8[2];   // links from the lists
-      st.c[22] = h8[6];   // listed nodes tested
-      nun2 = h8[1];       // left for tier 3
+      st.c[21] = h8[0];   // links from the lists
+      st.c[22] = h8[4];   // listed nodes tested by distance
+      st.c[32] = h8[5];   // pairs decided by intersecting both lists
+      st.c[33] = h8[6];   // intersection probes
+      st.c[34] = h8[7];   // list entries read
+      nun2 = n3;          // left for tier 3
       t3pairs = unres3.as<int2>();
     }
     tick(4);
@@ -1708,7 +2012,7 @@ void run_level(const LevelIn& in, LevelOut& out, LevelStats& st, cudaStream_t s,
       t3.amb = amb.as<int2>(); t3.amb_cnt = dc + 19; t3.amb_cap = amb_cap;
       t3.anc = in.anc;
       int grid3 = (int)std::min<unsigned long long>(nun2, (unsigned long long)T3_MINB * num_sms());
-      t3.fcap = 1 << 15;
+      t3.fcap = in.small_buffers ? 4 : 1 << 15;
       GRNG_CUDA(fbuf.alloc((size_t)grid3 * 2 * t3.fcap * sizeof(Front)));
       t3.fbuf = fbuf.as<Front>();
       t3.pdist_hi = in.pdist_hi;
@@ -1716,15 +2020,11 @@ void run_level(const LevelIn& in, LevelOut& out, LevelStats& st, cudaStream_t s,
       t3.tabw = 0;
       t3.dense = 0;
       t3.mkw = 0;
-      if (in.grng && in.anc.n > 0) {
-        // pivot layers: node x ancestor keys once, instead of per pair
-        int64_t w = 0;  // each level's columns start on a 16-byte boundary
-        for (int a = 0; a < in.anc.n; ++a) { t3.anc.toff[a] = w; w += (in.anc.m[a] + 3) & ~(int64_t)3; }
-        GRNG_CUDA(atab.alloc((size_t)n * w * 4));
-        for (int a = 0; a < in.anc.n; ++a)
-          launch_cross(in.X, n, in.anc.X[a], in.anc.m[a], in.Dp, in.metric, atab.as<float>() + t3.anc.toff[a], w, s);
+      if (in.grng && in.anc.n > 0 && atab.p) {
+        // pivot layers: the node x ancestor keys computed before the list tier
+        for (int a = 0; a < in.anc.n; ++a) t3.anc.toff[a] = toff[a];
         t3.atab = atab.as<float>();
-        t3.tabw = w;
+        t3.tabw = tabw;
         t3.dense = 1;
         for (int a = 1; a < in.anc.n; ++a) {
           t3.dense &= in.anc.m[a] <= 32 * T3_MKW;

@@ -171,3 +171,44 @@ def test_api_errors():
     with pytest.raises(g.GrngError) as e:
         ix.rng_build_exact()
     assert e.value.status == g.GRNG_ESTATE
+
+
+def test_small_buffers_take_every_overflow_path():
+    """With every internal buffer started tiny, the tier-1 sweep and tiers 2-3 repeat with
+    larger buffers and the exhaustive tier falls back to scanning every node; the graphs
+    stay the oracle's."""
+    w = wl.make("lin96", n=2500)
+    flags = g.GRNG_FLAG_SMALL_BUFFERS | g.GRNG_FLAG_SHORT_LISTS
+    ix = check_full(w.X, w.layers, wl.L2, knn_k=1, flags=flags)
+    st = ix.stats()
+    levels = [L["grng"] for L in st["layers"]] + [st["rng"]]
+    assert max(L["tier1_attempts"] for L in levels) >= 2
+    assert sum(L["tier3_overflows"] for L in levels) > 0
+    rng = np.random.default_rng(6)
+    X = rng.integers(0, 4, size=(300, 2)).astype(np.float32)   # exact ties: many FP64 rechecks
+    fine = np.sort(rng.choice(300, size=40, replace=False)).astype(np.int32)
+    coarse = np.sort(rng.choice(fine, size=6, replace=False)).astype(np.int32)
+    ix = check_full(X, [coarse, fine], wl.L2, knn_k=1, flags=flags)
+    st = ix.stats()
+    levels = [L["grng"] for L in st["layers"]] + [st["rng"]]
+    assert max(L["tier23_attempts"] for L in levels) >= 2
+    w = wl.make("mix16", n=3000, metric=wl.L1)
+    check_full(w.X, w.layers, wl.L1, knn_k=2, flags=flags)
+
+
+def test_small_buffers_tensor_core_sweep():
+    """The tensor-core exemplar sweep repeats with a larger survivor buffer."""
+    w = wl.make("lin96", n=3000)
+    ix, out = g.build_all(torch.from_numpy(w.X).cuda(), w.layers, precision=g.BF16, knn_k=4,
+                          flags=g.GRNG_FLAG_SMALL_BUFFERS)
+    assert _edge_set(out["edges"]) == _edge_set(oracle.rng_brute(w.X))
+    assert ix.stats()["rng"]["tier1_attempts"] >= 2
+
+
+def test_range_lists_intersect_and_scan():
+    """Pivot pairs decided from range lists: from both lists by intersection and from one
+    list by distance; the layer's GRNG stays the oracle's."""
+    w = wl.make("lin96", n=6000)
+    ix = check_full(w.X, w.layers, wl.L2, knn_k=1)
+    G = ix.stats()["layers"][-1]["grng"]
+    assert G["range_pairs"] > 0 and G["range_intersected"] > 0, G

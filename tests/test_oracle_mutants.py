@@ -32,7 +32,8 @@ MUTANTS = {
     "delta_max_with_member_radius": ("if (delta_max && ds[t] > delta_max[as[t]]) delta_max[as[t]] = ds[t];",
                                      "if (delta_max && rr > delta_max[as[t]]) delta_max[as[t]] = rr;"),
     "witness_closed_lune": ("return m < dxy ? 1 : 0;", "return m <= dxy ? 1 : 0;"),
-    "emst_wrong_endpoint": ("edges[2 * e] = (int32_t)from[u];", "edges[2 * e] = (int32_t)(u > 0 ? u - 1 : 1);"),
+    "emst_wrong_endpoint": ("edges[2 * (e - 1)] = (int32_t)from[u];",
+                            "edges[2 * (e - 1)] = (int32_t)(u > 0 ? u - 1 : 1);"),
 }
 
 RUNNER = r"""
