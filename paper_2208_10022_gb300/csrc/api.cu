@@ -72,6 +72,20 @@ __global__ void edges_to_pairs_kernel(const uint64_t* __restrict__ k, int64_t m,
   }
 }
 
+// batch points in sorted positions: is_new[s] = 1 when the point at s has id >= n0
+__global__ void mark_new_kernel(const int32_t* __restrict__ order, int64_t n, int64_t n0, uint8_t* __restrict__ is_new) {
+  int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s < n) is_new[s] = order[s] >= n0 ? 1 : 0;
+}
+__global__ void batch_pos_kernel(const int32_t* __restrict__ rank, int64_t n0, int64_t m, uint64_t* __restrict__ out) {
+  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < m) out[t] = (uint64_t)(uint32_t)rank[n0 + t];
+}
+__global__ void narrow_kernel(const uint64_t* __restrict__ in, int64_t m, int32_t* __restrict__ out) {
+  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < m) out[t] = (int32_t)in[t];
+}
+
 static inline unsigned nblk(int64_t m, int b = 256) { return (unsigned)((m + b - 1) / b); }
 
 struct Layer {
@@ -132,6 +146,10 @@ struct grng_index {
   double rng_ms = 0, rng_tile_ms = 0, sort_ms = 0;
   double insert_ms = 0;  // batched insertion totals
   int64_t insert_batches = 0, inserted = 0;
+  struct {
+    long long changed_pivots = 0, grng_pairs = 0, grng_linked = 0, candidates = 0, survivors = 0,
+              s7_candidates = 0, s7_tests = 0, s7_fp64 = 0, new_edges = 0, removed_edges = 0;
+  } ins;
   DevBuf mlp;            // ranking network parameters (learned shortlist), or empty
   DevBuf rec_f, rec_y;   // recorded training samples of the last RNG build
   int64_t rec_n = 0;
@@ -168,6 +186,8 @@ void copy_out(void* dst, const void* src_dev, size_t bytes, cudaStream_t s) {
 }
 
 int padded_dim(int d) { return d <= 8 ? 8 : d <= 16 ? 16 : ((d + 31) / 32) * 32; }
+
+void sort_exemplars(grng_index* ix);
 
 // DFS order of every layer (pivots grouped under their parents, coarsest first) and
 // of the points; coordinates and radii gathered into that order.
@@ -220,6 +240,18 @@ void ensure_sorted(grng_index* ix) {
     GRNG_CUDA(ly.cstart.alloc((ly.m + 1) * 4));
     child_ranges(ix->layers[l + 1].parent_s.as<int32_t>(), ix->layers[l + 1].m, ly.m, ly.cstart.as<int32_t>(), s);
   }
+  sort_exemplars(ix);
+  GRNG_CUDA(cudaStreamSynchronize(s));
+  ix->sort_ms = tm.stop();
+  ix->sorted = true;
+}
+
+// The points in DFS order of the finest layer (grouped under their pivots, pivots in their
+// own DFS order), with their parents, parent distances and coordinates in that order.
+void sort_exemplars(grng_index* ix) {
+  cudaStream_t s = ix->stream;
+  const int L = (int)ix->layers.size();
+  DevBuf key, tmp;
   const int64_t n = ix->n;
   Layer& fin = ix->layers[L - 1];
   GRNG_CUDA(ix->xorder.alloc(n * 4));
@@ -240,8 +272,6 @@ void ensure_sorted(grng_index* ix) {
   gather_rows(ix->X.as<float>(), ix->Dp, ix->xorder.as<int32_t>(), n, ix->Xs.as<float>(), s);
   GRNG_CUDA(cudaGetLastError());
   GRNG_CUDA(cudaStreamSynchronize(s));
-  ix->sort_ms = tm.stop();
-  ix->sorted = true;
 }
 
 // layers 0..count-1 as the ancestors of a level (the last one is the direct parent,
@@ -642,35 +672,221 @@ grng_status rng_insert_batch(grng_index* ix, const float* pts, int64_t m) {
     if (ix->n + m >= (int64_t)1 << 31) fail(GRNG_EINVAL, "n + m must stay below 2^31");
     cudaStream_t s = ix->stream;
     Timer tm(s);
-    // the enlarged point set: old rows, then the batch (ids n .. n+m-1)
-    const int64_t n0 = ix->n, n1 = n0 + m;
-    DevBuf X2, ids2;
-    GRNG_CUDA(X2.alloc((size_t)n1 * ix->Dp * 4));
-    GRNG_CUDA(cudaMemcpyAsync(X2.p, ix->X.p, (size_t)n0 * ix->Dp * 4, cudaMemcpyDeviceToDevice, s));
-    float* Xnew = X2.as<float>() + n0 * ix->Dp;
-    GRNG_CUDA(cudaMemsetAsync(Xnew, 0, (size_t)m * ix->Dp * 4, s));
-    GRNG_CUDA(cudaMemcpy2DAsync(Xnew, (size_t)ix->Dp * 4, pts, (size_t)ix->D * 4, (size_t)ix->D * 4, (size_t)m,
-                                cudaMemcpyDefault, s));
-    GRNG_CUDA(ids2.alloc((size_t)n1 * 4));
-    iota_kernel<<<nblk(n1), 256, 0, s>>>(ids2.as<int32_t>(), n1); note_launch();
-    GRNG_CUDA(cudaGetLastError());
-    GRNG_CUDA(cudaStreamSynchronize(s));
-    ix->X = std::move(X2);
-    ix->ids = std::move(ids2);
-    ix->n = n1;
-    // Every layer keeps its pivots; the batch joins the finest domains, radii and
-    // delta_max follow (Eq. 2), every GRNG and the RNG are recomputed over the enlarged
-    // set, so the stored graphs are those of a build from scratch on it.
     const int L = (int)ix->layers.size();
-    std::vector<std::vector<int32_t>> piv(L);
-    for (int l = 0; l < L; ++l) piv[l] = ix->layers[l].piv_h;
-    auto call = [&](grng_status st) {
-      if (st != GRNG_OK) fail(st, g_last_error);
-    };
-    for (int l = L - 1; l >= 0; --l)
-      call(grng_build_layer(ix, l, piv[l].data(), (int32_t)piv[l].size(), nullptr, nullptr, nullptr));
-    for (int l = 0; l < L; ++l) call(grng_link_pivots(ix, l, nullptr, nullptr, nullptr, 0, nullptr));
-    call(rng_build_exact(ix));
+    const int Dp = ix->Dp, D = ix->D, K = ix->K, metric = ix->metric;
+    // ---- the enlarged point set: old rows, then the batch (ids n .. n+m-1) ----------------
+    const int64_t n0 = ix->n, n1 = n0 + m;
+    {
+      DevBuf X2, ids2;
+      GRNG_CUDA(X2.alloc((size_t)n1 * Dp * 4));
+      GRNG_CUDA(cudaMemcpyAsync(X2.p, ix->X.p, (size_t)n0 * Dp * 4, cudaMemcpyDeviceToDevice, s));
+      float* Xnew = X2.as<float>() + n0 * Dp;
+      GRNG_CUDA(cudaMemsetAsync(Xnew, 0, (size_t)m * Dp * 4, s));
+      GRNG_CUDA(cudaMemcpy2DAsync(Xnew, (size_t)Dp * 4, pts, (size_t)D * 4, (size_t)D * 4, (size_t)m,
+                                  cudaMemcpyDefault, s));
+      GRNG_CUDA(ids2.alloc((size_t)n1 * 4));
+      iota_kernel<<<nblk(n1), 256, 0, s>>>(ids2.as<int32_t>(), n1); note_launch();
+      GRNG_CUDA(cudaGetLastError());
+      GRNG_CUDA(cudaStreamSynchronize(s));
+      ix->X = std::move(X2);
+      ix->ids = std::move(ids2);
+    }
+    // ---- radii (Eq. 2; relative pivot domains, Sec. 3) ------------------------------------
+    std::vector<DevBuf> changed(L);
+    Layer& fin = ix->layers[L - 1];
+    {
+      const int64_t M = fin.m;
+      DevBuf ab, db, rb, ddb, a2, d2;
+      GRNG_CUDA(ab.alloc((size_t)m * 4));
+      GRNG_CUDA(db.alloc((size_t)m * 8));
+      GRNG_CUDA(rb.alloc((size_t)M * 8));
+      GRNG_CUDA(ddb.alloc((size_t)M * 8));
+      AssignOut ao{ab.as<int32_t>(), db.as<double>(), rb.as<double>(), ddb.as<double>()};
+      assign_layer(ix->X.as<float>() + n0 * Dp, ix->ids.as<int32_t>() + n0, nullptr, m, fin.Xp.as<float>(),
+                   fin.piv.as<int32_t>(), M, n1, D, Dp, metric, ao, nullptr, s);
+      GRNG_CUDA(a2.alloc((size_t)n1 * 4));
+      GRNG_CUDA(d2.alloc((size_t)n1 * 8));
+      GRNG_CUDA(cudaMemcpyAsync(a2.p, fin.assign.p, (size_t)n0 * 4, cudaMemcpyDeviceToDevice, s));
+      GRNG_CUDA(cudaMemcpyAsync(a2.as<int32_t>() + n0, ab.p, (size_t)m * 4, cudaMemcpyDeviceToDevice, s));
+      GRNG_CUDA(cudaMemcpyAsync(d2.p, fin.mdist.p, (size_t)n0 * 8, cudaMemcpyDeviceToDevice, s));
+      GRNG_CUDA(cudaMemcpyAsync(d2.as<double>() + n0, db.p, (size_t)m * 8, cudaMemcpyDeviceToDevice, s));
+      GRNG_CUDA(changed[L - 1].alloc((size_t)M));
+      merge_radii(fin.radius.as<double>(), fin.delta.as<double>(), rb.as<double>(), ddb.as<double>(), M,
+                  changed[L - 1].as<uint8_t>(), s);
+      GRNG_CUDA(cudaStreamSynchronize(s));
+      fin.assign = std::move(a2);
+      fin.mdist = std::move(d2);
+    }
+    for (int l = L - 2; l >= 0; --l) {  // coarse radii grow with their members' radii
+      Layer& ly = ix->layers[l];
+      Layer& fi = ix->layers[l + 1];
+      DevBuf oldr;
+      GRNG_CUDA(oldr.alloc((size_t)ly.m * 8));
+      GRNG_CUDA(cudaMemcpyAsync(oldr.p, ly.radius.p, (size_t)ly.m * 8, cudaMemcpyDeviceToDevice, s));
+      GRNG_CUDA(changed[l].alloc((size_t)ly.m));
+      coarse_radii(ly.mdist.as<double>(), fi.radius.as<double>(), ly.assign.as<int32_t>(), fi.m,
+                   ly.radius.as<double>(), oldr.as<double>(), ly.m, changed[l].as<uint8_t>(), s);
+      GRNG_CUDA(cudaStreamSynchronize(s));
+    }
+    for (int l = 0; l < L; ++l) {  // the sorted copies of radii and delta_max
+      Layer& ly = ix->layers[l];
+      permute_radius_kernel<<<nblk(ly.m), 256, 0, s>>>(ly.radius.as<double>(), ly.order.as<int32_t>(), ly.m,
+                                                       ly.r64s.as<double>(), ly.rlos.as<float>(),
+                                                       ly.rhis.as<float>()); note_launch();
+      permute_hi_kernel<<<nblk(ly.m), 256, 0, s>>>(ly.delta.as<double>(), ly.order.as<int32_t>(), ly.m,
+                                                   ly.dhis.as<float>()); note_launch();
+    }
+    GRNG_CUDA(cudaGetLastError());
+    // ---- GRNGs, coarsest first: a grown radius can only add links (definition, Sec. 2) ------
+    DevBuf newg_prev;
+    int64_t nnew_prev = 0;
+    for (int l = 0; l < L; ++l) {
+      Layer& ly = ix->layers[l];
+      DevBuf chg_s, chg_list, pairs, newg_cur;
+      GRNG_CUDA(chg_s.alloc((size_t)ly.m));
+      GRNG_CUDA(chg_list.alloc((size_t)ly.m * 4));
+      const int64_t nchg = changed_sorted(changed[l].as<uint8_t>(), ly.order.as<int32_t>(), ly.m,
+                                         chg_s.as<uint8_t>(), chg_list.as<int32_t>(), s);
+      const int64_t nnew = l > 0 ? nnew_prev : 0;
+      ix->ins.changed_pivots += nchg;
+      if (nchg == 0 && nnew == 0) {
+        nnew_prev = 0;
+        continue;
+      }
+      const int64_t np = grng_retest_pairs(
+          chg_list.as<int32_t>(), nchg, chg_s.as<uint8_t>(), ly.m, ly.gx.as<uint32_t>(), ly.gg.as<uint32_t>(),
+          ly.words, l > 0 ? ly.parent_s.as<int32_t>() : nullptr,
+          l > 0 ? ix->layers[l - 1].gg.as<uint32_t>() : nullptr, l > 0 ? ix->layers[l - 1].words : 0,
+          nnew ? newg_prev.as<int2>() : nullptr, nnew, l > 0 ? ix->layers[l - 1].cstart.as<int32_t>() : nullptr,
+          pairs, s);
+      ix->ins.grng_pairs += np;
+      LevelIn in{};
+      in.X = ly.Xs.as<float>();
+      in.n = ly.m;
+      in.D = D;
+      in.Dp = Dp;
+      in.metric = metric;
+      in.grng = 1;
+      in.K = K;
+      in.orig = ly.order.as<int32_t>();
+      in.anc = ancestors_of(ix, l);
+      in.pdist_hi = l > 0 ? ly.pdh.as<float>() : nullptr;
+      in.r64 = ly.r64s.as<double>();
+      in.rlo = ly.rlos.as<float>();
+      in.rhi = ly.rhis.as<float>();
+      if (l > 0) {
+        in.parent = ly.parent_s.as<int32_t>();
+        in.gpar = ix->layers[l - 1].gg.as<uint32_t>();
+        in.gpar_words = ix->layers[l - 1].words;
+      }
+      in.lists = 0;
+      if (ix->opts.spin_limit > 0) in.spin = ix->opts.spin_limit;
+      in.small_buffers = (ix->opts.flags & GRNG_FLAG_SMALL_BUFFERS) ? 1 : 0;
+      LevelOut lo;
+      lo.gx = ly.gx.as<uint32_t>();
+      lo.gg = ly.gg.as<uint32_t>();
+      lo.words = ly.words;
+      lo.new_gg = &newg_cur;
+      LevelStats st;
+      run_pairs(in, lo, st, s, pairs.as<int2>(), np, nullptr, nullptr, false);
+      ix->ins.grng_linked += lo.n_new_gg;
+      newg_prev = std::move(newg_cur);
+      nnew_prev = lo.n_new_gg;
+    }
+    // ---- the exemplars in DFS order of the finest layer, the batch among them ---------------
+    ix->n = n1;
+    sort_exemplars(ix);
+    DevBuf is_new, bpos64, rowpos, XB, AB, nbB_i, nbB_k, A, nb_i, nb_k, maxe, knn_k, knn_i, surv, s7, newE;
+    const int64_t strips = (m + 127) / 128;
+    const int64_t nb1 = (n1 + 127) / 128;
+    GRNG_CUDA(is_new.alloc((size_t)n1));
+    GRNG_CUDA(bpos64.alloc((size_t)m * 8));
+    GRNG_CUDA(rowpos.alloc((size_t)m * 4));
+    mark_new_kernel<<<nblk(n1), 256, 0, s>>>(ix->xorder.as<int32_t>(), n1, n0, is_new.as<uint8_t>()); note_launch();
+    batch_pos_kernel<<<nblk(m), 256, 0, s>>>(ix->xrank.as<int32_t>(), n0, m, bpos64.as<uint64_t>()); note_launch();
+    GRNG_CUDA(cudaGetLastError());
+    {
+      DevBuf tmp;
+      sort_u64(bpos64.as<uint64_t>(), m, tmp, s);  // batch rows in sorted order: coherent strips
+    }
+    narrow_kernel<<<nblk(m), 256, 0, s>>>(bpos64.as<uint64_t>(), m, rowpos.as<int32_t>()); note_launch();
+    GRNG_CUDA(XB.alloc((size_t)strips * 128 * Dp * 4));
+    GRNG_CUDA(cudaMemsetAsync(XB.p, 0, (size_t)strips * 128 * Dp * 4, s));
+    gather_rows(ix->Xs.as<float>(), Dp, rowpos.as<int32_t>(), m, XB.as<float>(), s);
+    GRNG_CUDA(AB.alloc((size_t)strips * 128 * 128 * 2));
+    GRNG_CUDA(nbB_i.alloc((size_t)strips * 128 * GRNG_KIN));
+    GRNG_CUDA(nbB_k.alloc((size_t)strips * 128 * GRNG_KIN * 4));
+    block_prep(XB.as<float>(), m, Dp, metric, AB.as<__half>(), nbB_i.as<uint8_t>(), nbB_k.as<float>(), s);
+    GRNG_CUDA(A.alloc((size_t)nb1 * 128 * 128 * 2));
+    GRNG_CUDA(nb_i.alloc((size_t)nb1 * 128 * GRNG_KIN));
+    GRNG_CUDA(nb_k.alloc((size_t)nb1 * 128 * GRNG_KIN * 4));
+    block_prep(ix->Xs.as<float>(), n1, Dp, metric, A.as<__half>(), nb_i.as<uint8_t>(), nb_k.as<float>(), s);
+    GRNG_CUDA(maxe.alloc((size_t)n1 * 4));
+    edge_max_keys(ix->edges.as<uint64_t>(), ix->n_edges, ix->xrank.as<int32_t>(), ix->Xs.as<float>(), Dp, metric,
+                  maxe.as<float>(), n1, s);
+    GRNG_CUDA(knn_k.alloc((size_t)n1 * K * 4));
+    GRNG_CUDA(knn_i.alloc((size_t)n1 * K * 4));
+    InsertSweep S;
+    S.XB = XB.as<float>(); S.rowpos = rowpos.as<int32_t>(); S.mb = m;
+    S.AB = AB.as<__half>(); S.nbrB_i = nbB_i.as<uint8_t>(); S.nbrB_k = nbB_k.as<float>();
+    S.X = ix->Xs.as<float>(); S.n = n1; S.Dp = Dp; S.K = K; S.metric = metric;
+    S.A = A.as<__half>(); S.nbr_i = nb_i.as<uint8_t>(); S.nbr_k = nb_k.as<float>();
+    S.is_new = is_new.as<uint8_t>(); S.parent = ix->xparent.as<int32_t>();
+    S.gpar = fin.gg.as<uint32_t>(); S.gpar_words = fin.words; S.maxe = maxe.as<float>();
+    int64_t nsurv = 0, ns7 = 0;
+    unsigned long long sst[2] = {0, 0};
+    insert_sweep(S, surv, &nsurv, s7, &ns7, knn_k.as<float>(), knn_i.as<int32_t>(), sst, s);
+    ix->ins.candidates += sst[0];
+    ix->ins.survivors += nsurv;
+    ix->ins.s7_candidates += ns7;
+    // ---- new edges: tiers 2 (the batch rows' exact lists) and 3, FP64 recheck --------------
+    {
+      LevelIn in{};
+      in.X = ix->Xs.as<float>();
+      in.n = n1;
+      in.D = D;
+      in.Dp = Dp;
+      in.metric = metric;
+      in.grng = 0;
+      in.K = K;
+      in.parent = ix->xparent.as<int32_t>();
+      in.gpar = fin.gg.as<uint32_t>();
+      in.gpar_words = fin.words;
+      in.orig = ix->xorder.as<int32_t>();
+      in.anc = ancestors_of(ix, L);
+      in.pdist_hi = ix->xpdh.as<float>();
+      if (ix->opts.spin_limit > 0) in.spin = ix->opts.spin_limit;
+      in.small_buffers = (ix->opts.flags & GRNG_FLAG_SMALL_BUFFERS) ? 1 : 0;
+      LevelOut lo;
+      lo.edges = &newE;
+      LevelStats st;
+      run_pairs(in, lo, st, s, surv.as<int2>(), nsurv, knn_i.as<int32_t>(), knn_k.as<float>(), false);
+      ix->ins.new_edges += lo.n_edges;
+      // ---- Stage VII: old edges with a batch point strictly inside their lune ----------------
+      DevBuf all;
+      GRNG_CUDA(all.alloc((size_t)std::max<int64_t>(ix->n_edges + lo.n_edges, 1) * 8));
+      unsigned long long s7st[2] = {0, 0};
+      DevBuf s7c;
+      GRNG_CUDA(s7c.alloc(16));
+      GRNG_CUDA(cudaMemsetAsync(s7c.p, 0, 16, s));
+      const int64_t kept = stage7_remove(ix->edges.as<uint64_t>(), ix->n_edges, n0, s7.as<int4>(), ns7,
+                                         ix->Xs.as<float>(), D, Dp, metric, ix->xorder.as<int32_t>(),
+                                         ix->xrank.as<int32_t>(), all.as<uint64_t>(),
+                                         s7c.as<unsigned long long>(), s);
+      GRNG_CUDA(cudaMemcpyAsync(s7st, s7c.p, 16, cudaMemcpyDeviceToHost, s));
+      ix->ins.removed_edges += ix->n_edges - kept;
+      if (lo.n_edges)
+        GRNG_CUDA(cudaMemcpyAsync(all.as<uint64_t>() + kept, newE.p, (size_t)lo.n_edges * 8, cudaMemcpyDeviceToDevice,
+                                  s));
+      const int64_t ne = kept + lo.n_edges;
+      DevBuf tmp;
+      if (ne > 1) sort_u64(all.as<uint64_t>(), ne, tmp, s);
+      GRNG_CUDA(cudaStreamSynchronize(s));
+      ix->ins.s7_tests += s7st[0];
+      ix->ins.s7_fp64 += s7st[1];
+      ix->edges = std::move(all);
+      ix->n_edges = ne;
+    }
     ix->insert_ms += tm.stop();
     ix->insert_batches += 1;
     ix->inserted += m;
@@ -708,7 +924,7 @@ grng_status grng_stats(const grng_index* cix, char* json, size_t cap) {
     return GRNG_EINVAL;
   }
   std::string js = "{";
-  char buf[1024];
+  char buf[2048];
   snprintf(buf, sizeof(buf),
            "\"n\":%lld,\"dim\":%d,\"metric\":%d,\"knn_k\":%d,\"sort_ms\":%.4f,\"kernel_launches\":%llu,\"layers\":[",
            (long long)ix->n, ix->D, ix->metric, ix->K, ix->sort_ms, launches());
@@ -726,9 +942,14 @@ grng_status grng_stats(const grng_index* cix, char* json, size_t cap) {
   }
   snprintf(buf, sizeof(buf),
            "],\"rng_built\":%d,\"n_edges\":%lld,\"rng_ms\":%.4f,\"rng_tile_ms\":%.4f,"
-           "\"insert\":{\"batches\":%lld,\"points\":%lld,\"ms\":%.4f},",
+           "\"insert\":{\"batches\":%lld,\"points\":%lld,\"ms\":%.4f,\"changed_pivots\":%lld,"
+           "\"grng_pairs\":%lld,\"grng_links_added\":%lld,\"candidate_pairs\":%lld,\"tier1_survivors\":%lld,"
+           "\"stage7_candidates\":%lld,\"stage7_tests\":%lld,\"stage7_fp64\":%lld,\"new_edges\":%lld,"
+           "\"removed_edges\":%lld},",
            (int)ix->rng_built, (long long)ix->n_edges, ix->rng_ms, ix->rng_tile_ms, (long long)ix->insert_batches,
-           (long long)ix->inserted, ix->insert_ms);
+           (long long)ix->inserted, ix->insert_ms, ix->ins.changed_pivots, ix->ins.grng_pairs, ix->ins.grng_linked,
+           ix->ins.candidates, ix->ins.survivors, ix->ins.s7_candidates, ix->ins.s7_tests, ix->ins.s7_fp64,
+           ix->ins.new_edges, ix->ins.removed_edges);
   js += buf;
   level_json(js, "rng", ix->rng_st);
   js += "}";

@@ -122,6 +122,7 @@ struct LevelIn {
   int kshort = 0;                     // shortlist length tried before tier 3 (0: off)
   int mlp_record = 0;                 // RNG level: record features and labels of the tier-3 pairs' pools
   int small_buffers = 0;              // testing: tiny first capacities, so every retry and fallback runs
+  int lists = 1;                      // GRNG levels: range lists for the pairs tier 2 leaves open
 };
 
 // ---- tensor-core tiles (kernels_tc.cu) ------------------------------------------------------
@@ -170,6 +171,9 @@ struct LevelOut {
   DevBuf* rec_f = nullptr;
   DevBuf* rec_y = nullptr;
   int64_t rec_n = 0;
+  // GRNG level, optional: the pairs whose guidance bit was newly set ([n_new_gg] int2, a < b)
+  DevBuf* new_gg = nullptr;
+  int64_t n_new_gg = 0;
 };
 struct LevelStats {
   unsigned long long c[40];
@@ -207,5 +211,62 @@ void mlp_stage(const MlpStage& P, cudaStream_t s);
 
 void run_level(const LevelIn& in, LevelOut& out, LevelStats& st, cudaStream_t s,
                float* tile_ms = nullptr);
+// tiers 2-3, recheck and emission for explicit candidate pairs of a level (sorted positions);
+// knn_idx null: straight to the exhaustive tiers.  GRNG levels OR their bits into out.gx /
+// out.gg (never clearing one), the RNG level emits its edges.
+void run_pairs(const LevelIn& in, LevelOut& out, LevelStats& st, cudaStream_t s, const int2* pairs, int64_t m,
+               const int32_t* knn_idx, const float* knn_key, bool tier2b);
+// in-block FP16 keys (rounded up) and the GRNG_KIN in-block nearest neighbours of every
+// 128-node block of X [n][Dp]
+void block_prep(const float* X, int64_t n, int Dp, int metric, __half* A, uint8_t* nbr_idx, float* nbr_key,
+                cudaStream_t s);
+
+// ---- batched insertion (kernels_insert.cu) ---------------------------------------------------
+void merge_radii(double* r, double* dmax, const double* rb, const double* db, int64_t m, uint8_t* changed,
+                 cudaStream_t s);
+// radius[c] (holding the old radii) = max over members of mdist + member radius; changed[c] = grew
+void coarse_radii(const double* mdist, const double* mem_r, const int32_t* assign, int64_t nmem, double* radius,
+                  const double* old_radius, int64_t m, uint8_t* changed, cudaStream_t s);
+// changed flags in sorted order and the list of changed sorted positions; returns its length
+int64_t changed_sorted(const uint8_t* changed, const int32_t* order, int64_t m, uint8_t* chg_s, int32_t* list,
+                       cudaStream_t s);
+// the GRNG pairs an insertion may link: pairs of changed nodes not yet linked (parents equal or
+// guidance-linked) and the children pairs of the coarse pairs newp[nnew] whose guidance link is new
+int64_t grng_retest_pairs(const int32_t* chg_list, int64_t nchg, const uint8_t* chg_s, int64_t m, const uint32_t* gx,
+                          const uint32_t* gg, int64_t words, const int32_t* parent, const uint32_t* gpar,
+                          int64_t gpar_words, const int2* newp, int64_t nnew, const int32_t* cstart_par,
+                          DevBuf& out, cudaStream_t s);
+struct InsertSweep {
+  const float* XB;        // batch rows in sorted order, padded to whole 128-row strips (zeros)
+  const int32_t* rowpos;  // [mb] their sorted positions (ascending)
+  int64_t mb;
+  const __half* AB;       // block_prep of XB
+  const uint8_t* nbrB_i;
+  const float* nbrB_k;
+  const float* X;         // every point in sorted order [n][Dp]
+  int64_t n;
+  int Dp, K, metric;
+  const __half* A;        // block_prep of X
+  const uint8_t* nbr_i;
+  const float* nbr_k;
+  const uint8_t* is_new;  // [n] 1 for batch points (sorted positions)
+  const int32_t* parent;  // [n] finest pivot, sorted position
+  const uint32_t* gpar;   // finest layer's guidance bitmask
+  int64_t gpar_words;
+  const float* maxe;      // [n] FP32 upper bound of each old point's longest edge key (0: none)
+};
+// candidate pairs (row, point) of the batch rows left open by tier 1, Stage VII candidates
+// (row, old point, key) and the rows' exact K nearest neighbours (written at their sorted
+// positions of knn_k / knn_i [n][K]); stats[0] += candidate pairs, stats[1] += Stage VII ones
+void insert_sweep(const InsertSweep& S, DevBuf& surv, int64_t* nsurv, DevBuf& s7, int64_t* ns7, float* knn_k,
+                  int32_t* knn_i, unsigned long long* stats, cudaStream_t s);
+// maxe[sorted position] = FP32 upper bound of the point's longest edge key (edges in original ids)
+void edge_max_keys(const uint64_t* edges, int64_t ne, const int32_t* rank, const float* X, int Dp, int metric,
+                   float* maxe, int64_t n, cudaStream_t s);
+// the old edges no batch point lies strictly inside of (Stage VII), written to kept; returns
+// their count; stats[0] += lune tests, stats[1] += FP64 decisions
+int64_t stage7_remove(const uint64_t* edges, int64_t ne, int64_t n_old, const int4* s7, int64_t ns7, const float* X,
+                      int D, int Dp, int metric, const int32_t* order, const int32_t* rank, uint64_t* kept,
+                      unsigned long long* stats, cudaStream_t s);
 
 }  // namespace grng

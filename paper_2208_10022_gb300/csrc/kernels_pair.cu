@@ -26,6 +26,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cstring>
+#include <functional>
 #include <vector>
 
 #include "common.cuh"
@@ -1319,11 +1320,293 @@ __device__ __forceinline__ int2 bucket_span(const ListParams& p, int s, float kl
 
 __device__ __forceinline__ unsigned lt_hash(int k) { return ((unsigned)k * 2654435761u) >> (32 - 10); }
 
-// One warp per pair.  G lanes share one listed node in the distance scan (G = 8 for
-// dimensions that are multiples of 32, fewer for 8 and 16); NQ = float4 columns per lane
-// (0: any dimension, the other endpoint's row read from memory).
+// Decision of one list-tier pair from the intersection or the scan, counted per warp.
+struct LtCount {
+  unsigned long long link = 0, pend = 0, un = 0, blk = 0, test = 0, isect = 0, probe = 0, read = 0;
+};
+
+// Ambiguous triples of a pair that nothing blocked are recorded in a second pass; the
+// pair takes a pending slot first.
+__device__ __forceinline__ unsigned long long lt_pend_slot(const ListParams& p, int2 pr, int lane) {
+  unsigned long long slot = 0;
+  if (lane == 0) slot = atomicAdd(p.pend_cnt, 1ull);
+  slot = __shfl_sync(FULLMASK, slot, 0);
+  if (lane == 0 && slot < p.pend_cap) p.pend[slot] = pr;
+  return slot;
+}
+
+#define LT_U 4  // list entries per lane per round of the intersection (loads in flight)
+
+// Pairs covered from both sides: a blocker is a node of both annuli.  The shorter annulus
+// goes into a per-warp hash table (in chunks of LT_CHUNK entries), the other one probes it.
+__device__ __forceinline__ void lt_intersect(const ListParams& p, int2 pr, const PairThr& P, float ekx, float eky,
+                                             Err e, int lane, int* tab_i, float* tab_k, LtCount& c, bool& blocked,
+                                             bool& anyamb) {
+  const int x = pr.x, y = pr.y;
+  const int2 ax = bucket_span(p, x, ekx, P.t1hi), ay = bucket_span(p, y, eky, P.t2hi);
+  const bool hy = (ay.y - ay.x) <= (ax.y - ax.x);  // hash the shorter annulus
+  const int hs = hy ? y : x, qs = hy ? x : y;
+  const int2 hspan = hy ? ay : ax, qspan = hy ? ax : ay;
+  const float hlo = hy ? eky : ekx, hhi = hy ? P.t2hi : P.t1hi;
+  const float qlo = hy ? ekx : eky, qhi = hy ? P.t1hi : P.t2hi;
+  const int64_t hb = (int64_t)hs * GRNG_LCAP, qb = (int64_t)qs * GRNG_LCAP;
+  unsigned long long slot = 0;
+  for (int pass = 0; pass < 2; ++pass) {  // pass 1 records the ambiguous triples
+    if (pass == 1) {
+      if (blocked || !anyamb) break;
+      slot = lt_pend_slot(p, pr, lane);
+    }
+    for (int h0 = hspan.x; h0 < hspan.y && !blocked; h0 += LT_CHUNK) {
+      __syncwarp();
+      for (int i = lane; i < LT_TAB; i += 32) tab_i[i] = -1;
+      __syncwarp();
+      const int h1 = min(h0 + LT_CHUNK, hspan.y);
+      for (int j0 = h0; j0 < h1; j0 += 32 * LT_U) {
+        float kk[LT_U];
+        int kj[LT_U];
+#pragma unroll
+        for (int u = 0; u < LT_U; ++u) {
+          const int j = j0 + lane + 32 * u;
+          kk[u] = j < h1 ? p.lkey[hb + j] : -1.0f;
+          kj[u] = j < h1 ? p.lidx[hb + j] : -1;
+        }
+#pragma unroll
+        for (int u = 0; u < LT_U; ++u) {
+          if (kj[u] < 0) continue;
+          c.read += pass == 0;
+          if (lo_b(kk[u], e) < hhi && hi_b(kk[u], e) > hlo) {
+            unsigned h = lt_hash(kj[u]);
+            for (int probe = 0; probe < LT_TAB; ++probe) {  // at most half the slots are taken
+              if (atomicCAS(tab_i + h, -1, kj[u]) == -1) { tab_k[h] = kk[u]; break; }
+              h = (h + 1) & (LT_TAB - 1);
+            }
+          }
+        }
+      }
+      __syncwarp();
+      for (int j0 = qspan.x; j0 < qspan.y; j0 += 32 * LT_U) {
+        float kk[LT_U];
+        int kj[LT_U];
+#pragma unroll
+        for (int u = 0; u < LT_U; ++u) {
+          const int j = j0 + lane + 32 * u;
+          kk[u] = j < qspan.y ? p.lkey[qb + j] : -1.0f;
+          kj[u] = j < qspan.y ? p.lidx[qb + j] : -1;
+        }
+        bool b2 = false, b1 = false;
+#pragma unroll
+        for (int u = 0; u < LT_U; ++u) {
+          if (kj[u] < 0) continue;
+          c.read += pass == 0;
+          if (!(lo_b(kk[u], e) < qhi && hi_b(kk[u], e) > qlo)) continue;
+          c.probe += pass == 0;
+          unsigned h = lt_hash(kj[u]);
+          for (int probe = 0; probe < LT_TAB; ++probe) {
+            const int w = tab_i[h];
+            if (w == -1) break;
+            if (w == kj[u]) {
+              const float other = tab_k[h];
+              const float a = hy ? kk[u] : other, b = hy ? other : kk[u];  // keys to x and to y
+              const int stt = block_state(a, b, P, e);
+              b2 |= stt == 2;
+              b1 |= stt == 1;
+              if (pass == 1 && stt == 1) push_pair(p.amb, p.amb_cnt, p.amb_cap, make_int2((int)slot, kj[u]));
+              break;
+            }
+            h = (h + 1) & (LT_TAB - 1);
+          }
+        }
+        if (pass == 0) {
+          blocked = __any_sync(FULLMASK, b2);
+          anyamb |= __any_sync(FULLMASK, b1);
+          if (blocked) break;
+        }
+      }
+    }
+  }
+  c.isect += lane == 0;
+}
+
+// Pairs covered from one side s: the annulus of s's list, tested against the other
+// endpoint o.  Each listed node k is first bounded through its parent c, whose keys to x and
+// y the ancestor table holds: d(k,o) >= d(c,o) - d(k,c) settles "k fails the condition at o"
+// (triangle inequality); for L2, a lower bound of |k - c*| (Stewart's identity, from k's own
+// key to s and that bound, or from c) of at least rho puts k outside the ball around the
+// G-lune, as in tier 3; and d(k,o) <= d(c,o) + d(k,c) can settle "k blocks".  Only the nodes
+// no bound settles get their distance to o, computed by groups of G lanes.
 template <int G, int NQ>
-__global__ void __launch_bounds__(LT_WARPS * 32, 2) list_tier_kernel(ListParams p) {
+__device__ __forceinline__ void lt_scan(const ListParams& p, int2 pr, int sd, float v, const PairThr& P, float ekx,
+                                        float eky, Err e, int lane, LtCount& c, bool& blocked, bool& anyamb) {
+  const int x = pr.x, y = pr.y;
+  const int gl = lane % G, gi = lane / G;
+  const int s = sd ? y : x, o = sd ? x : y;
+  const float slo = sd ? eky : ekx, shi = sd ? P.t2hi : P.t1hi;
+  const float olo_k = sd ? P.t1lo : P.t2lo, ohi_k = sd ? P.t1hi : P.t2hi;  // thresholds at o (keys)
+  const float slo_k = sd ? P.t2lo : P.t1lo;                                // certain side at s
+  const int2 sp = bucket_span(p, s, slo, shi);
+  const int64_t sb = (int64_t)s * GRNG_LCAP;
+  const float* xo = p.X + (int64_t)o * p.Dp;
+  const float u2 = 1.1920928955078125e-07f;
+  // thresholds at o in distance units: above ohd no node satisfies it, below old every one does
+  const float ohd = p.metric == L2 ? sqrtf(fmaxf(ohi_k, 0.0f)) * (1.0f + u2) : ohi_k;
+  const float old_ = p.metric == L2 ? (olo_k > 0.0f ? sqrtf(olo_k) * (1.0f - u2) : -1.0f) : olo_k;
+  // ball around the G-lune (L2): centre c* = (1-lam) x + lam y, radius rho
+  const float vlo = fmaxf(lo_b(v, e), 0.0f), vhi = hi_b(v, e);
+  float lam = 0.5f, rho2 = -1.0f;
+  if (p.metric == L2) {
+    lam = fminf(fmaxf((vhi + P.t1hi - P.t2hi) / (2.0f * fmaxf(vhi, 1e-30f)), 0.0f), 1.0f);
+    const float m1 = (1.0f - lam) * P.t1hi + lam * P.t2hi;
+    rho2 = m1 - lam * (1.0f - lam) * vlo + 8.0f * u2 * (m1 + lam * (1.0f - lam) * vhi);
+  }
+  const float rho = rho2 >= 0.0f ? sqrtf(rho2) * (1.0f + u2) : -1.0f;
+  const float* tab_x = p.atab ? p.atab + (int64_t)x * p.tabw + p.toff : nullptr;
+  const float* tab_y = p.atab ? p.atab + (int64_t)y * p.tabw + p.toff : nullptr;
+  float4 orow[NQ > 0 ? NQ : 1];
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) orow[q] = __ldg(reinterpret_cast<const float4*>(xo) + gl + G * q);
+  unsigned long long slot = 0;
+  for (int pass = 0; pass < 2; ++pass) {
+    if (pass == 1) {
+      if (blocked || !anyamb) break;
+      slot = lt_pend_slot(p, pr, lane);
+    }
+    for (int jb = sp.x; jb < sp.y; jb += 64) {
+      // ---- two entries per lane: filters and bounds ----
+      float kk[2];
+      int kj[2];
+      bool need[2];
+      int stt = 0;
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const int j = jb + lane + 32 * u;
+        kk[u] = j < sp.y ? p.lkey[sb + j] : 0.0f;
+        kj[u] = j < sp.y ? p.lidx[sb + j] : -1;
+      }
+      int cpar[2] = {0, 0};
+      float dk[2] = {0.0f, 0.0f};
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        if (kj[u] >= 0) c.read += pass == 0;
+        need[u] = kj[u] >= 0 && kj[u] != o && lo_b(kk[u], e) < shi && hi_b(kk[u], e) > slo;
+        if (need[u] && p.atab) {
+          cpar[u] = p.parent[kj[u]];
+          dk[u] = p.pdh[kj[u]];
+        }
+      }
+      if (p.atab) {
+        float kcx[2], kcy[2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          kcx[u] = need[u] ? tab_x[cpar[u]] : 0.0f;
+          kcy[u] = need[u] ? tab_y[cpar[u]] : 0.0f;
+        }
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          if (!need[u]) continue;
+          const float kco = sd ? kcx[u] : kcy[u];
+          const float dlo_ = dist_lo(kco, p.metric, e), dhi_ = dist_hi(kco, p.metric, e);
+          const float dko = dlo_ - dk[u] - u2 * (dlo_ + dk[u]);  // lower bound of d(k,o)
+          if (dko >= ohd) {
+            need[u] = false;  // k fails the condition at o
+          } else if (rho >= 0.0f) {
+            // |k - c*|^2 from k's own key to s and the lower bound of its distance to o
+            const float ko2 = dko > 0.0f ? dko * dko * (1.0f - u2) : 0.0f;
+            const float ks2 = fmaxf(lo_b(kk[u], e), 0.0f);
+            const float Ak = sd ? ko2 : ks2, Bk = sd ? ks2 : ko2;  // lower bounds of the keys to x and y
+            const float mk = (1.0f - lam) * Ak + lam * Bk + lam * (1.0f - lam) * vhi;
+            const float qk = (1.0f - lam) * Ak + lam * Bk - lam * (1.0f - lam) * vhi - 8.0f * u2 * mk;
+            if (qk > 0.0f && qk >= rho * rho * (1.0f + 4.0f * u2)) {
+              need[u] = false;
+            } else {  // the same through the parent's keys to both endpoints
+              const float Alo = fmaxf(lo_b(kcx[u], e), 0.0f), Blo = fmaxf(lo_b(kcy[u], e), 0.0f);
+              const float Ahi = hi_b(kcx[u], e), Bhi = hi_b(kcy[u], e);
+              const float mm = (1.0f - lam) * Ahi + lam * Bhi + lam * (1.0f - lam) * vhi;
+              const float qq = (1.0f - lam) * Alo + lam * Blo - lam * (1.0f - lam) * vhi - 8.0f * u2 * mm;
+              const float dcs = qq > 0.0f ? sqrtf(qq) * (1.0f - u2) : 0.0f;
+              if (dcs - dk[u] - u2 * (dcs + dk[u]) >= rho) need[u] = false;  // outside the lune's ball
+            }
+          }
+          if (need[u] && old_ > 0.0f && dhi_ + dk[u] + u2 * (dhi_ + dk[u]) < old_ && hi_b(kk[u], e) < slo_k) {
+            need[u] = false;  // d(k,o) < the certain threshold at o, and k certainly meets s's
+            stt = 2;
+          }
+        }
+      }
+      if (pass == 0) {
+        blocked = __any_sync(FULLMASK, stt == 2);
+        if (blocked) break;
+      }
+      // ---- the unsettled entries, G lanes per distance ----
+#pragma unroll 1
+      for (int u = 0; u < 2; ++u) {
+        unsigned nm = __ballot_sync(FULLMASK, need[u]);
+        while (nm) {
+          // group gi takes the gi-th remaining entry
+          unsigned mm_ = nm;
+          for (int t = 0; t < gi && mm_; ++t) mm_ &= mm_ - 1u;
+          const int src = mm_ ? __ffs(mm_) - 1 : -1;
+          for (int t = 0; t < 32 / G && nm; ++t) nm &= nm - 1u;
+          const int kq = __shfl_sync(FULLMASK, kj[u], src < 0 ? 0 : src);
+          const float kkq = __shfl_sync(FULLMASK, kk[u], src < 0 ? 0 : src);
+          const int krow = src < 0 ? o : kq;  // a safe row to read when the group has no entry
+          const float4* xk = reinterpret_cast<const float4*>(p.X + (int64_t)krow * p.Dp);
+          float acc = 0.0f;
+          if (NQ > 0) {
+#pragma unroll
+            for (int q = 0; q < (NQ > 0 ? NQ : 1); ++q) {
+              const float4 a4 = __ldg(xk + gl + G * q), b4 = orow[q];
+              if (p.metric == L2) {
+                float d;
+                d = a4.x - b4.x; acc = fmaf(d, d, acc); d = a4.y - b4.y; acc = fmaf(d, d, acc);
+                d = a4.z - b4.z; acc = fmaf(d, d, acc); d = a4.w - b4.w; acc = fmaf(d, d, acc);
+              } else {
+                acc += fabsf(a4.x - b4.x); acc += fabsf(a4.y - b4.y); acc += fabsf(a4.z - b4.z);
+                acc += fabsf(a4.w - b4.w);
+              }
+            }
+          } else {
+            const float4* x4 = reinterpret_cast<const float4*>(xo);
+            for (int q = gl; q < (p.Dp >> 2); q += G) {
+              const float4 a4 = __ldg(xk + q), b4 = __ldg(x4 + q);
+              if (p.metric == L2) {
+                float d;
+                d = a4.x - b4.x; acc = fmaf(d, d, acc); d = a4.y - b4.y; acc = fmaf(d, d, acc);
+                d = a4.z - b4.z; acc = fmaf(d, d, acc); d = a4.w - b4.w; acc = fmaf(d, d, acc);
+              } else {
+                acc += fabsf(a4.x - b4.x); acc += fabsf(a4.y - b4.y); acc += fabsf(a4.z - b4.z);
+                acc += fabsf(a4.w - b4.w);
+              }
+            }
+          }
+#pragma unroll
+          for (int sh = G / 2; sh > 0; sh >>= 1) acc += __shfl_xor_sync(FULLMASK, acc, sh);
+          int st2 = 0;
+          if (src >= 0) {
+            // keys of kq to x and to y: the listed key is to s
+            const float a = sd ? acc : kkq, b = sd ? kkq : acc;
+            st2 = block_state(a, b, P, e);
+            c.test += (gl == 0 && pass == 0);
+          }
+          if (pass == 0) {
+            if (__any_sync(FULLMASK, st2 == 2)) { blocked = true; break; }
+            anyamb |= __any_sync(FULLMASK, st2 == 1);
+          } else if (st2 == 1 && gl == 0) {
+            push_pair(p.amb, p.amb_cnt, p.amb_cap, make_int2((int)slot, kq));
+          }
+        }
+        if (blocked) break;
+      }
+      if (pass == 0 && blocked) break;
+    }
+  }
+}
+
+// One warp per pair.  MODE 0 decides the pairs covered from both sides (and forwards the
+// trivial ones); MODE 1 the pairs covered from one side, G lanes sharing one listed node in
+// the distance tests (G = 8 for dimensions that are multiples of 32, fewer for 8 and 16),
+// NQ float4 columns per lane (0: any dimension, the other endpoint's row read from memory).
+template <int MODE, int G, int NQ>
+__global__ void __launch_bounds__(LT_WARPS * 32, 3) list_tier_kernel(ListParams p) {
   extern __shared__ __align__(16) int lt_sm[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   int* tab_i = lt_sm + wib * 2 * LT_TAB;                          // node ids (-1: empty)
@@ -1331,19 +1614,19 @@ __global__ void __launch_bounds__(LT_WARPS * 32, 2) list_tier_kernel(ListParams 
   const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const Err e = err_fp32(p.Dp);
-  const int gl = lane % G, gi = lane / G;
-  unsigned long long c_link = 0, c_pend = 0, c_un = 0, c_blk = 0, c_test = 0, c_isect = 0, c_probe = 0, c_read = 0;
+  LtCount c;
   for (int64_t t = wid; t < p.m; t += nw) {
     const int sd = p.side[t];
+    if ((MODE == 0) != (sd >= 2)) continue;  // the other kernel's pair
     const int2 pr = p.pairs[t];
     if (sd == 3) {
       if (lane == 0) push_pair(p.links, p.link_cnt, p.link_cap, pr);
-      c_link += lane == 0;
+      c.link += lane == 0;
       continue;
     }
     if (sd == 2) {
       if (lane == 0) push_pair(p.unres, p.unres_cnt, p.unres_cap, pr);
-      c_un += lane == 0;
+      c.un += lane == 0;
       continue;
     }
     const int x = pr.x, y = pr.y;
@@ -1352,244 +1635,38 @@ __global__ void __launch_bounds__(LT_WARPS * 32, 2) list_tier_kernel(ListParams 
                                       p.rlo ? p.rlo[y] : 0.0f, p.rhi ? p.rhi[y] : 0.0f, p.metric, e, p.guide);
     if (P.quick) {
       if (lane == 0) push_pair(p.links, p.link_cnt, p.link_cap, pr);
-      c_link += lane == 0;
+      c.link += lane == 0;
       continue;
     }
     // nodes within E of one endpoint cannot satisfy the other endpoint's condition
     const float ekx = excl_key(excl_dist(v, P.t2hi, p.metric, e), p.metric);
     const float eky = excl_key(excl_dist(v, P.t1hi, p.metric, e), p.metric);
     bool blocked = false, anyamb = false;
-    unsigned long long slot = 0;
-    if (sd == 4) {
-      // ---- both lists cover: a blocker is a node of both annuli ----------------------
-      const int2 ax = bucket_span(p, x, ekx, P.t1hi), ay = bucket_span(p, y, eky, P.t2hi);
-      const bool hy = (ay.y - ay.x) <= (ax.y - ax.x);  // hash the shorter annulus
-      const int hs = hy ? y : x, qs = hy ? x : y;
-      const int2 hspan = hy ? ay : ax, qspan = hy ? ax : ay;
-      const float hlo = hy ? eky : ekx, hhi = hy ? P.t2hi : P.t1hi;
-      const float qlo = hy ? ekx : eky, qhi = hy ? P.t1hi : P.t2hi;
-      const int64_t hb = (int64_t)hs * GRNG_LCAP, qb = (int64_t)qs * GRNG_LCAP;
-      for (int pass = 0; pass < 2; ++pass) {  // pass 1 records the ambiguous triples
-        if (pass == 1) {
-          if (blocked || !anyamb) break;
-          if (lane == 0) slot = atomicAdd(p.pend_cnt, 1ull);
-          slot = __shfl_sync(FULLMASK, slot, 0);
-          if (lane == 0 && slot < p.pend_cap) p.pend[slot] = pr;
-        }
-        for (int h0 = hspan.x; h0 < hspan.y && !blocked; h0 += LT_CHUNK) {
-          __syncwarp();
-          for (int i = lane; i < LT_TAB; i += 32) tab_i[i] = -1;
-          __syncwarp();
-          const int h1 = min(h0 + LT_CHUNK, hspan.y);
-          for (int j = h0 + lane; j < h1; j += 32) {
-            ++c_read;
-            const float kk = p.lkey[hb + j];
-            if (lo_b(kk, e) < hhi && hi_b(kk, e) > hlo) {
-              const int k = p.lidx[hb + j];
-              unsigned h = lt_hash(k);
-              for (int probe = 0; probe < LT_TAB; ++probe) {  // at most half the slots are taken
-                if (atomicCAS(tab_i + h, -1, k) == -1) { tab_k[h] = kk; break; }
-                h = (h + 1) & (LT_TAB - 1);
-              }
-            }
-          }
-          __syncwarp();
-          for (int jb = qspan.x; jb < qspan.y; jb += 32) {
-            const int j = jb + lane;
-            int stt = 0, k = -1;
-            if (j < qspan.y) {
-              c_read += pass == 0;
-              const float kk = p.lkey[qb + j];
-              if (lo_b(kk, e) < qhi && hi_b(kk, e) > qlo) {
-                k = p.lidx[qb + j];
-                unsigned h = lt_hash(k);
-                ++c_probe;
-                for (int probe = 0; probe < LT_TAB; ++probe) {
-                  const int w = tab_i[h];
-                  if (w == -1) break;
-                  if (w == k) {
-                    const float other = tab_k[h];
-                    const float a = hy ? kk : other, b = hy ? other : kk;  // keys to x and to y
-                    stt = block_state(a, b, P, e);
-                    break;
-                  }
-                  h = (h + 1) & (LT_TAB - 1);
-                }
-              }
-            }
-            if (pass == 0) {
-              blocked = __any_sync(FULLMASK, stt == 2);
-              anyamb |= __any_sync(FULLMASK, stt == 1);
-              if (blocked) break;
-            } else if (stt == 1) {
-              push_pair(p.amb, p.amb_cnt, p.amb_cap, make_int2((int)slot, k));
-            }
-          }
-        }
-      }
-      c_isect += lane == 0;
-    } else {
-      // ---- one list covers: its annulus, tested against the other endpoint o ----------------
-      // Each listed node k is first bounded through its parent c, whose keys to s and o the
-      // ancestor table holds: d(k,o) >= d(c,o) - d(k,c) settles "k fails the condition at o"
-      // (triangle inequality), and for L2 |k - c*| >= |c - c*| - d(k,c) >= rho puts k outside
-      // the ball around the G-lune (Stewart's identity, as in tier 3); d(k,o) <= d(c,o) + d(k,c)
-      // can settle "k blocks".  Only the nodes no bound settles get their distance to o.
-      const int s = sd ? y : x, o = sd ? x : y;
-      const float slo = sd ? eky : ekx, shi = sd ? P.t2hi : P.t1hi;
-      const float olo_k = sd ? P.t1lo : P.t2lo, ohi_k = sd ? P.t1hi : P.t2hi;  // thresholds at o (keys)
-      const float slo_k = sd ? P.t2lo : P.t1lo;                                // certain side at s
-      const int2 sp = bucket_span(p, s, slo, shi);
-      const int64_t sb = (int64_t)s * GRNG_LCAP;
-      const float* xo = p.X + (int64_t)o * p.Dp;
-      const float u2 = 1.1920928955078125e-07f;
-      // thresholds at o in distance units: above ohd no node satisfies it, below old every one does
-      const float ohd = p.metric == L2 ? sqrtf(fmaxf(ohi_k, 0.0f)) * (1.0f + u2) : ohi_k;
-      const float old_ = p.metric == L2 ? (olo_k > 0.0f ? sqrtf(olo_k) * (1.0f - u2) : -1.0f) : olo_k;
-      // ball around the G-lune (L2): centre c* = (1-lam) x + lam y, radius rho
-      const float vlo = fmaxf(lo_b(v, e), 0.0f), vhi = hi_b(v, e);
-      float lam = 0.5f, rho2 = -1.0f;
-      if (p.metric == L2) {
-        lam = fminf(fmaxf((vhi + P.t1hi - P.t2hi) / (2.0f * fmaxf(vhi, 1e-30f)), 0.0f), 1.0f);
-        const float m1 = (1.0f - lam) * P.t1hi + lam * P.t2hi;
-        rho2 = m1 - lam * (1.0f - lam) * vlo + 8.0f * u2 * (m1 + lam * (1.0f - lam) * vhi);
-      }
-      const float rho = rho2 >= 0.0f ? sqrtf(rho2) * (1.0f + u2) : -1.0f;
-      const float* tab_x = p.atab ? p.atab + (int64_t)x * p.tabw + p.toff : nullptr;
-      const float* tab_y = p.atab ? p.atab + (int64_t)y * p.tabw + p.toff : nullptr;
-      float4 orow[NQ > 0 ? NQ : 1];
-#pragma unroll
-      for (int q = 0; q < NQ; ++q) orow[q] = __ldg(reinterpret_cast<const float4*>(xo) + gl + G * q);
-      for (int pass = 0; pass < 2; ++pass) {
-        if (pass == 1) {
-          if (blocked || !anyamb) break;
-          if (lane == 0) slot = atomicAdd(p.pend_cnt, 1ull);
-          slot = __shfl_sync(FULLMASK, slot, 0);
-          if (lane == 0 && slot < p.pend_cap) p.pend[slot] = pr;
-        }
-        for (int jb = sp.x; jb < sp.y; jb += 32) {
-          // ---- one entry per lane: filters and bounds ----
-          const int j = jb + lane;
-          bool need = false;
-          float kk = 0.0f;
-          int k = -1, stt = 0;
-          if (j < sp.y) {
-            c_read += pass == 0;
-            kk = p.lkey[sb + j];
-            const int kj = p.lidx[sb + j];
-            if (kj != o && lo_b(kk, e) < shi && hi_b(kk, e) > slo) {
-              k = kj;
-              need = true;
-              if (p.atab) {
-                const int c = p.parent[k];
-                const float dk = p.pdh[k];
-                const float kcx = tab_x[c], kcy = tab_y[c];
-                const float kco = sd ? kcx : kcy;
-                const float dlo_ = dist_lo(kco, p.metric, e), dhi_ = dist_hi(kco, p.metric, e);
-                if (dlo_ - dk - u2 * (dlo_ + dk) >= ohd) {
-                  need = false;  // k fails the condition at o
-                } else if (rho >= 0.0f) {
-                  const float Alo = fmaxf(lo_b(kcx, e), 0.0f), Blo = fmaxf(lo_b(kcy, e), 0.0f);
-                  const float Ahi = hi_b(kcx, e), Bhi = hi_b(kcy, e);
-                  const float mm = (1.0f - lam) * Ahi + lam * Bhi + lam * (1.0f - lam) * vhi;
-                  const float qq = (1.0f - lam) * Alo + lam * Blo - lam * (1.0f - lam) * vhi - 8.0f * u2 * mm;
-                  const float dcs = qq > 0.0f ? sqrtf(qq) * (1.0f - u2) : 0.0f;
-                  if (dcs - dk - u2 * (dcs + dk) >= rho) need = false;  // k outside the lune's ball
-                }
-                if (need && old_ > 0.0f && dhi_ + dk + u2 * (dhi_ + dk) < old_ && hi_b(kk, e) < slo_k) {
-                  need = false;  // d(k,o) < the certain threshold at o, and k certainly meets s's
-                  stt = 2;
-                }
-              }
-            }
-          }
-          if (pass == 0) {
-            blocked = __any_sync(FULLMASK, stt == 2);
-            if (blocked) break;
-          }
-          // ---- the unsettled entries, G lanes per distance ----
-          unsigned nm = __ballot_sync(FULLMASK, need);
-          while (nm) {
-            // group gi takes the gi-th remaining entry
-            unsigned mm_ = nm;
-            for (int t = 0; t < gi && mm_; ++t) mm_ &= mm_ - 1u;
-            const int src = mm_ ? __ffs(mm_) - 1 : -1;
-            for (int t = 0; t < 32 / G && nm; ++t) nm &= nm - 1u;
-            const int kq = __shfl_sync(FULLMASK, k, src < 0 ? 0 : src);
-            const float kkq = __shfl_sync(FULLMASK, kk, src < 0 ? 0 : src);
-            const int krow = src < 0 ? o : kq;  // a safe row to read when the group has no entry
-            const float4* xk = reinterpret_cast<const float4*>(p.X + (int64_t)krow * p.Dp);
-            float acc = 0.0f;
-            if (NQ > 0) {
-#pragma unroll
-              for (int q = 0; q < (NQ > 0 ? NQ : 1); ++q) {
-                const float4 a4 = __ldg(xk + gl + G * q), b4 = orow[q];
-                if (p.metric == L2) {
-                  float d;
-                  d = a4.x - b4.x; acc = fmaf(d, d, acc); d = a4.y - b4.y; acc = fmaf(d, d, acc);
-                  d = a4.z - b4.z; acc = fmaf(d, d, acc); d = a4.w - b4.w; acc = fmaf(d, d, acc);
-                } else {
-                  acc += fabsf(a4.x - b4.x); acc += fabsf(a4.y - b4.y); acc += fabsf(a4.z - b4.z);
-                  acc += fabsf(a4.w - b4.w);
-                }
-              }
-            } else {
-              const float4* x4 = reinterpret_cast<const float4*>(xo);
-              for (int q = gl; q < (p.Dp >> 2); q += G) {
-                const float4 a4 = __ldg(xk + q), b4 = __ldg(x4 + q);
-                if (p.metric == L2) {
-                  float d;
-                  d = a4.x - b4.x; acc = fmaf(d, d, acc); d = a4.y - b4.y; acc = fmaf(d, d, acc);
-                  d = a4.z - b4.z; acc = fmaf(d, d, acc); d = a4.w - b4.w; acc = fmaf(d, d, acc);
-                } else {
-                  acc += fabsf(a4.x - b4.x); acc += fabsf(a4.y - b4.y); acc += fabsf(a4.z - b4.z);
-                  acc += fabsf(a4.w - b4.w);
-                }
-              }
-            }
-#pragma unroll
-            for (int sh = G / 2; sh > 0; sh >>= 1) acc += __shfl_xor_sync(FULLMASK, acc, sh);
-            int st2 = 0;
-            if (src >= 0) {
-              // keys of kq to x and to y: the listed key is to s
-              const float a = sd ? acc : kkq, b = sd ? kkq : acc;
-              st2 = block_state(a, b, P, e);
-              c_test += (gl == 0 && pass == 0);
-            }
-            if (pass == 0) {
-              if (__any_sync(FULLMASK, st2 == 2)) { blocked = true; break; }
-              anyamb |= __any_sync(FULLMASK, st2 == 1);
-            } else if (st2 == 1 && gl == 0) {
-              push_pair(p.amb, p.amb_cnt, p.amb_cap, make_int2((int)slot, kq));
-            }
-          }
-          if (pass == 0 && blocked) break;
-        }
-      }
-    }
+    if (MODE == 0) lt_intersect(p, pr, P, ekx, eky, e, lane, tab_i, tab_k, c, blocked, anyamb);
+    else lt_scan<G, NQ>(p, pr, sd, v, P, ekx, eky, e, lane, c, blocked, anyamb);
     if (blocked) {
-      c_blk += lane == 0;
+      c.blk += lane == 0;
     } else if (!anyamb) {
       if (lane == 0) push_pair(p.links, p.link_cnt, p.link_cap, pr);
-      c_link += lane == 0;
+      c.link += lane == 0;
     } else {
-      c_pend += lane == 0;
+      c.pend += lane == 0;
     }
   }
   for (int sh = 16; sh > 0; sh >>= 1) {
-    c_test += __shfl_down_sync(FULLMASK, c_test, sh);
-    c_probe += __shfl_down_sync(FULLMASK, c_probe, sh);
-    c_read += __shfl_down_sync(FULLMASK, c_read, sh);
+    c.test += __shfl_down_sync(FULLMASK, c.test, sh);
+    c.probe += __shfl_down_sync(FULLMASK, c.probe, sh);
+    c.read += __shfl_down_sync(FULLMASK, c.read, sh);
   }
   if (lane == 0) {
-    atomicAdd(p.stats + 0, c_link);
-    atomicAdd(p.stats + 1, c_pend);
-    atomicAdd(p.stats + 2, c_un);
-    atomicAdd(p.stats + 3, c_blk);
-    atomicAdd(p.stats + 4, c_test);
-    atomicAdd(p.stats + 5, c_isect);
-    atomicAdd(p.stats + 6, c_probe);
-    atomicAdd(p.stats + 7, c_read);
+    atomicAdd(p.stats + 0, c.link);
+    atomicAdd(p.stats + 1, c.pend);
+    atomicAdd(p.stats + 2, c.un);
+    atomicAdd(p.stats + 3, c.blk);
+    atomicAdd(p.stats + 4, c.test);
+    atomicAdd(p.stats + 5, c.isect);
+    atomicAdd(p.stats + 6, c.probe);
+    atomicAdd(p.stats + 7, c.read);
   }
 }
 
@@ -1617,7 +1694,8 @@ __global__ void resolve_emit_kernel(const int2* __restrict__ pend, const int* __
                                     int64_t m, int grng, uint32_t* gx, uint32_t* gg,
                                     int64_t words, const int32_t* __restrict__ orig,
                                     unsigned long long* ecnt, unsigned long long ecap,
-                                    uint64_t* edges) {
+                                    uint64_t* edges, int2* newg, unsigned long long* newg_cnt,
+                                    unsigned long long newg_cap) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= m) return;
   int f = pflag ? pflag[i] : 0;
@@ -1625,7 +1703,14 @@ __global__ void resolve_emit_kernel(const int2* __restrict__ pend, const int* __
   int a = min(pr.x, pr.y), b = max(pr.x, pr.y);
   if (grng) {
     if (!(f & 1)) atomicOr(gx + (int64_t)a * words + (b >> 5), 1u << (b & 31));
-    if (!(f & 2)) atomicOr(gg + (int64_t)a * words + (b >> 5), 1u << (b & 31));
+    if (!(f & 2)) {
+      const unsigned bit = 1u << (b & 31);
+      const unsigned old = atomicOr(gg + (int64_t)a * words + (b >> 5), bit);
+      if (newg && !(old & bit)) {
+        const unsigned long long pos = atomicAdd(newg_cnt, 1ull);
+        if (pos < newg_cap) newg[pos] = make_int2(a, b);
+      }
+    }
   } else if (!(f & 1)) {
     int oa = orig[pr.x], ob = orig[pr.y];
     uint64_t key = ((uint64_t)(uint32_t)min(oa, ob) << 32) | (uint32_t)max(oa, ob);
@@ -1649,6 +1734,20 @@ static void launch_prep(const LevelIn& in, __half* A, uint8_t* ni, float* nk, cu
     block_prep_kernel<KC, L1><<<(unsigned)nb, GRNG_THREADS, smem, s>>>(in.X, in.n, in.Dp, A, ni, nk); note_launch();
   }
   GRNG_CUDA(cudaGetLastError());
+}
+
+void block_prep(const float* X, int64_t n, int Dp, int metric, __half* A, uint8_t* nbr_idx, float* nbr_key,
+                cudaStream_t s) {
+  if (n < 1) return;
+  LevelIn in{};
+  in.X = X;
+  in.n = n;
+  in.Dp = Dp;
+  in.metric = metric;
+  const int KC = Dp % 32 == 0 ? 32 : (Dp % 16 == 0 ? 16 : 8);
+  if (KC == 32) launch_prep<32>(in, A, nbr_idx, nbr_key, s);
+  else if (KC == 16) launch_prep<16>(in, A, nbr_idx, nbr_key, s);
+  else launch_prep<8>(in, A, nbr_idx, nbr_key, s);
 }
 
 template <int KC>
@@ -1690,9 +1789,12 @@ static void launch_range(const LevelIn& in, const unsigned int* tk, int* hist, c
 
 template <int G, int NQ>
 static void launch_list_gq(const ListParams& lp, unsigned grid, cudaStream_t s) {
+  // the pairs covered from both sides (with the hash tables), then those covered from one
   const size_t smem = (size_t)LT_WARPS * 2 * LT_TAB * 4;
-  GRNG_CUDA(cudaFuncSetAttribute(list_tier_kernel<G, NQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  list_tier_kernel<G, NQ><<<grid, LT_WARPS * 32, smem, s>>>(lp); note_launch();
+  GRNG_CUDA(cudaFuncSetAttribute(list_tier_kernel<0, G, NQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  list_tier_kernel<0, G, NQ><<<grid, LT_WARPS * 32, smem, s>>>(lp); note_launch();
+  GRNG_CUDA(cudaGetLastError());
+  list_tier_kernel<1, G, NQ><<<grid, LT_WARPS * 32, 0, s>>>(lp); note_launch();
   GRNG_CUDA(cudaGetLastError());
 }
 // group width and float4 columns per lane for the padded dimension (8, 16 or a multiple of 32)
@@ -1725,10 +1827,320 @@ static int num_sms() {
   return sms;
 }
 
+// Tiers 2 and 3, the FP64 recheck and the emission, for the candidate pairs surv[nsurv]
+// that tier 1 (or an incremental update) leaves open.  knn_idx / knn_key / knn_rb are the
+// level's neighbour lists (knn_idx null: no tier 2, every pair goes on); tier2b = false
+// skips the lists of the pairs' second endpoints (when only the first ones are exact).
+static void finish_level(const LevelIn& in, LevelOut& out, LevelStats& st, cudaStream_t s, const int2* surv,
+                         unsigned long long nsurv, const int32_t* knn_idx, const float* knn_key,
+                         const float* knn_rb, bool tier2b, unsigned long long* dc,
+                         const std::function<void(int)>& tick) {
+  const int64_t n = in.n;
+  // ---- tiers 2 and 3 ---------------------------------------------------------------------
+  DevBuf off, oth, tmp, links, unres, pend, amb, pflag, unres2, off2, oth2, fbuf;
+  DevBuf side, tkey, tcut, hist, lcnt, lastb, boff, lidx, lkey, unres3, atab;
+  int64_t toff[GRNG_MAXL] = {0}, tabw = 0;  // columns of the node x ancestor key table
+  if (knn_idx) {
+    GRNG_CUDA(off.alloc((size_t)(n + 1) * 8));
+    GRNG_CUDA(oth.alloc(std::max<size_t>(nsurv, 1) * 4));
+    group_pairs(surv, (int64_t)nsurv, 0, n, off.as<int64_t>(), oth.as<int32_t>(), tmp, s);
+  }
+  unsigned long long cap = std::max<unsigned long long>(nsurv, 1024);
+  unsigned long long amb_cap = in.small_buffers ? 8ull : std::max<unsigned long long>(4 * nsurv, 1 << 20);
+  for (int attempt = 0;; ++attempt) {
+    st.c[31] = attempt + 1;  // passes of tiers 2-3 (an ambiguity buffer overflow repeats them)
+    GRNG_CUDA(links.alloc(cap * 8));
+    GRNG_CUDA(unres.alloc(cap * 8));
+    GRNG_CUDA(pend.alloc(cap * 8 * 2));
+    GRNG_CUDA(amb.alloc(amb_cap * 8));
+    GRNG_CUDA(cudaMemsetAsync(dc + 8, 0, 16 * sizeof(unsigned long long), s));
+    Tier2Params t2;
+    t2.X = in.X; t2.n = n; t2.Dp = in.Dp; t2.metric = in.metric; t2.guide = in.grng; t2.K = in.K;
+    t2.rlo = in.rlo; t2.rhi = in.rhi; t2.knn_idx = knn_idx; t2.knn_key = knn_key;
+    t2.knn_rb = knn_rb;
+    t2.off = off.as<int64_t>(); t2.other = oth.as<int32_t>();
+    t2.links = links.as<int2>(); t2.link_cnt = dc + 16; t2.link_cap = cap;
+    t2.unres = unres.as<int2>(); t2.unres_cnt = dc + 18; t2.unres_cap = cap;
+    t2.pend = pend.as<int2>(); t2.pend_cnt = dc + 17; t2.pend_cap = 2 * cap;
+    t2.amb = amb.as<int2>(); t2.amb_cnt = dc + 19; t2.amb_cap = amb_cap;
+    t2.stats = dc + 8;
+    size_t smem2 = (size_t)(in.Dp * 32 + in.Dp + 4 * in.Dp) * 4;
+    int grid2 = (int)std::min<int64_t>(n, 32 * num_sms());
+    unsigned long long nun = nsurv;
+    if (knn_idx) {
+      if (nsurv) {
+        tier2_kernel<<<grid2, 128, smem2, s>>>(t2); note_launch();
+        GRNG_CUDA(cudaGetLastError());
+      }
+      nun = read_u64(dc + 18, s);
+    } else if (nsurv) {  // no neighbour lists: every pair goes on
+      GRNG_CUDA(cudaMemcpyAsync(unres.p, surv, (size_t)nsurv * sizeof(int2), cudaMemcpyDeviceToDevice, s));
+    }
+    tick(2);
+    // tier 2b: the other endpoint's neighbours
+    GRNG_CUDA(unres2.alloc(std::max<unsigned long long>(nun, 1) * 8));
+    unsigned long long nun2 = nun;
+    if (knn_idx && tier2b) {
+      GRNG_CUDA(off2.alloc((size_t)(n + 1) * 8));
+      GRNG_CUDA(oth2.alloc(std::max<unsigned long long>(nun, 1) * 4));
+      group_pairs(unres.as<int2>(), (int64_t)std::min(nun, cap), 1, n, off2.as<int64_t>(),
+                  oth2.as<int32_t>(), tmp, s);
+      t2.off = off2.as<int64_t>(); t2.other = oth2.as<int32_t>();
+      t2.unres = unres2.as<int2>(); t2.unres_cnt = dc + 20; t2.unres_cap = std::max<unsigned long long>(nun, 1);
+      t2.stats = dc + 12;
+      if (nun) {
+        tier2_kernel<<<grid2, 128, smem2, s>>>(t2); note_launch();
+        GRNG_CUDA(cudaGetLastError());
+      }
+      nun2 = read_u64(dc + 20, s);
+    } else if (nun) {
+      GRNG_CUDA(cudaMemcpyAsync(unres2.p, unres.p, (size_t)nun * sizeof(int2), cudaMemcpyDeviceToDevice, s));
+    }
+    tick(3);
+    const int2* t3pairs = unres2.as<int2>();
+    GRNG_CUDA(cudaMemsetAsync(dc + 26, 0, 8 * sizeof(unsigned long long), s));
+    GRNG_CUDA(cudaMemsetAsync(dc + 50, 0, 8 * sizeof(unsigned long long), s));
+    if (in.grng && in.anc.n > 0 && nun2 && !atab.p) {
+      // pivot layers: node x ancestor keys once (the list tier's bounds and tier 3)
+      tabw = 0;  // each level's columns start on a 16-byte boundary
+      for (int a = 0; a < in.anc.n; ++a) { toff[a] = tabw; tabw += (in.anc.m[a] + 3) & ~(int64_t)3; }
+      GRNG_CUDA(atab.alloc((size_t)n * tabw * 4));
+      for (int a = 0; a < in.anc.n; ++a)
+        launch_cross(in.X, n, in.anc.X[a], in.anc.m[a], in.Dp, in.metric, atab.as<float>() + toff[a], tabw, s);
+    }
+    if (in.grng && in.lists && nun2) {
+      // range lists for the pairs no neighbour list covers
+      GRNG_CUDA(side.alloc(nun2));
+      GRNG_CUDA(tkey.alloc((size_t)n * 4));
+      GRNG_CUDA(tcut.alloc((size_t)n * 4));
+      GRNG_CUDA(hist.alloc((size_t)n * GRNG_HBINS * 4));
+      GRNG_CUDA(lcnt.alloc((size_t)n * 4));
+      GRNG_CUDA(lastb.alloc((size_t)n * 4));
+      GRNG_CUDA(boff.alloc((size_t)n * (GRNG_HBINS + 1) * 4));
+      GRNG_CUDA(cudaMemsetAsync(tkey.p, 0, (size_t)n * 4, s));
+      SideParams sp;
+      sp.X = in.X; sp.Dp = in.Dp; sp.metric = in.metric; sp.guide = in.grng; sp.K = in.K;
+      sp.rlo = in.rlo; sp.rhi = in.rhi; sp.pairs = unres2.as<int2>(); sp.m = (int64_t)nun2;
+      sp.side = side.as<int8_t>(); sp.tkey = tkey.as<unsigned int>(); sp.tcut = tcut.as<unsigned int>();
+      sp.lcnt = lcnt.as<int>();
+      cudaEvent_t l0, l1;
+      GRNG_CUDA(cudaEventCreate(&l0));
+      GRNG_CUDA(cudaEventCreate(&l1));
+      GRNG_CUDA(cudaEventRecord(l0, s));
+      range_thresholds_kernel<<<(unsigned)((nun2 + 255) / 256), 256, 0, s>>>(sp); note_launch();
+      GRNG_CUDA(cudaGetLastError());
+      launch_range(in, tkey.as<unsigned int>(), hist.as<int>(), nullptr, nullptr, nullptr, nullptr, 0, s);
+      const int lmax = in.lmax > 0 ? (int)std::min<int64_t>(in.lmax, GRNG_LCAP) : GRNG_LMAX;
+      range_cut_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(tkey.as<unsigned int>(), hist.as<int>(), n,
+                                                                  tcut.as<unsigned int>(), lastb.as<int>(),
+                                                                  boff.as<int>(), lcnt.as<int>(), lmax); note_launch();
+      GRNG_CUDA(cudaGetLastError());
+      GRNG_CUDA(lidx.alloc((size_t)n * GRNG_LCAP * 4));
+      GRNG_CUDA(lkey.alloc((size_t)n * GRNG_LCAP * 4));
+      launch_range(in, tkey.as<unsigned int>(), nullptr, lastb.as<int>(), boff.as<int>(), lidx.as<int32_t>(),
+                   lkey.as<float>(), 1, s);
+      pick_side_kernel<<<(unsigned)((nun2 + 255) / 256), 256, 0, s>>>(sp); note_launch();
+      GRNG_CUDA(cudaGetLastError());
+      GRNG_CUDA(unres3.alloc(nun2 * 8));
+      ListParams lp;
+      lp.X = in.X; lp.Dp = in.Dp; lp.metric = in.metric; lp.guide = in.grng; lp.rlo = in.rlo; lp.rhi = in.rhi;
+      lp.pairs = unres2.as<int2>(); lp.m = (int64_t)nun2; lp.side = side.as<int8_t>();
+      lp.tkey = tkey.as<unsigned int>(); lp.lastb = lastb.as<int>(); lp.boff = boff.as<int>();
+      lp.lidx = lidx.as<int32_t>(); lp.lkey = lkey.as<float>();
+      lp.atab = atab.p ? atab.as<float>() : nullptr;
+      lp.tabw = tabw;
+      lp.toff = in.anc.n > 0 ? toff[in.anc.n - 1] : 0;
+      lp.parent = in.parent;
+      lp.pdh = in.pdist_hi;
+      if (!in.parent || !in.pdist_hi) lp.atab = nullptr;
+      lp.links = links.as<int2>(); lp.link_cnt = dc + 16; lp.link_cap = cap;
+      lp.unres = unres3.as<int2>(); lp.unres_cnt = dc + 27; lp.unres_cap = nun2;
+      lp.pend = pend.as<int2>(); lp.pend_cnt = dc + 17; lp.pend_cap = 2 * cap;
+      lp.amb = amb.as<int2>(); lp.amb_cnt = dc + 19; lp.amb_cap = amb_cap;
+      lp.stats = dc + 50;
+      cudaEvent_t k0;
+      GRNG_CUDA(cudaEventCreate(&k0));
+      GRNG_CUDA(cudaEventRecord(k0, s));
+      launch_list(lp, (unsigned)std::min<unsigned long long>((nun2 + LT_WARPS - 1) / LT_WARPS,
+                                                             (unsigned long long)3 * num_sms()), s);
+      GRNG_CUDA(cudaEventRecord(l1, s));
+      GRNG_CUDA(cudaEventSynchronize(l1));
+      float lms = 0.0f, kms = 0.0f;
+      GRNG_CUDA(cudaEventElapsedTime(&lms, l0, l1));
+      GRNG_CUDA(cudaEventElapsedTime(&kms, k0, l1));
+      cudaEventDestroy(l0);
+      cudaEventDestroy(l1);
+      cudaEventDestroy(k0);
+      st.kms[2] += kms;   // the list tier kernel
+      st.kms[3] += lms;   // thresholds, both sweeps, cut, sides and the list tier
+      unsigned long long h8[8];  // links, pending, to tier 3, blocked, tested by distance, intersections, probes
+      GRNG_CUDA(cudaMemcpyAsync(h8, dc + 50, sizeof(h8), cudaMemcpyDeviceToHost, s));
+      unsigned long long n3 = 0;
+      GRNG_CUDA(cudaMemcpyAsync(&n3, dc + 27, sizeof(n3), cudaMemcpyDeviceToHost, s));
+      std::vector<int> hl((size_t)n), hlb((size_t)n);
+      std::vector<unsigned int> htk((size_t)n);
+      GRNG_CUDA(cudaMemcpyAsync(hl.data(), lcnt.p, (size_t)n * 4, cudaMemcpyDeviceToHost, s));
+      GRNG_CUDA(cudaMemcpyAsync(hlb.data(), lastb.p, (size_t)n * 4, cudaMemcpyDeviceToHost, s));
+      GRNG_CUDA(cudaMemcpyAsync(htk.data(), tkey.p, (size_t)n * 4, cudaMemcpyDeviceToHost, s));
+      GRNG_CUDA(cudaStreamSynchronize(s));
+      unsigned long long ltot = 0, lcut = 0;
+      for (size_t i = 0; i < hl.size(); ++i) {
+        ltot += (unsigned long long)hl[i];
+        lcut += htk[i] != 0 && hlb[i] < GRNG_HBINS - 1;
+      }
+      st.c[18] = nun2;    // pairs given range lists
+      st.c[19] = lcut;    // lists cut below their T_s
+      st.c[20] = ltot;    // listed nodes
+      st.c[21] = h8[0];   // links from the lists
+      st.c[22] = h8[4];   // listed nodes tested by distance
+      st.c[32] = h8[5];   // pairs decided by intersecting both lists
+      st.c[33] = h8[6];   // intersection probes
+      st.c[34] = h8[7];   // list entries read
+      nun2 = n3;          // left for tier 3
+      t3pairs = unres3.as<int2>();
+    }
+    tick(4);
+    unsigned long long npend = read_u64(dc + 17, s);
+    unsigned long long nlink = read_u64(dc + 16, s);
+    if (npend + nun2 > 2 * cap || nlink > cap || nun > cap) fail(6, "tier-2 buffer overflow");
+    // tier 3 appends its pairs after the tier-2 pendings
+    GRNG_CUDA(pflag.alloc((size_t)std::max<unsigned long long>(npend + nun2, 1) * 4));
+    GRNG_CUDA(cudaMemsetAsync(pflag.p, 0, (size_t)std::max<unsigned long long>(npend + nun2, 1) * 4, s));
+    if (nun2) {
+      Tier3Params t3;
+      t3.X = in.X; t3.n = n; t3.Dp = in.Dp; t3.metric = in.metric; t3.guide = in.grng;
+      t3.rlo = in.rlo; t3.rhi = in.rhi; t3.pairs = t3pairs; t3.m = (int64_t)nun2;
+      t3.pend = pend.as<int2>(); t3.pflag = pflag.as<int>(); t3.slot0 = (int64_t)npend;
+      t3.amb = amb.as<int2>(); t3.amb_cnt = dc + 19; t3.amb_cap = amb_cap;
+      t3.anc = in.anc;
+      int grid3 = (int)std::min<unsigned long long>(nun2, (unsigned long long)T3_MINB * num_sms());
+      t3.fcap = in.small_buffers ? 4 : 1 << 15;
+      GRNG_CUDA(fbuf.alloc((size_t)grid3 * 2 * t3.fcap * sizeof(Front)));
+      t3.fbuf = fbuf.as<Front>();
+      t3.pdist_hi = in.pdist_hi;
+      t3.atab = nullptr;
+      t3.tabw = 0;
+      t3.dense = 0;
+      t3.mkw = 0;
+      if (in.grng && in.anc.n > 0 && atab.p) {
+        // pivot layers: the node x ancestor keys computed before the list tier
+        for (int a = 0; a < in.anc.n; ++a) t3.anc.toff[a] = toff[a];
+        t3.atab = atab.as<float>();
+        t3.tabw = tabw;
+        t3.dense = 1;
+        for (int a = 1; a < in.anc.n; ++a) {
+          t3.dense &= in.anc.m[a] <= 32 * T3_MKW;
+          t3.mkw = std::max<int>(t3.mkw, (int)((in.anc.m[a] + 31) / 32));
+        }
+        if (!t3.dense) t3.mkw = 0;
+      }
+      t3.stats = dc + 34;
+      GRNG_CUDA(cudaMemsetAsync(dc + 34, 0, 4 * sizeof(unsigned long long), s));
+      if (!in.grng && knn_idx && tier2b && ((in.mlp_params && in.kshort > 0) || (in.mlp_record && out.rec_f))) {
+        // learned shortlist (extension of Stage V): k scored candidates per pair first
+        MlpStage ms;
+        ms.X = in.X; ms.n = n; ms.Dp = in.Dp; ms.metric = in.metric; ms.K = in.K;
+        ms.knn_idx = knn_idx; ms.knn_key = knn_key;
+        ms.parent = in.parent; ms.pdist_hi = in.pdist_hi;
+        ms.prad = in.anc.n ? in.anc.Rhi[in.anc.n - 1] : nullptr;
+        ms.pairs = t3pairs; ms.m = (int64_t)nun2; ms.slot0 = (int64_t)npend; ms.pflag = pflag.as<int>();
+        ms.amb = amb.as<int2>(); ms.amb_cnt = dc + 19; ms.amb_cap = amb_cap;
+        ms.params = in.kshort > 0 ? in.mlp_params : nullptr;
+        ms.kshort = in.kshort;
+        ms.rec_f = nullptr; ms.rec_y = nullptr; ms.rec_cnt = dc + 47; ms.rec_cap = 0;
+        if (in.mlp_record && out.rec_f) {
+          const unsigned long long rc = std::min<unsigned long long>(
+              nun2 * 2ull * GRNG_MLP_PW * in.K, 4ull << 20);
+          GRNG_CUDA(out.rec_f->alloc((size_t)rc * GRNG_MLP_IN * 4));
+          GRNG_CUDA(out.rec_y->alloc((size_t)rc * 4));
+          ms.rec_f = out.rec_f->as<float>(); ms.rec_y = out.rec_y->as<float>(); ms.rec_cap = rc;
+        }
+        ms.stats = dc + 44;
+        GRNG_CUDA(cudaMemsetAsync(dc + 44, 0, 5 * sizeof(unsigned long long), s));
+        mlp_stage(ms, s);
+        unsigned long long hm[5];
+        GRNG_CUDA(cudaMemcpyAsync(hm, dc + 44, sizeof(hm), cudaMemcpyDeviceToHost, s));
+        GRNG_CUDA(cudaStreamSynchronize(s));
+        st.c[25] = ms.params ? nun2 : 0;  // pairs given a shortlist
+        st.c[26] = hm[0];                 // candidates scored
+        st.c[27] = hm[1];                 // shortlist tests
+        st.c[28] = hm[2];                 // pairs blocked by the shortlist
+        st.c[29] = hm[4];                 // recording: pairs with a blocker among the candidates
+        if (ms.rec_f) out.rec_n = (int64_t)std::min<unsigned long long>(hm[3], ms.rec_cap);
+      }
+      cudaEvent_t f0, f1;
+      GRNG_CUDA(cudaEventCreate(&f0));
+      GRNG_CUDA(cudaEventCreate(&f1));
+      GRNG_CUDA(cudaEventRecord(f0, s));
+      tier3_kernel<<<grid3, T3_T, 2 * in.Dp * 4 + 2 * (size_t)t3.mkw * 4, s>>>(t3); note_launch();
+      GRNG_CUDA(cudaGetLastError());
+      GRNG_CUDA(cudaEventRecord(f1, s));
+      GRNG_CUDA(cudaEventSynchronize(f1));
+      float fms = 0.0f;
+      GRNG_CUDA(cudaEventElapsedTime(&fms, f0, f1));
+      cudaEventDestroy(f0);
+      cudaEventDestroy(f1);
+      st.kms[1] += fms;
+    }
+    unsigned long long namb = read_u64(dc + 19, s);
+    tick(5);
+    if (namb > amb_cap) {
+      if (attempt >= 3) fail(2, "ambiguity buffer overflow");
+      amb_cap = namb + namb / 4;
+      continue;
+    }
+    if (namb) {
+      recheck_kernel<<<(unsigned)((namb + 255) / 256), 256, 0, s>>>(
+          in.X, in.D, in.Dp, in.metric, in.r64, amb.as<int2>(), (int64_t)namb, pend.as<int2>(),
+          pflag.as<int>(), dc + 22); note_launch();
+      GRNG_CUDA(cudaGetLastError());
+    }
+    // ---- emission ----------------------------------------------------------------------
+    const unsigned long long npp = npend + nun2;
+    unsigned long long ecap = nlink + npp + 1;
+    if (!in.grng) {
+      GRNG_CUDA(out.edges->alloc(ecap * 8));
+    }
+    int2* newg = nullptr;
+    unsigned long long newg_cap = 0;
+    if (in.grng && out.new_gg) {  // pairs whose guidance bit this pass sets (incremental updates)
+      newg_cap = nlink + npp + 1;
+      GRNG_CUDA(out.new_gg->alloc(newg_cap * sizeof(int2)));
+      newg = out.new_gg->as<int2>();
+    }
+    if (nlink)
+      resolve_emit_kernel<<<(unsigned)((nlink + 255) / 256), 256, 0, s>>>(
+          links.as<int2>(), nullptr, (int64_t)nlink, in.grng, out.gx, out.gg, out.words, in.orig,
+          dc + 21, ecap, in.grng ? nullptr : out.edges->as<uint64_t>(), newg, dc + 23, newg_cap); note_launch();
+    if (npp)
+      resolve_emit_kernel<<<(unsigned)((npp + 255) / 256), 256, 0, s>>>(
+          pend.as<int2>(), pflag.as<int>(), (int64_t)npp, in.grng, out.gx, out.gg, out.words,
+          in.orig, dc + 21, ecap, in.grng ? nullptr : out.edges->as<uint64_t>(), newg, dc + 23, newg_cap); note_launch();
+    GRNG_CUDA(cudaGetLastError());
+    unsigned long long h[40];
+    GRNG_CUDA(cudaMemcpyAsync(h, dc, sizeof(h), cudaMemcpyDeviceToHost, s));
+    GRNG_CUDA(cudaStreamSynchronize(s));
+    st.c[15] = nun2 ? h[34] : 0;  // tier-3 frontier overflows
+    st.c[16] = nun2 ? h[35] : 0;  // tier-3 nodes tested
+    st.c[23] = nun2 ? h[36] : 0;  // tier-3 pairs blocked
+    st.c[24] = nun2 ? h[37] : 0;  // of which by the greedy descent
+    out.n_edges = (int64_t)h[21];
+    out.n_new_gg = newg ? (int64_t)std::min<unsigned long long>(h[23], newg_cap) : 0;
+    st.c[3] = h[8];  st.c[4] = h[9];  st.c[5] = h[10]; st.c[6] = h[11];   // tier 2a
+    st.c[7] = h[12]; st.c[8] = h[13]; st.c[9] = h[14]; st.c[10] = h[15];  // tier 2b
+    st.c[11] = nun2;   // tier-3 pairs
+    st.c[12] = namb;   // ambiguous triples rechecked in FP64
+    st.c[13] = h[22];  // of which blocking
+    st.c[14] = h[21];  // edges emitted (RNG level)
+    tick(6);
+    break;
+  }
+}
+
 void run_level(const LevelIn& in, LevelOut& out, LevelStats& st, cudaStream_t s, float* tile_ms) {
   memset(&st, 0, sizeof(st));
   auto t_last = std::chrono::steady_clock::now();
-  auto tick = [&](int slot) {  // host time of one phase (the phases end in a synchronisation)
+  std::function<void(int)> tick = [&](int slot) {  // host time of one phase (each ends in a synchronisation)
     GRNG_CUDA(cudaStreamSynchronize(s));
     auto now = std::chrono::steady_clock::now();
     st.ms[slot] += std::chrono::duration<double, std::milli>(now - t_last).count();
@@ -1846,285 +2258,31 @@ void run_level(const LevelIn& in, LevelOut& out, LevelStats& st, cudaStream_t s,
   st.c[17] = hst[2];  // links certified from the neighbour lists in the tile
 
   tick(1);
-  // ---- tiers 2 and 3 ---------------------------------------------------------------------
-  DevBuf off, oth, tmp, links, unres, pend, amb, pflag, unres2, off2, oth2, fbuf;
-  DevBuf side, tkey, tcut, hist, lcnt, lastb, boff, lidx, lkey, unres3, atab;
-  int64_t toff[GRNG_MAXL] = {0}, tabw = 0;  // columns of the node x ancestor key table
-  GRNG_CUDA(off.alloc((size_t)(n + 1) * 8));
-  GRNG_CUDA(oth.alloc(std::max<size_t>(nsurv, 1) * 4));
-  group_pairs(surv.as<int2>(), (int64_t)nsurv, 0, n, off.as<int64_t>(), oth.as<int32_t>(), tmp, s);
-  unsigned long long cap = std::max<unsigned long long>(nsurv, 1024);
-  unsigned long long amb_cap = in.small_buffers ? 8ull : std::max<unsigned long long>(4 * nsurv, 1 << 20);
-  for (int attempt = 0;; ++attempt) {
-    st.c[31] = attempt + 1;  // passes of tiers 2-3 (an ambiguity buffer overflow repeats them)
-    GRNG_CUDA(links.alloc(cap * 8));
-    GRNG_CUDA(unres.alloc(cap * 8));
-    GRNG_CUDA(pend.alloc(cap * 8 * 2));
-    GRNG_CUDA(amb.alloc(amb_cap * 8));
-    GRNG_CUDA(cudaMemsetAsync(dc + 8, 0, 16 * sizeof(unsigned long long), s));
-    Tier2Params t2;
-    t2.X = in.X; t2.n = n; t2.Dp = in.Dp; t2.metric = in.metric; t2.guide = in.grng; t2.K = in.K;
-    t2.rlo = in.rlo; t2.rhi = in.rhi; t2.knn_idx = knni.as<int32_t>(); t2.knn_key = knnk.as<float>();
-    t2.knn_rb = use_tc ? knnrb.as<float>() : nullptr;
-    t2.off = off.as<int64_t>(); t2.other = oth.as<int32_t>();
-    t2.links = links.as<int2>(); t2.link_cnt = dc + 16; t2.link_cap = cap;
-    t2.unres = unres.as<int2>(); t2.unres_cnt = dc + 18; t2.unres_cap = cap;
-    t2.pend = pend.as<int2>(); t2.pend_cnt = dc + 17; t2.pend_cap = 2 * cap;
-    t2.amb = amb.as<int2>(); t2.amb_cnt = dc + 19; t2.amb_cap = amb_cap;
-    t2.stats = dc + 8;
-    size_t smem2 = (size_t)(in.Dp * 32 + in.Dp + 4 * in.Dp) * 4;
-    int grid2 = (int)std::min<int64_t>(n, 32 * num_sms());
-    if (nsurv) {
-      tier2_kernel<<<grid2, 128, smem2, s>>>(t2); note_launch();
-      GRNG_CUDA(cudaGetLastError());
-    }
-    unsigned long long nun = read_u64(dc + 18, s);
-    tick(2);
-    // tier 2b: the other endpoint's neighbours
-    GRNG_CUDA(off2.alloc((size_t)(n + 1) * 8));
-    GRNG_CUDA(oth2.alloc(std::max<unsigned long long>(nun, 1) * 4));
-    group_pairs(unres.as<int2>(), (int64_t)std::min(nun, cap), 1, n, off2.as<int64_t>(),
-                oth2.as<int32_t>(), tmp, s);
-    t2.off = off2.as<int64_t>(); t2.other = oth2.as<int32_t>();
-    GRNG_CUDA(unres2.alloc(std::max<unsigned long long>(nun, 1) * 8));
-    t2.unres = unres2.as<int2>(); t2.unres_cnt = dc + 20; t2.unres_cap = std::max<unsigned long long>(nun, 1);
-    t2.stats = dc + 12;
-    if (nun) {
-      tier2_kernel<<<grid2, 128, smem2, s>>>(t2); note_launch();
-      GRNG_CUDA(cudaGetLastError());
-    }
-    unsigned long long nun2 = read_u64(dc + 20, s);
-    tick(3);
-    const int2* t3pairs = unres2.as<int2>();
-    GRNG_CUDA(cudaMemsetAsync(dc + 26, 0, 8 * sizeof(unsigned long long), s));
-    GRNG_CUDA(cudaMemsetAsync(dc + 50, 0, 8 * sizeof(unsigned long long), s));
-    if (in.grng && in.anc.n > 0 && nun2 && !atab.p) {
-      // pivot layers: node x ancestor keys once (the list tier's bounds and tier 3)
-      tabw = 0;  // each level's columns start on a 16-byte boundary
-      for (int a = 0; a < in.anc.n; ++a) { toff[a] = tabw; tabw += (in.anc.m[a] + 3) & ~(int64_t)3; }
-      GRNG_CUDA(atab.alloc((size_t)n * tabw * 4));
-      for (int a = 0; a < in.anc.n; ++a)
-        launch_cross(in.X, n, in.anc.X[a], in.anc.m[a], in.Dp, in.metric, atab.as<float>() + toff[a], tabw, s);
-    }
-    if (in.grng && nun2) {
-      // range lists for the pairs no neighbour list covers
-      GRNG_CUDA(side.alloc(nun2));
-      GRNG_CUDA(tkey.alloc((size_t)n * 4));
-      GRNG_CUDA(tcut.alloc((size_t)n * 4));
-      GRNG_CUDA(hist.alloc((size_t)n * GRNG_HBINS * 4));
-      GRNG_CUDA(lcnt.alloc((size_t)n * 4));
-      GRNG_CUDA(lastb.alloc((size_t)n * 4));
-      GRNG_CUDA(boff.alloc((size_t)n * (GRNG_HBINS + 1) * 4));
-      GRNG_CUDA(cudaMemsetAsync(tkey.p, 0, (size_t)n * 4, s));
-      SideParams sp;
-      sp.X = in.X; sp.Dp = in.Dp; sp.metric = in.metric; sp.guide = in.grng; sp.K = in.K;
-      sp.rlo = in.rlo; sp.rhi = in.rhi; sp.pairs = unres2.as<int2>(); sp.m = (int64_t)nun2;
-      sp.side = side.as<int8_t>(); sp.tkey = tkey.as<unsigned int>(); sp.tcut = tcut.as<unsigned int>();
-      sp.lcnt = lcnt.as<int>();
-      cudaEvent_t l0, l1;
-      GRNG_CUDA(cudaEventCreate(&l0));
-      GRNG_CUDA(cudaEventCreate(&l1));
-      GRNG_CUDA(cudaEventRecord(l0, s));
-      range_thresholds_kernel<<<(unsigned)((nun2 + 255) / 256), 256, 0, s>>>(sp); note_launch();
-      GRNG_CUDA(cudaGetLastError());
-      launch_range(in, tkey.as<unsigned int>(), hist.as<int>(), nullptr, nullptr, nullptr, nullptr, 0, s);
-      const int lmax = in.lmax > 0 ? (int)std::min<int64_t>(in.lmax, GRNG_LCAP) : GRNG_LMAX;
-      range_cut_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(tkey.as<unsigned int>(), hist.as<int>(), n,
-                                                                  tcut.as<unsigned int>(), lastb.as<int>(),
-                                                                  boff.as<int>(), lcnt.as<int>(), lmax); note_launch();
-      GRNG_CUDA(cudaGetLastError());
-      GRNG_CUDA(lidx.alloc((size_t)n * GRNG_LCAP * 4));
-      GRNG_CUDA(lkey.alloc((size_t)n * GRNG_LCAP * 4));
-      launch_range(in, tkey.as<unsigned int>(), nullptr, lastb.as<int>(), boff.as<int>(), lidx.as<int32_t>(),
-                   lkey.as<float>(), 1, s);
-      pick_side_kernel<<<(unsigned)((nun2 + 255) / 256), 256, 0, s>>>(sp); note_launch();
-      GRNG_CUDA(cudaGetLastError());
-      GRNG_CUDA(unres3.alloc(nun2 * 8));
-      ListParams lp;
-      lp.X = in.X; lp.Dp = in.Dp; lp.metric = in.metric; lp.guide = in.grng; lp.rlo = in.rlo; lp.rhi = in.rhi;
-      lp.pairs = unres2.as<int2>(); lp.m = (int64_t)nun2; lp.side = side.as<int8_t>();
-      lp.tkey = tkey.as<unsigned int>(); lp.lastb = lastb.as<int>(); lp.boff = boff.as<int>();
-      lp.lidx = lidx.as<int32_t>(); lp.lkey = lkey.as<float>();
-      lp.atab = atab.p ? atab.as<float>() : nullptr;
-      lp.tabw = tabw;
-      lp.toff = in.anc.n > 0 ? toff[in.anc.n - 1] : 0;
-      lp.parent = in.parent;
-      lp.pdh = in.pdist_hi;
-      if (!in.parent || !in.pdist_hi) lp.atab = nullptr;
-      lp.links = links.as<int2>(); lp.link_cnt = dc + 16; lp.link_cap = cap;
-      lp.unres = unres3.as<int2>(); lp.unres_cnt = dc + 27; lp.unres_cap = nun2;
-      lp.pend = pend.as<int2>(); lp.pend_cnt = dc + 17; lp.pend_cap = 2 * cap;
-      lp.amb = amb.as<int2>(); lp.amb_cnt = dc + 19; lp.amb_cap = amb_cap;
-      lp.stats = dc + 50;
-      cudaEvent_t k0;
-      GRNG_CUDA(cudaEventCreate(&k0));
-      GRNG_CUDA(cudaEventRecord(k0, s));
-      launch_list(lp, (unsigned)std::min<unsigned long long>((nun2 + LT_WARPS - 1) / LT_WARPS,
-                                                             (unsigned long long)2 * num_sms()), s);
-      GRNG_CUDA(cudaEventRecord(l1, s));
-      GRNG_CUDA(cudaEventSynchronize(l1));
-      float lms = 0.0f, kms = 0.0f;
-      GRNG_CUDA(cudaEventElapsedTime(&lms, l0, l1));
-      GRNG_CUDA(cudaEventElapsedTime(&kms, k0, l1));
-      cudaEventDestroy(l0);
-      cudaEventDestroy(l1);
-      cudaEventDestroy(k0);
-      st.kms[2] += kms;   // the list tier kernel
-      st.kms[3] += lms;   // thresholds, both sweeps, cut, sides and the list tier
-      unsigned long long h8[8];  // links, pending, to tier 3, blocked, tested by distance, intersections, probes
-      GRNG_CUDA(cudaMemcpyAsync(h8, dc + 50, sizeof(h8), cudaMemcpyDeviceToHost, s));
-      unsigned long long n3 = 0;
-      GRNG_CUDA(cudaMemcpyAsync(&n3, dc + 27, sizeof(n3), cudaMemcpyDeviceToHost, s));
-      std::vector<int> hl((size_t)n), hlb((size_t)n);
-      std::vector<unsigned int> htk((size_t)n);
-      GRNG_CUDA(cudaMemcpyAsync(hl.data(), lcnt.p, (size_t)n * 4, cudaMemcpyDeviceToHost, s));
-      GRNG_CUDA(cudaMemcpyAsync(hlb.data(), lastb.p, (size_t)n * 4, cudaMemcpyDeviceToHost, s));
-      GRNG_CUDA(cudaMemcpyAsync(htk.data(), tkey.p, (size_t)n * 4, cudaMemcpyDeviceToHost, s));
-      GRNG_CUDA(cudaStreamSynchronize(s));
-      unsigned long long ltot = 0, lcut = 0;
-      for (size_t i = 0; i < hl.size(); ++i) {
-        ltot += (unsigned long long)hl[i];
-        lcut += htk[i] != 0 && hlb[i] < GRNG_HBINS - 1;
-      }
-      st.c[18] = nun2;    // pairs given range lists
-      st.c[19] = lcut;    // lists cut below their T_s
-      st.c[20] = ltot;    // listed nodes
-      st.c[21] = h8[0];   // links from the lists
-      st.c[22] = h8[4];   // listed nodes tested by distance
-      st.c[32] = h8[5];   // pairs decided by intersecting both lists
-      st.c[33] = h8[6];   // intersection probes
-      st.c[34] = h8[7];   // list entries read
-      nun2 = n3;          // left for tier 3
-      t3pairs = unres3.as<int2>();
-    }
-    tick(4);
-    unsigned long long npend = read_u64(dc + 17, s);
-    unsigned long long nlink = read_u64(dc + 16, s);
-    if (npend + nun2 > 2 * cap || nlink > cap || nun > cap) fail(6, "tier-2 buffer overflow");
-    // tier 3 appends its pairs after the tier-2 pendings
-    GRNG_CUDA(pflag.alloc((size_t)std::max<unsigned long long>(npend + nun2, 1) * 4));
-    GRNG_CUDA(cudaMemsetAsync(pflag.p, 0, (size_t)std::max<unsigned long long>(npend + nun2, 1) * 4, s));
-    if (nun2) {
-      Tier3Params t3;
-      t3.X = in.X; t3.n = n; t3.Dp = in.Dp; t3.metric = in.metric; t3.guide = in.grng;
-      t3.rlo = in.rlo; t3.rhi = in.rhi; t3.pairs = t3pairs; t3.m = (int64_t)nun2;
-      t3.pend = pend.as<int2>(); t3.pflag = pflag.as<int>(); t3.slot0 = (int64_t)npend;
-      t3.amb = amb.as<int2>(); t3.amb_cnt = dc + 19; t3.amb_cap = amb_cap;
-      t3.anc = in.anc;
-      int grid3 = (int)std::min<unsigned long long>(nun2, (unsigned long long)T3_MINB * num_sms());
-      t3.fcap = in.small_buffers ? 4 : 1 << 15;
-      GRNG_CUDA(fbuf.alloc((size_t)grid3 * 2 * t3.fcap * sizeof(Front)));
-      t3.fbuf = fbuf.as<Front>();
-      t3.pdist_hi = in.pdist_hi;
-      t3.atab = nullptr;
-      t3.tabw = 0;
-      t3.dense = 0;
-      t3.mkw = 0;
-      if (in.grng && in.anc.n > 0 && atab.p) {
-        // pivot layers: the node x ancestor keys computed before the list tier
-        for (int a = 0; a < in.anc.n; ++a) t3.anc.toff[a] = toff[a];
-        t3.atab = atab.as<float>();
-        t3.tabw = tabw;
-        t3.dense = 1;
-        for (int a = 1; a < in.anc.n; ++a) {
-          t3.dense &= in.anc.m[a] <= 32 * T3_MKW;
-          t3.mkw = std::max<int>(t3.mkw, (int)((in.anc.m[a] + 31) / 32));
-        }
-        if (!t3.dense) t3.mkw = 0;
-      }
-      t3.stats = dc + 34;
-      GRNG_CUDA(cudaMemsetAsync(dc + 34, 0, 4 * sizeof(unsigned long long), s));
-      if (!in.grng && ((in.mlp_params && in.kshort > 0) || (in.mlp_record && out.rec_f))) {
-        // learned shortlist (extension of Stage V): k scored candidates per pair first
-        MlpStage ms;
-        ms.X = in.X; ms.n = n; ms.Dp = in.Dp; ms.metric = in.metric; ms.K = in.K;
-        ms.knn_idx = knni.as<int32_t>(); ms.knn_key = knnk.as<float>();
-        ms.parent = in.parent; ms.pdist_hi = in.pdist_hi;
-        ms.prad = in.anc.n ? in.anc.Rhi[in.anc.n - 1] : nullptr;
-        ms.pairs = t3pairs; ms.m = (int64_t)nun2; ms.slot0 = (int64_t)npend; ms.pflag = pflag.as<int>();
-        ms.amb = amb.as<int2>(); ms.amb_cnt = dc + 19; ms.amb_cap = amb_cap;
-        ms.params = in.kshort > 0 ? in.mlp_params : nullptr;
-        ms.kshort = in.kshort;
-        ms.rec_f = nullptr; ms.rec_y = nullptr; ms.rec_cnt = dc + 47; ms.rec_cap = 0;
-        if (in.mlp_record && out.rec_f) {
-          const unsigned long long rc = std::min<unsigned long long>(
-              nun2 * 2ull * GRNG_MLP_PW * in.K, 4ull << 20);
-          GRNG_CUDA(out.rec_f->alloc((size_t)rc * GRNG_MLP_IN * 4));
-          GRNG_CUDA(out.rec_y->alloc((size_t)rc * 4));
-          ms.rec_f = out.rec_f->as<float>(); ms.rec_y = out.rec_y->as<float>(); ms.rec_cap = rc;
-        }
-        ms.stats = dc + 44;
-        GRNG_CUDA(cudaMemsetAsync(dc + 44, 0, 5 * sizeof(unsigned long long), s));
-        mlp_stage(ms, s);
-        unsigned long long hm[5];
-        GRNG_CUDA(cudaMemcpyAsync(hm, dc + 44, sizeof(hm), cudaMemcpyDeviceToHost, s));
-        GRNG_CUDA(cudaStreamSynchronize(s));
-        st.c[25] = ms.params ? nun2 : 0;  // pairs given a shortlist
-        st.c[26] = hm[0];                 // candidates scored
-        st.c[27] = hm[1];                 // shortlist tests
-        st.c[28] = hm[2];                 // pairs blocked by the shortlist
-        st.c[29] = hm[4];                 // recording: pairs with a blocker among the candidates
-        if (ms.rec_f) out.rec_n = (int64_t)std::min<unsigned long long>(hm[3], ms.rec_cap);
-      }
-      cudaEvent_t f0, f1;
-      GRNG_CUDA(cudaEventCreate(&f0));
-      GRNG_CUDA(cudaEventCreate(&f1));
-      GRNG_CUDA(cudaEventRecord(f0, s));
-      tier3_kernel<<<grid3, T3_T, 2 * in.Dp * 4 + 2 * (size_t)t3.mkw * 4, s>>>(t3); note_launch();
-      GRNG_CUDA(cudaGetLastError());
-      GRNG_CUDA(cudaEventRecord(f1, s));
-      GRNG_CUDA(cudaEventSynchronize(f1));
-      float fms = 0.0f;
-      GRNG_CUDA(cudaEventElapsedTime(&fms, f0, f1));
-      cudaEventDestroy(f0);
-      cudaEventDestroy(f1);
-      st.kms[1] += fms;
-    }
-    unsigned long long namb = read_u64(dc + 19, s);
-    tick(5);
-    if (namb > amb_cap) {
-      if (attempt >= 3) fail(2, "ambiguity buffer overflow");
-      amb_cap = namb + namb / 4;
-      continue;
-    }
-    if (namb) {
-      recheck_kernel<<<(unsigned)((namb + 255) / 256), 256, 0, s>>>(
-          in.X, in.D, in.Dp, in.metric, in.r64, amb.as<int2>(), (int64_t)namb, pend.as<int2>(),
-          pflag.as<int>(), dc + 22); note_launch();
-      GRNG_CUDA(cudaGetLastError());
-    }
-    // ---- emission ----------------------------------------------------------------------
-    const unsigned long long npp = npend + nun2;
-    unsigned long long ecap = nlink + npp + 1;
-    if (!in.grng) {
-      GRNG_CUDA(out.edges->alloc(ecap * 8));
-    }
-    if (nlink)
-      resolve_emit_kernel<<<(unsigned)((nlink + 255) / 256), 256, 0, s>>>(
-          links.as<int2>(), nullptr, (int64_t)nlink, in.grng, out.gx, out.gg, out.words, in.orig,
-          dc + 21, ecap, in.grng ? nullptr : out.edges->as<uint64_t>()); note_launch();
-    if (npp)
-      resolve_emit_kernel<<<(unsigned)((npp + 255) / 256), 256, 0, s>>>(
-          pend.as<int2>(), pflag.as<int>(), (int64_t)npp, in.grng, out.gx, out.gg, out.words,
-          in.orig, dc + 21, ecap, in.grng ? nullptr : out.edges->as<uint64_t>()); note_launch();
-    GRNG_CUDA(cudaGetLastError());
-    unsigned long long h[40];
-    GRNG_CUDA(cudaMemcpyAsync(h, dc, sizeof(h), cudaMemcpyDeviceToHost, s));
+  finish_level(in, out, st, s, surv.as<int2>(), nsurv, knni.as<int32_t>(), knnk.as<float>(),
+               use_tc ? knnrb.as<float>() : nullptr, true, dc, tick);
+}
+
+// The pair pipeline from tier 2 on, for explicit candidate pairs (sorted positions of the
+// level): an incremental update hands over the pairs whose decision may have changed.
+void run_pairs(const LevelIn& in, LevelOut& out, LevelStats& st, cudaStream_t s, const int2* pairs, int64_t m,
+               const int32_t* knn_idx, const float* knn_key, bool tier2b) {
+  memset(&st, 0, sizeof(st));
+  auto t_last = std::chrono::steady_clock::now();
+  std::function<void(int)> tick = [&](int slot) {
     GRNG_CUDA(cudaStreamSynchronize(s));
-    st.c[15] = nun2 ? h[34] : 0;  // tier-3 frontier overflows
-    st.c[16] = nun2 ? h[35] : 0;  // tier-3 nodes tested
-    st.c[23] = nun2 ? h[36] : 0;  // tier-3 pairs blocked
-    st.c[24] = nun2 ? h[37] : 0;  // of which by the greedy descent
-    out.n_edges = (int64_t)h[21];
-    st.c[3] = h[8];  st.c[4] = h[9];  st.c[5] = h[10]; st.c[6] = h[11];   // tier 2a
-    st.c[7] = h[12]; st.c[8] = h[13]; st.c[9] = h[14]; st.c[10] = h[15];  // tier 2b
-    st.c[11] = nun2;   // tier-3 pairs
-    st.c[12] = namb;   // ambiguous triples rechecked in FP64
-    st.c[13] = h[22];  // of which blocking
-    st.c[14] = h[21];  // edges emitted (RNG level)
-    tick(6);
-    break;
-  }
+    auto now = std::chrono::steady_clock::now();
+    st.ms[slot] += std::chrono::duration<double, std::milli>(now - t_last).count();
+    t_last = now;
+  };
+  out.n_edges = 0;
+  out.n_new_gg = 0;
+  if (in.n < 2 || m == 0) return;
+  DevBuf ctr;
+  GRNG_CUDA(ctr.alloc(64 * sizeof(unsigned long long)));
+  GRNG_CUDA(cudaMemsetAsync(ctr.p, 0, 64 * sizeof(unsigned long long), s));
+  st.c[2] = (unsigned long long)m;
+  finish_level(in, out, st, s, pairs, (unsigned long long)m, knn_idx, knn_key, nullptr, tier2b,
+               ctr.as<unsigned long long>(), tick);
 }
 
 }  // namespace grng
