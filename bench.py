@@ -60,6 +60,8 @@ def parse():
                     help="instead of the build benchmark: insert B batches of uneven size (log-uniform in "
                          "[1,000, 65,536] points, scaled to --n) into an index built on the rest, and print "
                          "points/s and per-batch latency")
+    ap.add_argument("--insert-verify", action="store_true",
+                    help="with --insert: compare the final edges with a build from scratch on all points")
     return ap.parse_args()
 
 
@@ -520,8 +522,11 @@ def run_gpu(a, rank, world, local):
 
 
 def run_insert(a, rank):
-    """Batched insertion (rng_insert_batch): the index is built on the first points of the
-    workload, then the batches arrive in order; every batch is timed with CUDA events."""
+    """Batched insertion (rng_insert_batch): an index is built on n points of the workload,
+    then the batches (sizes drawn log-uniformly in [1,000, 65,536], scaled by n / 2,000,000
+    below 2M points) of further points of the same generator arrive in order; every batch is
+    timed with CUDA events on the index's stream.  With --insert-verify the final edge list
+    is compared element by element with a build from scratch on all points (same pivots)."""
     import numpy as np
     import torch
 
@@ -529,34 +534,60 @@ def run_insert(a, rank):
     from paper_2208_10022_gb300 import build as gb
     from paper_2208_10022_gb300 import workloads as wl
     gb.build()
-    w = wl.make(a.kind, n=a.n)
-    scale = w.n / 2_000_000
+    N0, D, _, ds, ps = wl.SPECS[a.kind]
+    n = a.n or N0
+    scale = min(1.0, n / 2_000_000)
     sizes = [max(1, int(b * scale)) for b in wl.insertion_batches(a.insert)]
-    n0 = w.n - sum(sizes)
-    rng = np.random.default_rng(4001)
-    layers = [np.sort(rng.choice(n0, len(l), replace=False)).astype(np.int32) for l in w.layers[-1:]]
-    sub = []
-    for l in reversed(w.layers[:-1]):  # nested coarser layers drawn from the finer one
-        sub.insert(0, np.sort(rng.choice(layers[0] if not sub else sub[0], len(l), replace=False)).astype(np.int32))
-    layers = sub + layers
+    total = n + sum(sizes)
+    X = wl.gen_points(a.kind, total, ds)
+    layers = wl.nested_pivots(n, wl.scaled_layer_sizes(a.kind, n), ps)
     prec = g.BF16 if a.precision == "bf16" else g.FP32
-    ix, _ = g.build_all(w.X[:n0], layers, precision=prec)
     stream = torch.cuda.current_stream()
-    lat, at = [], n0
+    Xd = torch.from_numpy(X).cuda()
+    t0 = time.perf_counter()
+    ix, _ = g.build_all(Xd[:n], layers, precision=prec, stream=stream)
+    torch.cuda.synchronize()
+    build_s = time.perf_counter() - t0
+    edges0 = ix.n_edges()
+    lat, at = [], n
     for b in sizes:
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        ix.rng_insert_batch(w.X[at:at + b])
+        ix.rng_insert_batch(Xd[at:at + b])
         e1.record(stream)
         torch.cuda.synchronize()
         lat.append(e0.elapsed_time(e1))
         at += b
     tot = sum(lat)
+    ne = ix.n_edges()
+    st = ix.stats()["insert"]
+    verify = None
+    if a.insert_verify:
+        got = torch.empty((max(ne, 1), 2), dtype=torch.int32, device="cuda")
+        ix.rng_edges(out=got)
+        ix.close()
+        ix2, _ = g.build_all(Xd, layers, precision=prec, stream=stream)
+        ne2 = ix2.n_edges()
+        want = torch.empty((max(ne2, 1), 2), dtype=torch.int32, device="cuda")
+        ix2.rng_edges(out=want)
+        verify = bool(ne2 == ne and torch.equal(got[:ne], want[:ne2]))
+        ix2.close()
+    small = [t for t, b in zip(lat, sizes) if b <= np.median(sizes)]
+    large = [t for t, b in zip(lat, sizes) if b > np.median(sizes)]
     line = {"metric": "batched insertion points/s", "value": sum(sizes) / (tot / 1000.0), "unit": "points/s",
             "higher_is_better": True, "n_gpus": 1, "batches": len(sizes), "points": int(sum(sizes)),
-            "base_points": int(n0), "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-            "edges_after": int(ix.n_edges()), "method": "pivots kept; radii, GRNGs and RNG recomputed per batch",
-            "config": {"workload": a.kind, "n": int(w.n), "layers": [len(l) for l in layers],
+            "base_points": int(n), "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "p50_ms_small_half": float(np.percentile(small, 50)) if small else None,
+            "p50_ms_large_half": float(np.percentile(large, 50)) if large else None,
+            "edges_before": int(edges0), "edges_after": int(ne), "edge_set_equal_rebuild": verify,
+            "base_build_s": build_s,
+            "method": "incremental: batch points join their finest domains; pivot pairs whose radii grew are "
+                      "re-tested; batch rows swept against all points for new edges; Stage VII removes old edges "
+                      "a batch point enters",
+            "work": st,
+            "config": {"workload": f"{a.kind}: index of {n:,} x {D} FP32 + {len(sizes)} batches of the same "
+                                   f"generator, L2, nested random pivot layers "
+                                   f"{'/'.join(str(len(l)) for l in layers)}",
                        "batch_sizes": sizes, "precision": a.precision}}
     if rank == 0:
         print(json.dumps(line), flush=True)

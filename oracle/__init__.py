@@ -46,6 +46,8 @@ def lib():
         _lib.orc_set_threads.argtypes = [i32]
         _lib.orc_max_threads.restype = i32
         _lib.orc_max_threads.argtypes = []
+        _lib.orc_rng_guided.restype = i64
+        _lib.orc_rng_guided.argtypes = [P, i64, i32, i32, P, P, i32, P, i64, P]
         _lib.orc_emst.restype = i64
         _lib.orc_emst.argtypes = [P, i64, i32, i32, P]
         _lib.orc_grng_brute.restype = i64
@@ -135,6 +137,24 @@ def rng_rows(X, xs, metric=L2, row_cap=4096):
     if len(xs) and cnt.max() > row_cap:
         raise ValueError("a neighbourhood exceeds row_cap")
     return [nb[t, :cnt[t]].copy() for t in range(len(xs))]
+
+
+def rng_guided(X, layers, metric=L2, with_stats=False):
+    """RNG of X by the paper's pivot-guided method (Secs. 2-3: layers, GRNGs under Theorem 2,
+    exemplar pairs under Theorem 1, Stages IV and VI), FP64 on the host: sorted edges [E, 2]
+    and, with with_stats, (distance computations, candidate pairs, Stage VI member tests)."""
+    X = _f32(X)
+    piv = np.ascontiguousarray(np.concatenate([np.asarray(l, np.int32) for l in layers]), dtype=np.int32)
+    ms = np.ascontiguousarray([len(l) for l in layers], dtype=np.int32)
+    st = np.zeros(3, np.int64)
+    args = (_p(X), X.shape[0], X.shape[1], metric, _p(piv), _p(ms), len(layers))
+    cnt = lib().orc_rng_guided(*args, None, 0, _p(st))
+    if cnt < 0:
+        raise MemoryError("oracle allocation failed")
+    out = np.zeros((max(cnt, 1), 2), dtype=np.int32)
+    cnt2 = lib().orc_rng_guided(*args, _p(out), cnt, _p(st))
+    assert cnt2 == cnt
+    return (out[:cnt], tuple(int(v) for v in st)) if with_stats else out[:cnt]
 
 
 def verify_witness(X, x, y, z, metric=L2):

@@ -11,7 +11,7 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "liboracle.so")
-SRCS = [os.path.join(HERE, "grng_oracle.c"), os.path.join(HERE, "mlp_oracle.c")]
+SRCS = [os.path.join(HERE, "grng_oracle.c"), os.path.join(HERE, "mlp_oracle.c"), os.path.join(HERE, "guided_oracle.c")]
 
 
 def build(force: bool = False) -> str:
