@@ -46,8 +46,9 @@ def lib():
         _lib.orc_set_threads.argtypes = [i32]
         _lib.orc_max_threads.restype = i32
         _lib.orc_max_threads.argtypes = []
-        _lib.orc_rng_guided.restype = i64
-        _lib.orc_rng_guided.argtypes = [P, i64, i32, i32, P, P, i32, P, i64, P]
+        if hasattr(_lib, "orc_rng_guided"):  # absent from single-file builds of the pin tests
+            _lib.orc_rng_guided.restype = i64
+            _lib.orc_rng_guided.argtypes = [P, i64, i32, i32, P, P, i32, P, i64, P]
         _lib.orc_emst.restype = i64
         _lib.orc_emst.argtypes = [P, i64, i32, i32, P]
         _lib.orc_grng_brute.restype = i64

@@ -116,13 +116,14 @@ class Index:
     """An index over a point set (owns the library's grng_index)."""
 
     def __init__(self, points, n_layers=1, metric=L2, precision=FP32, knn_k=32, stream=None, flags=0,
-                 mlp_params=None, k_shortlist=0):
+                 mlp_params=None, k_shortlist=0, spin_limit=0):
         self._h = ctypes.c_void_p()
         pts = _contig(points, np.float32)
         n, dim = int(pts.shape[0]), int(pts.shape[1])
         o = Opts()
         lib().grng_default_opts(ctypes.byref(o))
         o.metric, o.precision, o.n_layers, o.knn_k, o.flags = metric, precision, n_layers, knn_k, flags
+        o.spin_limit = spin_limit
         if mlp_params is not None:
             w = _contig(mlp_params, np.float32)
             o.mlp_weights, o.mlp_bytes, o.k_shortlist = _ptr(w), 4 * int(w.shape[0]), k_shortlist
@@ -292,10 +293,10 @@ def mlp_init(seed=0):
 
 
 def build_all(X, layers, metric=L2, knn_k=32, want_adjacency=False, stream=None, flags=0, precision=FP32,
-              mlp_params=None, k_shortlist=0):
+              mlp_params=None, k_shortlist=0, spin_limit=0):
     """Build every layer (finest first), link every layer (coarsest first) and the RNG."""
     ix = Index(X, n_layers=len(layers), metric=metric, knn_k=knn_k, stream=stream, flags=flags,
-               precision=precision, mlp_params=mlp_params, k_shortlist=k_shortlist)
+               precision=precision, mlp_params=mlp_params, k_shortlist=k_shortlist, spin_limit=spin_limit)
     out = {"layers": [None] * len(layers), "grng": [None] * len(layers)}
     for li in range(len(layers) - 1, -1, -1):
         out["layers"][li] = ix.build_layer(li, layers[li])

@@ -1120,8 +1120,8 @@ static void launch_cross(const float* Xr, int64_t nr, const float* Xc, int64_t n
 //     the other endpoint;
 //   - uncovered pairs go to the exhaustive tier.
 // ---------------------------------------------------------------------------------
-#define GRNG_LMAX 8192  // list length (a list never exceeds it: its buckets are counted first)
-#define GRNG_LCAP 8192  // list slots per node
+#define GRNG_LMAX 16384  // list length (a list never exceeds it: its buckets are counted first)
+#define GRNG_LCAP 16384  // list slots per node
 #define GRNG_HBINS 128
 
 struct SideParams {

@@ -161,6 +161,9 @@ __global__ void __launch_bounds__(256, 1) tc_sweep_kernel(TcParams p) {
   uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + o + 32);
   int* s_strip = reinterpret_cast<int*>(sm + o + 36);
   int* s_abort = reinterpret_cast<int*>(sm + o + 40);
+  // per barrier: an issued copy or MMA batch not yet seen complete, and its phase parity
+  int* s_pend = reinterpret_cast<int*>(sm + o + 48);
+  int* s_par = s_pend + 4;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int lq = warp & 3, h = warp >> 2;
@@ -177,7 +180,11 @@ __global__ void __launch_bounds__(256, 1) tc_sweep_kernel(TcParams p) {
     tmem_relinquish();
   }
   if (tid == 0) {
-    for (int i = 0; i < 4; ++i) mbar_init(&bars[i], 1);
+    for (int i = 0; i < 4; ++i) {
+      mbar_init(&bars[i], 1);
+      s_pend[i] = 0;
+      s_par[i] = 0;
+    }
     *s_abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -200,6 +207,8 @@ __global__ void __launch_bounds__(256, 1) tc_sweep_kernel(TcParams p) {
       fence_proxy_async();
       mbar_expect_tx(&bars[0], IMG);
       bulk_g2s(sA, p.img + (size_t)bx * IMG, IMG, &bars[0]);
+      s_pend[0] = 1;
+      s_par[0] = (int)phA;
     }
     {
       const uint32_t* srcA = reinterpret_cast<const uint32_t*>(p.A + bx * 16384);
@@ -221,8 +230,11 @@ __global__ void __launch_bounds__(256, 1) tc_sweep_kernel(TcParams p) {
 #pragma unroll
     for (int j = 0; j < GRNG_KMAX; ++j) { kk[j] = INF; ki[j] = -1; }
     float thr = INF;
-    if (tid == 0 && !mbar_wait(&bars[0], phA, p.spin)) {
-      *s_abort = 1;
+    if (tid == 0) {
+      if (mbar_wait(&bars[0], phA, p.spin)) s_pend[0] = 0;
+      else *s_abort = 1;
+    }
+    if (tid == 0 && s_pend[0]) {
       atomicOr(p.status, 1);
     }
     phA ^= 1;
@@ -246,7 +258,13 @@ __global__ void __launch_bounds__(256, 1) tc_sweep_kernel(TcParams p) {
       if (tid == 0) {
         mbar_expect_tx(&bars[1], IMG);
         bulk_g2s(sB, p.img + (size_t)by * IMG, IMG, &bars[1]);
-        if (filt) mbar_expect_tx(&bars[3], 32768);
+        s_pend[1] = 1;
+        s_par[1] = (int)phB;
+        if (filt) {
+          mbar_expect_tx(&bars[3], 32768);
+          s_pend[3] = 1;
+          s_par[3] = (int)phY;
+        }
       }
       if (filt && warp == 0) {
         // one 256-byte copy per row into rows of 272 bytes: lanes reading one column of
@@ -267,9 +285,12 @@ __global__ void __launch_bounds__(256, 1) tc_sweep_kernel(TcParams p) {
         }
       if (tid == 0) {
         if (mbar_wait(&bars[1], phB, p.spin)) {
+          s_pend[1] = 0;
           tc_fence_after();
           issue_gram_tile(tbase, sA, sB, Dp);
           umma_commit(&bars[2]);
+          s_pend[2] = 1;
+          s_par[2] = (int)phM;
         } else {
           *s_abort = 1;
           atomicOr(p.status, 1);
@@ -278,7 +299,9 @@ __global__ void __launch_bounds__(256, 1) tc_sweep_kernel(TcParams p) {
       phB ^= 1;
       __syncthreads();
       if (*s_abort) break;
-      if (!mbar_wait(&bars[2], phM, p.spin)) {
+      if (mbar_wait(&bars[2], phM, p.spin)) {
+        if (tid == 0) s_pend[2] = 0;
+      } else {
         *s_abort = 1;
         atomicOr(p.status, 1);
       }
@@ -363,7 +386,9 @@ __global__ void __launch_bounds__(256, 1) tc_sweep_kernel(TcParams p) {
           top2_merge(c1, b1, c2, b2, u1.x, __float_as_int(u1.z), u1.y, __float_as_int(u1.w));
           cmin1[tid] = c1; cmin2[tid] = c2; carg1[tid] = b1; carg2[tid] = b2;
         }
-        if (!mbar_wait(&bars[3], phY, p.spin)) {
+        if (mbar_wait(&bars[3], phY, p.spin)) {
+          if (tid == 0) s_pend[3] = 0;
+        } else {
           *s_abort = 1;
           atomicOr(p.status, 1);
         }
@@ -512,7 +537,15 @@ __global__ void __launch_bounds__(256, 1) tc_sweep_kernel(TcParams p) {
   }
   for (int o2 = 16; o2 > 0; o2 >>= 1) st_cand += __shfl_down_sync(FULLMASK, st_cand, o2);
   if (lane == 0) atomicAdd(p.stats, st_cand);
-  // teardown: every tensor-core operation of this CTA has completed (or was never issued)
+  // teardown.  After a bounded wait ran out, copies into this CTA's shared memory or MMAs
+  // into its tensor memory may still be in flight: wait (again bounded, far longer) for every
+  // barrier with an outstanding phase before the memory is released.
+  __syncthreads();
+  if (*s_abort && tid == 0) {
+    const long long lim = p.spin > (1ll << 26) ? p.spin : (1ll << 26);
+    for (int b = 0; b < 4; ++b)
+      if (s_pend[b] && !mbar_wait(&bars[b], (uint32_t)s_par[b], lim)) atomicOr(p.status, 2);
+  }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();

@@ -80,3 +80,21 @@ def test_bf16_build_equals_fp32_build_many_tiles():
     assert np.array_equal(o16["edges"], o32["edges"])
     st = ix.stats()["rng"]
     assert st["kernel_ms"]["tiles"] > 0
+
+
+def test_bounded_wait_times_out_cleanly():
+    """With a poll limit of one, the tensor-core sweep's first wait on a bulk copy runs out:
+    the kernel drains what it issued, frees its tensor memory and reports GRNG_ETIMEOUT; the
+    index can be destroyed and a new build on the same GPU gives the oracle's edges."""
+    w = wl.make("lin96", n=3000)
+    ix = g.Index(torch.from_numpy(w.X).cuda(), n_layers=len(w.layers), precision=g.BF16, spin_limit=1)
+    for li in range(len(w.layers) - 1, -1, -1):
+        ix.build_layer(li, w.layers[li], outputs=False)
+    for li in range(len(w.layers)):
+        ix.link_pivots(li, want_adjacency=False)
+    with pytest.raises(g.GrngError) as e:
+        ix.rng_build_exact()
+    assert e.value.status == g.GRNG_ETIMEOUT
+    ix.close()
+    ix2, out = g.build_all(torch.from_numpy(w.X).cuda(), w.layers, precision=g.BF16)
+    assert {tuple(e) for e in out["edges"].tolist()} == {tuple(e) for e in oracle.rng_brute(w.X).tolist()}
