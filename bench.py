@@ -267,20 +267,40 @@ def step_measures(stats, step_ms):
     """Work counters of one step, from the library's statistics (grng_stats):
     candidate lune tests are the candidate pairs every level decides (tier 1 to the FP64
     recheck), interceptor evaluations the exact tests of one interceptor against one pair
-    outside the tile sweeps (tier 3, range-list distance tests and list intersections, the
-    learned shortlist), the recheck fraction the FP64 triples among those evaluations."""
+    outside the tile sweeps (tier 3, range-list distance tests, the learned shortlist), the
+    recheck fraction the FP64 triples among those evaluations."""
     levels = [L["grng"] for L in stats["layers"]] + [stats["rng"]]
     cand = sum(L["candidate_pairs"] for L in levels)
-    ev = sum(L["tier3_nodes_tested"] + L["range_nodes_tested"] + L.get("range_probes", 0) + L["learned_tests"]
-             for L in levels)
+    ev = sum(L["tier3_nodes_tested"] + L["range_nodes_tested"] + L["learned_tests"] for L in levels)
     fp64 = sum(L["fp64_triples"] for L in levels)
     s = step_ms / 1000.0
     n = stats["n"]
+    # distance computations, the paper's cost measure (Sec. 1), by where they are made: tile
+    # sweeps count every key of every tile (both orientations), the assignment every
+    # member x pivot key, the exact tiers each tested interceptor (two distances in tier 3)
+    ms = [L["m"] for L in stats["layers"]]
+    blk = lambda k: ((k + 127) // 128) ** 2 * 128 * 128
+    dist = {"exemplar_tiles": blk(n), "assignment": n * ms[-1] + sum(ms[i + 1] * ms[i] for i in range(len(ms) - 1)),
+            "pivot_layer_tiles": sum(2 * blk(m) + (2 * blk(m) if L["grng"]["range_pairs"] else 0)
+                                     for m, L in zip(ms, stats["layers"])),
+            "node_ancestor_tables": sum(m * sum(ms[:i]) for i, m in enumerate(ms) if L_has_tier3(stats, i)),
+            "exact_tiers": sum(2 * L["tier3_nodes_tested"] + L["range_nodes_tested"] + 2 * L["learned_tests"]
+                               for L in levels)}
+    dist["total"] = sum(dist.values())
     return {"candidate_pairs_per_step": cand, "candidate_lune_tests_per_s": cand / s,
             "exemplar_candidate_pairs": stats["rng"]["candidate_pairs"],
             "exemplar_pairs_of_all": stats["rng"]["candidate_pairs"] / max(1.0, n * (n - 1) / 2),
             "interceptor_evaluations_per_step": ev, "interceptor_evaluations_per_s": ev / s,
-            "fp64_triples_per_step": fp64, "fp64_recheck_fraction": fp64 / max(1, ev)}
+            "fp64_triples_per_step": fp64, "fp64_recheck_fraction": fp64 / max(1, ev),
+            "distance_computations_per_step": dist,
+            "distance_computations_over_all_pairs": dist["total"] / max(1.0, n * (n - 1) / 2)}
+
+
+def L_has_tier3(stats, i):
+    """Whether pivot layer i built its node x ancestor key table (a lower layer with pairs
+    left for the exhaustive or range-list tiers)."""
+    G = stats["layers"][i]["grng"]
+    return i > 0 and (G["range_pairs"] > 0 or G["tier3_pairs"] > 0)
 
 
 def tc_key_error(g, X, n=256, seed=3003):

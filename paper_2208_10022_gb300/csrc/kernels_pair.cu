@@ -588,12 +588,15 @@ struct Tier3Params {
   Ancestors anc;
   Front* fbuf;     // per CTA: two frontier buffers of fcap ranges
   const float* pdist_hi;  // [n] upper bound of d(node, its parent), or null
+  const int32_t* idx;     // pairs to search: pairs[idx[t]] with slot slot0 + idx[t] (null: all, in order)
   const float* atab;      // [n][tabw] FP32 keys node x ancestor (columns anc.toff[a] + c), or null
   int64_t tabw;
   int fcap;
   int dense;              // ancestor levels scanned densely (needs atab, levels <= 65,536 nodes)
   int mkw;                // words of one candidate bitmask (dynamic shared memory, dense scans)
   unsigned long long* stats;  // [0] frontier overflows, [1] nodes tested, [2] pairs blocked, [3] by the descent
+  unsigned long long* prof;   // SM cycles of thread 0: [0] top level and descents [1] lower ancestor levels
+                              // [2] node level; [3] pairs reaching the lower ancestor levels
 };
 
 // asynchronous 16-byte copy global -> shared (src_bytes < 16: the rest is zero-filled, 0: no read)
@@ -687,7 +690,11 @@ __global__ void __launch_bounds__(T3_T, T3_MINB) tier3_kernel(Tier3Params p) {
   Front* bufA = p.fbuf + (int64_t)blockIdx.x * 2 * p.fcap;
   Front* bufB = bufA + p.fcap;
   unsigned long long n_over = 0, n_tested = 0, n_blk = 0, n_probe = 0;
-  for (int64_t t = blockIdx.x; t < p.m; t += gridDim.x) {
+  __shared__ unsigned long long s_prof[4];  // thread 0's phase cycles (kept out of registers)
+  __shared__ long long s_ck[2];
+  if (tid == 0) s_prof[0] = s_prof[1] = s_prof[2] = s_prof[3] = 0ull;
+  for (int64_t t0 = blockIdx.x; t0 < p.m; t0 += gridDim.x) {
+    const int64_t t = p.idx ? p.idx[t0] : t0;
     const int2 pr = p.pairs[t];
     const int64_t g = pr.x, o = pr.y;
     __syncthreads();
@@ -784,10 +791,18 @@ __global__ void __launch_bounds__(T3_T, T3_MINB) tier3_kernel(Tier3Params p) {
       int ncur = 1;
       bool all = false;
       int a_leaf = 0;  // first level handled by the range loop below
+      if (tid == 0) {
+        s_ck[0] = clock64();
+        s_ck[1] = -1;
+      }
       if (p.dense) {
         // ---- dense ancestor levels ------------------------------------------------------
         const bool probe = rho2 >= 0.0f;
         for (int a = 0; a < p.anc.n; ++a) {
+          if (a == 1 && tid == 0) {
+            s_ck[1] = clock64();
+            s_prof[3] += 1;
+          }
           const bool last = a == p.anc.n - 1;
           const int ma = (int)p.anc.m[a];
           const unsigned* mk_in = (a & 1) ? mk1 : mk0;
@@ -926,6 +941,12 @@ __global__ void __launch_bounds__(T3_T, T3_MINB) tier3_kernel(Tier3Params p) {
           }
         }
       }
+      if (tid == 0) {  // the top level and descents, then the lower ancestor levels
+        const long long ck2 = clock64();
+        s_prof[0] += (unsigned long long)((s_ck[1] >= 0 ? s_ck[1] : ck2) - s_ck[0]);
+        if (s_ck[1] >= 0) s_prof[1] += (unsigned long long)(ck2 - s_ck[1]);
+        s_ck[0] = ck2;
+      }
       // ---- range levels (a >= a_leaf); level a = anc.n is the layer's own nodes ----------
       for (int a = a_leaf; a <= p.anc.n && !all && !s_block; ++a) {
         const bool leaf = a == p.anc.n;
@@ -1040,6 +1061,7 @@ __global__ void __launch_bounds__(T3_T, T3_MINB) tier3_kernel(Tier3Params p) {
           }
         }
       }
+      if (tid == 0) s_prof[2] += (unsigned long long)(clock64() - s_ck[0]);  // the node level
     }
     __syncthreads();
     if (tid == 0) {
@@ -1053,6 +1075,122 @@ __global__ void __launch_bounds__(T3_T, T3_MINB) tier3_kernel(Tier3Params p) {
   if (tid == 0 && n_over) atomicAdd(p.stats + 0, n_over);
   if (tid == 0 && n_blk) atomicAdd(p.stats + 2, n_blk);
   if (tid == 0 && n_probe) atomicAdd(p.stats + 3, n_probe);
+  if (tid == 0 && p.prof)
+    for (int i = 0; i < 4; ++i) atomicAdd(p.prof + i, s_prof[i]);
+}
+
+// Before the exhaustive tier, one warp per pair: the centre c* of the ball around the G-lune
+// is located through the ancestor key table (Stewart's identity, as in tier 3), and from each
+// of the T3P_DESC top-level nodes nearest c* the warp descends greedily to one finest domain
+// and tests its nodes.  A pair some node certainly blocks is decided here (its pending slot
+// is flagged); the others are listed for the exhaustive tier.  Which pairs are decided here
+// changes the work only, never a decision.
+#define T3P_DESC 3
+#define T3P_WARPS 8
+__global__ void __launch_bounds__(T3P_WARPS * 32) tier3_probe_kernel(Tier3Params p, int32_t* __restrict__ rest,
+                                                                     unsigned long long* __restrict__ nrest,
+                                                                     unsigned long long* __restrict__ nblocked) {
+  extern __shared__ __align__(16) float t3p_sm[];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int l8 = lane & 7;
+  const unsigned gmask = 0xffu << (lane & 24);
+  float* gs = t3p_sm + wib * 2 * p.Dp;
+  float* os = gs + p.Dp;
+  const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const Err e = err_fp32(p.Dp);
+  const float u2 = 1.1920928955078125e-07f;
+  const int na = p.anc.n;
+  unsigned long long c_blk = 0;
+  for (int64_t t = wid; t < p.m; t += nw) {
+    const int2 pr = p.pairs[t];
+    const int64_t g = pr.x, o = pr.y;
+    __syncwarp();
+    for (int d = lane; d < p.Dp; d += 32) {
+      gs[d] = p.X[g * p.Dp + d];
+      os[d] = p.X[o * p.Dp + d];
+    }
+    __syncwarp();
+    float v = 0.0f;
+    if (lane == 0) v = key32(gs, os, p.Dp, p.metric);
+    v = __shfl_sync(FULLMASK, v, 0);
+    const PairThr P = pair_thresholds(v, p.rlo ? p.rlo[g] : 0.0f, p.rhi ? p.rhi[g] : 0.0f,
+                                      p.rlo ? p.rlo[o] : 0.0f, p.rhi ? p.rhi[o] : 0.0f, p.metric, e, p.guide);
+    bool blocked = false;
+    if (!P.quick) {
+      const float vlo = fmaxf(lo_b(v, e), 0.0f), vhi = hi_b(v, e);
+      const float lam = fminf(fmaxf((vhi + P.t1hi - P.t2hi) / (2.0f * fmaxf(vhi, 1e-30f)), 0.0f), 1.0f);
+      (void)vlo;
+      (void)u2;
+      // the lane's three top-level nodes nearest c* (Stewart estimate of |c - c*|^2)
+      unsigned long long b0 = ~0ull, b1 = ~0ull, b2 = ~0ull;
+      const float* rg = p.atab + g * p.tabw + p.anc.toff[0];
+      const float* ro = p.atab + o * p.tabw + p.anc.toff[0];
+      for (int c = lane; c < (int)p.anc.m[0]; c += 32) {
+        const float s2 = fmaxf((1.0f - lam) * rg[c] + lam * ro[c] - lam * (1.0f - lam) * v, 0.0f);
+        const unsigned long long key = ((unsigned long long)__float_as_uint(s2) << 32) | (unsigned)c;
+        if (key < b2) {
+          if (key < b1) {
+            b2 = b1;
+            if (key < b0) { b1 = b0; b0 = key; }
+            else b1 = key;
+          } else {
+            b2 = key;
+          }
+        }
+      }
+      for (int round = 0; round < T3P_DESC && !blocked; ++round) {
+        unsigned long long best = b0;
+        for (int sh = 16; sh > 0; sh >>= 1) {
+          const unsigned long long y2 = __shfl_xor_sync(FULLMASK, best, sh);
+          best = y2 < best ? y2 : best;
+        }
+        if (best == ~0ull) break;
+        if (b0 == best) { b0 = b1; b1 = b2; b2 = ~0ull; }  // the winning lane moves on
+        int cn = (int)(best & 0xffffffffu);
+        int lvl = 0;
+        bool ok = true;
+        while (lvl < na - 1) {
+          const int c0 = p.anc.cstart[lvl][cn], c1 = p.anc.cstart[lvl][cn + 1];
+          if (c1 <= c0) { ok = false; break; }
+          ++lvl;
+          unsigned long long bb = ~0ull;
+          for (int c = c0 + lane; c < c1; c += 32) {
+            const float kg = p.atab[g * p.tabw + p.anc.toff[lvl] + c];
+            const float kq = p.atab[o * p.tabw + p.anc.toff[lvl] + c];
+            const float s2 = fmaxf((1.0f - lam) * kg + lam * kq - lam * (1.0f - lam) * v, 0.0f);
+            const unsigned long long key = ((unsigned long long)__float_as_uint(s2) << 32) | (unsigned)c;
+            bb = key < bb ? key : bb;
+          }
+          for (int sh = 16; sh > 0; sh >>= 1) {
+            const unsigned long long y2 = __shfl_xor_sync(FULLMASK, bb, sh);
+            bb = y2 < bb ? y2 : bb;
+          }
+          cn = (int)(bb & 0xffffffffu);
+        }
+        if (!ok) continue;
+        const int k0 = p.anc.cstart[lvl][cn], k1 = p.anc.cstart[lvl][cn + 1];
+        for (int kb = k0; kb < k1; kb += 4) {
+          const int k = kb + (lane >> 3);
+          const bool in = k < k1 && k != (int)g && k != (int)o;  // uniform within the group
+          float ka = 0.0f, kb2 = 0.0f;
+          group_keys(p.X + (int64_t)(in ? k : (int)g) * p.Dp, gs, os, p.Dp, p.metric, l8, gmask, ka, kb2);
+          const bool hit = in && l8 == 0 && block_state(ka, kb2, P, e) == 2;
+          if (__any_sync(FULLMASK, hit)) { blocked = true; break; }
+        }
+      }
+    }
+    if (lane == 0) {
+      if (blocked) {
+        p.pend[p.slot0 + t] = pr;
+        p.pflag[p.slot0 + t] = 3;
+        ++c_blk;
+      } else {
+        rest[atomicAdd(nrest, 1ull)] = (int32_t)t;
+      }
+    }
+  }
+  if (lane == 0 && c_blk) atomicAdd(nblocked, c_blk);
 }
 
 // node x ancestor keys: out[r * ld + c] = key(Xr[r], Xc[c]) for a 128 x 128 tile per CTA
@@ -1112,12 +1250,9 @@ static void launch_cross(const float* Xr, int64_t nr, const float* Xc, int64_t n
 // lower bound of every key the list leaves out, decides coverage: a pair is covered
 // from a side whose T'_s reaches past its threshold on that side, because every node
 // that could satisfy that condition is then listed (GRNG definition, Sec. 2).
-//   - covered from both sides: a blocker must appear in both lists (a node missing
-//     from a covering list certainly fails that side's condition), and both lists
-//     carry the node's keys to their endpoint, so the test is the intersection of the
-//     two lists' annuli, with no distance computed;
-//   - covered from one side: the annulus of that side's list is tested by distance to
-//     the other endpoint;
+//   - covered from one side (or both: the shorter annulus): that list's annulus is
+//     bounded node by node through the node's parent (ancestor key table) and only the
+//     nodes no bound settles are tested by distance to the other endpoint;
 //   - uncovered pairs go to the exhaustive tier.
 // ---------------------------------------------------------------------------------
 #define GRNG_LMAX 16384  // list length (a list never exceeds it: its buckets are counted first)
@@ -1295,8 +1430,7 @@ struct ListParams {
   int2* pend; unsigned long long* pend_cnt; unsigned long long pend_cap;
   int2* amb; unsigned long long* amb_cnt; unsigned long long amb_cap;
   unsigned long long* stats;  // [0] links [1] pending [2] to tier 3 [3] blocked [4] listed nodes tested by
-                              // distance [5] pairs decided by intersection [6] intersection probes
-                              // [7] list entries read
+                              // distance [5] pairs covered from both sides [7] list entries read
 };
 
 // Entries [first, last) of s's list whose keys may lie in (klo, khi): the buckets from
@@ -1315,14 +1449,10 @@ __device__ __forceinline__ int2 bucket_span(const ListParams& p, int s, float kl
 }
 
 #define LT_WARPS 8
-#define LT_TAB 1024            // hash slots per warp (intersection of two list annuli)
-#define LT_CHUNK (LT_TAB / 2)  // entries hashed per round: load factor at most 1/2
 
-__device__ __forceinline__ unsigned lt_hash(int k) { return ((unsigned)k * 2654435761u) >> (32 - 10); }
-
-// Decision of one list-tier pair from the intersection or the scan, counted per warp.
+// Decision of one list-tier pair, counted per warp.
 struct LtCount {
-  unsigned long long link = 0, pend = 0, un = 0, blk = 0, test = 0, isect = 0, probe = 0, read = 0;
+  unsigned long long link = 0, pend = 0, un = 0, blk = 0, test = 0, both = 0, read = 0;
 };
 
 // Ambiguous triples of a pair that nothing blocked are recorded in a second pass; the
@@ -1333,98 +1463,6 @@ __device__ __forceinline__ unsigned long long lt_pend_slot(const ListParams& p, 
   slot = __shfl_sync(FULLMASK, slot, 0);
   if (lane == 0 && slot < p.pend_cap) p.pend[slot] = pr;
   return slot;
-}
-
-#define LT_U 4  // list entries per lane per round of the intersection (loads in flight)
-
-// Pairs covered from both sides: a blocker is a node of both annuli.  The shorter annulus
-// goes into a per-warp hash table (in chunks of LT_CHUNK entries), the other one probes it.
-__device__ __forceinline__ void lt_intersect(const ListParams& p, int2 pr, const PairThr& P, float ekx, float eky,
-                                             Err e, int lane, int* tab_i, float* tab_k, LtCount& c, bool& blocked,
-                                             bool& anyamb) {
-  const int x = pr.x, y = pr.y;
-  const int2 ax = bucket_span(p, x, ekx, P.t1hi), ay = bucket_span(p, y, eky, P.t2hi);
-  const bool hy = (ay.y - ay.x) <= (ax.y - ax.x);  // hash the shorter annulus
-  const int hs = hy ? y : x, qs = hy ? x : y;
-  const int2 hspan = hy ? ay : ax, qspan = hy ? ax : ay;
-  const float hlo = hy ? eky : ekx, hhi = hy ? P.t2hi : P.t1hi;
-  const float qlo = hy ? ekx : eky, qhi = hy ? P.t1hi : P.t2hi;
-  const int64_t hb = (int64_t)hs * GRNG_LCAP, qb = (int64_t)qs * GRNG_LCAP;
-  unsigned long long slot = 0;
-  for (int pass = 0; pass < 2; ++pass) {  // pass 1 records the ambiguous triples
-    if (pass == 1) {
-      if (blocked || !anyamb) break;
-      slot = lt_pend_slot(p, pr, lane);
-    }
-    for (int h0 = hspan.x; h0 < hspan.y && !blocked; h0 += LT_CHUNK) {
-      __syncwarp();
-      for (int i = lane; i < LT_TAB; i += 32) tab_i[i] = -1;
-      __syncwarp();
-      const int h1 = min(h0 + LT_CHUNK, hspan.y);
-      for (int j0 = h0; j0 < h1; j0 += 32 * LT_U) {
-        float kk[LT_U];
-        int kj[LT_U];
-#pragma unroll
-        for (int u = 0; u < LT_U; ++u) {
-          const int j = j0 + lane + 32 * u;
-          kk[u] = j < h1 ? p.lkey[hb + j] : -1.0f;
-          kj[u] = j < h1 ? p.lidx[hb + j] : -1;
-        }
-#pragma unroll
-        for (int u = 0; u < LT_U; ++u) {
-          if (kj[u] < 0) continue;
-          c.read += pass == 0;
-          if (lo_b(kk[u], e) < hhi && hi_b(kk[u], e) > hlo) {
-            unsigned h = lt_hash(kj[u]);
-            for (int probe = 0; probe < LT_TAB; ++probe) {  // at most half the slots are taken
-              if (atomicCAS(tab_i + h, -1, kj[u]) == -1) { tab_k[h] = kk[u]; break; }
-              h = (h + 1) & (LT_TAB - 1);
-            }
-          }
-        }
-      }
-      __syncwarp();
-      for (int j0 = qspan.x; j0 < qspan.y; j0 += 32 * LT_U) {
-        float kk[LT_U];
-        int kj[LT_U];
-#pragma unroll
-        for (int u = 0; u < LT_U; ++u) {
-          const int j = j0 + lane + 32 * u;
-          kk[u] = j < qspan.y ? p.lkey[qb + j] : -1.0f;
-          kj[u] = j < qspan.y ? p.lidx[qb + j] : -1;
-        }
-        bool b2 = false, b1 = false;
-#pragma unroll
-        for (int u = 0; u < LT_U; ++u) {
-          if (kj[u] < 0) continue;
-          c.read += pass == 0;
-          if (!(lo_b(kk[u], e) < qhi && hi_b(kk[u], e) > qlo)) continue;
-          c.probe += pass == 0;
-          unsigned h = lt_hash(kj[u]);
-          for (int probe = 0; probe < LT_TAB; ++probe) {
-            const int w = tab_i[h];
-            if (w == -1) break;
-            if (w == kj[u]) {
-              const float other = tab_k[h];
-              const float a = hy ? kk[u] : other, b = hy ? other : kk[u];  // keys to x and to y
-              const int stt = block_state(a, b, P, e);
-              b2 |= stt == 2;
-              b1 |= stt == 1;
-              if (pass == 1 && stt == 1) push_pair(p.amb, p.amb_cnt, p.amb_cap, make_int2((int)slot, kj[u]));
-              break;
-            }
-            h = (h + 1) & (LT_TAB - 1);
-          }
-        }
-        if (pass == 0) {
-          blocked = __any_sync(FULLMASK, b2);
-          anyamb |= __any_sync(FULLMASK, b1);
-          if (blocked) break;
-        }
-      }
-    }
-  }
-  c.isect += lane == 0;
 }
 
 // Pairs covered from one side s: the annulus of s's list, tested against the other
@@ -1601,23 +1639,21 @@ __device__ __forceinline__ void lt_scan(const ListParams& p, int2 pr, int sd, fl
   }
 }
 
-// One warp per pair.  MODE 0 decides the pairs covered from both sides (and forwards the
-// trivial ones); MODE 1 the pairs covered from one side, G lanes sharing one listed node in
-// the distance tests (G = 8 for dimensions that are multiples of 32, fewer for 8 and 16),
-// NQ float4 columns per lane (0: any dimension, the other endpoint's row read from memory).
-template <int MODE, int G, int NQ>
+// One warp per pair.  A pair covered from one side is scanned in that side's annulus; a
+// pair covered from both sides in the shorter annulus of the two (intersecting the two
+// annuli in shared-memory hash tables was measured slower: 3.02 s against 2.74 s for the
+// 131,072-pivot layer at 1,000,000 points).  G lanes share one listed node in the distance
+// tests (G = 8 for dimensions that are multiples of 32, fewer for 8 and 16), NQ float4
+// columns per lane (0: any dimension, the other endpoint's row read from memory).
+template <int G, int NQ>
 __global__ void __launch_bounds__(LT_WARPS * 32, 3) list_tier_kernel(ListParams p) {
-  extern __shared__ __align__(16) int lt_sm[];
-  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  int* tab_i = lt_sm + wib * 2 * LT_TAB;                          // node ids (-1: empty)
-  float* tab_k = reinterpret_cast<float*>(tab_i + LT_TAB);       // their keys
+  const int lane = threadIdx.x & 31;
   const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const Err e = err_fp32(p.Dp);
   LtCount c;
   for (int64_t t = wid; t < p.m; t += nw) {
-    const int sd = p.side[t];
-    if ((MODE == 0) != (sd >= 2)) continue;  // the other kernel's pair
+    int sd = p.side[t];
     const int2 pr = p.pairs[t];
     if (sd == 3) {
       if (lane == 0) push_pair(p.links, p.link_cnt, p.link_cap, pr);
@@ -1641,9 +1677,13 @@ __global__ void __launch_bounds__(LT_WARPS * 32, 3) list_tier_kernel(ListParams 
     // nodes within E of one endpoint cannot satisfy the other endpoint's condition
     const float ekx = excl_key(excl_dist(v, P.t2hi, p.metric, e), p.metric);
     const float eky = excl_key(excl_dist(v, P.t1hi, p.metric, e), p.metric);
+    if (sd == 4) {  // both lists cover: the shorter annulus
+      const int2 ax = bucket_span(p, x, ekx, P.t1hi), ay = bucket_span(p, y, eky, P.t2hi);
+      sd = (ay.y - ay.x) < (ax.y - ax.x) ? 1 : 0;
+      c.both += lane == 0;
+    }
     bool blocked = false, anyamb = false;
-    if (MODE == 0) lt_intersect(p, pr, P, ekx, eky, e, lane, tab_i, tab_k, c, blocked, anyamb);
-    else lt_scan<G, NQ>(p, pr, sd, v, P, ekx, eky, e, lane, c, blocked, anyamb);
+    lt_scan<G, NQ>(p, pr, sd, v, P, ekx, eky, e, lane, c, blocked, anyamb);
     if (blocked) {
       c.blk += lane == 0;
     } else if (!anyamb) {
@@ -1655,7 +1695,6 @@ __global__ void __launch_bounds__(LT_WARPS * 32, 3) list_tier_kernel(ListParams 
   }
   for (int sh = 16; sh > 0; sh >>= 1) {
     c.test += __shfl_down_sync(FULLMASK, c.test, sh);
-    c.probe += __shfl_down_sync(FULLMASK, c.probe, sh);
     c.read += __shfl_down_sync(FULLMASK, c.read, sh);
   }
   if (lane == 0) {
@@ -1664,8 +1703,7 @@ __global__ void __launch_bounds__(LT_WARPS * 32, 3) list_tier_kernel(ListParams 
     atomicAdd(p.stats + 2, c.un);
     atomicAdd(p.stats + 3, c.blk);
     atomicAdd(p.stats + 4, c.test);
-    atomicAdd(p.stats + 5, c.isect);
-    atomicAdd(p.stats + 6, c.probe);
+    atomicAdd(p.stats + 5, c.both);
     atomicAdd(p.stats + 7, c.read);
   }
 }
@@ -1789,12 +1827,7 @@ static void launch_range(const LevelIn& in, const unsigned int* tk, int* hist, c
 
 template <int G, int NQ>
 static void launch_list_gq(const ListParams& lp, unsigned grid, cudaStream_t s) {
-  // the pairs covered from both sides (with the hash tables), then those covered from one
-  const size_t smem = (size_t)LT_WARPS * 2 * LT_TAB * 4;
-  GRNG_CUDA(cudaFuncSetAttribute(list_tier_kernel<0, G, NQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  list_tier_kernel<0, G, NQ><<<grid, LT_WARPS * 32, smem, s>>>(lp); note_launch();
-  GRNG_CUDA(cudaGetLastError());
-  list_tier_kernel<1, G, NQ><<<grid, LT_WARPS * 32, 0, s>>>(lp); note_launch();
+  list_tier_kernel<G, NQ><<<grid, LT_WARPS * 32, 0, s>>>(lp); note_launch();
   GRNG_CUDA(cudaGetLastError());
 }
 // group width and float4 columns per lane for the padded dimension (8, 16 or a multiple of 32)
@@ -1993,8 +2026,8 @@ static void finish_level(const LevelIn& in, LevelOut& out, LevelStats& st, cudaS
       st.c[20] = ltot;    // listed nodes
       st.c[21] = h8[0];   // links from the lists
       st.c[22] = h8[4];   // listed nodes tested by distance
-      st.c[32] = h8[5];   // pairs decided by intersecting both lists
-      st.c[33] = h8[6];   // intersection probes
+      st.c[32] = h8[5];   // pairs covered from both sides
+      st.c[33] = 0;
       st.c[34] = h8[7];   // list entries read
       nun2 = n3;          // left for tier 3
       t3pairs = unres3.as<int2>();
@@ -2035,7 +2068,9 @@ static void finish_level(const LevelIn& in, LevelOut& out, LevelStats& st, cudaS
         if (!t3.dense) t3.mkw = 0;
       }
       t3.stats = dc + 34;
+      t3.prof = dc + 58;
       GRNG_CUDA(cudaMemsetAsync(dc + 34, 0, 4 * sizeof(unsigned long long), s));
+      GRNG_CUDA(cudaMemsetAsync(dc + 58, 0, 4 * sizeof(unsigned long long), s));
       if (!in.grng && knn_idx && tier2b && ((in.mlp_params && in.kshort > 0) || (in.mlp_record && out.rec_f))) {
         // learned shortlist (extension of Stage V): k scored candidates per pair first
         MlpStage ms;
@@ -2072,7 +2107,27 @@ static void finish_level(const LevelIn& in, LevelOut& out, LevelStats& st, cudaS
       GRNG_CUDA(cudaEventCreate(&f0));
       GRNG_CUDA(cudaEventCreate(&f1));
       GRNG_CUDA(cudaEventRecord(f0, s));
-      tier3_kernel<<<grid3, T3_T, 2 * in.Dp * 4 + 2 * (size_t)t3.mkw * 4, s>>>(t3); note_launch();
+      DevBuf rest;
+      t3.idx = nullptr;
+      if (t3.dense && in.metric == L2 && in.anc.n > 0) {
+        // warp-per-pair descents first; the exhaustive tier takes the pairs they leave
+        GRNG_CUDA(rest.alloc((size_t)nun2 * 4));
+        GRNG_CUDA(cudaMemsetAsync(dc + 62, 0, 2 * sizeof(unsigned long long), s));
+        const unsigned gp = (unsigned)std::min<unsigned long long>((nun2 + T3P_WARPS - 1) / T3P_WARPS,
+                                                                   (unsigned long long)8 * num_sms());
+        tier3_probe_kernel<<<gp, T3P_WARPS * 32, (size_t)T3P_WARPS * 2 * in.Dp * 4, s>>>(
+            t3, rest.as<int32_t>(), dc + 62, dc + 63); note_launch();
+        GRNG_CUDA(cudaGetLastError());
+        unsigned long long hr[2];
+        GRNG_CUDA(cudaMemcpyAsync(hr, dc + 62, sizeof(hr), cudaMemcpyDeviceToHost, s));
+        GRNG_CUDA(cudaStreamSynchronize(s));
+        st.c[39] = hr[1];  // pairs the probe descents block
+        t3.idx = rest.as<int32_t>();
+        t3.m = (int64_t)hr[0];
+      }
+      if (t3.m) {
+        tier3_kernel<<<grid3, T3_T, 2 * in.Dp * 4 + 2 * (size_t)t3.mkw * 4, s>>>(t3); note_launch();
+      }
       GRNG_CUDA(cudaGetLastError());
       GRNG_CUDA(cudaEventRecord(f1, s));
       GRNG_CUDA(cudaEventSynchronize(f1));
@@ -2120,6 +2175,15 @@ static void finish_level(const LevelIn& in, LevelOut& out, LevelStats& st, cudaS
     unsigned long long h[40];
     GRNG_CUDA(cudaMemcpyAsync(h, dc, sizeof(h), cudaMemcpyDeviceToHost, s));
     GRNG_CUDA(cudaStreamSynchronize(s));
+    {
+      unsigned long long hp[4] = {0, 0, 0, 0};
+      if (nun2) GRNG_CUDA(cudaMemcpyAsync(hp, dc + 58, sizeof(hp), cudaMemcpyDeviceToHost, s));
+      GRNG_CUDA(cudaStreamSynchronize(s));
+      st.c[35] = hp[0];  // tier-3 cycles: top level and descents
+      st.c[36] = hp[1];  //   lower ancestor levels
+      st.c[37] = hp[2];  //   node level
+      st.c[38] = hp[3];  // tier-3 pairs reaching the lower ancestor levels
+    }
     st.c[15] = nun2 ? h[34] : 0;  // tier-3 frontier overflows
     st.c[16] = nun2 ? h[35] : 0;  // tier-3 nodes tested
     st.c[23] = nun2 ? h[36] : 0;  // tier-3 pairs blocked

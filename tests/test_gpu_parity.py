@@ -206,9 +206,9 @@ def test_small_buffers_tensor_core_sweep():
 
 
 def test_range_lists_intersect_and_scan():
-    """Pivot pairs decided from range lists: from both lists by intersection and from one
-    list by distance; the layer's GRNG stays the oracle's."""
+    """Pivot pairs decided from range lists, covered from one side and from both; the
+    layer's GRNG stays the oracle's."""
     w = wl.make("lin96", n=6000)
     ix = check_full(w.X, w.layers, wl.L2, knn_k=1)
     G = ix.stats()["layers"][-1]["grng"]
-    assert G["range_pairs"] > 0 and G["range_intersected"] > 0, G
+    assert G["range_pairs"] > 0 and G["range_both_covered"] > 0 and G["range_nodes_tested"] > 0, G
