@@ -1312,6 +1312,20 @@ __device__ __forceinline__ int hist_bin(float v, float T) {
   return max(0, min(GRNG_HBINS - 1, (int)floorf(16.0f * l) + GRNG_HBINS));
 }
 
+// Per list entry, when the level has parents and a node x ancestor key table: the listed
+// node's parent, the upper bound of its distance to that parent, and the parent's key to
+// the list's own node -- what the list tier's bounds read, kept beside the entry so that
+// one pass over a list streams them.
+struct ListAux {
+  const int32_t* parent = nullptr;  // [n] parent positions
+  const float* pdist = nullptr;     // [n] upper bounds of d(node, parent)
+  const float* atab = nullptr;      // node x ancestor keys, the parent level at column toff
+  int64_t tabw = 0, toff = 0;
+  int32_t* par = nullptr;           // [n][GRNG_LCAP] outputs beside lidx / lkey
+  float* pdh = nullptr;
+  float* pkey = nullptr;
+};
+
 // mode 0: per-row histogram of keys below T_s; mode 1: every node with key < T_s whose
 // bucket is at most the row's last listed bucket, written at its bucket's cursor
 template <int KC, int METRIC>
@@ -1321,7 +1335,8 @@ __global__ void __launch_bounds__(GRNG_THREADS) range_sweep_kernel(const float* 
                                                                    const int* __restrict__ lastb,
                                                                    const int* __restrict__ boff,
                                                                    int32_t* __restrict__ lidx,
-                                                                   float* __restrict__ lkey, int fill) {
+                                                                   float* __restrict__ lkey, int fill,
+                                                                   ListAux aux) {
   extern __shared__ __align__(16) unsigned char sm_raw[];
   float* sA = reinterpret_cast<float*>(sm_raw);
   float* sB = sA + KC * GRNG_SSTRIDE;
@@ -1361,8 +1376,15 @@ __global__ void __launch_bounds__(GRNG_THREADS) range_sweep_kernel(const float* 
           } else if (b <= lastr) {
             const int pos = H[b * 128 + tid]++;
             if (pos < GRNG_LCAP) {  // always: the counts of both sweeps agree
-              lidx[(xb + tid) * GRNG_LCAP + pos] = (int32_t)k;
-              lkey[(xb + tid) * GRNG_LCAP + pos] = v;
+              const int64_t q = (xb + tid) * GRNG_LCAP + pos;
+              lidx[q] = (int32_t)k;
+              lkey[q] = v;
+              if (aux.par) {  // the listed node's parent, its distance bound and the parent's key to the row
+                const int c = aux.parent[k];
+                aux.par[q] = c;
+                aux.pdh[q] = aux.pdist[k];
+                aux.pkey[q] = aux.atab[(xb + tid) * aux.tabw + aux.toff + c];
+              }
             }
           }
         }
@@ -1423,8 +1445,9 @@ struct ListParams {
   // parent[k] is k's parent, pdh[k] an upper bound of d(k, parent[k])
   const float* atab;
   int64_t tabw, toff;
-  const int32_t* parent;
-  const float* pdh;
+  const int32_t* lpar;   // per entry: the listed node's parent, d(node, parent) bound, parent's key to s
+  const float* lpdh;
+  const float* lpk;
   int2* links; unsigned long long* link_cnt; unsigned long long link_cap;
   int2* unres; unsigned long long* unres_cnt; unsigned long long unres_cap;
   int2* pend; unsigned long long* pend_cnt; unsigned long long pend_cap;
@@ -1521,22 +1544,26 @@ __device__ __forceinline__ void lt_scan(const ListParams& p, int2 pr, int sd, fl
         kj[u] = j < sp.y ? p.lidx[sb + j] : -1;
       }
       int cpar[2] = {0, 0};
-      float dk[2] = {0.0f, 0.0f};
+      float dk[2] = {0.0f, 0.0f}, kcs[2] = {0.0f, 0.0f};
 #pragma unroll
       for (int u = 0; u < 2; ++u) {
         if (kj[u] >= 0) c.read += pass == 0;
         need[u] = kj[u] >= 0 && kj[u] != o && lo_b(kk[u], e) < shi && hi_b(kk[u], e) > slo;
         if (need[u] && p.atab) {
-          cpar[u] = p.parent[kj[u]];
-          dk[u] = p.pdh[kj[u]];
+          const int64_t q = sb + jb + lane + 32 * u;
+          cpar[u] = p.lpar[q];
+          dk[u] = p.lpdh[q];
+          kcs[u] = p.lpk[q];
         }
       }
       if (p.atab) {
         float kcx[2], kcy[2];
+        const float* tab_o = sd ? tab_x : tab_y;
 #pragma unroll
         for (int u = 0; u < 2; ++u) {
-          kcx[u] = need[u] ? tab_x[cpar[u]] : 0.0f;
-          kcy[u] = need[u] ? tab_y[cpar[u]] : 0.0f;
+          const float kco = need[u] ? tab_o[cpar[u]] : 0.0f;  // the parent's key to o
+          kcx[u] = sd ? kco : kcs[u];
+          kcy[u] = sd ? kcs[u] : kco;
         }
 #pragma unroll
         for (int u = 0; u < 2; ++u) {
@@ -1803,26 +1830,26 @@ static void launch_tile(const LevelIn& in, TileParams tp, int grid, cudaStream_t
 
 template <int KC>
 static void launch_range_kc(const LevelIn& in, const unsigned int* tk, int* hist, const int* lastb, const int* boff,
-                            int32_t* li, float* lk, int fill, cudaStream_t s) {
+                            int32_t* li, float* lk, int fill, cudaStream_t s, const ListAux& aux) {
   const int64_t nb = (in.n + GRNG_TILE - 1) / GRNG_TILE;
   const size_t smem = (size_t)(2 * KC * GRNG_SSTRIDE + 128 * 129) * 4 + (size_t)GRNG_HBINS * 128 * 4;
   if (in.metric == L2) {
     GRNG_CUDA(cudaFuncSetAttribute(range_sweep_kernel<KC, L2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     range_sweep_kernel<KC, L2><<<(unsigned)nb, GRNG_THREADS, smem, s>>>(in.X, in.n, in.Dp, tk, hist, lastb, boff, li,
-                                                                         lk, fill); note_launch();
+                                                                         lk, fill, aux); note_launch();
   } else {
     GRNG_CUDA(cudaFuncSetAttribute(range_sweep_kernel<KC, L1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     range_sweep_kernel<KC, L1><<<(unsigned)nb, GRNG_THREADS, smem, s>>>(in.X, in.n, in.Dp, tk, hist, lastb, boff, li,
-                                                                         lk, fill); note_launch();
+                                                                         lk, fill, aux); note_launch();
   }
   GRNG_CUDA(cudaGetLastError());
 }
 static void launch_range(const LevelIn& in, const unsigned int* tk, int* hist, const int* lastb, const int* boff,
-                         int32_t* li, float* lk, int fill, cudaStream_t s) {
+                         int32_t* li, float* lk, int fill, cudaStream_t s, const ListAux& aux) {
   const int KC = in.Dp % 32 == 0 ? 32 : (in.Dp % 16 == 0 ? 16 : 8);
-  if (KC == 32) launch_range_kc<32>(in, tk, hist, lastb, boff, li, lk, fill, s);
-  else if (KC == 16) launch_range_kc<16>(in, tk, hist, lastb, boff, li, lk, fill, s);
-  else launch_range_kc<8>(in, tk, hist, lastb, boff, li, lk, fill, s);
+  if (KC == 32) launch_range_kc<32>(in, tk, hist, lastb, boff, li, lk, fill, s, aux);
+  else if (KC == 16) launch_range_kc<16>(in, tk, hist, lastb, boff, li, lk, fill, s, aux);
+  else launch_range_kc<8>(in, tk, hist, lastb, boff, li, lk, fill, s, aux);
 }
 
 template <int G, int NQ>
@@ -1871,7 +1898,7 @@ static void finish_level(const LevelIn& in, LevelOut& out, LevelStats& st, cudaS
   const int64_t n = in.n;
   // ---- tiers 2 and 3 ---------------------------------------------------------------------
   DevBuf off, oth, tmp, links, unres, pend, amb, pflag, unres2, off2, oth2, fbuf;
-  DevBuf side, tkey, tcut, hist, lcnt, lastb, boff, lidx, lkey, unres3, atab;
+  DevBuf side, tkey, tcut, hist, lcnt, lastb, boff, lidx, lkey, lpar, lpdh, lpk, unres3, atab;
   int64_t toff[GRNG_MAXL] = {0}, tabw = 0;  // columns of the node x ancestor key table
   if (knn_idx) {
     GRNG_CUDA(off.alloc((size_t)(n + 1) * 8));
@@ -1962,7 +1989,7 @@ static void finish_level(const LevelIn& in, LevelOut& out, LevelStats& st, cudaS
       GRNG_CUDA(cudaEventRecord(l0, s));
       range_thresholds_kernel<<<(unsigned)((nun2 + 255) / 256), 256, 0, s>>>(sp); note_launch();
       GRNG_CUDA(cudaGetLastError());
-      launch_range(in, tkey.as<unsigned int>(), hist.as<int>(), nullptr, nullptr, nullptr, nullptr, 0, s);
+      launch_range(in, tkey.as<unsigned int>(), hist.as<int>(), nullptr, nullptr, nullptr, nullptr, 0, s, ListAux());
       const int lmax = in.lmax > 0 ? (int)std::min<int64_t>(in.lmax, GRNG_LCAP) : GRNG_LMAX;
       range_cut_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(tkey.as<unsigned int>(), hist.as<int>(), n,
                                                                   tcut.as<unsigned int>(), lastb.as<int>(),
@@ -1970,8 +1997,22 @@ static void finish_level(const LevelIn& in, LevelOut& out, LevelStats& st, cudaS
       GRNG_CUDA(cudaGetLastError());
       GRNG_CUDA(lidx.alloc((size_t)n * GRNG_LCAP * 4));
       GRNG_CUDA(lkey.alloc((size_t)n * GRNG_LCAP * 4));
+      ListAux aux;
+      if (atab.p && in.parent && in.pdist_hi) {
+        GRNG_CUDA(lpar.alloc((size_t)n * GRNG_LCAP * 4));
+        GRNG_CUDA(lpdh.alloc((size_t)n * GRNG_LCAP * 4));
+        GRNG_CUDA(lpk.alloc((size_t)n * GRNG_LCAP * 4));
+        aux.parent = in.parent;
+        aux.pdist = in.pdist_hi;
+        aux.atab = atab.as<float>();
+        aux.tabw = tabw;
+        aux.toff = toff[in.anc.n - 1];
+        aux.par = lpar.as<int32_t>();
+        aux.pdh = lpdh.as<float>();
+        aux.pkey = lpk.as<float>();
+      }
       launch_range(in, tkey.as<unsigned int>(), nullptr, lastb.as<int>(), boff.as<int>(), lidx.as<int32_t>(),
-                   lkey.as<float>(), 1, s);
+                   lkey.as<float>(), 1, s, aux);
       pick_side_kernel<<<(unsigned)((nun2 + 255) / 256), 256, 0, s>>>(sp); note_launch();
       GRNG_CUDA(cudaGetLastError());
       GRNG_CUDA(unres3.alloc(nun2 * 8));
@@ -1980,12 +2021,12 @@ static void finish_level(const LevelIn& in, LevelOut& out, LevelStats& st, cudaS
       lp.pairs = unres2.as<int2>(); lp.m = (int64_t)nun2; lp.side = side.as<int8_t>();
       lp.tkey = tkey.as<unsigned int>(); lp.lastb = lastb.as<int>(); lp.boff = boff.as<int>();
       lp.lidx = lidx.as<int32_t>(); lp.lkey = lkey.as<float>();
-      lp.atab = atab.p ? atab.as<float>() : nullptr;
+      lp.atab = aux.par ? atab.as<float>() : nullptr;  // the bounds need the per-entry fields
       lp.tabw = tabw;
       lp.toff = in.anc.n > 0 ? toff[in.anc.n - 1] : 0;
-      lp.parent = in.parent;
-      lp.pdh = in.pdist_hi;
-      if (!in.parent || !in.pdist_hi) lp.atab = nullptr;
+      lp.lpar = lpar.as<int32_t>();
+      lp.lpdh = lpdh.as<float>();
+      lp.lpk = lpk.as<float>();
       lp.links = links.as<int2>(); lp.link_cnt = dc + 16; lp.link_cap = cap;
       lp.unres = unres3.as<int2>(); lp.unres_cnt = dc + 27; lp.unres_cap = nun2;
       lp.pend = pend.as<int2>(); lp.pend_cnt = dc + 17; lp.pend_cap = 2 * cap;

@@ -310,7 +310,7 @@ __global__ void __launch_bounds__(256, 1) tc_sweep_kernel(TcParams p) {
       __syncthreads();
       if (*s_abort) break;
       // ---- pass 1: keys -> T16, row minima, neighbour lists (thread = row, half) ----------
-      // 8 columns per TMEM load; list insertions, rare once the lists fill, are taken out
+      // 16 columns per TMEM load; list insertions, rare once the lists fill, are taken out
       // of the unrolled part so that the loop stays small
       const float nxr = nx[r];
       float m1 = INF, m2 = INF;
@@ -318,14 +318,15 @@ __global__ void __launch_bounds__(256, 1) tc_sweep_kernel(TcParams p) {
       // lower tiles feed only the neighbour lists; full tiles need no per-key mask
       const bool full = vr && nc == 128 && !diag;
 #pragma unroll 1
-      for (int q = 0; q < 8; ++q) {
-        float g[8], vv[8];
-        tmem_ld8(trow + (uint32_t)(q * 8), g);
+      for (int q = 0; q < 4; ++q) {
+        float g[16], vv[16];
+        tmem_ld16(trow + (uint32_t)(q * 16), g);
         unsigned pm = 0;
+        const int c0 = cb + q * 16;
         if (!filt) {
 #pragma unroll
-          for (int j = 0; j < 8; ++j) {
-            const int c = cb + q * 8 + j;
+          for (int j = 0; j < 16; ++j) {
+            const int c = c0 + j;
             float v = nxr + ny[c] - 2.0f * g[j];
             if (!full && (!vr || c >= nc)) v = INF;
             vv[j] = v;
@@ -333,17 +334,23 @@ __global__ void __launch_bounds__(256, 1) tc_sweep_kernel(TcParams p) {
           }
         } else {
 #pragma unroll
-          for (int j = 0; j < 8; ++j) {
-            const int c = cb + q * 8 + j;
-            float v = nxr + ny[c] - 2.0f * g[j];
-            if (!full && (!vr || c >= nc || (diag && c == r))) v = INF;
-            vv[j] = v;
-            T16[r * 130 + c] = __float2half_ru(v);
-            if (v < m2) {
-              if (v < m1) { m2 = m1; a2 = a1; m1 = v; a1 = c; }
-              else { m2 = v; a2 = c; }
+          for (int j = 0; j < 16; j += 2) {
+            float w[2];
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+              const int c = c0 + j + u;
+              float v = nxr + ny[c] - 2.0f * g[j + u];
+              if (!full && (!vr || c >= nc || (diag && c == r))) v = INF;
+              vv[j + u] = v;
+              w[u] = v;
+              if (v < m2) {
+                if (v < m1) { m2 = m1; a2 = a1; m1 = v; a1 = c; }
+                else { m2 = v; a2 = c; }
+              }
+              if (v < thr) pm |= 1u << (j + u);
             }
-            if (v < thr) pm |= 1u << j;
+            // two keys per 4-byte store (rows of T16 start on 4-byte boundaries)
+            *reinterpret_cast<__half2*>(T16 + r * 130 + c0 + j) = __halves2half2(__float2half_ru(w[0]), __float2half_ru(w[1]));
           }
         }
         while (pm) {
@@ -351,9 +358,9 @@ __global__ void __launch_bounds__(256, 1) tc_sweep_kernel(TcParams p) {
           pm &= pm - 1u;
           float v = vv[0];
 #pragma unroll
-          for (int k = 1; k < 8; ++k)
+          for (int k = 1; k < 16; ++k)
             if (j == k) v = vv[k];
-          if (v < thr) thr = knn_insert_reg(kk, ki, v, (int)(yb + cb + q * 8 + j), K);
+          if (v < thr) thr = knn_insert_reg(kk, ki, v, (int)(yb + c0 + j), K);
         }
       }
       tc_fence_before();
@@ -423,76 +430,100 @@ __global__ void __launch_bounds__(256, 1) tc_sweep_kernel(TcParams p) {
             }
           }
         }
+        // quick test: the row minimum z = a1 of x over the column block blocks (x, y) once
+        // key(x, z) and key(z, y) (the in-block key, AY row z) are both certainly below
+        // key(x, y); uniform over the row's 64 columns, so the warp stays converged.  The
+        // columns it leaves (rare away from the diagonal) take the full test below, each
+        // lane on its own (a warp-wide step per column would run whenever any lane needs it).
+        const float A1 = hi_b(m1 + E, e);
+        const bool rq = vr && a1 >= 0;
+        const __half* AYz = AY + (rq ? a1 : 0) * 136 + cb;
 #pragma unroll 1
-        for (int q = 0; q < 8; ++q) {
-          float g[8];
-          tmem_ld8(trow + (uint32_t)(q * 8), g);
+        for (int q = 0; q < 2; ++q) {  // two chunks of 32 columns, one tensor-memory wait each
+          float g[32];
+          tmem_ld32(trow + (uint32_t)(q * 32), g);
+          unsigned nd = 0;
 #pragma unroll
-          for (int j = 0; j < 8; ++j) {
-            const int c = cb + q * 8 + j;
-            bool cand = vr && c < nc && (!diag || c > r);
-            if (cand && !all_linked) {
-              const int qy = parY[c];
-              if (qy != px) {
-                const int b = qy - (wlo << 5);
-                if (qy > px && b >= 0 && (b >> 5) < nw && nw <= 5) {
-                  const int wi = b >> 5;
-                  uint32_t w = gw[0];
+          for (int q8 = 0; q8 < 4; ++q8) {
+            const int c8 = cb + q * 32 + q8 * 8;
+            const uint4 ayw = *reinterpret_cast<const uint4*>(AYz + q * 32 + q8 * 8);
+            const __half2* ay2 = reinterpret_cast<const __half2*>(&ayw);
+            const float4 nya = *reinterpret_cast<const float4*>(ny + c8);
+            const float4 nyb = *reinterpret_cast<const float4*>(ny + c8 + 4);
+            const float nyv[8] = {nya.x, nya.y, nya.z, nya.w, nyb.x, nyb.y, nyb.z, nyb.w};
 #pragma unroll
-                  for (int k = 1; k < 5; ++k)
-                    if (wi == k) w = gw[k];
-                  cand = (w >> (b & 31)) & 1u;
-                } else {
-                  const int lo = min(px, qy), hi = max(px, qy);
-                  cand = (__ldg(p.gpar + (int64_t)lo * p.gpar_words + (hi >> 5)) >> (hi & 31)) & 1u;
+            for (int j = 0; j < 8; ++j) {
+              const int c = c8 + j;
+              bool cand = vr && c < nc && (!diag || c > r);
+              if (cand && !all_linked) {
+                const int qy = parY[c];
+                if (qy != px) {
+                  const int b = qy - (wlo << 5);
+                  if (qy > px && b >= 0 && (b >> 5) < nw && nw <= 5) {
+                    const int wi = b >> 5;
+                    uint32_t w = gw[0];
+#pragma unroll
+                    for (int k = 1; k < 5; ++k)
+                      if (wi == k) w = gw[k];
+                    cand = (w >> (b & 31)) & 1u;
+                  } else {
+                    const int lo = min(px, qy), hi = max(px, qy);
+                    cand = (__ldg(p.gpar + (int64_t)lo * p.gpar_words + (hi >> 5)) >> (hi & 31)) & 1u;
+                  }
                 }
               }
-            }
-            bool surv = false;
-            if (cand) {
-              ++st_cand;
-              const float v = nxr + ny[c] - 2.0f * g[j];
+              st_cand += cand ? 1 : 0;
+              const float v = nxr + nyv[j] - 2.0f * g[q8 * 8 + j];
               const float vlo = lo_b(v - E, e);  // below every key this pair can have
-              bool blocked = false;
-              {  // row minimum of x over the column block
-                const int z = (a1 != c) ? a1 : a2;
-                if (z >= 0) {
-                  const float a = (a1 != c) ? m1 : m2;
-                  blocked = hi_b(a + E, e) < vlo && hi_b(__half2float(AY[z * 136 + c]), e) < vlo;
-                }
-              }
-              if (!blocked) {  // column minimum of y over the row block
-                const int z = (carg1[c] != r) ? carg1[c] : carg2[c];
-                if (z >= 0) {
-                  const float b = (carg1[c] != r) ? cmin1[c] : cmin2[c];
-                  blocked = hi_b(__half2float(AX[r * 130 + z]), e) < vlo && hi_b(b + E, e) < vlo;
-                }
-              }
-              for (int t = 0; t < GRNG_KIN && !blocked; ++t) {  // neighbours of x
-                const int z = nbrXi[t * 128 + r];
-                if (z == 255) break;
-                if (diag && z == c) continue;
-                blocked = hi_b(nbrXk[t * 128 + r], e) < vlo &&
-                          hi_b(__half2float(T16[z * 130 + c]) + E, e) < vlo;
-              }
-              for (int t = 0; t < GRNG_KIN && !blocked; ++t) {  // neighbours of y
-                const int z = nbrYi[c * GRNG_KIN + t];
-                if (z == 255) break;
-                if (diag && z == r) continue;
-                blocked = hi_b(__half2float(T16[r * 130 + z]) + E, e) < vlo &&
-                          hi_b(nbrYk[c * GRNG_KIN + t], e) < vlo;
-              }
-              surv = !blocked;
+              const float2 a2f = __half22float2(ay2[j >> 1]);
+              const float ayz = (j & 1) ? a2f.y : a2f.x;
+              const bool quick = rq && c != a1 && A1 < vlo && hi_b(ayz, e) < vlo;
+              if (cand && !quick) nd |= 1u << (q8 * 8 + j);
             }
-            const unsigned sm_ = __ballot_sync(FULLMASK, surv);
-            if (sm_) {
-              unsigned long long base = 0;
-              if (lane == 0) base = atomicAdd(p.surv_cnt, (unsigned long long)__popc(sm_));
-              base = __shfl_sync(FULLMASK, base, 0);
-              if (surv) {
-                const unsigned long long pos = base + __popc(sm_ & ((1u << lane) - 1u));
-                if (pos < p.surv_cap) p.surv[pos] = make_int2((int)(xb + r), (int)(yb + c));
+          }
+          // ---- full test of the columns the quick test left, lane by lane -----------------
+          while (nd) {
+            const int jj = __ffs(nd) - 1;
+            nd &= nd - 1u;
+            const int c = cb + q * 32 + jj;
+            float gj = g[0];
+#pragma unroll
+            for (int k = 1; k < 32; ++k)
+              if (jj == k) gj = g[k];
+            const float v = nxr + ny[c] - 2.0f * gj;
+            const float vlo = lo_b(v - E, e);
+            bool blocked = false;
+            {  // row minimum of x over the column block
+              const int z = (a1 != c) ? a1 : a2;
+              if (z >= 0) {
+                const float a = (a1 != c) ? m1 : m2;
+                blocked = hi_b(a + E, e) < vlo && hi_b(__half2float(AY[z * 136 + c]), e) < vlo;
               }
+            }
+            if (!blocked) {  // column minimum of y over the row block
+              const int z = (carg1[c] != r) ? carg1[c] : carg2[c];
+              if (z >= 0) {
+                const float b = (carg1[c] != r) ? cmin1[c] : cmin2[c];
+                blocked = hi_b(__half2float(AX[r * 130 + z]), e) < vlo && hi_b(b + E, e) < vlo;
+              }
+            }
+            for (int t = 0; t < GRNG_KIN && !blocked; ++t) {  // neighbours of x
+              const int z = nbrXi[t * 128 + r];
+              if (z == 255) break;
+              if (diag && z == c) continue;
+              blocked = hi_b(nbrXk[t * 128 + r], e) < vlo &&
+                        hi_b(__half2float(T16[z * 130 + c]) + E, e) < vlo;
+            }
+            for (int t = 0; t < GRNG_KIN && !blocked; ++t) {  // neighbours of y
+              const int z = nbrYi[c * GRNG_KIN + t];
+              if (z == 255) break;
+              if (diag && z == r) continue;
+              blocked = hi_b(__half2float(T16[r * 130 + z]) + E, e) < vlo &&
+                        hi_b(nbrYk[c * GRNG_KIN + t], e) < vlo;
+            }
+            if (!blocked) {  // a survivor (rare): its own slot
+              const unsigned long long pos = atomicAdd(p.surv_cnt, 1ull);
+              if (pos < p.surv_cap) p.surv[pos] = make_int2((int)(xb + r), (int)(yb + c));
             }
           }
         }
