@@ -41,6 +41,7 @@ def parse():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--n", type=int, default=None, help="points (default: the full 1,000,000)")
     ap.add_argument("--kind", default="lin96")
+    ap.add_argument("--metric", default="l2", choices=["l2", "l1"])
     ap.add_argument("--precision", default="bf16", choices=["fp32", "bf16"],
                     help="distance tiles of the exemplar level: tensor cores (bf16) or CUDA cores (fp32)")
     ap.add_argument("--no-compare", action="store_true", help="skip the one-step plain FP32 comparison")
@@ -321,7 +322,7 @@ def tc_key_error(g, X, n=256, seed=3003):
             "max_rel_err": float((err / np.maximum(want, 1e-30))[~np.eye(S.shape[0], dtype=bool)].max())}
 
 
-def check_rows(X, E, count, seed=3004):
+def check_rows(X, E, count, seed=3004, metric=0):
     """The RNG neighbourhoods of `count` seeded points of the GPU edge list E against the
     FP64 oracle's exact rows (each row: every y tested against every z closer to x, Eq. 1),
     computed on the host's cores after the timed region."""
@@ -330,7 +331,7 @@ def check_rows(X, E, count, seed=3004):
     n = X.shape[0]
     xs = np.sort(np.random.default_rng(seed).choice(n, size=min(count, n), replace=False))
     t0 = time.perf_counter()
-    want = oracle.rng_rows(X, xs)
+    want = oracle.rng_rows(X, xs, metric)
     dt = time.perf_counter() - t0
     both = np.concatenate([E, E[:, ::-1]])
     order = np.argsort(both[:, 0], kind="stable")
@@ -345,8 +346,10 @@ def check_rows(X, E, count, seed=3004):
             "neighbours_checked": int(sum(len(r) for r in want))}
 
 
-def workload_name(kind, n, D, sizes):
-    return (f"{kind}: {n:,} x {D} FP32, intrinsic dim 8, L2, nested random pivot layers "
+def workload_name(kind, n, D, sizes, metric="l2"):
+    shape = {"lin96": "intrinsic dim 8", "lin128": "intrinsic dim 12", "mix16": "64-Gaussian mixture",
+             "uniform8": "uniform in the unit cube"}.get(kind, kind)
+    return (f"{kind}: {n:,} x {D} FP32, {shape}, {metric.upper()}, nested random pivot layers "
             f"{'/'.join(str(s) for s in sizes)}")
 
 
@@ -396,7 +399,8 @@ def run_gpu(a, rank, world, local):
         dist.init_process_group("nccl")
         pg = dist
     N0, D, sizes0, _, _ = wl.SPECS[a.kind]
-    w = wl.make(a.kind, n=a.n)
+    metric = wl.L1 if a.metric == "l1" else wl.L2
+    w = wl.make(a.kind, n=a.n, metric=metric)
     n, L = w.n, len(w.layers)
     sizes = [len(l) for l in w.layers]
     stream = torch.cuda.current_stream()
@@ -410,7 +414,8 @@ def run_gpu(a, rank, world, local):
     mlp = {"mlp_params": learned["params"], "k_shortlist": learned["k"]} if learned else {}
 
     def step_device(plain=False):
-        ix = g.Index(Xd, n_layers=L, stream=stream, precision=g.FP32 if plain else prec, **({} if plain else mlp))
+        ix = g.Index(Xd, n_layers=L, stream=stream, precision=g.FP32 if plain else prec, metric=metric,
+                     **({} if plain else mlp))
         for li in range(L - 1, -1, -1):
             ix.build_layer(li, piv_d[li], outputs=False)
         for li in range(L):
@@ -464,7 +469,7 @@ def run_gpu(a, rank, world, local):
         e_edges = 0
         e2e_steps = max(1, min(a.steps, a.e2e_steps))
         for _ in range(e2e_steps):
-            ix = g.Index(Xh, n_layers=L, stream=stream, precision=prec, **mlp)
+            ix = g.Index(Xh, n_layers=L, stream=stream, precision=prec, metric=metric, **mlp)
             for li in range(L - 1, -1, -1):
                 ix.build_layer(li, pivh[li], outputs=False)
             for li in range(L):
@@ -493,8 +498,8 @@ def run_gpu(a, rank, world, local):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
             "ms_per_step": ms / a.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "bf16+f32" if a.precision == "bf16" else "f32", "data": "synthetic",
-            "config": {"workload": workload_name(a.kind, n, D, sizes), "n": n, "dim": D, "layers": sizes,
-                       "metric": "L2", "precision": ("split-bf16 tcgen05 exemplar tiles" if a.precision == "bf16" else "fp32 tiles") + "; fp32 exact tiers; fp64 near-tie recheck",
+            "config": {"workload": workload_name(a.kind, n, D, sizes, a.metric), "n": n, "dim": D, "layers": sizes,
+                       "metric": a.metric.upper(), "precision": ("split-bf16 tcgen05 exemplar tiles" if a.precision == "bf16" else "fp32 tiles") + "; fp32 exact tiers; fp64 near-tie recheck",
                        "learned": ({k: learned[k] for k in ("k", "train_points", "samples", "positives", "train_s",
                                                             "final_loss")} if learned else None),
                        "l2_flush": "inputs larger than L2 (points alone are %d MB)" % (w.X.nbytes >> 20),
@@ -524,10 +529,10 @@ def run_gpu(a, rank, world, local):
                            "edge_set_equal": same, "speedup_vs_plain_fp32": (ms32 / (ms / a.steps)),
                            "plain_fp32_tile_ms": st32["rng_tile_ms"]}
         del e32
-    if prec == g.BF16:
+    if prec == g.BF16 and metric == wl.L2:
         line["tc_key_error"] = tc_key_error(g, w.X)
     if rank == 0 and a.check_rows > 0:
-        line["rng_row_check"] = check_rows(w.X, e_last.cpu().numpy(), a.check_rows)
+        line["rng_row_check"] = check_rows(w.X, e_last.cpu().numpy(), a.check_rows, metric=metric)
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         cb = cpu_baseline(a.kind, a.cpu_sample)
         line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
