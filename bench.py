@@ -31,6 +31,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "exact RNG edges/s at 1M pts: BF16+learned vs plain FP32, edges = oracle"
 UNIT = "edges/s"
+L2_BYTES = 129 * 1000 * 1000  # GB300 L2
 
 
 def parse():
@@ -310,7 +311,10 @@ def tc_key_error(g, X, n=256, seed=3003):
     import numpy as np
     rng = np.random.default_rng(seed)
     S = X[rng.choice(X.shape[0], size=min(n, X.shape[0]), replace=False)]
-    got = g.tc_keys(S).astype(np.float64)
+    try:
+        got = g.tc_keys(S).astype(np.float64)
+    except g.GrngError as ex:  # a diagnostic: report, never end the run
+        return {"error": str(ex)}
     S64 = S.astype(np.float64)
     nrm = (S64 ** 2).sum(1)
     want = ((S64[:, None, :] - S64[None, :, :]) ** 2).sum(-1)
@@ -443,18 +447,37 @@ def run_gpu(a, rank, world, local):
         probe = g.Index(np.zeros((1, 1), np.float32))  # its creation launches one kernel
         launches0 = probe.stats()["kernel_launches"]
         probe.close()
+    # inputs smaller than twice the L2 (129 MB) are flushed from it before every timed step:
+    # a 512 MB write outside the step's events; larger inputs stream through it anyway
+    flush = None
+    if w.X.nbytes < 2 * L2_BYTES:
+        flush = torch.empty(4 * L2_BYTES, dtype=torch.uint8, device="cuda")
+
+    def timed_steps(fn, k):
+        """k calls of fn, each bracketed by CUDA events on the launching stream (an L2 flush
+        before each, outside its events, when the inputs would fit in L2); total ms, results."""
+        tot, res = 0.0, []
+        for _ in range(k):
+            if flush is not None:
+                flush.zero_()
+            t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            t0.record(stream)
+            res.append(fn())
+            t1.record(stream)
+            t1.synchronize()
+            tot += t0.elapsed_time(t1)
+        return tot, res
+
     clk = Clocks(local)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    edges, stats, e_last = 0, None, None
-    for _ in range(a.steps):
-        ne, stats, e_last = step_device()
-        edges += ne
-    e1.record(stream)
+    tms, outs = timed_steps(step_device, a.steps)
     torch.cuda.synchronize()
     clocks = clk.stop()
+    edges = sum(o[0] for o in outs)
+    _, stats, e_last = outs[-1]
+    del outs
     launches1 = stats["kernel_launches"]  # counter after the last timed step
-    ms = max_over_ranks(e0.elapsed_time(e1), pg, "cuda")
+    barrier()
+    ms = max_over_ranks(tms, pg, "cuda")
     value = aggregate_rate(edges, world, ms)
 
     # end to end through the C ABI with host buffers: H2D of points and pivots, D2H of edges
@@ -464,11 +487,10 @@ def run_gpu(a, rank, world, local):
         pivh = [torch.from_numpy(l).pin_memory() for l in w.layers]
         eh = torch.empty((max(edges // max(a.steps, 1), 1) + 16, 2), dtype=torch.int32).pin_memory()
         barrier()
-        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        f0.record(stream)
-        e_edges = 0
         e2e_steps = max(1, min(a.steps, a.e2e_steps))
-        for _ in range(e2e_steps):
+
+        def step_host():
+            nonlocal eh
             ix = g.Index(Xh, n_layers=L, stream=stream, precision=prec, metric=metric, **mlp)
             for li in range(L - 1, -1, -1):
                 ix.build_layer(li, pivh[li], outputs=False)
@@ -479,11 +501,13 @@ def run_gpu(a, rank, world, local):
             if ne > eh.shape[0]:
                 eh = torch.empty((ne, 2), dtype=torch.int32).pin_memory()
             ix.rng_edges(out=eh)
-            e_edges += ne
             ix.close()
-        f1.record(stream)
-        torch.cuda.synchronize()
-        ems = max_over_ranks(f0.elapsed_time(f1), pg, "cuda")
+            return ne
+
+        etot, ens = timed_steps(step_host, e2e_steps)
+        barrier()
+        e_edges = sum(ens)
+        ems = max_over_ranks(etot, pg, "cuda")
         e2e = {"value": aggregate_rate(e_edges, world, ems), "unit": UNIT,
                "h2d_bytes_per_step": int(w.X.nbytes + sum(l.nbytes for l in w.layers)),
                "d2h_bytes_per_step": int(8 * (e_edges // e2e_steps)), "steps": e2e_steps,
@@ -502,7 +526,10 @@ def run_gpu(a, rank, world, local):
                        "metric": a.metric.upper(), "precision": ("split-bf16 tcgen05 exemplar tiles" if a.precision == "bf16" else "fp32 tiles") + "; fp32 exact tiers; fp64 near-tie recheck",
                        "learned": ({k: learned[k] for k in ("k", "train_points", "samples", "positives", "train_s",
                                                             "final_loss")} if learned else None),
-                       "l2_flush": "inputs larger than L2 (points alone are %d MB)" % (w.X.nbytes >> 20),
+                       "l2_flush": ("inputs larger than L2 (points alone are %d MB)" % (w.X.nbytes >> 20)
+                                    if flush is None else
+                                    "L2 flushed before every timed step (a %d MB write outside the step's events; "
+                                    "points are %d MB)" % (flush.numel() >> 20, w.X.nbytes >> 20)),
                        "parallelism": f"replicas x{world}"},
             "edges_per_step": edges // max(a.steps, 1), "roofline": roof, "clocks": clocks,
             "gpu_launches": launches1 - launches0, "e2e": e2e,
@@ -515,14 +542,11 @@ def run_gpu(a, rank, world, local):
         # BF16 + learned build's element by element on the device
         step_device(plain=True)
         barrier()
-        c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         k32 = max(1, a.plain_steps)
-        c0.record(stream)
-        for _ in range(k32):
-            ne32, st32, e32 = step_device(plain=True)
-        c1.record(stream)
-        torch.cuda.synchronize()
-        ms32 = c0.elapsed_time(c1) / k32
+        t32, o32 = timed_steps(lambda: step_device(plain=True), k32)
+        ne32, st32, e32 = o32[-1]
+        del o32
+        ms32 = t32 / k32
         same = bool(ne32 == e_last.shape[0] and torch.equal(e32, e_last))
         line["compare"] = {"plain_fp32_value": ne32 / (ms32 / 1000.0), "plain_fp32_ms_per_step": ms32,
                            "plain_fp32_steps": k32, "plain_fp32_warmup": 1, "plain_fp32_edges": ne32,
@@ -574,8 +598,13 @@ def run_insert(a, rank):
     torch.cuda.synchronize()
     build_s = time.perf_counter() - t0
     edges0 = ix.n_edges()
+    # an index smaller than twice the L2 is flushed from it before every batch (outside the
+    # batch's events); a larger one does not fit in it anyway
+    flush = torch.empty(4 * L2_BYTES, dtype=torch.uint8, device="cuda") if X.nbytes < 2 * L2_BYTES else None
     lat, at = [], n
     for b in sizes:
+        if flush is not None:
+            flush.zero_()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         ix.rng_insert_batch(Xd[at:at + b])
@@ -613,7 +642,9 @@ def run_insert(a, rank):
             "config": {"workload": f"{a.kind}: index of {n:,} x {D} FP32 + {len(sizes)} batches of the same "
                                    f"generator, L2, nested random pivot layers "
                                    f"{'/'.join(str(len(l)) for l in layers)}",
-                       "batch_sizes": sizes, "precision": a.precision}}
+                       "batch_sizes": sizes, "precision": a.precision,
+                       "l2_flush": ("L2 flushed before every batch (outside its events)" if flush is not None
+                                    else "index larger than L2 (points alone are %d MB)" % (X.nbytes >> 20))}}
     if rank == 0:
         print(json.dumps(line), flush=True)
     return 0

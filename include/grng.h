@@ -210,7 +210,7 @@ const char* grng_last_error(void);
 
 /* Diagnostic of the tensor-core distance tiles used when opts.precision = GRNG_BF16
  * (L2): keys[i*n + j] = |x_i|^2 + |x_j|^2 - 2 x_i.x_j for all pairs of n <= 256 points
- * pts[n][dim] (host or device, dim <= 96), with the dot products computed by tcgen05
+ * pts[n][dim] (host or device, dim <= 128), with the dot products computed by tcgen05
  * MMAs on split BF16 operands (x = hi + lo; hi.hi + hi.lo + lo.hi) accumulated in FP32.
  * Their absolute error is at most (2^-12 + (3*Dp + 16) 2^-24) (|x_i|^2 + |x_j|^2),
  * Dp = dim rounded up to 16.  keys may be host or device memory. */

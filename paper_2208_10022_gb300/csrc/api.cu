@@ -325,12 +325,13 @@ void level_json(std::string& js, const char* name, const LevelStats& st) {
                              "tier3_descent_blocked", "learned_pairs", "learned_candidates", "learned_tests",
                              "learned_blocked", "learned_pool_hits", "tier1_attempts", "tier23_attempts",
                              "range_both_covered", "range_unused", "range_entries_read", "tier3_cycles_top",
-                             "tier3_cycles_mid", "tier3_cycles_leaf", "tier3_pairs_mid", "tier3_probe_blocked"};
+                             "tier3_cycles_mid", "tier3_cycles_leaf", "tier3_pairs_mid", "tier3_probe_blocked",
+                             "tier1_full_tests", "probe_blocked_before_lists"};
   char buf[1024];
   js += "\"";
   js += name;
   js += "\":{";
-  for (int i = 0; i < 40; ++i) {
+  for (int i = 0; i < 42; ++i) {
     snprintf(buf, sizeof(buf), "%s\"%s\":%llu", i ? "," : "", nm[i], (unsigned long long)st.c[i]);
     js += buf;
   }

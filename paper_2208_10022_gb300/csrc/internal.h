@@ -176,7 +176,7 @@ struct LevelOut {
   int64_t n_new_gg = 0;
 };
 struct LevelStats {
-  unsigned long long c[40];
+  unsigned long long c[42];
   double ms[8];  // prep, tile sweeps, tier-2 grouping + 2a, tier 2b, range lists, tier 3, recheck + emit
   double kms[4];  // CUDA-event time of the tile sweep kernel(s), the tier-3 kernel, the list tier kernel
                   // and the whole range-list phase (thresholds, both sweeps, cut, sides, list tier)

@@ -1182,8 +1182,10 @@ __global__ void __launch_bounds__(T3P_WARPS * 32) tier3_probe_kernel(Tier3Params
     }
     if (lane == 0) {
       if (blocked) {
-        p.pend[p.slot0 + t] = pr;
-        p.pflag[p.slot0 + t] = 3;
+        if (p.pend) {  // null: a blocked pair is dropped (its bits are zero in both graphs)
+          p.pend[p.slot0 + t] = pr;
+          p.pflag[p.slot0 + t] = 3;
+        }
         ++c_blk;
       } else {
         rest[atomicAdd(nrest, 1ull)] = (int32_t)t;
@@ -1191,6 +1193,12 @@ __global__ void __launch_bounds__(T3P_WARPS * 32) tier3_probe_kernel(Tier3Params
     }
   }
   if (lane == 0 && c_blk) atomicAdd(nblocked, c_blk);
+}
+
+__global__ void gather_pairs_kernel(const int2* __restrict__ pairs, const int32_t* __restrict__ idx, int64_t m,
+                                    int2* __restrict__ out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < m) out[i] = pairs[idx[i]];
 }
 
 // node x ancestor keys: out[r * ld + c] = key(Xr[r], Xc[c]) for a 128 x 128 tile per CTA
@@ -1266,10 +1274,13 @@ struct SideParams {
   const float* rhi;
   const int2* pairs;
   int64_t m;
-  int8_t* side;               // 3: linked; 0 / 1: covered from x / y only; 4: both; 2: neither
+  int8_t* side;               // 3: linked; 0 / 1: covered from x / y only; 4 / 5: both, x's / y's annulus
+                              // the shorter; 2: neither
   unsigned int* tkey;         // [n] float bits of T_s (key units)
   const unsigned int* tcut;   // [n] float bits of T'_s
   const int* lcnt;            // [n] listed nodes
+  const int* lastb;           // [n] last listed bucket (side choice, once the lists exist)
+  const int* boff;            // [n][GRNG_HBINS + 1] bucket starts
 };
 
 __device__ __forceinline__ PairThr thr_of(const SideParams& p, int a, int b, float v, Err e) {
@@ -1291,7 +1302,31 @@ __global__ void range_thresholds_kernel(SideParams p) {
   atomicMax(p.tkey + b, __float_as_uint(P.t2hi));
 }
 
-// which sides cover the pair
+// Bucket of a key below T: 16 buckets per octave of key, 0 for everything under
+// T / 2^(127/16).  The same function (same inputs, same code) places keys in the
+// histogram and in the lists, so the bucket counts are the list's.
+__device__ __forceinline__ int hist_bin(float v, float T) {
+  const float l = log2f(fmaxf(v, 1e-37f) / T);  // < 0 for v < T
+  return max(0, min(GRNG_HBINS - 1, (int)floorf(16.0f * l) + GRNG_HBINS));
+}
+
+// Entries [first, last) of s's list whose keys may lie in (klo, khi): the buckets from
+// one below klo's to one above khi's (hist_bin carries far less than a bucket of error,
+// the FP32 brackets of the filters less again; for bounds below 1e-30 the absolute term
+// of the bracket could span buckets, so the span then runs to the end of the list).
+__device__ __forceinline__ int2 list_span(const int* lastb, const int* boff, const unsigned int* tkey, int s,
+                                          float klo, float khi) {
+  const int last = lastb[s];
+  if (last < 0 || !(khi > 0.0f)) return make_int2(0, 0);
+  const float T = __uint_as_float(tkey[s]);
+  const int b0 = klo > 1e-30f ? max(hist_bin(klo, T) - 1, 0) : 0;
+  const int b1 = khi > 1e-30f ? min(hist_bin(khi, T) + 1, last) : last;
+  if (b1 < b0) return make_int2(0, 0);
+  const int* bo = boff + (int64_t)s * (GRNG_HBINS + 1);
+  return make_int2(bo[b0], bo[b1 + 1]);
+}
+
+// which sides cover the pair; covered from both, the side whose annulus is shorter
 __global__ void pick_side_kernel(SideParams p) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= p.m || p.side[t] == 3) return;
@@ -1301,15 +1336,35 @@ __global__ void pick_side_kernel(SideParams p) {
   const PairThr P = thr_of(p, a, b, v, e);
   const bool ca = p.lcnt[a] <= GRNG_LCAP && lo_b(__uint_as_float(p.tcut[a]), e) >= P.t1hi;
   const bool cb = p.lcnt[b] <= GRNG_LCAP && lo_b(__uint_as_float(p.tcut[b]), e) >= P.t2hi;
-  p.side[t] = (int8_t)(ca && cb ? 4 : ca ? 0 : cb ? 1 : 2);
+  int sd = ca && cb ? 4 : ca ? 0 : cb ? 1 : 2;
+  if (sd == 4 && !P.quick) {
+    const float ekx = excl_key(excl_dist(v, P.t2hi, p.metric, e), p.metric);
+    const float eky = excl_key(excl_dist(v, P.t1hi, p.metric, e), p.metric);
+    const int2 ax = list_span(p.lastb, p.boff, p.tkey, a, ekx, P.t1hi);
+    const int2 ay = list_span(p.lastb, p.boff, p.tkey, b, eky, P.t2hi);
+    sd = (ay.y - ay.x) < (ax.y - ax.x) ? 5 : 4;
+  }
+  p.side[t] = (int8_t)sd;
 }
 
-// Bucket of a key below T: 16 buckets per octave of key, 0 for everything under
-// T / 2^(127/16).  The same function (same inputs, same code) places keys in the
-// histogram and in the lists, so the bucket counts are the list's.
-__device__ __forceinline__ int hist_bin(float v, float T) {
-  const float l = log2f(fmaxf(v, 1e-37f) / T);  // < 0 for v < T
-  return max(0, min(GRNG_HBINS - 1, (int)floorf(16.0f * l) + GRNG_HBINS));
+// The list tier's pairs regrouped by the endpoint whose list they scan (counting sort),
+// so that the warps at work at one time read a few lists and, the endpoints of one pair
+// being near each other in the nodes' order, a few rows of the ancestor key table.
+static __device__ __forceinline__ int scan_node(int2 pr, int sd) { return (sd == 1 || sd == 5) ? pr.y : pr.x; }
+__global__ void side_count_kernel(const int2* __restrict__ pairs, const int8_t* __restrict__ side, int64_t m,
+                                  int64_t* __restrict__ cnt) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < m) atomicAdd(reinterpret_cast<unsigned long long*>(cnt + scan_node(pairs[t], side[t])), 1ull);
+}
+__global__ void side_scatter_kernel(const int2* __restrict__ pairs, const int8_t* __restrict__ side, int64_t m,
+                                    int64_t* __restrict__ cur, int2* __restrict__ opairs, int8_t* __restrict__ oside) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= m) return;
+  const int2 pr = pairs[t];
+  const int sd = side[t];
+  const int64_t q = (int64_t)atomicAdd(reinterpret_cast<unsigned long long*>(cur + scan_node(pr, sd)), 1ull);
+  opairs[q] = pr;
+  oside[q] = (int8_t)sd;
 }
 
 // Per list entry, when the level has parents and a node x ancestor key table: the listed
@@ -1456,19 +1511,8 @@ struct ListParams {
                               // distance [5] pairs covered from both sides [7] list entries read
 };
 
-// Entries [first, last) of s's list whose keys may lie in (klo, khi): the buckets from
-// one below klo's to one above khi's (hist_bin carries far less than a bucket of error,
-// the FP32 brackets of the filters less again; for bounds below 1e-30 the absolute term
-// of the bracket could span buckets, so the span then runs to the end of the list).
 __device__ __forceinline__ int2 bucket_span(const ListParams& p, int s, float klo, float khi) {
-  const int last = p.lastb[s];
-  if (last < 0 || !(khi > 0.0f)) return make_int2(0, 0);
-  const float T = __uint_as_float(p.tkey[s]);
-  const int b0 = klo > 1e-30f ? max(hist_bin(klo, T) - 1, 0) : 0;
-  const int b1 = khi > 1e-30f ? min(hist_bin(khi, T) + 1, last) : last;
-  if (b1 < b0) return make_int2(0, 0);
-  const int* bo = p.boff + (int64_t)s * (GRNG_HBINS + 1);
-  return make_int2(bo[b0], bo[b1 + 1]);
+  return list_span(p.lastb, p.boff, p.tkey, s, klo, khi);
 }
 
 #define LT_WARPS 8
@@ -1531,30 +1575,46 @@ __device__ __forceinline__ void lt_scan(const ListParams& p, int2 pr, int sd, fl
       if (blocked || !anyamb) break;
       slot = lt_pend_slot(p, pr, lane);
     }
+    // the next 64 entries' fields are loaded while the current ones are filtered and
+    // tested, so that one chunk's loads overlap the previous chunk's work
+    float nkk[2];
+    int nkj[2], npar[2] = {0, 0};
+    float ndk[2] = {0.0f, 0.0f}, nkcs[2] = {0.0f, 0.0f};
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const int j = sp.x + lane + 32 * u;
+      nkk[u] = j < sp.y ? p.lkey[sb + j] : 0.0f;
+      nkj[u] = j < sp.y ? p.lidx[sb + j] : -1;
+      if (p.atab && j < sp.y) {
+        npar[u] = p.lpar[sb + j];
+        ndk[u] = p.lpdh[sb + j];
+        nkcs[u] = p.lpk[sb + j];
+      }
+    }
     for (int jb = sp.x; jb < sp.y; jb += 64) {
       // ---- two entries per lane: filters and bounds ----
       float kk[2];
       int kj[2];
       bool need[2];
       int stt = 0;
+      int cpar[2];
+      float dk[2], kcs[2];
 #pragma unroll
       for (int u = 0; u < 2; ++u) {
-        const int j = jb + lane + 32 * u;
-        kk[u] = j < sp.y ? p.lkey[sb + j] : 0.0f;
-        kj[u] = j < sp.y ? p.lidx[sb + j] : -1;
+        kk[u] = nkk[u]; kj[u] = nkj[u]; cpar[u] = npar[u]; dk[u] = ndk[u]; kcs[u] = nkcs[u];
+        const int j = jb + 64 + lane + 32 * u;
+        nkk[u] = j < sp.y ? p.lkey[sb + j] : 0.0f;
+        nkj[u] = j < sp.y ? p.lidx[sb + j] : -1;
+        if (p.atab && j < sp.y) {
+          npar[u] = p.lpar[sb + j];
+          ndk[u] = p.lpdh[sb + j];
+          nkcs[u] = p.lpk[sb + j];
+        }
       }
-      int cpar[2] = {0, 0};
-      float dk[2] = {0.0f, 0.0f}, kcs[2] = {0.0f, 0.0f};
 #pragma unroll
       for (int u = 0; u < 2; ++u) {
         if (kj[u] >= 0) c.read += pass == 0;
         need[u] = kj[u] >= 0 && kj[u] != o && lo_b(kk[u], e) < shi && hi_b(kk[u], e) > slo;
-        if (need[u] && p.atab) {
-          const int64_t q = sb + jb + lane + 32 * u;
-          cpar[u] = p.lpar[q];
-          dk[u] = p.lpdh[q];
-          kcs[u] = p.lpk[q];
-        }
       }
       if (p.atab) {
         float kcx[2], kcy[2];
@@ -1704,9 +1764,8 @@ __global__ void __launch_bounds__(LT_WARPS * 32, 3) list_tier_kernel(ListParams 
     // nodes within E of one endpoint cannot satisfy the other endpoint's condition
     const float ekx = excl_key(excl_dist(v, P.t2hi, p.metric, e), p.metric);
     const float eky = excl_key(excl_dist(v, P.t1hi, p.metric, e), p.metric);
-    if (sd == 4) {  // both lists cover: the shorter annulus
-      const int2 ax = bucket_span(p, x, ekx, P.t1hi), ay = bucket_span(p, y, eky, P.t2hi);
-      sd = (ay.y - ay.x) < (ax.y - ax.x) ? 1 : 0;
+    if (sd >= 4) {  // both lists cover: the shorter annulus, chosen with the sides
+      sd -= 4;
       c.both += lane == 0;
     }
     bool blocked = false, anyamb = false;
@@ -1968,6 +2027,42 @@ static void finish_level(const LevelIn& in, LevelOut& out, LevelStats& st, cudaS
       for (int a = 0; a < in.anc.n; ++a)
         launch_cross(in.X, n, in.anc.X[a], in.anc.m[a], in.Dp, in.metric, atab.as<float>() + toff[a], tabw, s);
     }
+    DevBuf prest, pkept;
+    bool probed = false;  // the descents ran: tier 3 does not repeat them
+    if (in.grng && in.lists && nun2 && atab.p && in.metric == L2) {
+      // warp-per-pair descents towards the ball around each G-lune first: a pair a node
+      // certainly blocks is dropped before the range lists are sized and scanned
+      bool dense = true;
+      for (int a = 1; a < in.anc.n; ++a) dense &= in.anc.m[a] <= 32 * T3_MKW;
+      if (dense) {
+        Tier3Params pp{};
+        pp.X = in.X; pp.n = n; pp.Dp = in.Dp; pp.metric = in.metric; pp.guide = in.grng;
+        pp.rlo = in.rlo; pp.rhi = in.rhi; pp.pairs = unres2.as<int2>(); pp.m = (int64_t)nun2;
+        pp.anc = in.anc;
+        for (int a = 0; a < in.anc.n; ++a) pp.anc.toff[a] = toff[a];
+        pp.atab = atab.as<float>(); pp.tabw = tabw; pp.dense = 1;
+        GRNG_CUDA(prest.alloc((size_t)nun2 * 4));
+        GRNG_CUDA(cudaMemsetAsync(dc + 62, 0, 2 * sizeof(unsigned long long), s));
+        const unsigned gp = (unsigned)std::min<unsigned long long>((nun2 + T3P_WARPS - 1) / T3P_WARPS,
+                                                                   (unsigned long long)8 * num_sms());
+        tier3_probe_kernel<<<gp, T3P_WARPS * 32, (size_t)T3P_WARPS * 2 * in.Dp * 4, s>>>(
+            pp, prest.as<int32_t>(), dc + 62, dc + 63); note_launch();
+        GRNG_CUDA(cudaGetLastError());
+        unsigned long long hr[2];
+        GRNG_CUDA(cudaMemcpyAsync(hr, dc + 62, sizeof(hr), cudaMemcpyDeviceToHost, s));
+        GRNG_CUDA(cudaStreamSynchronize(s));
+        st.c[41] = hr[1];  // pairs the descents block before the range lists
+        GRNG_CUDA(pkept.alloc(std::max<unsigned long long>(hr[0], 1) * 8));
+        if (hr[0])
+          gather_pairs_kernel<<<(unsigned)((hr[0] + 255) / 256), 256, 0, s>>>(
+              unres2.as<int2>(), prest.as<int32_t>(), (int64_t)hr[0], pkept.as<int2>()); note_launch();
+        GRNG_CUDA(cudaGetLastError());
+        std::swap(unres2, pkept);
+        nun2 = hr[0];
+        probed = true;
+        t3pairs = unres2.as<int2>();
+      }
+    }
     if (in.grng && in.lists && nun2) {
       // range lists for the pairs no neighbour list covers
       GRNG_CUDA(side.alloc(nun2));
@@ -1978,7 +2073,7 @@ static void finish_level(const LevelIn& in, LevelOut& out, LevelStats& st, cudaS
       GRNG_CUDA(lastb.alloc((size_t)n * 4));
       GRNG_CUDA(boff.alloc((size_t)n * (GRNG_HBINS + 1) * 4));
       GRNG_CUDA(cudaMemsetAsync(tkey.p, 0, (size_t)n * 4, s));
-      SideParams sp;
+      SideParams sp{};
       sp.X = in.X; sp.Dp = in.Dp; sp.metric = in.metric; sp.guide = in.grng; sp.K = in.K;
       sp.rlo = in.rlo; sp.rhi = in.rhi; sp.pairs = unres2.as<int2>(); sp.m = (int64_t)nun2;
       sp.side = side.as<int8_t>(); sp.tkey = tkey.as<unsigned int>(); sp.tcut = tcut.as<unsigned int>();
@@ -2013,12 +2108,29 @@ static void finish_level(const LevelIn& in, LevelOut& out, LevelStats& st, cudaS
       }
       launch_range(in, tkey.as<unsigned int>(), nullptr, lastb.as<int>(), boff.as<int>(), lidx.as<int32_t>(),
                    lkey.as<float>(), 1, s, aux);
+      sp.lastb = lastb.as<int>();
+      sp.boff = boff.as<int>();
       pick_side_kernel<<<(unsigned)((nun2 + 255) / 256), 256, 0, s>>>(sp); note_launch();
+      GRNG_CUDA(cudaGetLastError());
+      // the pairs grouped by the endpoint whose list they scan
+      DevBuf scnt, soff, spairs, sside;
+      GRNG_CUDA(scnt.alloc((size_t)(n + 1) * 8));
+      GRNG_CUDA(soff.alloc((size_t)(n + 1) * 8));
+      GRNG_CUDA(spairs.alloc(nun2 * 8));
+      GRNG_CUDA(sside.alloc(nun2));
+      GRNG_CUDA(cudaMemsetAsync(scnt.p, 0, (size_t)(n + 1) * 8, s));
+      side_count_kernel<<<(unsigned)((nun2 + 255) / 256), 256, 0, s>>>(unres2.as<int2>(), side.as<int8_t>(),
+                                                                      (int64_t)nun2, scnt.as<int64_t>()); note_launch();
+      GRNG_CUDA(cudaGetLastError());
+      exclusive_scan_i64(scnt.as<int64_t>(), soff.as<int64_t>(), n, s);
+      side_scatter_kernel<<<(unsigned)((nun2 + 255) / 256), 256, 0, s>>>(
+          unres2.as<int2>(), side.as<int8_t>(), (int64_t)nun2, soff.as<int64_t>(), spairs.as<int2>(),
+          sside.as<int8_t>()); note_launch();
       GRNG_CUDA(cudaGetLastError());
       GRNG_CUDA(unres3.alloc(nun2 * 8));
       ListParams lp;
       lp.X = in.X; lp.Dp = in.Dp; lp.metric = in.metric; lp.guide = in.grng; lp.rlo = in.rlo; lp.rhi = in.rhi;
-      lp.pairs = unres2.as<int2>(); lp.m = (int64_t)nun2; lp.side = side.as<int8_t>();
+      lp.pairs = spairs.as<int2>(); lp.m = (int64_t)nun2; lp.side = sside.as<int8_t>();
       lp.tkey = tkey.as<unsigned int>(); lp.lastb = lastb.as<int>(); lp.boff = boff.as<int>();
       lp.lidx = lidx.as<int32_t>(); lp.lkey = lkey.as<float>();
       lp.atab = aux.par ? atab.as<float>() : nullptr;  // the bounds need the per-entry fields
@@ -2150,7 +2262,7 @@ static void finish_level(const LevelIn& in, LevelOut& out, LevelStats& st, cudaS
       GRNG_CUDA(cudaEventRecord(f0, s));
       DevBuf rest;
       t3.idx = nullptr;
-      if (t3.dense && in.metric == L2 && in.anc.n > 0) {
+      if (t3.dense && in.metric == L2 && in.anc.n > 0 && !probed) {
         // warp-per-pair descents first; the exhaustive tier takes the pairs they leave
         GRNG_CUDA(rest.alloc((size_t)nun2 * 4));
         GRNG_CUDA(cudaMemsetAsync(dc + 62, 0, 2 * sizeof(unsigned long long), s));
@@ -2278,7 +2390,12 @@ void run_level(const LevelIn& in, LevelOut& out, LevelStats& st, cudaStream_t s,
 
   tick(0);
   // ---- tier 1 -------------------------------------------------------------------------
-  unsigned long long surv_cap = in.small_buffers ? 64ull : (unsigned long long)std::max<int64_t>(1 << 20, 256 * n);
+  // survivors per node: about 160 at the exemplar level of the 1M-point workloads, about
+  // 1,500 at its finest pivot layer (the overflow path repeats only the filter sweep)
+  unsigned long long surv_cap =
+      in.small_buffers ? 64ull
+                       : (unsigned long long)std::max<int64_t>(1 << 20, std::min<int64_t>((in.grng ? 2048 : 256) * n,
+                                                                                          n * (n - 1) / 2 + 1));
   const bool use_tc = !in.grng && in.precision == 1 && in.metric == L2 && tc_supported(in.Dp);
   DevBuf tcimg, tcnrm, tcbmax, knnrb;
   float nmax_all = 0.0f;
@@ -2324,7 +2441,9 @@ void run_level(const LevelIn& in, LevelOut& out, LevelStats& st, cudaStream_t s,
       L.status = reinterpret_cast<int*>(dc + 40); L.spin = in.spin;
       tc_sweep(L, s);
     } else {
-      for (int sweep = 0; sweep < (in.grng ? 2 : 1); ++sweep) {
+      // pivot layers: the lists of the first sweep are final, so a repeat after a survivor
+      // buffer overflow runs the filter sweep alone
+      for (int sweep = (in.grng && attempt > 0) ? 1 : 0; sweep < (in.grng ? 2 : 1); ++sweep) {
         if (sweep == 1) {
           GRNG_CUDA(cudaMemsetAsync(dc, 0, sizeof(unsigned long long), s));  // strip counter
           tp.mode = 2;
@@ -2361,6 +2480,7 @@ void run_level(const LevelIn& in, LevelOut& out, LevelStats& st, cudaStream_t s,
   st.c[1] = hst[1];  // quick links
   st.c[2] = nsurv;
   st.c[17] = hst[2];  // links certified from the neighbour lists in the tile
+  st.c[40] = use_tc ? hst[3] : 0;  // pairs the tensor-core sweep's quick test left to the full filter
 
   tick(1);
   finish_level(in, out, st, s, surv.as<int2>(), nsurv, knni.as<int32_t>(), knnk.as<float>(),

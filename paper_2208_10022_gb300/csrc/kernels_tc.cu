@@ -71,7 +71,7 @@ struct TcParams {
   unsigned long long* surv_cnt;
   unsigned long long surv_cap;
   int* strip_ctr;
-  unsigned long long* stats;  // [0] candidate pairs
+  unsigned long long* stats;  // [0] candidate pairs, [3] pairs taking the full filter
   int* status;                // bit 0: a bounded wait ran out
   long long spin;
 };
@@ -173,7 +173,7 @@ __global__ void __launch_bounds__(256, 1) tc_sweep_kernel(TcParams p) {
   const int64_t nb = (n + 127) / 128;
   const Err e = err_fp32(Dp);
   const float INF = finf_tc();
-  unsigned long long st_cand = 0;
+  unsigned long long st_cand = 0, st_full = 0;
 
   if (warp == 0) {
     tmem_alloc(tslot, 128);
@@ -482,6 +482,7 @@ __global__ void __launch_bounds__(256, 1) tc_sweep_kernel(TcParams p) {
             }
           }
           // ---- full test of the columns the quick test left, lane by lane -----------------
+          st_full += __popc(nd);
           while (nd) {
             const int jj = __ffs(nd) - 1;
             nd &= nd - 1u;
@@ -566,8 +567,14 @@ __global__ void __launch_bounds__(256, 1) tc_sweep_kernel(TcParams p) {
       p.knn_rb[xb + r] = lasti >= 0 ? lastk - p.gam * (nx[r] + p.nmax_all) : INF;
     }
   }
-  for (int o2 = 16; o2 > 0; o2 >>= 1) st_cand += __shfl_down_sync(FULLMASK, st_cand, o2);
-  if (lane == 0) atomicAdd(p.stats, st_cand);
+  for (int o2 = 16; o2 > 0; o2 >>= 1) {
+    st_cand += __shfl_down_sync(FULLMASK, st_cand, o2);
+    st_full += __shfl_down_sync(FULLMASK, st_full, o2);
+  }
+  if (lane == 0) {
+    atomicAdd(p.stats, st_cand);
+    atomicAdd(p.stats + 3, st_full);
+  }
   // teardown.  After a bounded wait ran out, copies into this CTA's shared memory or MMAs
   // into its tensor memory may still be in flight: wait (again bounded, far longer) for every
   // barrier with an outstanding phase before the memory is released.
@@ -729,7 +736,7 @@ void tc_knn_fix(const float* X, int64_t n, int Dp, int K, int metric, const int3
 extern "C" grng_status grng_tc_keys(const float* pts, int64_t n, int32_t dim, float* keys) {
   using namespace grng;
   try {
-    if (!pts || !keys || n < 1 || n > 256 || dim < 1 || dim > 96) fail(GRNG_EINVAL, "need 1 <= n <= 256, 1 <= dim <= 96");
+    if (!pts || !keys || n < 1 || n > 256 || dim < 1 || dim > 128) fail(GRNG_EINVAL, "need 1 <= n <= 256, 1 <= dim <= 128");
     const int Dp = ((dim + 15) / 16) * 16;
     cudaStream_t s = nullptr;
     DevBuf X, img, nrm, bmax, out, st;

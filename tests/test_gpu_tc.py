@@ -33,7 +33,7 @@ def _tc_keys(X):
     return out
 
 
-@pytest.mark.parametrize("n,d,scale", [(200, 96, 1.0), (256, 64, 10.0), (37, 16, 0.1)])
+@pytest.mark.parametrize("n,d,scale", [(200, 96, 1.0), (256, 64, 10.0), (37, 16, 0.1), (130, 128, 1.0)])
 def test_tc_tile_keys_within_bound(n, d, scale):
     rng = np.random.default_rng(n + d)
     X = (scale * rng.standard_normal((n, d))).astype(np.float32)
