@@ -78,9 +78,18 @@ struct TcParams {
 
 static __host__ __device__ constexpr size_t tc_img_bytes(int Dp) { return (size_t)128 * Dp * 4; }  // hi + lo
 static __host__ __device__ constexpr size_t tc_t16_bytes() { return (size_t)128 * 130 * 2; }
+static __host__ __device__ constexpr size_t tc_base_bytes(int Dp) {
+  return 2 * tc_img_bytes(Dp) + (tc_img_bytes(Dp) >= tc_t16_bytes() ? 0 : tc_t16_bytes()) + 33280 + 34816 +
+         128 * GRNG_KIN * 10 + 8 * 512 + 2 * 4096 + 128;
+}
+#define TC_SMEM_MAX (227 * 1024)
+#define TC_QMAX 4096  // full-filter queue entries (8 bytes each), as many as shared memory leaves room for
+static __host__ __device__ constexpr int tc_qcap(int Dp) {
+  return tc_base_bytes(Dp) >= TC_SMEM_MAX ? 0
+         : (int)((TC_SMEM_MAX - tc_base_bytes(Dp)) / 8 < TC_QMAX ? (TC_SMEM_MAX - tc_base_bytes(Dp)) / 8 : TC_QMAX);
+}
 static __host__ __device__ constexpr size_t tc_smem_bytes(int Dp, int K) {
-  return (void)K, 2 * tc_img_bytes(Dp) + (tc_img_bytes(Dp) >= tc_t16_bytes() ? 0 : tc_t16_bytes()) + 33280 + 34816 +
-                      128 * GRNG_KIN * 10 + 8 * 512 + 2 * 4096 + 128;
+  return (void)K, tc_base_bytes(Dp) + (size_t)tc_qcap(Dp) * 8;
 }
 
 // Insert (v, id) into the ascending register list kk/ki (32 slots, the first K in use)
@@ -118,6 +127,56 @@ __device__ __forceinline__ void top2_merge(float& m1, int& a1, float& m2, int& a
   } else if (b1 < m2) {
     m2 = b1; a2 = i1;
   }
+}
+
+// Shared-memory views of one tile that the full tier-1 test reads.
+struct TcTile {
+  const __half* T16;    // [128][130] keys of the tile, rounded up
+  const __half* AX;     // [128][130] in-block keys of the row block
+  const __half* AY;     // [128][136] in-block keys of the column block
+  const float* nbrXk;   // [t][row]
+  const uint8_t* nbrXi;
+  const float* nbrYk;   // [row][t]
+  const uint8_t* nbrYi;
+  const float* cmin1; const float* cmin2; const int* carg1; const int* carg2;
+  float E;
+  bool diag;
+};
+
+// Whether a tile-local interceptor certainly blocks (x = row r, y = column c) with key v:
+// the row minimum of x over the column block (the second one when the first is y), the
+// column minimum of y over the row block, the in-block neighbours of x and of y.
+// (m1, a1), (m2, a2): the two smallest keys of row r over the column block.
+__device__ __forceinline__ bool tc_full_test(const TcTile& T, int r, int c, float v, Err e, float m1, float m2,
+                                             int a1, int a2) {
+  const float vlo = lo_b(v - T.E, e);
+  {  // row minimum of x over the column block
+    const int z = (a1 != c) ? a1 : a2;
+    if (z >= 0) {
+      const float a = (a1 != c) ? m1 : m2;
+      if (hi_b(a + T.E, e) < vlo && hi_b(__half2float(T.AY[z * 136 + c]), e) < vlo) return true;
+    }
+  }
+  {  // column minimum of y over the row block
+    const int z = (T.carg1[c] != r) ? T.carg1[c] : T.carg2[c];
+    if (z >= 0) {
+      const float b = (T.carg1[c] != r) ? T.cmin1[c] : T.cmin2[c];
+      if (hi_b(__half2float(T.AX[r * 130 + z]), e) < vlo && hi_b(b + T.E, e) < vlo) return true;
+    }
+  }
+  for (int t = 0; t < GRNG_KIN; ++t) {  // neighbours of x
+    const int z = T.nbrXi[t * 128 + r];
+    if (z == 255) break;
+    if (T.diag && z == c) continue;
+    if (hi_b(T.nbrXk[t * 128 + r], e) < vlo && hi_b(__half2float(T.T16[z * 130 + c]) + T.E, e) < vlo) return true;
+  }
+  for (int t = 0; t < GRNG_KIN; ++t) {  // neighbours of y
+    const int z = T.nbrYi[c * GRNG_KIN + t];
+    if (z == 255) break;
+    if (T.diag && z == r) continue;
+    if (hi_b(__half2float(T.T16[r * 130 + z]) + T.E, e) < vlo && hi_b(T.nbrYk[c * GRNG_KIN + t], e) < vlo) return true;
+  }
+  return false;
 }
 
 // One CTA of 256 threads per SM, persistent over row strips.  Per 128 x 128 tile: one
@@ -161,9 +220,12 @@ __global__ void __launch_bounds__(256, 1) tc_sweep_kernel(TcParams p) {
   uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + o + 32);
   int* s_strip = reinterpret_cast<int*>(sm + o + 36);
   int* s_abort = reinterpret_cast<int*>(sm + o + 40);
+  int* s_qn = reinterpret_cast<int*>(sm + o + 44);               // full-filter queue length
   // per barrier: an issued copy or MMA batch not yet seen complete, and its phase parity
   int* s_pend = reinterpret_cast<int*>(sm + o + 48);
   int* s_par = s_pend + 4;
+  uint2* Q = reinterpret_cast<uint2*>(sm + o + 128);              // (row | column << 8, key bits)
+  const int qcap = tc_qcap(Dp);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int lq = warp & 3, h = warp >> 2;
@@ -256,6 +318,7 @@ __global__ void __launch_bounds__(256, 1) tc_sweep_kernel(TcParams p) {
       __syncthreads();
       if (*s_abort) break;
       if (tid == 0) {
+        *s_qn = 0;
         mbar_expect_tx(&bars[1], IMG);
         bulk_g2s(sB, p.img + (size_t)by * IMG, IMG, &bars[1]);
         s_pend[1] = 1;
@@ -430,13 +493,19 @@ __global__ void __launch_bounds__(256, 1) tc_sweep_kernel(TcParams p) {
             }
           }
         }
+        // the whole tile's row minima, for the full tests of any thread (the other half read
+        // its slot of rowx before the last barrier)
+        if (h == 0) rowx[r] = make_float4(m1, m2, __int_as_float(a1), __int_as_float(a2));
         // quick test: the row minimum z = a1 of x over the column block blocks (x, y) once
         // key(x, z) and key(z, y) (the in-block key, AY row z) are both certainly below
-        // key(x, y); uniform over the row's 64 columns, so the warp stays converged.  The
-        // columns it leaves (rare away from the diagonal) take the full test below, each
-        // lane on its own (a warp-wide step per column would run whenever any lane needs it).
+        // key(x, y); uniform over the row's 64 columns, so the warp stays converged.  (For
+        // y = z the test fails by itself: key(x, z) cannot be certainly below itself.)  The
+        // columns it leaves go to a queue that all 256 threads share once the tile's TMEM has
+        // been read, so that no warp waits for another's divergent tests.
         const float A1 = hi_b(m1 + E, e);
         const bool rq = vr && a1 >= 0;
+        const bool fast = vr && nc == 128 && !diag && all_linked;  // every column a candidate
+        if (fast) st_cand += 64;
         const __half* AYz = AY + (rq ? a1 : 0) * 136 + cb;
 #pragma unroll 1
         for (int q = 0; q < 2; ++q) {  // two chunks of 32 columns, one tensor-memory wait each
@@ -454,35 +523,50 @@ __global__ void __launch_bounds__(256, 1) tc_sweep_kernel(TcParams p) {
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
               const int c = c8 + j;
-              bool cand = vr && c < nc && (!diag || c > r);
-              if (cand && !all_linked) {
-                const int qy = parY[c];
-                if (qy != px) {
-                  const int b = qy - (wlo << 5);
-                  if (qy > px && b >= 0 && (b >> 5) < nw && nw <= 5) {
-                    const int wi = b >> 5;
-                    uint32_t w = gw[0];
+              bool cand = true;
+              if (!fast) {
+                cand = vr && c < nc && (!diag || c > r);
+                if (cand && !all_linked) {
+                  const int qy = parY[c];
+                  if (qy != px) {
+                    const int b = qy - (wlo << 5);
+                    if (qy > px && b >= 0 && (b >> 5) < nw && nw <= 5) {
+                      const int wi = b >> 5;
+                      uint32_t w = gw[0];
 #pragma unroll
-                    for (int k = 1; k < 5; ++k)
-                      if (wi == k) w = gw[k];
-                    cand = (w >> (b & 31)) & 1u;
-                  } else {
-                    const int lo = min(px, qy), hi = max(px, qy);
-                    cand = (__ldg(p.gpar + (int64_t)lo * p.gpar_words + (hi >> 5)) >> (hi & 31)) & 1u;
+                      for (int k = 1; k < 5; ++k)
+                        if (wi == k) w = gw[k];
+                      cand = (w >> (b & 31)) & 1u;
+                    } else {
+                      const int lo = min(px, qy), hi = max(px, qy);
+                      cand = (__ldg(p.gpar + (int64_t)lo * p.gpar_words + (hi >> 5)) >> (hi & 31)) & 1u;
+                    }
                   }
                 }
+                st_cand += cand ? 1 : 0;
               }
-              st_cand += cand ? 1 : 0;
               const float v = nxr + nyv[j] - 2.0f * g[q8 * 8 + j];
               const float vlo = lo_b(v - E, e);  // below every key this pair can have
               const float2 a2f = __half22float2(ay2[j >> 1]);
               const float ayz = (j & 1) ? a2f.y : a2f.x;
-              const bool quick = rq && c != a1 && A1 < vlo && hi_b(ayz, e) < vlo;
+              const bool quick = rq && fmaxf(A1, hi_b(ayz, e)) < vlo;
               if (cand && !quick) nd |= 1u << (q8 * 8 + j);
             }
           }
-          // ---- full test of the columns the quick test left, lane by lane -----------------
-          st_full += __popc(nd);
+          // ---- the columns the quick test left: queued (key from the registers) -----------
+          const int cnt = __popc(nd);
+          st_full += cnt;
+          int incl = cnt;
+#pragma unroll
+          for (int o2 = 1; o2 < 32; o2 <<= 1) {
+            const int y2 = __shfl_up_sync(FULLMASK, incl, o2);
+            if (lane >= o2) incl += y2;
+          }
+          int base = 0;
+          const int wtot = __shfl_sync(FULLMASK, incl, 31);
+          if (lane == 31 && wtot) base = atomicAdd(s_qn, wtot);
+          base = __shfl_sync(FULLMASK, base, 31);
+          int pos = base + incl - cnt;
           while (nd) {
             const int jj = __ffs(nd) - 1;
             nd &= nd - 1u;
@@ -492,39 +576,45 @@ __global__ void __launch_bounds__(256, 1) tc_sweep_kernel(TcParams p) {
             for (int k = 1; k < 32; ++k)
               if (jj == k) gj = g[k];
             const float v = nxr + ny[c] - 2.0f * gj;
-            const float vlo = lo_b(v - E, e);
-            bool blocked = false;
-            {  // row minimum of x over the column block
-              const int z = (a1 != c) ? a1 : a2;
-              if (z >= 0) {
-                const float a = (a1 != c) ? m1 : m2;
-                blocked = hi_b(a + E, e) < vlo && hi_b(__half2float(AY[z * 136 + c]), e) < vlo;
+            if (pos < qcap) {
+              Q[pos] = make_uint2((unsigned)r | ((unsigned)c << 8), __float_as_uint(v));
+            } else {  // queue full (near the diagonal): this lane tests the pair itself
+              const TcTile Tt{T16, AX, AY, nbrXk, nbrXi, nbrYk, nbrYi, cmin1, cmin2, carg1, carg2, E, diag};
+              if (!tc_full_test(Tt, r, c, v, e, m1, m2, a1, a2)) {
+                const unsigned long long sp = atomicAdd(p.surv_cnt, 1ull);
+                if (sp < p.surv_cap) p.surv[sp] = make_int2((int)(xb + r), (int)(yb + c));
               }
             }
-            if (!blocked) {  // column minimum of y over the row block
-              const int z = (carg1[c] != r) ? carg1[c] : carg2[c];
-              if (z >= 0) {
-                const float b = (carg1[c] != r) ? cmin1[c] : cmin2[c];
-                blocked = hi_b(__half2float(AX[r * 130 + z]), e) < vlo && hi_b(b + E, e) < vlo;
+            ++pos;
+          }
+        }
+        tc_fence_before();
+        __syncthreads();
+        // ---- the queued full tests, shared by all threads; survivors by warp ------------
+        {
+          const int qn = min(*s_qn, qcap);
+          const TcTile Tt{T16, AX, AY, nbrXk, nbrXi, nbrYk, nbrYi, cmin1, cmin2, carg1, carg2, E, diag};
+          for (int i0 = 0; i0 < qn; i0 += 256) {
+            const int i = i0 + tid;
+            bool sv = false;
+            int sr = 0, sc = 0;
+            if (i < qn) {
+              const uint2 it = Q[i];
+              sr = (int)(it.x & 255u);
+              sc = (int)(it.x >> 8);
+              const float4 rm = rowx[sr];
+              sv = !tc_full_test(Tt, sr, sc, __uint_as_float(it.y), e, rm.x, rm.y, __float_as_int(rm.z),
+                                 __float_as_int(rm.w));
+            }
+            const unsigned bm = __ballot_sync(FULLMASK, sv);
+            if (bm) {
+              unsigned long long b0 = 0;
+              if (lane == 0) b0 = atomicAdd(p.surv_cnt, (unsigned long long)__popc(bm));
+              b0 = __shfl_sync(FULLMASK, b0, 0);
+              if (sv) {
+                const unsigned long long sp = b0 + (unsigned long long)__popc(bm & ((1u << lane) - 1u));
+                if (sp < p.surv_cap) p.surv[sp] = make_int2((int)(xb + sr), (int)(yb + sc));
               }
-            }
-            for (int t = 0; t < GRNG_KIN && !blocked; ++t) {  // neighbours of x
-              const int z = nbrXi[t * 128 + r];
-              if (z == 255) break;
-              if (diag && z == c) continue;
-              blocked = hi_b(nbrXk[t * 128 + r], e) < vlo &&
-                        hi_b(__half2float(T16[z * 130 + c]) + E, e) < vlo;
-            }
-            for (int t = 0; t < GRNG_KIN && !blocked; ++t) {  // neighbours of y
-              const int z = nbrYi[c * GRNG_KIN + t];
-              if (z == 255) break;
-              if (diag && z == r) continue;
-              blocked = hi_b(__half2float(T16[r * 130 + z]) + E, e) < vlo &&
-                        hi_b(nbrYk[c * GRNG_KIN + t], e) < vlo;
-            }
-            if (!blocked) {  // a survivor (rare): its own slot
-              const unsigned long long pos = atomicAdd(p.surv_cnt, 1ull);
-              if (pos < p.surv_cap) p.surv[pos] = make_int2((int)(xb + r), (int)(yb + c));
             }
           }
         }
