@@ -138,7 +138,8 @@ def kernel_rooflines(stats, n, D, precision, peaks, sms):
       FP32 tiles (CUDA cores): 2*D lane instructions (subtract + FMA) per unordered pair;
       tier 3: 2 distances (to both endpoints) x 2*D lane instructions per node tested;
       range-list tier: 8 bytes (node id and key) per list entry read, plus one padded row
-      (4*Dp bytes) per listed node tested by distance -- a streaming bound against HBM.
+      (4*Dp bytes) per listed node tested by distance -- a streaming bound against HBM;
+      assignment: 2*D flops (tensor cores) or lane instructions (FP32 tiles) per (member, pivot).
     Peaks: bf16 sustained tensor rate from MEASURED_PEAKS.json (the kernels run inside a
     long step); FP32 lanes: SMs x 128 x the maximum SM clock (derived)."""
     sm_max = peaks.get("sm_max_mhz", 2070.0)
@@ -171,6 +172,17 @@ def kernel_rooflines(stats, n, D, precision, peaks, sms):
             pairs * 2 * D, "Gop/s", alu, alu_src)
     add("tier3_kernel (exemplar level)", "alu", km.get("tier3", 0),
         stats["rng"]["tier3_nodes_tested"] * 2 * 2 * D, "Gop/s", alu, alu_src)
+    nmem = n
+    for L in reversed(stats["layers"]):  # finest first: its members are the points
+        m = L["m"]
+        if L.get("assign_kernel_ms", 0) > 0:
+            if L.get("assign_tensor_cores"):
+                add(f"tc_assign_kernel (pivot layer m={m}, members {nmem})", "tensor", L["assign_kernel_ms"],
+                    nmem * m * 2 * D, "TFLOP/s", bf, bf_src)
+            else:
+                add(f"assign_tile_kernel (pivot layer m={m}, members {nmem})", "alu", L["assign_kernel_ms"],
+                    nmem * m * 2 * D, "Gop/s", alu, alu_src)
+        nmem = m
     for L in stats["layers"]:
         m, G = L["m"], L["grng"]
         k = G.get("kernel_ms", {})

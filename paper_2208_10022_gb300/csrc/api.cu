@@ -100,8 +100,8 @@ struct Layer {
   DevBuf gx, gg;
   int64_t words = 0;
   LevelStats st{};
-  double assign_ms = 0, link_ms = 0, link_tile_ms = 0;
-  unsigned long long assign_amb = 0, assign_fp64 = 0;
+  double assign_ms = 0, link_ms = 0, link_tile_ms = 0, assign_kernel_ms = 0;
+  unsigned long long assign_amb = 0, assign_fp64 = 0, assign_tc = 0, assign_full = 0;
 };
 
 struct Timer {
@@ -474,11 +474,15 @@ grng_status grng_build_layer(grng_index* ix, int32_t layer, const int32_t* pivot
     GRNG_CUDA(ly.radius.alloc((size_t)m * 8));
     GRNG_CUDA(ly.delta.alloc((size_t)m * 8));
     AssignOut ao{ly.assign.as<int32_t>(), ly.mdist.as<double>(), ly.radius.as<double>(), ly.delta.as<double>()};
-    unsigned long long ast[2] = {0, 0};
+    unsigned long long ast[5] = {0, 0, 0, 0, 0};
     assign_layer(Xmem, mem_id, mem_r, nmem, ly.Xp.as<float>(), ly.piv.as<int32_t>(), m, ix->n, ix->D, ix->Dp,
-                 ix->metric, ao, ast, s);
+                 ix->metric, ao, ast, s, ix->opts.precision == GRNG_BF16,
+                 ix->opts.spin_limit > 0 ? ix->opts.spin_limit : 1ll << 24);
     ly.assign_amb = ast[0];
     ly.assign_fp64 = ast[1];
+    ly.assign_kernel_ms = (double)ast[2] / 1000.0;
+    ly.assign_tc = ast[3];
+    ly.assign_full = ast[4];
     ly.built = true;
     ly.assign_ms = tm.stop();
     copy_out(assign, ly.assign.p, (size_t)nmem * 4, s);
@@ -705,7 +709,8 @@ grng_status rng_insert_batch(grng_index* ix, const float* pts, int64_t m) {
       GRNG_CUDA(ddb.alloc((size_t)M * 8));
       AssignOut ao{ab.as<int32_t>(), db.as<double>(), rb.as<double>(), ddb.as<double>()};
       assign_layer(ix->X.as<float>() + n0 * Dp, ix->ids.as<int32_t>() + n0, nullptr, m, fin.Xp.as<float>(),
-                   fin.piv.as<int32_t>(), M, n1, D, Dp, metric, ao, nullptr, s);
+                   fin.piv.as<int32_t>(), M, n1, D, Dp, metric, ao, nullptr, s, ix->opts.precision == GRNG_BF16,
+                   ix->opts.spin_limit > 0 ? ix->opts.spin_limit : 1ll << 24);
       GRNG_CUDA(a2.alloc((size_t)n1 * 4));
       GRNG_CUDA(d2.alloc((size_t)n1 * 8));
       GRNG_CUDA(cudaMemcpyAsync(a2.p, fin.assign.p, (size_t)n0 * 4, cudaMemcpyDeviceToDevice, s));
@@ -935,9 +940,9 @@ grng_status grng_stats(const grng_index* cix, char* json, size_t cap) {
     const Layer& ly = ix->layers[l];
     snprintf(buf, sizeof(buf),
              "%s{\"m\":%lld,\"built\":%d,\"linked\":%d,\"assign_ms\":%.4f,\"link_ms\":%.4f,\"link_tile_ms\":%.4f,"
-             "\"assign_ambiguous\":%llu,\"assign_fp64_keys\":%llu,",
+             "\"assign_ambiguous\":%llu,\"assign_fp64_keys\":%llu,\"assign_kernel_ms\":%.4f,\"assign_tensor_cores\":%llu,\"assign_full_rechecks\":%llu,",
              l ? "," : "", (long long)ly.m, (int)ly.built, (int)ly.linked, ly.assign_ms, ly.link_ms,
-             ly.link_tile_ms, ly.assign_amb, ly.assign_fp64);
+             ly.link_tile_ms, ly.assign_amb, ly.assign_fp64, ly.assign_kernel_ms, ly.assign_tc, ly.assign_full);
     js += buf;
     level_json(js, "grng", ly.st);
     js += "}";

@@ -82,10 +82,12 @@ struct AssignOut {
 };
 // members: contiguous coordinates [nmem][Dp] (mem_id = their point indices, for the
 // self-assignment rule); pivots: contiguous coordinates [m][Dp] (piv_id point indices)
+// tc: the member x pivot keys from the tensor cores (L2, at least 256 pivots; split-BF16
+// Gram keys with their error bound, the undecided members re-decided exactly), else FP32 tiles
 void assign_layer(const float* Xmem, const int32_t* mem_id, const double* mem_r, int64_t nmem,
                   const float* Xpiv, const int32_t* piv_id, int64_t m, int64_t npoints, int D,
                   int Dp, int metric, const AssignOut& out, unsigned long long* stats,
-                  cudaStream_t s);
+                  cudaStream_t s, bool tc = false, long long spin = 1ll << 24);
 
 // ---- pair pipeline (kernels_pair.cu) ----------------------------------------------------
 #define GRNG_MAXL 16
@@ -155,6 +157,12 @@ float tc_gamma(int Dp);
 void tc_prepare(const float* X, int64_t n, int Dp, DevBuf& img, DevBuf& nrm, DevBuf& bmax, float* nmax_all,
                 cudaStream_t s);
 void tc_sweep(const TcLaunch& L, cudaStream_t s);
+// nearest pivot by split-BF16 Gram keys, per member: best1 (upper bound of the smallest
+// exact key), arg1, best2 (lower bound of every other pivot's exact key), cand[4] (the
+// pivots of the 4 smallest Gram keys) and rest (lower bound of every other pivot's exact key)
+void tc_assign(const float* Xm, int64_t nmem, const float* Xp, int64_t m, int Dp, float* best1, int32_t* arg1,
+               float* best2, int32_t* cand, float* rest, long long spin, cudaStream_t s,
+               cudaEvent_t start = nullptr, cudaEvent_t done = nullptr);  // events around the kernel, if given
 void tc_knn_fix(const float* X, int64_t n, int Dp, int K, int metric, const int32_t* knn_idx, float* knn_key,
                 cudaStream_t s);
 // children ranges: parent[] (non-decreasing, values in [0, m)) -> cstart[m+1]

@@ -123,6 +123,47 @@ __global__ void assign_recheck_kernel(const float* __restrict__ Xm, const float*
   atomicAdd(n64, cnt);
 }
 
+// Tensor-core form: an undecided member whose four listed pivots include every pivot that
+// could be nearest (every other pivot's key certainly above the smallest listed one's) is
+// decided among those four -- FP32 keys with their brackets, canonical FP64 keys where the
+// brackets overlap, ties to the lowest pivot position; the others go to the full recheck.
+__global__ void assign_cand_kernel(const float* __restrict__ Xm, const float* __restrict__ Xp, int D, int Dp,
+                                   int metric, const int32_t* __restrict__ amb, int64_t namb,
+                                   const float* __restrict__ best1, const int32_t* __restrict__ cand,
+                                   const float* __restrict__ rest, int32_t* __restrict__ assign,
+                                   int32_t* __restrict__ amb2, unsigned long long* __restrict__ n2,
+                                   unsigned long long* __restrict__ n64) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= namb) return;
+  const int64_t t = amb[i];
+  const Err e = err_fp32(Dp);
+  const float lim = hi_b(best1[t], e);  // at least the smallest exact key
+  if (!(rest[t] > lim)) {
+    amb2[atomicAdd(n2, 1ull)] = (int32_t)t;
+    return;
+  }
+  const float* x = Xm + t * Dp;
+  float k32[4];
+  float m32 = __int_as_float(0x7f800000);
+  for (int k = 0; k < 4; ++k) {
+    const int j = cand[t * 4 + k];
+    k32[k] = j >= 0 ? key32(x, Xp + (int64_t)j * Dp, Dp, metric) : __int_as_float(0x7f800000);
+    m32 = fminf(m32, hi_b(k32[k], e));
+  }
+  double bk = 0.0;
+  int bi = -1;
+  unsigned long long c64 = 0;
+  for (int k = 0; k < 4; ++k) {
+    const int j = cand[t * 4 + k];
+    if (j < 0 || lo_b(k32[k], e) > m32) continue;  // certainly above another candidate's key
+    const double kk = key64(x, Xp + (int64_t)j * Dp, D, metric);
+    ++c64;
+    if (bi < 0 || kk < bk || (kk == bk && j < bi)) { bk = kk; bi = j; }
+  }
+  assign[t] = bi;
+  atomicAdd(n64, c64);
+}
+
 __global__ void member_dist_kernel(const float* __restrict__ Xm, const float* __restrict__ Xp,
                                    const double* __restrict__ mem_r, int64_t nmem, int D, int Dp,
                                    int metric, const int32_t* __restrict__ assign,
@@ -161,9 +202,10 @@ static void launch_assign_tile(const float* Xm, int64_t nmem, const float* Xp, i
 
 void assign_layer(const float* Xmem, const int32_t* mem_id, const double* mem_r, int64_t nmem,
                   const float* Xpiv, const int32_t* piv_id, int64_t m, int64_t npoints, int D, int Dp,
-                  int metric, const AssignOut& out, unsigned long long* stats, cudaStream_t s) {
+                  int metric, const AssignOut& out, unsigned long long* stats, cudaStream_t s, bool tc,
+                  long long spin) {
   if (nmem == 0 || m == 0) return;
-  DevBuf pivpos, b1, a1, b2, amb, cnt;
+  DevBuf pivpos, b1, a1, b2, amb, cnt, cand, rest, amb2;
   GRNG_CUDA(pivpos.alloc((size_t)npoints * 4));
   GRNG_CUDA(cudaMemsetAsync(pivpos.p, 0xff, (size_t)npoints * 4, s));
   pivpos_kernel<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(piv_id, m, pivpos.as<int32_t>()); note_launch();
@@ -171,12 +213,29 @@ void assign_layer(const float* Xmem, const int32_t* mem_id, const double* mem_r,
   GRNG_CUDA(a1.alloc((size_t)nmem * 4));
   GRNG_CUDA(b2.alloc((size_t)nmem * 4));
   GRNG_CUDA(amb.alloc((size_t)nmem * 4));
-  GRNG_CUDA(cnt.alloc(16));
-  GRNG_CUDA(cudaMemsetAsync(cnt.p, 0, 16, s));
+  GRNG_CUDA(cnt.alloc(32));
+  GRNG_CUDA(cudaMemsetAsync(cnt.p, 0, 32, s));
   const int KC = Dp % 32 == 0 ? 32 : (Dp % 16 == 0 ? 16 : 8);
-  if (KC == 32) launch_assign_tile<32>(Xmem, nmem, Xpiv, m, Dp, metric, b1.as<float>(), a1.as<int32_t>(), b2.as<float>(), s);
+  const bool use_tc = tc && metric == L2 && tc_supported(Dp) && m >= 256;  // two pivot blocks or more
+  cudaEvent_t k0, k1;  // the member x pivot key kernel, on the launching stream
+  GRNG_CUDA(cudaEventCreate(&k0));
+  GRNG_CUDA(cudaEventCreate(&k1));
+  if (!use_tc) GRNG_CUDA(cudaEventRecord(k0, s));
+  if (use_tc) {
+    GRNG_CUDA(cand.alloc((size_t)nmem * 16));
+    GRNG_CUDA(rest.alloc((size_t)nmem * 4));
+    tc_assign(Xmem, nmem, Xpiv, m, Dp, b1.as<float>(), a1.as<int32_t>(), b2.as<float>(), cand.as<int32_t>(),
+              rest.as<float>(), spin, s, k0, k1);
+  }
+  else if (KC == 32) launch_assign_tile<32>(Xmem, nmem, Xpiv, m, Dp, metric, b1.as<float>(), a1.as<int32_t>(), b2.as<float>(), s);
   else if (KC == 16) launch_assign_tile<16>(Xmem, nmem, Xpiv, m, Dp, metric, b1.as<float>(), a1.as<int32_t>(), b2.as<float>(), s);
   else launch_assign_tile<8>(Xmem, nmem, Xpiv, m, Dp, metric, b1.as<float>(), a1.as<int32_t>(), b2.as<float>(), s);
+  if (!use_tc) GRNG_CUDA(cudaEventRecord(k1, s));
+  GRNG_CUDA(cudaEventSynchronize(k1));
+  float kms = 0.0f;
+  GRNG_CUDA(cudaEventElapsedTime(&kms, k0, k1));
+  cudaEventDestroy(k0);
+  cudaEventDestroy(k1);
   unsigned long long* dc = cnt.as<unsigned long long>();
   assign_decide_kernel<<<(unsigned)((nmem + 255) / 256), 256, 0, s>>>(
       mem_id, nmem, pivpos.as<int32_t>(), b1.as<float>(), a1.as<int32_t>(), b2.as<float>(), Dp, out.assign,
@@ -185,9 +244,21 @@ void assign_layer(const float* Xmem, const int32_t* mem_id, const double* mem_r,
   unsigned long long namb = 0;
   GRNG_CUDA(cudaMemcpyAsync(&namb, dc, 8, cudaMemcpyDeviceToHost, s));
   GRNG_CUDA(cudaStreamSynchronize(s));
+  const int32_t* full = amb.as<int32_t>();  // members re-decided against every pivot
+  if (namb && use_tc) {
+    GRNG_CUDA(amb2.alloc((size_t)namb * 4));
+    GRNG_CUDA(cudaMemsetAsync(dc + 2, 0, 8, s));
+    assign_cand_kernel<<<(unsigned)((namb + 127) / 128), 128, 0, s>>>(
+        Xmem, Xpiv, D, Dp, metric, amb.as<int32_t>(), (int64_t)namb, b1.as<float>(), cand.as<int32_t>(),
+        rest.as<float>(), out.assign, amb2.as<int32_t>(), dc + 2, dc + 1); note_launch();
+    GRNG_CUDA(cudaGetLastError());
+    GRNG_CUDA(cudaMemcpyAsync(&namb, dc + 2, 8, cudaMemcpyDeviceToHost, s));
+    GRNG_CUDA(cudaStreamSynchronize(s));
+    full = amb2.as<int32_t>();
+  }
   if (namb) {
-    assign_recheck_kernel<<<(unsigned)namb, 256, 0, s>>>(Xmem, Xpiv, m, D, Dp, metric, amb.as<int32_t>(),
-                                                         b1.as<float>(), out.assign, dc + 1); note_launch();
+    assign_recheck_kernel<<<(unsigned)namb, 256, 0, s>>>(Xmem, Xpiv, m, D, Dp, metric, full, b1.as<float>(),
+                                                         out.assign, dc + 1); note_launch();
     GRNG_CUDA(cudaGetLastError());
   }
   GRNG_CUDA(cudaMemsetAsync(out.radius, 0, (size_t)m * 8, s));
@@ -202,6 +273,12 @@ void assign_layer(const float* Xmem, const int32_t* mem_id, const double* mem_r,
     GRNG_CUDA(cudaStreamSynchronize(s));
     stats[0] += h[0];  // ambiguous members
     stats[1] += h[1];  // FP64 member-pivot keys
+    stats[2] += (unsigned long long)(kms * 1000.0f);  // key kernel, microseconds
+    stats[3] = use_tc ? 1 : 0;
+    unsigned long long hf = 0;
+    if (use_tc) GRNG_CUDA(cudaMemcpyAsync(&hf, dc + 2, 8, cudaMemcpyDeviceToHost, s));
+    GRNG_CUDA(cudaStreamSynchronize(s));
+    stats[4] += hf;  // members re-decided against every pivot
   }
   GRNG_CUDA(cudaStreamSynchronize(s));
 }

@@ -1089,20 +1089,23 @@ __global__ void __launch_bounds__(T3_T, T3_MINB) tier3_kernel(Tier3Params p) {
 #define T3P_WARPS 8
 __global__ void __launch_bounds__(T3P_WARPS * 32) tier3_probe_kernel(Tier3Params p, int32_t* __restrict__ rest,
                                                                      unsigned long long* __restrict__ nrest,
-                                                                     unsigned long long* __restrict__ nblocked) {
+                                                                     unsigned long long* __restrict__ nblocked,
+                                                                     unsigned long long* __restrict__ next) {
   extern __shared__ __align__(16) float t3p_sm[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int l8 = lane & 7;
   const unsigned gmask = 0xffu << (lane & 24);
   float* gs = t3p_sm + wib * 2 * p.Dp;
   float* os = gs + p.Dp;
-  const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const Err e = err_fp32(p.Dp);
   const float u2 = 1.1920928955078125e-07f;
   const int na = p.anc.n;
   unsigned long long c_blk = 0;
-  for (int64_t t = wid; t < p.m; t += nw) {
+  for (;;) {  // pairs in order, from an atomic counter (neighbouring pairs share table rows)
+    unsigned long long tt = 0;
+    if (lane == 0) tt = atomicAdd(next, 1ull);
+    const int64_t t = (int64_t)__shfl_sync(FULLMASK, tt, 0);
+    if (t >= p.m) break;
     const int2 pr = p.pairs[t];
     const int64_t g = pr.x, o = pr.y;
     __syncwarp();
@@ -1347,22 +1350,29 @@ __global__ void pick_side_kernel(SideParams p) {
   p.side[t] = (int8_t)sd;
 }
 
-// The list tier's pairs regrouped by the endpoint whose list they scan (counting sort),
-// so that the warps at work at one time read a few lists and, the endpoints of one pair
-// being near each other in the nodes' order, a few rows of the ancestor key table.
+// The list tier's pairs regrouped (counting sort) by the block of 256 (or more) nodes of the
+// endpoint whose list they scan and the block of the other endpoint, and handed to the warps
+// in that order by an atomic counter: the warps at work at one time then read a few lists
+// and a few rows of the ancestor key table, which stay in L2.
 static __device__ __forceinline__ int scan_node(int2 pr, int sd) { return (sd == 1 || sd == 5) ? pr.y : pr.x; }
+// group key: (block of the scanned node, block of the other node), blocks of `bs` nodes
+static __device__ __forceinline__ int64_t side_key(int2 pr, int sd, int bs, int64_t nbk) {
+  const int sn = scan_node(pr, sd), on = (sn == pr.x) ? pr.y : pr.x;
+  return (int64_t)(sn / bs) * nbk + on / bs;
+}
 __global__ void side_count_kernel(const int2* __restrict__ pairs, const int8_t* __restrict__ side, int64_t m,
-                                  int64_t* __restrict__ cnt) {
+                                  int64_t* __restrict__ cnt, int bs, int64_t nbk) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t < m) atomicAdd(reinterpret_cast<unsigned long long*>(cnt + scan_node(pairs[t], side[t])), 1ull);
+  if (t < m) atomicAdd(reinterpret_cast<unsigned long long*>(cnt + side_key(pairs[t], side[t], bs, nbk)), 1ull);
 }
 __global__ void side_scatter_kernel(const int2* __restrict__ pairs, const int8_t* __restrict__ side, int64_t m,
-                                    int64_t* __restrict__ cur, int2* __restrict__ opairs, int8_t* __restrict__ oside) {
+                                    int64_t* __restrict__ cur, int2* __restrict__ opairs, int8_t* __restrict__ oside,
+                                    int bs, int64_t nbk) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= m) return;
   const int2 pr = pairs[t];
   const int sd = side[t];
-  const int64_t q = (int64_t)atomicAdd(reinterpret_cast<unsigned long long*>(cur + scan_node(pr, sd)), 1ull);
+  const int64_t q = (int64_t)atomicAdd(reinterpret_cast<unsigned long long*>(cur + side_key(pr, sd, bs, nbk)), 1ull);
   opairs[q] = pr;
   oside[q] = (int8_t)sd;
 }
@@ -1508,7 +1518,8 @@ struct ListParams {
   int2* pend; unsigned long long* pend_cnt; unsigned long long pend_cap;
   int2* amb; unsigned long long* amb_cnt; unsigned long long amb_cap;
   unsigned long long* stats;  // [0] links [1] pending [2] to tier 3 [3] blocked [4] listed nodes tested by
-                              // distance [5] pairs covered from both sides [7] list entries read
+                              // distance [5] pairs covered from both sides [6] the pair counter [7] list
+                              // entries read
 };
 
 __device__ __forceinline__ int2 bucket_span(const ListParams& p, int s, float klo, float khi) {
@@ -1735,11 +1746,13 @@ __device__ __forceinline__ void lt_scan(const ListParams& p, int2 pr, int sd, fl
 template <int G, int NQ>
 __global__ void __launch_bounds__(LT_WARPS * 32, 3) list_tier_kernel(ListParams p) {
   const int lane = threadIdx.x & 31;
-  const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const Err e = err_fp32(p.Dp);
   LtCount c;
-  for (int64_t t = wid; t < p.m; t += nw) {
+  for (;;) {  // the next pair in the grouped order (stats[6]: the counter)
+    unsigned long long tt = 0;
+    if (lane == 0) tt = atomicAdd(p.stats + 6, 1ull);
+    const int64_t t = (int64_t)__shfl_sync(FULLMASK, tt, 0);
+    if (t >= p.m) break;
     int sd = p.side[t];
     const int2 pr = p.pairs[t];
     if (sd == 3) {
@@ -2043,10 +2056,11 @@ static void finish_level(const LevelIn& in, LevelOut& out, LevelStats& st, cudaS
         pp.atab = atab.as<float>(); pp.tabw = tabw; pp.dense = 1;
         GRNG_CUDA(prest.alloc((size_t)nun2 * 4));
         GRNG_CUDA(cudaMemsetAsync(dc + 62, 0, 2 * sizeof(unsigned long long), s));
+        GRNG_CUDA(cudaMemsetAsync(dc + 24, 0, sizeof(unsigned long long), s));
         const unsigned gp = (unsigned)std::min<unsigned long long>((nun2 + T3P_WARPS - 1) / T3P_WARPS,
                                                                    (unsigned long long)8 * num_sms());
         tier3_probe_kernel<<<gp, T3P_WARPS * 32, (size_t)T3P_WARPS * 2 * in.Dp * 4, s>>>(
-            pp, prest.as<int32_t>(), dc + 62, dc + 63); note_launch();
+            pp, prest.as<int32_t>(), dc + 62, dc + 63, dc + 24); note_launch();
         GRNG_CUDA(cudaGetLastError());
         unsigned long long hr[2];
         GRNG_CUDA(cudaMemcpyAsync(hr, dc + 62, sizeof(hr), cudaMemcpyDeviceToHost, s));
@@ -2114,18 +2128,21 @@ static void finish_level(const LevelIn& in, LevelOut& out, LevelStats& st, cudaS
       GRNG_CUDA(cudaGetLastError());
       // the pairs grouped by the endpoint whose list they scan
       DevBuf scnt, soff, spairs, sside;
-      GRNG_CUDA(scnt.alloc((size_t)(n + 1) * 8));
-      GRNG_CUDA(soff.alloc((size_t)(n + 1) * 8));
+      int bs = 256;
+      while ((n + bs - 1) / bs > 2048) bs *= 2;
+      const int64_t nbk = (n + bs - 1) / bs, nkeys = nbk * nbk;
+      GRNG_CUDA(scnt.alloc((size_t)(nkeys + 1) * 8));
+      GRNG_CUDA(soff.alloc((size_t)(nkeys + 1) * 8));
       GRNG_CUDA(spairs.alloc(nun2 * 8));
       GRNG_CUDA(sside.alloc(nun2));
-      GRNG_CUDA(cudaMemsetAsync(scnt.p, 0, (size_t)(n + 1) * 8, s));
+      GRNG_CUDA(cudaMemsetAsync(scnt.p, 0, (size_t)(nkeys + 1) * 8, s));
       side_count_kernel<<<(unsigned)((nun2 + 255) / 256), 256, 0, s>>>(unres2.as<int2>(), side.as<int8_t>(),
-                                                                      (int64_t)nun2, scnt.as<int64_t>()); note_launch();
+                                                                      (int64_t)nun2, scnt.as<int64_t>(), bs, nbk); note_launch();
       GRNG_CUDA(cudaGetLastError());
-      exclusive_scan_i64(scnt.as<int64_t>(), soff.as<int64_t>(), n, s);
+      exclusive_scan_i64(scnt.as<int64_t>(), soff.as<int64_t>(), nkeys, s);
       side_scatter_kernel<<<(unsigned)((nun2 + 255) / 256), 256, 0, s>>>(
           unres2.as<int2>(), side.as<int8_t>(), (int64_t)nun2, soff.as<int64_t>(), spairs.as<int2>(),
-          sside.as<int8_t>()); note_launch();
+          sside.as<int8_t>(), bs, nbk); note_launch();
       GRNG_CUDA(cudaGetLastError());
       GRNG_CUDA(unres3.alloc(nun2 * 8));
       ListParams lp;
@@ -2266,10 +2283,11 @@ static void finish_level(const LevelIn& in, LevelOut& out, LevelStats& st, cudaS
         // warp-per-pair descents first; the exhaustive tier takes the pairs they leave
         GRNG_CUDA(rest.alloc((size_t)nun2 * 4));
         GRNG_CUDA(cudaMemsetAsync(dc + 62, 0, 2 * sizeof(unsigned long long), s));
+        GRNG_CUDA(cudaMemsetAsync(dc + 24, 0, sizeof(unsigned long long), s));
         const unsigned gp = (unsigned)std::min<unsigned long long>((nun2 + T3P_WARPS - 1) / T3P_WARPS,
                                                                    (unsigned long long)8 * num_sms());
         tier3_probe_kernel<<<gp, T3P_WARPS * 32, (size_t)T3P_WARPS * 2 * in.Dp * 4, s>>>(
-            t3, rest.as<int32_t>(), dc + 62, dc + 63); note_launch();
+            t3, rest.as<int32_t>(), dc + 62, dc + 63, dc + 24); note_launch();
         GRNG_CUDA(cudaGetLastError());
         unsigned long long hr[2];
         GRNG_CUDA(cudaMemcpyAsync(hr, dc + 62, sizeof(hr), cudaMemcpyDeviceToHost, s));
@@ -2382,8 +2400,9 @@ void run_level(const LevelIn& in, LevelOut& out, LevelStats& st, cudaStream_t s,
   GRNG_CUDA(ctr.alloc(64 * sizeof(unsigned long long)));
   unsigned long long* dc = ctr.as<unsigned long long>();
   // counters: 0 strip, 1 surv, 2..5 tile stats, 8.. tier2a, 12.. tier2b, 16 links, 17 pend,
-  // 18 unres, 19 amb, 20 unres2, 21 edges, 22 recheck blocked, 26..33 range lists,
-  // 34..37 tier 3, 40 tensor-core status, 44..47 learned shortlist
+  // 18 unres, 19 amb, 20 unres2, 21 edges, 22 recheck blocked, 23 new guidance links, 24 the
+  // descents' pair counter, 26..33 range lists, 34..37 tier 3, 40 tensor-core status, 44..48
+  // learned shortlist, 50..57 list tier, 58..61 tier-3 cycles, 62..63 descents
   if (KC == 32) launch_prep<32>(in, A.as<__half>(), nbi.as<uint8_t>(), nbk.as<float>(), s);
   else if (KC == 16) launch_prep<16>(in, A.as<__half>(), nbi.as<uint8_t>(), nbk.as<float>(), s);
   else launch_prep<8>(in, A.as<__half>(), nbi.as<uint8_t>(), nbk.as<float>(), s);

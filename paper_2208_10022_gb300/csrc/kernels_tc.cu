@@ -78,15 +78,35 @@ struct TcParams {
 
 static __host__ __device__ constexpr size_t tc_img_bytes(int Dp) { return (size_t)128 * Dp * 4; }  // hi + lo
 static __host__ __device__ constexpr size_t tc_t16_bytes() { return (size_t)128 * 130 * 2; }
-static __host__ __device__ constexpr size_t tc_base_bytes(int Dp) {
-  return 2 * tc_img_bytes(Dp) + (tc_img_bytes(Dp) >= tc_t16_bytes() ? 0 : tc_t16_bytes()) + 33280 + 34816 +
-         128 * GRNG_KIN * 10 + 8 * 512 + 2 * 4096 + 128;
-}
 #define TC_SMEM_MAX (227 * 1024)
 #define TC_QMAX 4096  // full-filter queue entries (8 bytes each), as many as shared memory leaves room for
+#define TC_QMIN 1024  // the fewest entries the pipelined form keeps
+static __host__ __device__ constexpr size_t tc_rest_bytes() { return 33280 + 34816 + 128 * GRNG_KIN * 10 + 8 * 512 + 2 * 4096 + 128; }
+// Pipelined form: T16 has a buffer of its own, so the next column block's image can be
+// copied into sB and multiplied into the second TMEM accumulator while this tile's
+// epilogue runs.  Without room for it, T16 reuses sB once the tile's MMAs have completed.
+static __host__ __device__ constexpr bool tc_pipe(int Dp) {
+  return 2 * tc_img_bytes(Dp) + tc_t16_bytes() + tc_rest_bytes() + (size_t)TC_QMIN * 8 <= TC_SMEM_MAX;
+}
+static __host__ __device__ constexpr size_t tc_base_bytes(int Dp) {
+  return 2 * tc_img_bytes(Dp) + ((tc_pipe(Dp) || tc_img_bytes(Dp) < tc_t16_bytes()) ? tc_t16_bytes() : 0) +
+         tc_rest_bytes();
+}
 static __host__ __device__ constexpr int tc_qcap(int Dp) {
   return tc_base_bytes(Dp) >= TC_SMEM_MAX ? 0
          : (int)((TC_SMEM_MAX - tc_base_bytes(Dp)) / 8 < TC_QMAX ? (TC_SMEM_MAX - tc_base_bytes(Dp)) / 8 : TC_QMAX);
+}
+// the s-th column block of strip bx in visiting order (bx, bx+1, bx-1, bx+2, ...), skipping
+// those out of range; s advances past the block returned
+__device__ __forceinline__ int64_t tc_next_by(int64_t bx, int64_t nb, int64_t& s) {
+  for (;; ++s) {
+    const int64_t off = (s & 1) ? ((s + 1) >> 1) : -(s >> 1);
+    const int64_t by = bx + off;
+    if (by >= 0 && by < nb) {
+      ++s;
+      return by;
+    }
+  }
 }
 static __host__ __device__ constexpr size_t tc_smem_bytes(int Dp, int K) {
   return (void)K, tc_base_bytes(Dp) + (size_t)tc_qcap(Dp) * 8;
@@ -157,11 +177,11 @@ __device__ __forceinline__ bool tc_full_test(const TcTile& T, int r, int c, floa
       if (hi_b(a + T.E, e) < vlo && hi_b(__half2float(T.AY[z * 136 + c]), e) < vlo) return true;
     }
   }
-  {  // column minimum of y over the row block
+  {  // column minimum of y over the row block (cmin: bounds of the exact keys, E included)
     const int z = (T.carg1[c] != r) ? T.carg1[c] : T.carg2[c];
     if (z >= 0) {
       const float b = (T.carg1[c] != r) ? T.cmin1[c] : T.cmin2[c];
-      if (hi_b(__half2float(T.AX[r * 130 + z]), e) < vlo && hi_b(b + T.E, e) < vlo) return true;
+      if (hi_b(__half2float(T.AX[r * 130 + z]), e) < vlo && b < vlo) return true;
     }
   }
   for (int t = 0; t < GRNG_KIN; ++t) {  // neighbours of x
@@ -193,8 +213,10 @@ __global__ void __launch_bounds__(256, 1) tc_sweep_kernel(TcParams p) {
   uint8_t* sA = sm;
   uint8_t* sB = sm + IMG;
   size_t o = 2 * (size_t)IMG;
+  const bool pipe = tc_pipe(Dp);
+  const uint32_t TCOLS = pipe ? 256u : 128u;  // two accumulators when pipelined
   __half* T16;
-  if (IMG >= tc_t16_bytes()) {
+  if (!pipe && IMG >= tc_t16_bytes()) {
     T16 = reinterpret_cast<__half*>(sB);  // the operand is dead once the MMA has completed
   } else {
     T16 = reinterpret_cast<__half*>(sm + o);
@@ -238,7 +260,7 @@ __global__ void __launch_bounds__(256, 1) tc_sweep_kernel(TcParams p) {
   unsigned long long st_cand = 0, st_full = 0;
 
   if (warp == 0) {
-    tmem_alloc(tslot, 128);
+    tmem_alloc(tslot, TCOLS);
     tmem_relinquish();
   }
   if (tid == 0) {
@@ -302,12 +324,34 @@ __global__ void __launch_bounds__(256, 1) tc_sweep_kernel(TcParams p) {
     phA ^= 1;
     const float bmx = __uint_as_float(p.bmax[bx]);
     const bool vr = r < nr;
-    int done = 0;
-    for (int s = 0; done < nb; ++s) {
-      const int64_t off = (s & 1) ? (int64_t)((s + 1) >> 1) : -(int64_t)(s >> 1);
-      const int64_t by = bx + off;
-      if (by < 0 || by >= nb) continue;
-      ++done;
+    int64_t sidx = 0;
+    int64_t by = tc_next_by(bx, nb, sidx);
+    uint32_t acc = 0;  // TMEM column of this tile's accumulator
+    int64_t by_nx = -1;
+    if (pipe) {        // the strip's first tile: copy and MMAs now, the later ones a tile ahead
+      if (tid == 0 && !*s_abort) {
+        mbar_expect_tx(&bars[1], IMG);
+        bulk_g2s(sB, p.img + (size_t)by * IMG, IMG, &bars[1]);
+        s_pend[1] = 1;
+        s_par[1] = (int)phB;
+        if (mbar_wait(&bars[1], phB, p.spin)) {
+          s_pend[1] = 0;
+          tc_fence_after();
+          issue_gram_tile(tbase, sA, sB, Dp);
+          umma_commit(&bars[2]);
+          s_pend[2] = 1;
+          s_par[2] = (int)phM;
+        } else {
+          *s_abort = 1;
+          atomicOr(p.status, 1);
+        }
+      }
+      phB ^= 1;
+    }
+    for (int64_t t = 0; t < nb; ++t, acc ^= (pipe ? 128u : 0u)) {
+      if (t > 0) by = by_nx;
+      const int64_t by_next = t + 1 < nb ? tc_next_by(bx, nb, sidx) : -1;
+      by_nx = by_next;
       const int64_t yb = by * 128;
       const int nc = (int)(n - yb < 128 ? n - yb : 128);
       const bool filt = by >= bx;
@@ -319,10 +363,12 @@ __global__ void __launch_bounds__(256, 1) tc_sweep_kernel(TcParams p) {
       if (*s_abort) break;
       if (tid == 0) {
         *s_qn = 0;
-        mbar_expect_tx(&bars[1], IMG);
-        bulk_g2s(sB, p.img + (size_t)by * IMG, IMG, &bars[1]);
-        s_pend[1] = 1;
-        s_par[1] = (int)phB;
+        if (!pipe) {
+          mbar_expect_tx(&bars[1], IMG);
+          bulk_g2s(sB, p.img + (size_t)by * IMG, IMG, &bars[1]);
+          s_pend[1] = 1;
+          s_par[1] = (int)phB;
+        }
         if (filt) {
           mbar_expect_tx(&bars[3], 32768);
           s_pend[3] = 1;
@@ -346,22 +392,24 @@ __global__ void __launch_bounds__(256, 1) tc_sweep_kernel(TcParams p) {
           nbrYi[i] = ok ? p.nbr_idx[yb * GRNG_KIN + i] : (uint8_t)255;
           nbrYk[i] = ok ? p.nbr_key[yb * GRNG_KIN + i] : INF;
         }
-      if (tid == 0) {
-        if (mbar_wait(&bars[1], phB, p.spin)) {
-          s_pend[1] = 0;
-          tc_fence_after();
-          issue_gram_tile(tbase, sA, sB, Dp);
-          umma_commit(&bars[2]);
-          s_pend[2] = 1;
-          s_par[2] = (int)phM;
-        } else {
-          *s_abort = 1;
-          atomicOr(p.status, 1);
+      if (!pipe) {
+        if (tid == 0) {
+          if (mbar_wait(&bars[1], phB, p.spin)) {
+            s_pend[1] = 0;
+            tc_fence_after();
+            issue_gram_tile(tbase, sA, sB, Dp);
+            umma_commit(&bars[2]);
+            s_pend[2] = 1;
+            s_par[2] = (int)phM;
+          } else {
+            *s_abort = 1;
+            atomicOr(p.status, 1);
+          }
         }
+        phB ^= 1;
+        __syncthreads();
+        if (*s_abort) break;
       }
-      phB ^= 1;
-      __syncthreads();
-      if (*s_abort) break;
       if (mbar_wait(&bars[2], phM, p.spin)) {
         if (tid == 0) s_pend[2] = 0;
       } else {
@@ -372,6 +420,14 @@ __global__ void __launch_bounds__(256, 1) tc_sweep_kernel(TcParams p) {
       tc_fence_after();
       __syncthreads();
       if (*s_abort) break;
+      if (pipe && tid == 0 && by_next >= 0) {
+        // this tile's MMAs have completed: sB takes the next column block's image now
+        mbar_expect_tx(&bars[1], IMG);
+        bulk_g2s(sB, p.img + (size_t)by_next * IMG, IMG, &bars[1]);
+        s_pend[1] = 1;
+        s_par[1] = (int)phB;
+      }
+      const uint32_t tacc = trow + acc;  // this thread's lane and half in this tile's accumulator
       // ---- pass 1: keys -> T16, row minima, neighbour lists (thread = row, half) ----------
       // 16 columns per TMEM load; list insertions, rare once the lists fill, are taken out
       // of the unrolled part so that the loop stays small
@@ -383,7 +439,7 @@ __global__ void __launch_bounds__(256, 1) tc_sweep_kernel(TcParams p) {
 #pragma unroll 1
       for (int q = 0; q < 4; ++q) {
         float g[16], vv[16];
-        tmem_ld16(trow + (uint32_t)(q * 16), g);
+        tmem_ld16(tacc + (uint32_t)(q * 16), g);
         unsigned pm = 0;
         const int c0 = cb + q * 16;
         if (!filt) {
@@ -429,6 +485,24 @@ __global__ void __launch_bounds__(256, 1) tc_sweep_kernel(TcParams p) {
       tc_fence_before();
       if (filt) rowx[h * 128 + r] = make_float4(m1, m2, __int_as_float(a1), __int_as_float(a2));
       __syncthreads();
+      if (pipe && by_next >= 0) {
+        // the next tile's MMAs into the other accumulator, under this tile's epilogue (that
+        // accumulator's last reads, in the previous tile, are ordered by the barriers since)
+        if (tid == 0 && !*s_abort) {
+          if (mbar_wait(&bars[1], phB, p.spin)) {
+            s_pend[1] = 0;
+            tc_fence_after();
+            issue_gram_tile(tbase + (acc ^ 128u), sA, sB, Dp);
+            umma_commit(&bars[2]);
+            s_pend[2] = 1;
+            s_par[2] = (int)phM;
+          } else {
+            *s_abort = 1;
+            atomicOr(p.status, 1);
+          }
+        }
+        phB ^= 1;
+      }
       if (filt) {
         // ---- column minima over the row block: thread = column, half of the rows -------
         {
@@ -449,12 +523,13 @@ __global__ void __launch_bounds__(256, 1) tc_sweep_kernel(TcParams p) {
           top2_merge(m1, a1, m2, a2, w4.x, __float_as_int(w4.z), w4.y, __float_as_int(w4.w));
         }
         __syncthreads();
-        if (tid < 128) {
+        const float E = p.gam * (bmx + __uint_as_float(p.bmax[by]));
+        if (tid < 128) {  // the column minima as certain upper bounds of the exact keys
           const float4 u0 = colx[tid], u1 = colx[128 + tid];
           float c1 = u0.x, c2 = u0.y;
           int b1 = __float_as_int(u0.z), b2 = __float_as_int(u0.w);
           top2_merge(c1, b1, c2, b2, u1.x, __float_as_int(u1.z), u1.y, __float_as_int(u1.w));
-          cmin1[tid] = c1; cmin2[tid] = c2; carg1[tid] = b1; carg2[tid] = b2;
+          cmin1[tid] = hi_b(c1 + E, e); cmin2[tid] = hi_b(c2 + E, e); carg1[tid] = b1; carg2[tid] = b2;
         }
         if (mbar_wait(&bars[3], phY, p.spin)) {
           if (tid == 0) s_pend[3] = 0;
@@ -466,7 +541,6 @@ __global__ void __launch_bounds__(256, 1) tc_sweep_kernel(TcParams p) {
         __syncthreads();
         tc_fence_after();
         // ---- tier-1 filter: thread = row x, one column y of its half at a time ----------
-        const float E = p.gam * (bmx + __uint_as_float(p.bmax[by]));
         const int px = parX[r];
         // link bits of px's row of the parents' GRNG: y parents lie in [parY[0], parY[nc-1]]
         // and are >= px in every upper tile (nodes are sorted by parent)
@@ -496,21 +570,24 @@ __global__ void __launch_bounds__(256, 1) tc_sweep_kernel(TcParams p) {
         // the whole tile's row minima, for the full tests of any thread (the other half read
         // its slot of rowx before the last barrier)
         if (h == 0) rowx[r] = make_float4(m1, m2, __int_as_float(a1), __int_as_float(a2));
-        // quick test: the row minimum z = a1 of x over the column block blocks (x, y) once
-        // key(x, z) and key(z, y) (the in-block key, AY row z) are both certainly below
-        // key(x, y); uniform over the row's 64 columns, so the warp stays converged.  (For
-        // y = z the test fails by itself: key(x, z) cannot be certainly below itself.)  The
-        // columns it leaves go to a queue that all 256 threads share once the tile's TMEM has
-        // been read, so that no warp waits for another's divergent tests.
+        // quick tests, uniform over the row's 64 columns so that the warp stays converged:
+        //  - the row minimum z = a1 of x over the column block blocks (x, y) once key(x, z)
+        //    and key(z, y) (the in-block key, AY row z) are both certainly below key(x, y);
+        //  - the column minimum z' of y over the row block blocks it once key(x, z') (the
+        //    in-block key, AX row x) and key(z', y) are.
+        // (For y = z or x = z' a test fails by itself: a key cannot be certainly below
+        // itself.)  The columns both leave go to a queue that all 256 threads share once the
+        // tile's TMEM has been read, so that no warp waits for another's divergent tests.
         const float A1 = hi_b(m1 + E, e);
         const bool rq = vr && a1 >= 0;
         const bool fast = vr && nc == 128 && !diag && all_linked;  // every column a candidate
         if (fast) st_cand += 64;
         const __half* AYz = AY + (rq ? a1 : 0) * 136 + cb;
+        const __half* AXr = AX + r * 130;  // x's in-block keys
 #pragma unroll 1
         for (int q = 0; q < 2; ++q) {  // two chunks of 32 columns, one tensor-memory wait each
           float g[32];
-          tmem_ld32(trow + (uint32_t)(q * 32), g);
+          tmem_ld32(tacc + (uint32_t)(q * 32), g);
           unsigned nd = 0;
 #pragma unroll
           for (int q8 = 0; q8 < 4; ++q8) {
@@ -520,6 +597,12 @@ __global__ void __launch_bounds__(256, 1) tc_sweep_kernel(TcParams p) {
             const float4 nya = *reinterpret_cast<const float4*>(ny + c8);
             const float4 nyb = *reinterpret_cast<const float4*>(ny + c8 + 4);
             const float nyv[8] = {nya.x, nya.y, nya.z, nya.w, nyb.x, nyb.y, nyb.z, nyb.w};
+            const int4 za = *reinterpret_cast<const int4*>(carg1 + c8);
+            const int4 zb = *reinterpret_cast<const int4*>(carg1 + c8 + 4);
+            const int zcv[8] = {za.x, za.y, za.z, za.w, zb.x, zb.y, zb.z, zb.w};
+            const float4 cma = *reinterpret_cast<const float4*>(cmin1 + c8);
+            const float4 cmb = *reinterpret_cast<const float4*>(cmin1 + c8 + 4);
+            const float cmv[8] = {cma.x, cma.y, cma.z, cma.w, cmb.x, cmb.y, cmb.z, cmb.w};
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
               const int c = c8 + j;
@@ -549,7 +632,10 @@ __global__ void __launch_bounds__(256, 1) tc_sweep_kernel(TcParams p) {
               const float vlo = lo_b(v - E, e);  // below every key this pair can have
               const float2 a2f = __half22float2(ay2[j >> 1]);
               const float ayz = (j & 1) ? a2f.y : a2f.x;
-              const bool quick = rq && fmaxf(A1, hi_b(ayz, e)) < vlo;
+              const int zc = zcv[j];
+              const float axz = __half2float(AXr[zc < 0 ? 0 : zc]);
+              const bool quick = (rq && fmaxf(A1, hi_b(ayz, e)) < vlo) ||
+                                 (zc >= 0 && fmaxf(hi_b(axz, e), cmv[j]) < vlo);
               if (cand && !quick) nd |= 1u << (q8 * 8 + j);
             }
           }
@@ -677,7 +763,7 @@ __global__ void __launch_bounds__(256, 1) tc_sweep_kernel(TcParams p) {
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  if (warp == 0) tmem_dealloc(tbase, 128);
+  if (warp == 0) tmem_dealloc(tbase, TCOLS);
 }
 
 // the listed neighbours' keys again, exactly in FP32 (the tiers compare FP32 keys)
@@ -688,6 +774,218 @@ __global__ void tc_knn_fix_kernel(const float* __restrict__ X, int64_t n, int Dp
   const int64_t x = i / K;
   const int k = knn_idx[i];
   if (k >= 0) knn_key[i] = key32(X + x * Dp, X + (int64_t)k * Dp, Dp, metric);
+}
+
+// ---- nearest pivot on the tensor cores (Eq. 2 assignment, split-BF16 Gram keys) ----------
+// One persistent CTA per SM walks 128-member strips; per strip the pivot blocks go by in
+// order through two image buffers and two TMEM accumulators: while the keys of block pb
+// are read, block pb+1's MMAs run and block pb+2's image is copied.  Thread (row r, half h)
+// keeps the two smallest Gram keys of its member over its 64 columns and the pivot of the
+// smallest; the halves merge at the end of the strip.  With E = gam (max |x|^2 of the strip +
+// max |p|^2 of all pivots) bounding every key's error, best1 = an upper bound of the
+// smallest exact key (its pivot in arg1) and best2 = a lower bound of every other pivot's
+// exact key; the caller accepts arg1 when best1 < best2 and re-decides the member exactly
+// otherwise.
+struct TcAssignParams {
+  const uint8_t* imgX; const float* nX; const unsigned int* bmaxX;
+  const uint8_t* imgP; const float* nP;
+  int64_t nmem, m;
+  int Dp;
+  float gam, pmax;
+  float* best1; int32_t* arg1; float* best2;
+  int32_t* cand;  // [nmem][TCA_K] the pivots of the TCA_K smallest Gram keys, smallest first
+  float* rest;    // [nmem] lower bound of every other pivot's exact key
+  int* strip_ctr; int* status; long long spin;
+};
+
+#define TCA_K 4
+static __host__ __device__ constexpr size_t tc_assign_smem(int Dp) {
+  return 3 * tc_img_bytes(Dp) + 512 + 128 * TCA_K * 8 + 128;
+}
+
+__global__ void __launch_bounds__(256, 1) tc_assign_kernel(TcAssignParams p) {
+  extern __shared__ __align__(1024) unsigned char sm[];
+  const int Dp = p.Dp;
+  const uint32_t IMG = (uint32_t)tc_img_bytes(Dp);
+  uint8_t* sA = sm;
+  uint8_t* sBb[2] = {sm + IMG, sm + 2 * IMG};
+  size_t o = 3 * (size_t)IMG;
+  float* np_ = reinterpret_cast<float*>(sm + o); o += 512;        // pivot norms of the block
+  float2* half2 = reinterpret_cast<float2*>(sm + o); o += 128 * TCA_K * 8;  // [TCA_K][128] the second half's list
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sm + o);            // A image, B images, MMA done
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + o + 32);
+  int* s_strip = reinterpret_cast<int*>(sm + o + 36);
+  int* s_abort = reinterpret_cast<int*>(sm + o + 40);
+  int* s_pend = reinterpret_cast<int*>(sm + o + 48);              // outstanding phases per barrier
+  int* s_par = s_pend + 4;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int lq = warp & 3, h = warp >> 2;
+  const int r = lq * 32 + lane;
+  const int cb = h * 64;
+  const int64_t nbx = (p.nmem + 127) / 128, npb = (p.m + 127) / 128;
+  const Err e = err_fp32(Dp);
+  const float INF = finf_tc();
+  if (warp == 0) {
+    tmem_alloc(tslot, 256);
+    tmem_relinquish();
+  }
+  if (tid == 0) {
+    for (int i = 0; i < 4; ++i) {
+      mbar_init(&bars[i], 1);
+      s_pend[i] = 0;
+      s_par[i] = 0;
+    }
+    *s_abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tbase = *tslot;
+  const uint32_t trow = tbase + ((uint32_t)(lq * 32) << 16) + (uint32_t)cb;
+  uint32_t phA = 0, phB = 0, phM = 0;
+  // tid 0: copy of pivot block q into its buffer (par: the parity its wait will use); wait
+  // for it and issue its MMAs
+  auto copy_b = [&](int64_t q, uint32_t par) {
+    mbar_expect_tx(&bars[1], IMG);
+    bulk_g2s(sBb[q & 1], p.imgP + (size_t)q * IMG, IMG, &bars[1]);
+    s_pend[1] = 1;
+    s_par[1] = (int)par;
+  };
+  auto mma_b = [&](int64_t q) -> bool {
+    if (!mbar_wait(&bars[1], phB, p.spin)) return false;
+    s_pend[1] = 0;
+    tc_fence_after();
+    issue_gram_tile(tbase + (uint32_t)(q & 1) * 128u, sA, sBb[q & 1], Dp);
+    umma_commit(&bars[2]);
+    s_pend[2] = 1;
+    s_par[2] = (int)phM;
+    return true;
+  };
+  for (;;) {
+    __syncthreads();
+    if (tid == 0) *s_strip = atomicAdd(p.strip_ctr, 1);
+    __syncthreads();
+    const int64_t bx = *s_strip;
+    if (bx >= nbx || *s_abort) break;
+    const int64_t xb = bx * 128;
+    const int nr = (int)(p.nmem - xb < 128 ? p.nmem - xb : 128);
+    if (tid == 0) {  // the strip's image, block 0's MMAs, block 1's copy
+      fence_proxy_async();
+      mbar_expect_tx(&bars[0], IMG);
+      bulk_g2s(sA, p.imgX + (size_t)bx * IMG, IMG, &bars[0]);
+      s_pend[0] = 1;
+      s_par[0] = (int)phA;
+      copy_b(0, phB);
+      bool ok = mbar_wait(&bars[0], phA, p.spin);
+      if (ok) s_pend[0] = 0;
+      ok = ok && mma_b(0);
+      if (ok && npb > 1) copy_b(1, phB ^ 1u);
+      if (!ok) {
+        *s_abort = 1;
+        atomicOr(p.status, 1);
+      }
+    }
+    phA ^= 1;
+    phB ^= 1;
+    const float nxr = r < nr ? p.nX[xb + r] : 0.0f;
+    const float E = p.gam * (__uint_as_float(p.bmaxX[bx]) + p.pmax);
+    float tv[TCA_K];  // the TCA_K smallest keys of this half, ascending, and their pivots
+    int ti[TCA_K];
+#pragma unroll
+    for (int k = 0; k < TCA_K; ++k) { tv[k] = INF; ti[k] = -1; }
+    for (int64_t pb = 0; pb < npb; ++pb) {
+      const int64_t pc = pb * 128;
+      const int nc = (int)(p.m - pc < 128 ? p.m - pc : 128);
+      if (tid < 128) np_[tid] = tid < nc ? p.nP[pc + tid] : 0.0f;
+      __syncthreads();  // also: every read of the accumulator block pb+1 will take is done
+      if (*s_abort) break;
+      if (mbar_wait(&bars[2], phM, p.spin)) {  // block pb's MMAs
+        if (tid == 0) s_pend[2] = 0;
+      } else {
+        *s_abort = 1;
+        atomicOr(p.status, 1);
+      }
+      phM ^= 1;
+      tc_fence_after();
+      if (tid == 0 && pb + 1 < npb && !*s_abort) {  // block pb+1's MMAs, block pb+2's copy
+        bool ok = mma_b(pb + 1);
+        if (ok && pb + 2 < npb) copy_b(pb + 2, phB ^ 1u);
+        if (!ok) {
+          *s_abort = 1;
+          atomicOr(p.status, 1);
+        }
+      }
+      if (pb + 1 < npb) phB ^= 1;
+      const uint32_t tacc = trow + (uint32_t)(pb & 1) * 128u;
+#pragma unroll 1
+      for (int q = 0; q < 2; ++q) {
+        float g[32];
+        tmem_ld32(tacc + (uint32_t)(q * 32), g);
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const int c = cb + q * 32 + j;
+          float v = nxr + np_[c] - 2.0f * g[j];
+          if (c >= nc) v = INF;
+          if (v < tv[TCA_K - 1]) {  // rare once the list holds near pivots
+            int id = (int)(pc + c);
+#pragma unroll
+            for (int k = 0; k < TCA_K; ++k)
+              if (v < tv[k]) {
+                const float tvk = tv[k];
+                const int tik = ti[k];
+                tv[k] = v; ti[k] = id;
+                v = tvk; id = tik;
+              }
+          }
+        }
+      }
+      tc_fence_before();
+      __syncthreads();  // np_ is rewritten next
+    }
+    // the two halves merged: h = 1 hands its list to h = 0.  Keys outside the merged list
+    // are at least the fifth of the eight listed or either half's last listed one.
+    __syncthreads();
+    if (h == 1)
+#pragma unroll
+      for (int k = 0; k < TCA_K; ++k) half2[k * 128 + r] = make_float2(tv[k], __int_as_float(ti[k]));
+    __syncthreads();
+    if (h == 0 && r < nr && !*s_abort) {
+      float lb = tv[TCA_K - 1];
+#pragma unroll
+      for (int k = 0; k < TCA_K; ++k) {
+        const float2 w = half2[k * 128 + r];
+        float v = w.x;
+        int id = __float_as_int(w.y);
+        if (k == TCA_K - 1) lb = fminf(lb, v);
+#pragma unroll
+        for (int q = 0; q < TCA_K; ++q)
+          if (v < tv[q]) {
+            const float tq = tv[q];
+            const int iq = ti[q];
+            tv[q] = v; ti[q] = id;
+            v = tq; id = iq;
+          }
+        lb = fminf(lb, v);  // pushed out of the list
+      }
+      p.best1[xb + r] = hi_b(tv[0] + E, e);
+      p.arg1[xb + r] = ti[0];
+      p.best2[xb + r] = lo_b(tv[1] - E, e);  // a tie keeps tv[1] = tv[0]: re-decided exactly
+#pragma unroll
+      for (int k = 0; k < TCA_K; ++k) p.cand[(xb + r) * TCA_K + k] = ti[k];
+      p.rest[xb + r] = lo_b(lb - E, e);
+    }
+  }
+  __syncthreads();
+  if (*s_abort && tid == 0) {
+    const long long lim = p.spin > (1ll << 26) ? p.spin : (1ll << 26);
+    for (int b = 0; b < 3; ++b)
+      if (s_pend[b] && !mbar_wait(&bars[b], (uint32_t)s_par[b], lim)) atomicOr(p.status, 2);
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 0) tmem_dealloc(tbase, 256);
 }
 
 // ---- diagnostic: tensor-core keys of all pairs among at most 256 points -------------------
@@ -810,6 +1108,34 @@ void tc_sweep(const TcLaunch& L, cudaStream_t s) {
   const int grid = (int)std::min<int64_t>(nb, sm_count());
   tc_sweep_kernel<<<grid, 256, smem, s>>>(p); note_launch();
   GRNG_CUDA(cudaGetLastError());
+}
+
+void tc_assign(const float* Xm, int64_t nmem, const float* Xp, int64_t m, int Dp, float* best1, int32_t* arg1,
+               float* best2, int32_t* cand, float* rest, long long spin, cudaStream_t s, cudaEvent_t start,
+               cudaEvent_t done) {
+  DevBuf imgX, nX, bX, imgP, nP, bP, ctr;
+  float pmax = 0.0f;
+  tc_prepare(Xm, nmem, Dp, imgX, nX, bX, nullptr, s);
+  tc_prepare(Xp, m, Dp, imgP, nP, bP, &pmax, s);
+  GRNG_CUDA(ctr.alloc(16));
+  GRNG_CUDA(cudaMemsetAsync(ctr.p, 0, 16, s));
+  TcAssignParams p;
+  p.imgX = imgX.as<uint8_t>(); p.nX = nX.as<float>(); p.bmaxX = bX.as<unsigned int>();
+  p.imgP = imgP.as<uint8_t>(); p.nP = nP.as<float>();
+  p.nmem = nmem; p.m = m; p.Dp = Dp; p.gam = tc_gamma(Dp); p.pmax = pmax;
+  p.best1 = best1; p.arg1 = arg1; p.best2 = best2; p.cand = cand; p.rest = rest;
+  p.strip_ctr = ctr.as<int>(); p.status = ctr.as<int>() + 1; p.spin = spin;
+  const size_t smem = tc_assign_smem(Dp);
+  GRNG_CUDA(cudaFuncSetAttribute(tc_assign_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const int64_t nbx = (nmem + 127) / 128;
+  if (start) GRNG_CUDA(cudaEventRecord(start, s));
+  tc_assign_kernel<<<(unsigned)std::min<int64_t>(nbx, sm_count()), 256, smem, s>>>(p); note_launch();
+  GRNG_CUDA(cudaGetLastError());
+  if (done) GRNG_CUDA(cudaEventRecord(done, s));
+  int st = 0;
+  GRNG_CUDA(cudaMemcpyAsync(&st, ctr.as<int>() + 1, 4, cudaMemcpyDeviceToHost, s));
+  GRNG_CUDA(cudaStreamSynchronize(s));
+  if (st) fail(4 /* GRNG_ETIMEOUT */, "a bounded tensor-core wait ran out");
 }
 
 void tc_knn_fix(const float* X, int64_t n, int Dp, int K, int metric, const int32_t* knn_idx, float* knn_key,
