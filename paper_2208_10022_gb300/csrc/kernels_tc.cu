@@ -80,8 +80,12 @@ static __host__ __device__ constexpr size_t tc_img_bytes(int Dp) { return (size_
 static __host__ __device__ constexpr size_t tc_t16_bytes() { return (size_t)128 * 130 * 2; }
 #define TC_SMEM_MAX (227 * 1024)
 #define TC_QMAX 4096  // full-filter queue entries (8 bytes each), as many as shared memory leaves room for
-#define TC_QMIN 1024  // the fewest entries the pipelined form keeps
-static __host__ __device__ constexpr size_t tc_rest_bytes() { return 33280 + 34816 + 128 * GRNG_KIN * 10 + 8 * 512 + 2 * 4096 + 128; }
+#define TC_QMIN 512   // the fewest entries the pipelined form keeps
+// AX, AY, the neighbour lists (the column block's twice), nx, ny x2, cmin/carg x4, parX,
+// parY x2, rowx, barriers
+static __host__ __device__ constexpr size_t tc_rest_bytes() {
+  return 33280 + 34816 + 128 * GRNG_KIN * 15 + 10 * 512 + 4096 + 128;
+}
 // Pipelined form: T16 has a buffer of its own, so the next column block's image can be
 // copied into sB and multiplied into the second TMEM accumulator while this tile's
 // epilogue runs.  Without room for it, T16 reuses sB once the tile's MMAs have completed.
@@ -135,6 +139,26 @@ __device__ __forceinline__ float knn_insert_reg(float (&kk)[GRNG_KMAX], int (&ki
   for (int i = 1; i < GRNG_KMAX; ++i)
     if (i == K - 1) t = kk[i];
   return t;
+}
+
+// a[j] for a runtime j in [0, 16), by a tree of selects on j's bits (the array stays in
+// registers; an indexed read would move it to local memory)
+__device__ __forceinline__ float sel16(const float (&a)[16], int j) {
+  float b[8], c[4], d[2];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) b[i] = (j & 1) ? a[2 * i + 1] : a[2 * i];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) c[i] = (j & 2) ? b[2 * i + 1] : b[2 * i];
+#pragma unroll
+  for (int i = 0; i < 2; ++i) d[i] = (j & 4) ? c[2 * i + 1] : c[2 * i];
+  return (j & 8) ? d[1] : d[0];
+}
+
+__device__ __forceinline__ float sel32(const float (&a)[32], int j) {
+  float b[16];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) b[i] = (j & 1) ? a[2 * i + 1] : a[2 * i];
+  return sel16(b, j >> 1);
 }
 
 // top-2 of (m1, a1), (m2, a2) merged with (b1, i1), (b2, i2)
@@ -224,19 +248,20 @@ __global__ void __launch_bounds__(256, 1) tc_sweep_kernel(TcParams p) {
   }
   __half* AX = reinterpret_cast<__half*>(sm + o); o += 33280;   // [128][130]
   __half* AY = reinterpret_cast<__half*>(sm + o); o += 34816;   // [128][136]: rows 16-byte aligned
-  float* nbrXk = reinterpret_cast<float*>(sm + o); o += 128 * GRNG_KIN * 4;  // [t][row]
-  float* nbrYk = reinterpret_cast<float*>(sm + o); o += 128 * GRNG_KIN * 4;  // [row][t]
+  // the column block's arrays come twice: the pipelined form loads the next tile's during
+  // this one
+  float* nbrXk = reinterpret_cast<float*>(sm + o); o += 128 * GRNG_KIN * 4;     // [t][row]
+  float* nbrYk2 = reinterpret_cast<float*>(sm + o); o += 2 * 128 * GRNG_KIN * 4;  // [2][row][t]
   uint8_t* nbrXi = sm + o; o += 128 * GRNG_KIN;
-  uint8_t* nbrYi = sm + o; o += 128 * GRNG_KIN;
+  uint8_t* nbrYi2 = sm + o; o += 2 * 128 * GRNG_KIN;
   float* nx = reinterpret_cast<float*>(sm + o); o += 512;
-  float* ny = reinterpret_cast<float*>(sm + o); o += 512;
+  float* ny2 = reinterpret_cast<float*>(sm + o); o += 1024;
   float* cmin1 = reinterpret_cast<float*>(sm + o); o += 512;
   float* cmin2 = reinterpret_cast<float*>(sm + o); o += 512;
   int* carg1 = reinterpret_cast<int*>(sm + o); o += 512;
   int* carg2 = reinterpret_cast<int*>(sm + o); o += 512;
   int* parX = reinterpret_cast<int*>(sm + o); o += 512;
-  int* parY = reinterpret_cast<int*>(sm + o); o += 512;
-  float4* colx = reinterpret_cast<float4*>(sm + o); o += 4096;  // [2][128] partial column top-2
+  int* parY2 = reinterpret_cast<int*>(sm + o); o += 1024;
   float4* rowx = reinterpret_cast<float4*>(sm + o); o += 4096;  // [2][128] partial row top-2
   uint64_t* bars = reinterpret_cast<uint64_t*>(sm + o);           // A image, B image, MMA done, AY
   uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + o + 32);
@@ -324,8 +349,24 @@ __global__ void __launch_bounds__(256, 1) tc_sweep_kernel(TcParams p) {
     phA ^= 1;
     const float bmx = __uint_as_float(p.bmax[bx]);
     const bool vr = r < nr;
+    // norms, parents and neighbour lists of column block yy into buffer b
+    auto load_cols = [&](int64_t yy, int b) {
+      const int64_t y0 = yy * 128;
+      const int ncc = (int)(n - y0 < 128 ? n - y0 : 128);
+      if (tid < 128) {
+        ny2[b * 128 + tid] = tid < ncc ? p.nrm[y0 + tid] : 0.0f;
+        parY2[b * 128 + tid] = (p.parent && tid < ncc) ? p.parent[y0 + tid] : 0;
+      }
+      if (yy >= bx)
+        for (int i = tid; i < 128 * GRNG_KIN; i += 256) {
+          const bool ok = i / GRNG_KIN < ncc;
+          nbrYi2[b * 128 * GRNG_KIN + i] = ok ? p.nbr_idx[y0 * GRNG_KIN + i] : (uint8_t)255;
+          nbrYk2[b * 128 * GRNG_KIN + i] = ok ? p.nbr_key[y0 * GRNG_KIN + i] : INF;
+        }
+    };
     int64_t sidx = 0;
     int64_t by = tc_next_by(bx, nb, sidx);
+    if (pipe) load_cols(by, 0);  // published by the first tile's barrier
     uint32_t acc = 0;  // TMEM column of this tile's accumulator
     int64_t by_nx = -1;
     if (pipe) {        // the strip's first tile: copy and MMAs now, the later ones a tile ahead
@@ -382,16 +423,13 @@ __global__ void __launch_bounds__(256, 1) tc_sweep_kernel(TcParams p) {
         for (int rr = lane; rr < 128; rr += 32)
           bulk_g2s(AY + rr * 136, p.A + by * 16384 + rr * 128, 256, &bars[3]);
       }
-      if (tid < 128) {
-        ny[tid] = tid < nc ? p.nrm[yb + tid] : 0.0f;
-        if (filt) parY[tid] = (p.parent && tid < nc) ? p.parent[yb + tid] : 0;
-      }
-      if (filt)
-        for (int i = tid; i < 128 * GRNG_KIN; i += 256) {
-          const bool ok = i / GRNG_KIN < nc;
-          nbrYi[i] = ok ? p.nbr_idx[yb * GRNG_KIN + i] : (uint8_t)255;
-          nbrYk[i] = ok ? p.nbr_key[yb * GRNG_KIN + i] : INF;
-        }
+      const int cbuf = pipe ? (int)(t & 1) : 0;
+      float* ny = ny2 + cbuf * 128;
+      int* parY = parY2 + cbuf * 128;
+      float* nbrYk = nbrYk2 + cbuf * 128 * GRNG_KIN;
+      uint8_t* nbrYi = nbrYi2 + cbuf * 128 * GRNG_KIN;
+      if (!pipe) load_cols(by, 0);       // published by the barrier after the MMAs
+      else if (by_next >= 0) load_cols(by_next, cbuf ^ 1);  // published by the next tile's first barrier
       if (!pipe) {
         if (tid == 0) {
           if (mbar_wait(&bars[1], phB, p.spin)) {
@@ -418,9 +456,11 @@ __global__ void __launch_bounds__(256, 1) tc_sweep_kernel(TcParams p) {
       }
       phM ^= 1;
       tc_fence_after();
-      __syncthreads();
-      if (*s_abort) break;
-      if (pipe && tid == 0 && by_next >= 0) {
+      if (!pipe) {  // also: this tile's column arrays are in place
+        __syncthreads();
+        if (*s_abort) break;
+      }
+      if (pipe && tid == 0 && by_next >= 0 && !*s_abort) {
         // this tile's MMAs have completed: sB takes the next column block's image now
         mbar_expect_tx(&bars[1], IMG);
         bulk_g2s(sB, p.img + (size_t)by_next * IMG, IMG, &bars[1]);
@@ -475,16 +515,14 @@ __global__ void __launch_bounds__(256, 1) tc_sweep_kernel(TcParams p) {
         while (pm) {
           const int j = __ffs(pm) - 1;
           pm &= pm - 1u;
-          float v = vv[0];
-#pragma unroll
-          for (int k = 1; k < 16; ++k)
-            if (j == k) v = vv[k];
+          const float v = sel16(vv, j);
           if (v < thr) thr = knn_insert_reg(kk, ki, v, (int)(yb + c0 + j), K);
         }
       }
       tc_fence_before();
       if (filt) rowx[h * 128 + r] = make_float4(m1, m2, __int_as_float(a1), __int_as_float(a2));
       __syncthreads();
+      if (*s_abort) break;
       if (pipe && by_next >= 0) {
         // the next tile's MMAs into the other accumulator, under this tile's epilogue (that
         // accumulator's last reads, in the previous tile, are ordered by the barriers since)
@@ -504,32 +542,33 @@ __global__ void __launch_bounds__(256, 1) tc_sweep_kernel(TcParams p) {
         phB ^= 1;
       }
       if (filt) {
-        // ---- column minima over the row block: thread = column, half of the rows -------
+        // ---- column minima over the row block: two lanes of a warp per column, 64 rows
+        // each (the second half-warp runs 16 rows ahead in its half: rows 65 words apart in
+        // T16 shift the bank by one, so the two half-warps read disjoint banks), merged by a
+        // shuffle ---------------------------------------------------------------------------
+        const float E = p.gam * (bmx + __uint_as_float(p.bmax[by]));
         {
-          const int c = tid & 127, hr = tid >> 7;
+          const int c = warp * 16 + (lane & 15), hr = lane >> 4;
           float c1 = INF, c2 = INF;
           int b1 = -1, b2 = -1;
-          for (int rr = hr * 64; rr < hr * 64 + 64; ++rr) {
+          for (int i = 0; i < 64; ++i) {
+            const int rr = hr * 64 + ((i + hr * 16) & 63);
             const float v = __half2float(T16[rr * 130 + c]);
             if (v < c2) {
               if (v < c1) { c2 = c1; b2 = b1; c1 = v; b1 = rr; }
               else { c2 = v; b2 = rr; }
             }
           }
-          colx[hr * 128 + c] = make_float4(c1, c2, __int_as_float(b1), __int_as_float(b2));
+          const float o1 = __shfl_xor_sync(FULLMASK, c1, 16), o2 = __shfl_xor_sync(FULLMASK, c2, 16);
+          const int ob1 = __shfl_xor_sync(FULLMASK, b1, 16), ob2 = __shfl_xor_sync(FULLMASK, b2, 16);
+          top2_merge(c1, b1, c2, b2, o1, ob1, o2, ob2);
+          if (hr == 0) {  // as certain upper bounds of the exact keys
+            cmin1[c] = hi_b(c1 + E, e); cmin2[c] = hi_b(c2 + E, e); carg1[c] = b1; carg2[c] = b2;
+          }
         }
         {  // the other half's row minima
           const float4 w4 = rowx[(1 - h) * 128 + r];
           top2_merge(m1, a1, m2, a2, w4.x, __float_as_int(w4.z), w4.y, __float_as_int(w4.w));
-        }
-        __syncthreads();
-        const float E = p.gam * (bmx + __uint_as_float(p.bmax[by]));
-        if (tid < 128) {  // the column minima as certain upper bounds of the exact keys
-          const float4 u0 = colx[tid], u1 = colx[128 + tid];
-          float c1 = u0.x, c2 = u0.y;
-          int b1 = __float_as_int(u0.z), b2 = __float_as_int(u0.w);
-          top2_merge(c1, b1, c2, b2, u1.x, __float_as_int(u1.z), u1.y, __float_as_int(u1.w));
-          cmin1[tid] = hi_b(c1 + E, e); cmin2[tid] = hi_b(c2 + E, e); carg1[tid] = b1; carg2[tid] = b2;
         }
         if (mbar_wait(&bars[3], phY, p.spin)) {
           if (tid == 0) s_pend[3] = 0;
@@ -653,23 +692,18 @@ __global__ void __launch_bounds__(256, 1) tc_sweep_kernel(TcParams p) {
           if (lane == 31 && wtot) base = atomicAdd(s_qn, wtot);
           base = __shfl_sync(FULLMASK, base, 31);
           int pos = base + incl - cnt;
+          // few columns per warp fail both tests: each lane walks its own bits; with the queue
+          // full (near the diagonal) the pair goes on to the exact tiers untested
           while (nd) {
             const int jj = __ffs(nd) - 1;
             nd &= nd - 1u;
             const int c = cb + q * 32 + jj;
-            float gj = g[0];
-#pragma unroll
-            for (int k = 1; k < 32; ++k)
-              if (jj == k) gj = g[k];
-            const float v = nxr + ny[c] - 2.0f * gj;
+            const float v = nxr + ny[c] - 2.0f * sel32(g, jj);
             if (pos < qcap) {
               Q[pos] = make_uint2((unsigned)r | ((unsigned)c << 8), __float_as_uint(v));
-            } else {  // queue full (near the diagonal): this lane tests the pair itself
-              const TcTile Tt{T16, AX, AY, nbrXk, nbrXi, nbrYk, nbrYi, cmin1, cmin2, carg1, carg2, E, diag};
-              if (!tc_full_test(Tt, r, c, v, e, m1, m2, a1, a2)) {
-                const unsigned long long sp = atomicAdd(p.surv_cnt, 1ull);
-                if (sp < p.surv_cap) p.surv[sp] = make_int2((int)(xb + r), (int)(yb + c));
-              }
+            } else {
+              const unsigned long long sp = atomicAdd(p.surv_cnt, 1ull);
+              if (sp < p.surv_cap) p.surv[sp] = make_int2((int)(xb + r), (int)(yb + c));
             }
             ++pos;
           }
