@@ -1392,32 +1392,43 @@ struct ListAux {
 };
 
 // mode 0: per-row histogram of keys below T_s; mode 1: every node with key < T_s whose
-// bucket is at most the row's last listed bucket, written at its bucket's cursor
+// bucket is at most the row's last listed bucket, written at its bucket's cursor.  Each
+// thread scans the 8 x 8 keys it holds in registers and counts (or claims list slots) with
+// shared-memory atomics, so all 256 threads scan and no key tile is staged; the order of
+// the nodes within one bucket of a list is then the order of the atomics (the list tier
+// reads a bucket whole or stops at a blocker, so the decisions do not depend on it).
 template <int KC, int METRIC>
-__global__ void __launch_bounds__(GRNG_THREADS) range_sweep_kernel(const float* __restrict__ X, int64_t n, int Dp,
-                                                                   const unsigned int* __restrict__ tkey,
-                                                                   int* __restrict__ hist,
-                                                                   const int* __restrict__ lastb,
-                                                                   const int* __restrict__ boff,
-                                                                   int32_t* __restrict__ lidx,
-                                                                   float* __restrict__ lkey, int fill,
-                                                                   ListAux aux) {
+__global__ void __launch_bounds__(GRNG_THREADS, 2) range_sweep_kernel(const float* __restrict__ X, int64_t n, int Dp,
+                                                                      const unsigned int* __restrict__ tkey,
+                                                                      int* __restrict__ hist,
+                                                                      const int* __restrict__ lastb,
+                                                                      const int* __restrict__ boff,
+                                                                      int32_t* __restrict__ lidx,
+                                                                      float* __restrict__ lkey, int fill,
+                                                                      ListAux aux) {
   extern __shared__ __align__(16) unsigned char sm_raw[];
   float* sA = reinterpret_cast<float*>(sm_raw);
   float* sB = sA + KC * GRNG_SSTRIDE;
-  float* T = sB + KC * GRNG_SSTRIDE;
-  int* H = reinterpret_cast<int*>(T + 128 * 129);  // [GRNG_HBINS][128]: lanes = rows (counts or cursors)
+  int* H = reinterpret_cast<int*>(sB + KC * GRNG_SSTRIDE);  // [GRNG_HBINS][128]: counts or cursors
+  float* Ts = reinterpret_cast<float*>(H + GRNG_HBINS * 128);  // [128] T_s of the rows (0: inactive)
+  int* Ls = reinterpret_cast<int*>(Ts + 128);                 // [128] last listed bucket
   const int64_t xb = (int64_t)blockIdx.x * GRNG_TILE;
   const int nr = (int)(n - xb < GRNG_TILE ? n - xb : GRNG_TILE);
   const int tid = threadIdx.x;
-  const float Tr = tid < nr ? __uint_as_float(tkey[xb + tid]) : 0.0f;
-  const int lastr = (fill && tid < nr) ? lastb[xb + tid] : GRNG_HBINS - 1;
-  const bool act = tid < nr && Tr > 0.0f && lastr >= 0;
+  bool act = false;
+  if (tid < 128) {
+    const float Tr = tid < nr ? __uint_as_float(tkey[xb + tid]) : 0.0f;
+    const int lastr = (fill && tid < nr) ? lastb[xb + tid] : GRNG_HBINS - 1;
+    act = tid < nr && Tr > 0.0f && lastr >= 0;
+    Ts[tid] = act ? Tr : 0.0f;
+    Ls[tid] = lastr;
+  }
   if (!__syncthreads_or(act)) return;
   for (int i = tid; i < GRNG_HBINS * 128; i += GRNG_THREADS) {
     const int b = i >> 7, r = i & 127;
     H[i] = (fill && r < nr) ? boff[(xb + r) * (GRNG_HBINS + 1) + b] : 0;
   }
+  __syncthreads();
   const int64_t nb = (n + GRNG_TILE - 1) / GRNG_TILE;
   for (int64_t by = 0; by < nb; ++by) {
     const int64_t yb = by * GRNG_TILE;
@@ -1425,38 +1436,38 @@ __global__ void __launch_bounds__(GRNG_THREADS) range_sweep_kernel(const float* 
     float acc[8][8];
     tile_keys<KC, METRIC>(X + xb * Dp, nr, X + yb * Dp, nc, Dp, sA, sB, acc);
 #pragma unroll
-    for (int i = 0; i < 8; ++i)
+    for (int i = 0; i < 8; ++i) {
+      const int row = tile_row(i);
+      const float Tr = Ts[row];
+      if (!(Tr > 0.0f)) continue;
+      const int lastr = Ls[row];
 #pragma unroll
-      for (int j = 0; j < 8; ++j) T[tile_row(i) * 129 + tile_col(j)] = acc[i][j];
-    __syncthreads();
-    if (act) {
-      for (int c = 0; c < nc; ++c) {
-        const int64_t k = yb + c;
-        if (k == xb + tid) continue;
-        const float v = T[tid * 129 + c];
-        if (v < Tr) {
-          const int b = hist_bin(v, Tr);
-          if (!fill) {
-            ++H[b * 128 + tid];
-          } else if (b <= lastr) {
-            const int pos = H[b * 128 + tid]++;
-            if (pos < GRNG_LCAP) {  // always: the counts of both sweeps agree
-              const int64_t q = (xb + tid) * GRNG_LCAP + pos;
-              lidx[q] = (int32_t)k;
-              lkey[q] = v;
-              if (aux.par) {  // the listed node's parent, its distance bound and the parent's key to the row
-                const int c = aux.parent[k];
-                aux.par[q] = c;
-                aux.pdh[q] = aux.pdist[k];
-                aux.pkey[q] = aux.atab[(xb + tid) * aux.tabw + aux.toff + c];
-              }
+      for (int j = 0; j < 8; ++j) {
+        const int col = tile_col(j);
+        const float v = acc[i][j];
+        if (!(v < Tr) || col >= nc || yb + col == xb + row) continue;
+        const int b = hist_bin(v, Tr);
+        if (!fill) {
+          atomicAdd(&H[b * 128 + row], 1);
+        } else if (b <= lastr) {
+          const int pos = atomicAdd(&H[b * 128 + row], 1);
+          if (pos < GRNG_LCAP) {  // always: the counts of both sweeps agree
+            const int64_t k = yb + col;
+            const int64_t q = (xb + row) * GRNG_LCAP + pos;
+            lidx[q] = (int32_t)k;
+            lkey[q] = v;
+            if (aux.par) {  // the listed node's parent, its distance bound and the parent's key to the row
+              const int c = aux.parent[k];
+              aux.par[q] = c;
+              aux.pdh[q] = aux.pdist[k];
+              aux.pkey[q] = aux.atab[(xb + row) * aux.tabw + aux.toff + c];
             }
           }
         }
       }
     }
-    __syncthreads();
   }
+  __syncthreads();
   if (!fill && tid < nr)
     for (int b = 0; b < GRNG_HBINS; ++b) hist[(xb + tid) * GRNG_HBINS + b] = H[b * 128 + tid];
 }
@@ -1904,7 +1915,7 @@ template <int KC>
 static void launch_range_kc(const LevelIn& in, const unsigned int* tk, int* hist, const int* lastb, const int* boff,
                             int32_t* li, float* lk, int fill, cudaStream_t s, const ListAux& aux) {
   const int64_t nb = (in.n + GRNG_TILE - 1) / GRNG_TILE;
-  const size_t smem = (size_t)(2 * KC * GRNG_SSTRIDE + 128 * 129) * 4 + (size_t)GRNG_HBINS * 128 * 4;
+  const size_t smem = (size_t)(2 * KC * GRNG_SSTRIDE) * 4 + (size_t)GRNG_HBINS * 128 * 4 + 2 * 128 * 4;
   if (in.metric == L2) {
     GRNG_CUDA(cudaFuncSetAttribute(range_sweep_kernel<KC, L2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     range_sweep_kernel<KC, L2><<<(unsigned)nb, GRNG_THREADS, smem, s>>>(in.X, in.n, in.Dp, tk, hist, lastb, boff, li,

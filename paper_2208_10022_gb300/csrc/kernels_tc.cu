@@ -520,9 +520,11 @@ __global__ void __launch_bounds__(256, 1) tc_sweep_kernel(TcParams p) {
         }
       }
       tc_fence_before();
-      if (filt) rowx[h * 128 + r] = make_float4(m1, m2, __int_as_float(a1), __int_as_float(a2));
-      __syncthreads();
-      if (*s_abort) break;
+      if (filt) {  // (a lower tile's epilogue ends here: the next tile's first barrier follows)
+        rowx[h * 128 + r] = make_float4(m1, m2, __int_as_float(a1), __int_as_float(a2));
+        __syncthreads();
+        if (*s_abort) break;
+      }
       if (pipe && by_next >= 0) {
         // the next tile's MMAs into the other accumulator, under this tile's epilogue (that
         // accumulator's last reads, in the previous tile, are ordered by the barriers since)
