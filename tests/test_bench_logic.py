@@ -41,20 +41,14 @@ def test_fp32_sweep_reports_lane_peak():
 
 
 def test_measured_traffic_lookup():
-    k = "tier3_kernel (pivot layer m=131072)"
-    saved = dict(bench.KERNEL_REVS)
-    bench.KERNEL_REVS["tier3_kernel"] = "tier3-r6"  # the revision the committed capture was taken at
-    try:
-        assert bench.measured_traffic(k, 1_000_000) > 0
-    finally:
-        bench.KERNEL_REVS.clear()
-        bench.KERNEL_REVS.update(saved)
-    assert bench.measured_traffic(k, 1_000_000) is None  # the current launch differs from the capture
-    assert bench.measured_traffic(k, 999_999) is None          # another size
-    assert bench.measured_traffic("tc_sweep_kernel (x)", 1_000_000) is None  # never captured
+    """roofline.traffic comes from the committed capture only for the same kernel, size and revision."""
+    k = "tc_sweep_kernel (exemplar Gram tiles, tcgen05 split-BF16)"
+    assert bench.measured_traffic(k, 1_000_000) == 3_126_235_908_096 + 12_864_667_648
+    assert bench.measured_traffic(k, 999_999) is None                      # another size
+    assert bench.measured_traffic("tier3_kernel (pivot layer m=131072)", 1_000_000) is None  # never captured
     saved = dict(bench.KERNEL_REVS)
     try:
-        bench.KERNEL_REVS["tier3_kernel"] = "changed"             # the kernel changed since the capture
+        bench.KERNEL_REVS["tc_sweep_kernel"] = "changed"                  # the kernel changed since the capture
         assert bench.measured_traffic(k, 1_000_000) is None
     finally:
         bench.KERNEL_REVS.clear()
