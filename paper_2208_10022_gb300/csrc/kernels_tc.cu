@@ -309,7 +309,7 @@ __global__ void __launch_bounds__(256, 1) tc_sweep_kernel(TcParams p) {
     if (tid == 0) *s_strip = atomicAdd(p.strip_ctr, 1);
     __syncthreads();
     const int64_t bx = *s_strip;
-    if (bx >= nb || *s_abort) break;
+    if (bx >= nb || __syncthreads_or(*s_abort)) break;
     const int64_t xb = bx * 128;
     const int nr = (int)(n - xb < 128 ? n - xb : 128);
     if (tid == 0) {
@@ -400,8 +400,7 @@ __global__ void __launch_bounds__(256, 1) tc_sweep_kernel(TcParams p) {
       // the previous tile's generic accesses to T16 (which may alias sB) and AY are
       // ordered before the bulk copies that overwrite them: each thread fences, then all meet
       fence_proxy_async();
-      __syncthreads();
-      if (*s_abort) break;
+      if (__syncthreads_or(*s_abort)) break;  // one answer for all threads
       if (tid == 0) {
         *s_qn = 0;
         if (!pipe) {
@@ -445,8 +444,7 @@ __global__ void __launch_bounds__(256, 1) tc_sweep_kernel(TcParams p) {
           }
         }
         phB ^= 1;
-        __syncthreads();
-        if (*s_abort) break;
+        if (__syncthreads_or(*s_abort)) break;
       }
       if (mbar_wait(&bars[2], phM, p.spin)) {
         if (tid == 0) s_pend[2] = 0;
@@ -457,8 +455,7 @@ __global__ void __launch_bounds__(256, 1) tc_sweep_kernel(TcParams p) {
       phM ^= 1;
       tc_fence_after();
       if (!pipe) {  // also: this tile's column arrays are in place
-        __syncthreads();
-        if (*s_abort) break;
+        if (__syncthreads_or(*s_abort)) break;
       }
       if (pipe && tid == 0 && by_next >= 0 && !*s_abort) {
         // this tile's MMAs have completed: sB takes the next column block's image now
@@ -522,8 +519,7 @@ __global__ void __launch_bounds__(256, 1) tc_sweep_kernel(TcParams p) {
       tc_fence_before();
       if (filt) {  // (a lower tile's epilogue ends here: the next tile's first barrier follows)
         rowx[h * 128 + r] = make_float4(m1, m2, __int_as_float(a1), __int_as_float(a2));
-        __syncthreads();
-        if (*s_abort) break;
+        if (__syncthreads_or(*s_abort)) break;
       }
       if (pipe && by_next >= 0) {
         // the next tile's MMAs into the other accumulator, under this tile's epilogue (that
@@ -903,7 +899,7 @@ __global__ void __launch_bounds__(256, 1) tc_assign_kernel(TcAssignParams p) {
     if (tid == 0) *s_strip = atomicAdd(p.strip_ctr, 1);
     __syncthreads();
     const int64_t bx = *s_strip;
-    if (bx >= nbx || *s_abort) break;
+    if (bx >= nbx || __syncthreads_or(*s_abort)) break;
     const int64_t xb = bx * 128;
     const int nr = (int)(p.nmem - xb < 128 ? p.nmem - xb : 128);
     if (tid == 0) {  // the strip's image, block 0's MMAs, block 1's copy
@@ -934,8 +930,8 @@ __global__ void __launch_bounds__(256, 1) tc_assign_kernel(TcAssignParams p) {
       const int64_t pc = pb * 128;
       const int nc = (int)(p.m - pc < 128 ? p.m - pc : 128);
       if (tid < 128) np_[tid] = tid < nc ? p.nP[pc + tid] : 0.0f;
-      __syncthreads();  // also: every read of the accumulator block pb+1 will take is done
-      if (*s_abort) break;
+      // also: every read of the accumulator block pb+1 will take is done
+      if (__syncthreads_or(*s_abort)) break;
       if (mbar_wait(&bars[2], phM, p.spin)) {  // block pb's MMAs
         if (tid == 0) s_pend[2] = 0;
       } else {
