@@ -480,15 +480,22 @@ __global__ void __launch_bounds__(256, 1) tc_sweep_kernel(TcParams p) {
         unsigned pm = 0;
         const int c0 = cb + q * 16;
         if (!filt) {
+          // only the chunk's smallest key is compared with the list's bound (insertions are rare)
+          float mn = INF;
 #pragma unroll
           for (int j = 0; j < 16; ++j) {
             const int c = c0 + j;
             float v = nxr + ny[c] - 2.0f * g[j];
             if (!full && (!vr || c >= nc)) v = INF;
             vv[j] = v;
-            if (v < thr) pm |= 1u << j;
+            mn = fminf(mn, v);
           }
+          if (mn < thr)
+#pragma unroll
+            for (int j = 0; j < 16; ++j)
+              if (vv[j] < thr) pm |= 1u << j;
         } else {
+          const float m1in = m1;  // the chunk's smallest key is below the row's minimum before it, or none is
 #pragma unroll
           for (int j = 0; j < 16; j += 2) {
             float w[2];
@@ -503,11 +510,16 @@ __global__ void __launch_bounds__(256, 1) tc_sweep_kernel(TcParams p) {
                 if (v < m1) { m2 = m1; a2 = a1; m1 = v; a1 = c; }
                 else { m2 = v; a2 = c; }
               }
-              if (v < thr) pm |= 1u << (j + u);
             }
             // two keys per 4-byte store (rows of T16 start on 4-byte boundaries)
             *reinterpret_cast<__half2*>(T16 + r * 130 + c0 + j) = __halves2half2(__float2half_ru(w[0]), __float2half_ru(w[1]));
           }
+          // a key below the list's bound is at most the running minimum m1 (m2 >= m1); the list
+          // is checked key by key only when the chunk lowered m1 below the bound or m2 lies below it
+          if (fminf(m1 < m1in ? m1 : INF, m2) < thr)
+#pragma unroll
+            for (int j = 0; j < 16; ++j)
+              if (vv[j] < thr) pm |= 1u << j;
         }
         while (pm) {
           const int j = __ffs(pm) - 1;
