@@ -1970,6 +1970,28 @@ static int num_sms() {
   return sms;
 }
 
+// pairs[m] (and their sides) regrouped by (block of the scanned endpoint, block of the other),
+// blocks of 256 or more nodes (at most 2,048 blocks), into opairs / oside
+static void group_by_blocks(const int2* pairs, const int8_t* side, int64_t m, int64_t n, DevBuf& opairs,
+                            DevBuf& oside, cudaStream_t s) {
+  int bs = 256;
+  while ((n + bs - 1) / bs > 2048) bs *= 2;
+  const int64_t nbk = (n + bs - 1) / bs, nkeys = nbk * nbk;
+  DevBuf cnt, off;
+  GRNG_CUDA(cnt.alloc((size_t)(nkeys + 1) * 8));
+  GRNG_CUDA(off.alloc((size_t)(nkeys + 1) * 8));
+  GRNG_CUDA(opairs.alloc((size_t)std::max<int64_t>(m, 1) * 8));
+  GRNG_CUDA(oside.alloc((size_t)std::max<int64_t>(m, 1)));
+  GRNG_CUDA(cudaMemsetAsync(cnt.p, 0, (size_t)(nkeys + 1) * 8, s));
+  if (m == 0) return;
+  side_count_kernel<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(pairs, side, m, cnt.as<int64_t>(), bs, nbk); note_launch();
+  GRNG_CUDA(cudaGetLastError());
+  exclusive_scan_i64(cnt.as<int64_t>(), off.as<int64_t>(), nkeys, s);
+  side_scatter_kernel<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(pairs, side, m, off.as<int64_t>(),
+                                                                   opairs.as<int2>(), oside.as<int8_t>(), bs, nbk); note_launch();
+  GRNG_CUDA(cudaGetLastError());
+}
+
 // Tiers 2 and 3, the FP64 recheck and the emission, for the candidate pairs surv[nsurv]
 // that tier 1 (or an incremental update) leaves open.  knn_idx / knn_key / knn_rb are the
 // level's neighbour lists (knn_idx null: no tier 2, every pair goes on); tier2b = false
@@ -2059,6 +2081,13 @@ static void finish_level(const LevelIn& in, LevelOut& out, LevelStats& st, cudaS
       bool dense = true;
       for (int a = 1; a < in.anc.n; ++a) dense &= in.anc.m[a] <= 32 * T3_MKW;
       if (dense) {
+        {  // in (block of x, block of y) order, so that the warps at work share ancestor-table rows
+          DevBuf zside, gpairs, gside;
+          GRNG_CUDA(zside.alloc(nun2));
+          GRNG_CUDA(cudaMemsetAsync(zside.p, 0, nun2, s));
+          group_by_blocks(unres2.as<int2>(), zside.as<int8_t>(), (int64_t)nun2, n, gpairs, gside, s);
+          std::swap(unres2, gpairs);
+        }
         Tier3Params pp{};
         pp.X = in.X; pp.n = n; pp.Dp = in.Dp; pp.metric = in.metric; pp.guide = in.grng;
         pp.rlo = in.rlo; pp.rhi = in.rhi; pp.pairs = unres2.as<int2>(); pp.m = (int64_t)nun2;
@@ -2138,23 +2167,8 @@ static void finish_level(const LevelIn& in, LevelOut& out, LevelStats& st, cudaS
       pick_side_kernel<<<(unsigned)((nun2 + 255) / 256), 256, 0, s>>>(sp); note_launch();
       GRNG_CUDA(cudaGetLastError());
       // the pairs grouped by the endpoint whose list they scan
-      DevBuf scnt, soff, spairs, sside;
-      int bs = 256;
-      while ((n + bs - 1) / bs > 2048) bs *= 2;
-      const int64_t nbk = (n + bs - 1) / bs, nkeys = nbk * nbk;
-      GRNG_CUDA(scnt.alloc((size_t)(nkeys + 1) * 8));
-      GRNG_CUDA(soff.alloc((size_t)(nkeys + 1) * 8));
-      GRNG_CUDA(spairs.alloc(nun2 * 8));
-      GRNG_CUDA(sside.alloc(nun2));
-      GRNG_CUDA(cudaMemsetAsync(scnt.p, 0, (size_t)(nkeys + 1) * 8, s));
-      side_count_kernel<<<(unsigned)((nun2 + 255) / 256), 256, 0, s>>>(unres2.as<int2>(), side.as<int8_t>(),
-                                                                      (int64_t)nun2, scnt.as<int64_t>(), bs, nbk); note_launch();
-      GRNG_CUDA(cudaGetLastError());
-      exclusive_scan_i64(scnt.as<int64_t>(), soff.as<int64_t>(), nkeys, s);
-      side_scatter_kernel<<<(unsigned)((nun2 + 255) / 256), 256, 0, s>>>(
-          unres2.as<int2>(), side.as<int8_t>(), (int64_t)nun2, soff.as<int64_t>(), spairs.as<int2>(),
-          sside.as<int8_t>(), bs, nbk); note_launch();
-      GRNG_CUDA(cudaGetLastError());
+      DevBuf spairs, sside;
+      group_by_blocks(unres2.as<int2>(), side.as<int8_t>(), (int64_t)nun2, n, spairs, sside, s);
       GRNG_CUDA(unres3.alloc(nun2 * 8));
       ListParams lp;
       lp.X = in.X; lp.Dp = in.Dp; lp.metric = in.metric; lp.guide = in.grng; lp.rlo = in.rlo; lp.rhi = in.rhi;
