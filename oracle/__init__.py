@@ -40,6 +40,8 @@ def lib():
         _lib.orc_rng_row.argtypes = [P, i64, i32, i32, i64, P, i64]
         _lib.orc_rng_rows.restype = i32
         _lib.orc_rng_rows.argtypes = [P, i64, i32, i32, P, i64, P, i64, P]
+        _lib.orc_rng_search.restype = i32
+        _lib.orc_rng_search.argtypes = [P, i64, P, i64, i32, i32, P, i64, P]
         _lib.orc_verify_witness.restype = i32
         _lib.orc_verify_witness.argtypes = [P, i32, i32, i64, i64, i64]
         _lib.orc_set_threads.restype = i32
@@ -138,6 +140,25 @@ def rng_rows(X, xs, metric=L2, row_cap=4096):
     if len(xs) and cnt.max() > row_cap:
         raise ValueError("a neighbourhood exceeds row_cap")
     return [nb[t, :cnt[t]].copy() for t in range(len(xs))]
+
+
+def rng_search(X, Q, metric=L2, row_cap=4096):
+    """RNG search (Sec. 2, Algorithm 1 without Stage VII): for each query row of Q, its
+    RNG neighbours among the index points X (a list of ascending int32 arrays).  A query
+    does not join the index: only index points block, never another query."""
+    X = _f32(X)
+    Q = _f32(Q)
+    if Q.shape[1] != X.shape[1]:
+        raise ValueError("queries and index differ in dimension")
+    m = Q.shape[0]
+    nb = np.zeros((max(m, 1), row_cap), np.int32)
+    cnt = np.zeros(max(m, 1), np.int64)
+    rc = lib().orc_rng_search(_p(X), X.shape[0], _p(Q), m, X.shape[1], metric, _p(nb), row_cap, _p(cnt))
+    if rc != 0:
+        raise MemoryError("oracle allocation failed")
+    if m and cnt.max() > row_cap:
+        raise ValueError("a neighbourhood exceeds row_cap")
+    return [nb[t, :cnt[t]].copy() for t in range(m)]
 
 
 def rng_guided(X, layers, metric=L2, with_stats=False):

@@ -202,6 +202,62 @@ int32_t orc_rng_rows(const float *X, int64_t n, int32_t D, int32_t metric, const
     return failed ? -1 : 0;
 }
 
+/* ---- RNG search (Sec. 2, Algorithm 1 without Stage VII) ------------------------
+ * The RNG neighbours among the n index points X of a query q that does not join the
+ * index: x is a neighbour iff no index point z other than x lies strictly inside the
+ * open lune of (q, x) (Eq. 1 over X plus q alone).  Other queries are not points of
+ * the index, so they never block.  As in rng_row_into, the candidates z are scanned in
+ * increasing key(q, z), and only while strictly closer to q than x is.
+ * Neighbours (ascending index) into nbrs[cap]; o[n], is[n] are caller scratch. */
+static int64_t search_row_into(const float *X, int64_t n, const float *q, int32_t D, int32_t metric,
+                               int32_t *nbrs, int64_t cap, kv_t *o, unsigned char *is) {
+    for (int64_t z = 0; z < n; ++z) { o[z].k = orc_key(q, X + z * D, D, metric); o[z].i = z; }
+    qsort(o, (size_t)n, sizeof(kv_t), kv_cmp);
+    for (int64_t p = 0; p < n; ++p) {
+        int64_t x = o[p].i;
+        double dqx = o[p].k;
+        int blocked = 0;
+        for (int64_t t = 0; t < n && !blocked; ++t) {
+            if (!(o[t].k < dqx)) break;              /* z not strictly closer to q */
+            int64_t z = o[t].i;
+            if (z == x) continue;
+            double dxz = orc_key(X + x * D, X + z * D, D, metric);
+            if (dxz < dqx) blocked = 1;             /* max(d(q,z), d(x,z)) < d(q,x) */
+        }
+        is[x] = (unsigned char)!blocked;
+    }
+    int64_t cnt = 0;
+    for (int64_t x = 0; x < n; ++x)
+        if (is[x]) { if (cnt < cap) nbrs[cnt] = (int32_t)x; ++cnt; }
+    return cnt;
+}
+
+/* The search neighbourhoods of m queries Q[m][D] over the index X[n][D] (queries spread
+ * over the OpenMP threads).  Query t's neighbours go to nbrs[t * row_cap ...], its count
+ * to cnt[t] (a count above row_cap means the row was cut).  Returns 0, or -1 on
+ * allocation failure. */
+int32_t orc_rng_search(const float *X, int64_t n, const float *Q, int64_t m, int32_t D, int32_t metric,
+                       int32_t *nbrs, int64_t row_cap, int64_t *cnt) {
+    int failed = 0;
+#pragma omp parallel
+    {
+        kv_t *o = (kv_t *)malloc(sizeof(kv_t) * (size_t)(n > 0 ? n : 1));
+        unsigned char *is = (unsigned char *)malloc((size_t)(n > 0 ? n : 1));
+        if (!o || !is) {
+#pragma omp atomic write
+            failed = 1;
+        }
+#pragma omp for schedule(dynamic, 1)
+        for (int64_t t = 0; t < m; ++t) {
+            if (o && is)
+                cnt[t] = search_row_into(X, n, Q + t * D, D, metric, nbrs + t * row_cap, row_cap, o, is);
+        }
+        free(o);
+        free(is);
+    }
+    return failed ? -1 : 0;
+}
+
 /* Witness check (Eq. 1): 1 if z is a point other than x and y lying strictly inside
  * the open lune of (x, y), i.e. max(d(x,z), d(y,z)) < d(x,y), so that z proves the pair
  * is not an RNG edge; else 0. */

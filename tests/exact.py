@@ -27,6 +27,20 @@ def rng(X, metric):
     return out
 
 
+def rng_search(X, Q, metric):
+    """For each query q of Q, the index points x of X (ascending) with no index point z
+    other than x strictly inside the open lune of (q, x): Eq. 1 over X plus q alone."""
+    out = []
+    for q in Q:
+        kq = [key(q, x, metric) for x in X]
+        row = []
+        for i, x in enumerate(X):
+            if not any(max(kq[k], key(X[k], x, metric)) < kq[i] for k in range(len(X)) if k != i):
+                row.append(i)
+        out.append(row)
+    return out
+
+
 def _sqrt_lt_sqrt_minus(a, b, c):
     """Exactly decide sqrt(a) < sqrt(b) - c for rationals a, b >= 0 and c >= 0."""
     # sqrt(a) + c < sqrt(b)  <=>  a + c^2 + 2c sqrt(a) < b

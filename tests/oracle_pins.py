@@ -20,6 +20,9 @@ What pins what:
                               every non-edge of Eq. 1 has a witness
   spanning_trees           -- Prim's tree has the weight of an exact Kruskal over all
                               pairs and lies in the RNG
+  search                   -- RNG search (Algorithm 1 without Stage VII) against the exact
+                              rational restatement, against the brute-force RNG of the
+                              index plus that one query, and batch = one query at a time
 """
 import json
 import os
@@ -292,5 +295,31 @@ def spanning_trees(orc, seed=17):
             assert {(min(int(a), int(b)), max(int(a), int(b))) for a, b in T} <= E
 
 
+def search(orc, trials=30, seed=18):
+    rng = np.random.default_rng(seed)
+    for t in range(trials):  # exact arithmetic on small integers: ties and duplicates
+        n = int(rng.integers(2, 10))
+        d = int(rng.integers(1, 4))
+        X = _rand_int_points(rng, n, d, 4)
+        Q = np.concatenate([_rand_int_points(rng, 3, d, 4), X[:1]])  # the last one duplicates x0
+        for metric in (exact.L2, exact.L1):
+            want = exact.rng_search(X.tolist(), Q.tolist(), metric)
+            got = [list(map(int, r)) for r in orc.rng_search(X, Q, metric)]
+            assert got == want, (t, metric, X.tolist(), Q.tolist(), want, got)
+    # a query alone: its neighbours are its edges in the RNG of the index plus it (Eq. 1)
+    for t in range(6):
+        X = rng.normal(size=(120, 5)).astype(np.float32)
+        Q = rng.normal(size=(8, 5)).astype(np.float32) * 1.5
+        Q[0] = X[7]                                               # a duplicate of an index point
+        for metric in (exact.L2, exact.L1):
+            got = orc.rng_search(X, Q, metric)
+            for j in range(len(Q)):
+                E = orc.rng_brute(np.concatenate([X, Q[j:j + 1]]), metric)
+                want = sorted(int(a) for a, b in E if b == len(X))
+                assert list(map(int, got[j])) == want, (t, metric, j)
+                assert list(map(int, orc.rng_search(X, Q[j:j + 1], metric)[0])) == want  # alone = in a batch
+            assert 7 in set(map(int, got[0]))                        # a duplicate is always linked
+
+
 ALL = [exact_rng, exact_grng, worked_examples, invariants, theorems, cross_checks, layer_examples, witnesses,
-       spanning_trees]
+       spanning_trees, search]

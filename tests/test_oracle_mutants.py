@@ -32,6 +32,9 @@ MUTANTS = {
     "delta_max_with_member_radius": ("if (delta_max && ds[t] > delta_max[as[t]]) delta_max[as[t]] = ds[t];",
                                      "if (delta_max && rr > delta_max[as[t]]) delta_max[as[t]] = rr;"),
     "witness_closed_lune": ("return m < dxy ? 1 : 0;", "return m <= dxy ? 1 : 0;"),
+    "search_closed_lune": ("if (dxz < dqx) blocked = 1;", "if (dxz <= dqx) blocked = 1;"),
+    "search_scan_stops_early": ("if (!(o[t].k < dqx)) break;", "if (!(o[t].k < 0.5 * dqx)) break;"),
+    "search_scan_not_strict": ("if (!(o[t].k < dqx)) break;", "if (!(o[t].k <= dqx)) break;"),
     "emst_wrong_endpoint": ("edges[2 * (e - 1)] = (int32_t)from[u];",
                             "edges[2 * (e - 1)] = (int32_t)(u > 0 ? u - 1 : 1);"),
 }
