@@ -62,6 +62,11 @@ def parse():
                     help="instead of the build benchmark: insert B batches of uneven size (log-uniform in "
                          "[1,000, 65,536] points, scaled to --n) into an index built on the rest, and print "
                          "points/s and per-batch latency")
+    ap.add_argument("--search", type=int, default=0, metavar="B",
+                    help="instead of the build benchmark: B batches of --search-m queries (RNG search)")
+    ap.add_argument("--search-m", type=int, default=1000, help="queries per search batch")
+    ap.add_argument("--search-check", type=int, default=32,
+                    help="queries of the first batch compared with the oracle (FP64 on the host)")
     ap.add_argument("--insert-verify", action="store_true",
                     help="with --insert: compare the final edges with a build from scratch on all points")
     return ap.parse_args()
@@ -662,6 +667,79 @@ def run_insert(a, rank):
     return 0
 
 
+def run_search(a, rank):
+    """RNG search (rng_search_batch): an index is built on n points of the workload, then B
+    batches of m queries of the same generator (points the index does not hold) are searched;
+    each batch is timed with CUDA events on the index's stream, its queries resident on the
+    device.  --search-check queries of the first batch are compared with the FP64 oracle
+    (Eq. 1 over the index plus the query), whose time per query is the CPU baseline."""
+    import numpy as np
+    import torch
+
+    import paper_2208_10022_gb300 as g
+    from paper_2208_10022_gb300 import build as gb
+    from paper_2208_10022_gb300 import workloads as wl
+    gb.build()
+    N0, D, _, ds, ps = wl.SPECS[a.kind]
+    n = a.n or N0
+    m, B = a.search_m, a.search
+    X = wl.gen_points(a.kind, n + m * B, ds)
+    layers = wl.nested_pivots(n, wl.scaled_layer_sizes(a.kind, n), ps)
+    prec = g.BF16 if a.precision == "bf16" else g.FP32
+    metric = g.L1 if a.metric == "l1" else g.L2
+    stream = torch.cuda.current_stream()
+    Xd = torch.from_numpy(X).cuda()
+    ix, _ = g.build_all(Xd[:n], layers, metric=metric, precision=prec, stream=stream)
+    flush = torch.empty(4 * L2_BYTES, dtype=torch.uint8, device="cuda") if X.nbytes < 2 * L2_BYTES else None
+    ix.rng_search_batch(Xd[n:n + min(m, 64)])  # warm-up: the cached index rows and block keys
+    lat, counts, first = [], [], None
+    for b in range(B):
+        Q = Xd[n + b * m:n + (b + 1) * m]
+        if flush is not None:
+            flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        counts.append(ix.rng_search_batch(Q))
+        e1.record(stream)
+        torch.cuda.synchronize()
+        lat.append(e0.elapsed_time(e1))
+        if b == 0:
+            off, nb = ix.rng_search_result()
+            first = (off.copy(), nb.copy())
+    st = ix.stats()["search"]
+    check = None
+    cpu = None
+    if a.search_check and rank == 0:
+        import oracle
+        k = min(a.search_check, m)
+        t0 = time.perf_counter()
+        want = oracle.rng_search(X[:n], X[n:n + k], metric)
+        cpu_s = time.perf_counter() - t0
+        off, nb = first
+        bad = sum(0 if np.array_equal(nb[off[j]:off[j + 1]], want[j]) else 1 for j in range(k))
+        check = {"queries": k, "mismatches": bad}
+        cpu = {"value": k / cpu_s, "unit": "queries/s", "cores": oracle.max_threads(), "kind": "oracle",
+               "sample": f"{k} queries of the first batch against all {n:,} index points"}
+    tot = sum(lat)
+    line = {"metric": "RNG search queries/s", "value": m * B / (tot / 1000.0), "unit": "queries/s",
+            "higher_is_better": True, "n_gpus": 1, "batches": B, "queries_per_batch": m,
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "neighbours_per_query": float(np.sum(counts)) / (m * B),
+            "candidate_pairs_per_query": st["candidate_pairs"] / max(st["queries"], 1),
+            "tier1_survivors_per_query": st["tier1_survivors"] / max(st["queries"], 1),
+            "outside_ball_fraction": st["outside_ball"] / max(st["queries"], 1),
+            "oracle_check": check, "cpu_baseline": cpu, "work": st,
+            "config": {"workload": f"{a.kind}: index of {n:,} x {D} FP32, L{1 if metric == g.L1 else 2}, nested "
+                                   f"random pivot layers {'/'.join(str(len(l)) for l in layers)}; queries: further "
+                                   f"points of the same generator",
+                       "precision": a.precision,
+                       "l2_flush": ("L2 flushed before every batch (outside its events)" if flush is not None
+                                    else "index larger than L2 (points alone are %d MB)" % (X.nbytes >> 20))}}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     a = parse()
     rank, world, local = dist_env()
@@ -669,6 +747,8 @@ def main():
         return run_reference(a, rank, world)
     if a.insert:
         return run_insert(a, rank)
+    if a.search:
+        return run_search(a, rank)
     return run_gpu(a, rank, world, local)
 
 

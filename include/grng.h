@@ -140,10 +140,29 @@ grng_status rng_build_exact(grng_index* idx);
  * the RNG of the enlarged set (Algorithm 1 and Stage VII, Sec. 2).  Requires a
  * built RNG.  The new points get ids n .. n+m-1 and join the finest layer's domains;
  * every layer keeps its pivots.  Radii, delta_max, every GRNG and the RNG are then
- * those of a build from scratch on the enlarged set with the same pivots (this
- * version recomputes them; results are exact, the cost is that of a rebuild).
+ * those of a build from scratch on the enlarged set with the same pivots; only what
+ * the batch can change is recomputed (grown radii, the GRNG pairs they reopen, the
+ * batch points' pairs, and Stage VII for the old edges a batch point may enter).
  * On failure the index must be destroyed. */
 grng_status rng_insert_batch(grng_index* idx, const float* pts, int64_t m);
+
+/* RNG search (Algorithm 1 without Stage VII, Sec. 2): for each of m query points
+ * queries[m][dim] (FP32, row-major, host or device), its RNG neighbours among the
+ * index points: x is a neighbour of q iff no index point other than x lies strictly
+ * inside the open lune of (q, x) (Eq. 1 over the index plus q alone).  The queries do
+ * not join the index and never block one another; the index is not changed.  Every
+ * layer must be built and linked (the finest GRNG restricts each query's candidates by
+ * Theorem 1 when the query lies in its nearest finest pivot's ball).  *total (if not
+ * NULL) receives the number of (query, neighbour) pairs; the result stays in the index
+ * until the next search and is read with rng_search_result.  Errors: GRNG_EINVAL for
+ * NULL queries, m < 1 or n + m >= 2^31; GRNG_ESTATE when a layer is not linked. */
+grng_status rng_search_batch(grng_index* idx, const float* queries, int64_t m, int64_t* total);
+
+/* The last search's result as CSR over the queries in input order: off[m+1] (int64) and
+ * nbrs[off[m]] (int32 original point ids, ascending within a query), host or device;
+ * either may be NULL.  GRNG_ESTATE before any search; GRNG_ETRUNC (off still written)
+ * when cap < off[m]. */
+grng_status rng_search_result(const grng_index* idx, int64_t* off, int32_t* nbrs, int64_t cap);
 
 /* Copy the RNG edges: ij[cap][2] int32 point indices with i < j, lexicographically
  * sorted (host or device).  *n_edges receives the edge count; if cap < count the

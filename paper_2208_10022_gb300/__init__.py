@@ -30,7 +30,8 @@ FP32, BF16, FP8 = 0, 1, 2
 
 EXPORTS = [
     "grng_default_opts", "grng_create", "grng_build_layer", "grng_link_pivots", "grng_adjacency_rows",
-    "rng_build_exact", "rng_insert_batch", "rng_edges", "grng_stats", "grng_destroy", "grng_last_error",
+    "rng_build_exact", "rng_insert_batch", "rng_search_batch", "rng_search_result", "rng_edges", "grng_stats",
+    "grng_destroy", "grng_last_error",
 ]
 
 
@@ -68,6 +69,8 @@ def lib():
         L.grng_adjacency_rows.argtypes = [P, i32, i64, i64, P, P, i64, ctypes.POINTER(i64)]
         L.rng_build_exact.argtypes = [P]
         L.rng_insert_batch.argtypes = [P, P, i64]
+        L.rng_search_batch.argtypes = [P, P, i64, ctypes.POINTER(i64)]
+        L.rng_search_result.argtypes = [P, P, P, i64]
         L.rng_edges.argtypes = [P, P, i64, ctypes.POINTER(i64)]
         L.grng_stats.argtypes = [P, ctypes.c_char_p, sz]
         L.grng_destroy.argtypes = [P]
@@ -83,7 +86,8 @@ def lib():
         L.grng_mlp_dataset.argtypes = [P, P, P, i64, ctypes.POINTER(i64)]
         L.grng_tc_keys.argtypes = [P, i64, i32, P]
         for f in ("grng_create", "grng_build_layer", "grng_link_pivots", "grng_adjacency_rows",
-                  "rng_build_exact", "rng_insert_batch", "rng_edges", "grng_stats", "grng_mlp_score",
+                  "rng_build_exact", "rng_insert_batch", "rng_search_batch", "rng_search_result", "rng_edges",
+                  "grng_stats", "grng_mlp_score",
                   "grng_mlp_loss_grad", "grng_mlp_train", "grng_mlp_dataset", "grng_tc_keys"):
             getattr(L, f).restype = i32
         _lib = L
@@ -196,6 +200,33 @@ class Index:
     def rng_insert_batch(self, points):
         pts = _contig(points, np.float32)
         _check(lib().rng_insert_batch(self._h, _ptr(pts), int(pts.shape[0])))
+
+    def rng_search_batch(self, queries):
+        """Search m queries [m, dim] (host or cuda); returns the number of (query, neighbour)
+        pairs, kept in the index for rng_search_result."""
+        q = _contig(queries, np.float32)
+        tot = ctypes.c_int64(0)
+        _check(lib().rng_search_batch(self._h, _ptr(q), int(q.shape[0]), ctypes.byref(tot)))
+        self._search_m = int(q.shape[0])
+        return tot.value
+
+    def rng_search_result(self, off=None, nbrs=None):
+        """(off int64 [m+1], nbrs int32 [off[m]]) of the last search; `off`/`nbrs` may be
+        preallocated numpy arrays or cuda tensors of at least that size."""
+        if off is None:
+            off = np.zeros(getattr(self, "_search_m", 0) + 1, np.int64)
+        _check(lib().rng_search_result(self._h, _ptr(off), None, 0))
+        total = int(off[-1]) if isinstance(off, np.ndarray) else int(off[-1].item())
+        if nbrs is None:
+            nbrs = np.zeros(max(total, 1), np.int32)
+        _check(lib().rng_search_result(self._h, _ptr(off), _ptr(nbrs), total))
+        return off, nbrs[:total]
+
+    def rng_search(self, queries):
+        """Neighbours of each query among the index points: a list of ascending int32 arrays."""
+        self.rng_search_batch(queries)
+        off, nb = self.rng_search_result()
+        return [nb[off[j]:off[j + 1]] for j in range(len(off) - 1)]
 
     def n_edges(self):
         ne = ctypes.c_int64(0)

@@ -86,6 +86,42 @@ __global__ void narrow_kernel(const uint64_t* __restrict__ in, int64_t m, int32_
   if (t < m) out[t] = (int32_t)in[t];
 }
 
+// ---- search (queries that do not join the index) ----------------------------------------
+__global__ void iota_from_kernel(int32_t* a, int64_t m, int64_t base) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < m) a[i] = (int32_t)(base + i);
+}
+// a query's parent for Theorem 1: its nearest finest pivot (sorted position) when the query
+// lies in that pivot's ball D(p, r) (Eq. 2), else -1 (no pivot's GRNG links cover it)
+__global__ void search_parent_kernel(const int32_t* __restrict__ assign, const double* __restrict__ dist,
+                                     const double* __restrict__ radius, const int32_t* __restrict__ rank, int64_t m,
+                                     int32_t* __restrict__ parent, unsigned long long* __restrict__ outside) {
+  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= m) return;
+  const int a = assign[t];
+  const bool in = dist[t] <= radius[a];
+  parent[t] = in ? rank[a] : -1;
+  if (!in) atomicAdd(outside, 1ull);
+}
+// an edge (index id, n + j) of the level's output becomes (j, index id)
+__global__ void search_key_kernel(uint64_t* __restrict__ k, int64_t ne, int64_t n) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= ne) return;
+  const uint64_t v = k[i];
+  const uint64_t lo = v >> 32, hi = v & 0xffffffffu;  // lo < n <= hi
+  k[i] = ((hi - (uint64_t)n) << 32) | lo;
+}
+// CSR of the sorted (query, id) keys: nbr[i] = id, off[j] = first i of query j, off[m] = ne
+__global__ void search_csr_kernel(const uint64_t* __restrict__ k, int64_t ne, int64_t m, int64_t* __restrict__ off,
+                                  int32_t* __restrict__ nbr) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i > ne) return;
+  if (i < ne) nbr[i] = (int32_t)(k[i] & 0xffffffffu);
+  const int64_t prev = i == 0 ? -1 : (int64_t)(k[i - 1] >> 32);
+  const int64_t cur = i == ne ? m : (int64_t)(k[i] >> 32);
+  for (int64_t j = prev + 1; j <= cur; ++j) off[j] = i;
+}
+
 static inline unsigned nblk(int64_t m, int b = 256) { return (unsigned)((m + b - 1) / b); }
 
 struct Layer {
@@ -153,6 +189,16 @@ struct grng_index {
   DevBuf mlp;            // ranking network parameters (learned shortlist), or empty
   DevBuf rec_f, rec_y;   // recorded training samples of the last RNG build
   int64_t rec_n = 0;
+  int64_t version = 0;   // bumped whenever the points, their order or their parents change
+  struct {               // search: rows kept for one index version, and the last result
+    int64_t version = -1, cap = 0;
+    DevBuf X, orig, parent, knn_k, knn_i;  // [n + cap] index rows (sorted order), then queries
+    DevBuf A, nb_i, nb_k;                  // in-block keys and neighbours of the index blocks
+    DevBuf off, nbrs;
+    int64_t m = 0, total = 0;
+    long long batches = 0, queries = 0, outside = 0, candidates = 0, survivors = 0, neighbours = 0;
+    double ms = 0, last_ms = 0;
+  } srch;
 };
 
 namespace {
@@ -272,6 +318,7 @@ void sort_exemplars(grng_index* ix) {
   gather_rows(ix->X.as<float>(), ix->Dp, ix->xorder.as<int32_t>(), n, ix->Xs.as<float>(), s);
   GRNG_CUDA(cudaGetLastError());
   GRNG_CUDA(cudaStreamSynchronize(s));
+  ix->version += 1;
 }
 
 // layers 0..count-1 as the ancestors of a level (the last one is the direct parent,
@@ -900,6 +947,165 @@ grng_status rng_insert_batch(grng_index* ix, const float* pts, int64_t m) {
   });
 }
 
+// RNG search (Algorithm 1 without Stage VII, Sec. 2).  The queries are appended as rows
+// n .. n+m-1 after the index's points in sorted order, with ids n + j; they are members of no
+// pivot domain, so the exhaustive tier never takes one as an interceptor, and the sweep runs
+// in its query mode, where only index points block.  Stage I: Theorem 1 restricts a query's
+// candidates when the query lies in its nearest finest pivot's ball (the GRNG's guarantee
+// covers exactly the points of the balls), else every index point is a candidate.
+grng_status rng_search_batch(grng_index* ix, const float* queries, int64_t m, int64_t* total) {
+  if (!ix) {
+    g_last_error = "index is NULL";
+    return GRNG_EINVAL;
+  }
+  return guarded(ix, [&] {
+    if (!queries || m < 1) fail(GRNG_EINVAL, "need queries and m >= 1");
+    if (ix->layers.empty()) fail(GRNG_ESTATE, "the index has no pivot layer");
+    for (auto& l : ix->layers)
+      if (!l.linked) fail(GRNG_ESTATE, "every layer must be built and linked");
+    if (ix->n + m >= (int64_t)1 << 31) fail(GRNG_EINVAL, "n + m must stay below 2^31");
+    ensure_sorted(ix);
+    cudaStream_t s = ix->stream;
+    Timer tm(s);
+    auto& W = ix->srch;
+    W.m = 0;
+    W.total = 0;
+    const int L = (int)ix->layers.size();
+    const int Dp = ix->Dp, D = ix->D, K = ix->K, metric = ix->metric;
+    const int64_t n = ix->n;
+    Layer& fin = ix->layers[L - 1];
+    if (W.version != ix->version) {  // in-block keys and neighbours of the index's 128-point blocks
+      const int64_t nb = (n + 127) / 128;
+      GRNG_CUDA(W.A.alloc((size_t)nb * 128 * 128 * 2));
+      GRNG_CUDA(W.nb_i.alloc((size_t)nb * 128 * GRNG_KIN));
+      GRNG_CUDA(W.nb_k.alloc((size_t)nb * 128 * GRNG_KIN * 4));
+      block_prep(ix->Xs.as<float>(), n, Dp, metric, W.A.as<__half>(), W.nb_i.as<uint8_t>(), W.nb_k.as<float>(), s);
+      W.cap = 0;
+    }
+    if (W.version != ix->version || W.cap < m) {  // index rows, then room for the queries
+      const int64_t cap = (std::max(m, W.cap) + 127) / 128 * 128;
+      const int64_t rows = n + cap;
+      GRNG_CUDA(W.X.alloc((size_t)rows * Dp * 4));
+      GRNG_CUDA(cudaMemcpyAsync(W.X.p, ix->Xs.p, (size_t)n * Dp * 4, cudaMemcpyDeviceToDevice, s));
+      GRNG_CUDA(cudaMemsetAsync(W.X.as<float>() + n * Dp, 0, (size_t)cap * Dp * 4, s));
+      GRNG_CUDA(W.orig.alloc((size_t)rows * 4));
+      GRNG_CUDA(cudaMemcpyAsync(W.orig.p, ix->xorder.p, (size_t)n * 4, cudaMemcpyDeviceToDevice, s));
+      iota_from_kernel<<<nblk(cap), 256, 0, s>>>(W.orig.as<int32_t>() + n, cap, n); note_launch();
+      GRNG_CUDA(W.parent.alloc((size_t)rows * 4));
+      GRNG_CUDA(cudaMemcpyAsync(W.parent.p, ix->xparent.p, (size_t)n * 4, cudaMemcpyDeviceToDevice, s));
+      GRNG_CUDA(W.knn_k.alloc((size_t)rows * K * 4));
+      GRNG_CUDA(W.knn_i.alloc((size_t)rows * K * 4));
+      GRNG_CUDA(cudaGetLastError());
+      W.cap = cap;
+      W.version = ix->version;
+    }
+    // ---- the queries as rows n .. n+m-1 (zero padded to Dp) -------------------------------
+    float* Xq = W.X.as<float>() + n * Dp;
+    GRNG_CUDA(cudaMemsetAsync(Xq, 0, (size_t)m * Dp * 4, s));
+    GRNG_CUDA(cudaMemcpy2DAsync(Xq, (size_t)Dp * 4, queries, (size_t)D * 4, (size_t)D * 4, (size_t)m,
+                                cudaMemcpyDefault, s));
+    // ---- nearest finest pivot (Eq. 2), and whether its ball holds the query ----------------
+    DevBuf ab, db, rb, ddb, ctr, surv, s7, E;
+    {
+      const int64_t M = fin.m;
+      GRNG_CUDA(ab.alloc((size_t)m * 4));
+      GRNG_CUDA(db.alloc((size_t)m * 8));
+      GRNG_CUDA(rb.alloc((size_t)M * 8));
+      GRNG_CUDA(ddb.alloc((size_t)M * 8));
+      AssignOut ao{ab.as<int32_t>(), db.as<double>(), rb.as<double>(), ddb.as<double>()};
+      assign_layer(Xq, W.orig.as<int32_t>() + n, nullptr, m, fin.Xp.as<float>(), fin.piv.as<int32_t>(), M, n + m, D,
+                   Dp, metric, ao, nullptr, s, ix->opts.precision == GRNG_BF16,
+                   ix->opts.spin_limit > 0 ? ix->opts.spin_limit : 1ll << 24);
+      GRNG_CUDA(ctr.alloc(8));
+      GRNG_CUDA(cudaMemsetAsync(ctr.p, 0, 8, s));
+      search_parent_kernel<<<nblk(m), 256, 0, s>>>(ab.as<int32_t>(), db.as<double>(), fin.radius.as<double>(),
+                                                   fin.rank.as<int32_t>(), m, W.parent.as<int32_t>() + n,
+                                                   ctr.as<unsigned long long>()); note_launch();
+      GRNG_CUDA(cudaGetLastError());
+      unsigned long long outside = 0;
+      GRNG_CUDA(cudaMemcpyAsync(&outside, ctr.p, 8, cudaMemcpyDeviceToHost, s));
+      GRNG_CUDA(cudaStreamSynchronize(s));
+      W.outside += (long long)outside;
+    }
+    // ---- Stages I-V: the query rows against every index point (tier 1, K nearest) -------
+    InsertSweep S;
+    S.XB = Xq; S.rowpos = W.orig.as<int32_t>() + n; S.mb = m;  // row j sits at position n + j
+    S.AB = nullptr; S.nbrB_i = nullptr; S.nbrB_k = nullptr;
+    S.X = W.X.as<float>(); S.n = n; S.Dp = Dp; S.K = K; S.metric = metric;
+    S.A = W.A.as<__half>(); S.nbr_i = W.nb_i.as<uint8_t>(); S.nbr_k = W.nb_k.as<float>();
+    S.is_new = nullptr; S.parent = W.parent.as<int32_t>();
+    S.gpar = fin.gg.as<uint32_t>(); S.gpar_words = fin.words; S.maxe = nullptr;
+    S.search = 1;
+    int64_t nsurv = 0, ns7 = 0;
+    unsigned long long sst[2] = {0, 0};
+    insert_sweep(S, surv, &nsurv, s7, &ns7, W.knn_k.as<float>(), W.knn_i.as<int32_t>(), sst, s);
+    W.candidates += (long long)sst[0];
+    W.survivors += nsurv;
+    // ---- Stage VI: tiers 2 (the queries' K nearest) and 3, FP64 recheck -------------------
+    LevelIn in{};
+    in.X = W.X.as<float>();
+    in.n = n + m;
+    in.D = D;
+    in.Dp = Dp;
+    in.metric = metric;
+    in.grng = 0;
+    in.K = K;
+    in.parent = W.parent.as<int32_t>();
+    in.gpar = fin.gg.as<uint32_t>();
+    in.gpar_words = fin.words;
+    in.orig = W.orig.as<int32_t>();
+    in.anc = ancestors_of(ix, L);
+    in.pdist_hi = ix->xpdh.as<float>();  // read for index points only (the interceptors)
+    in.npts = n;
+    if (ix->opts.spin_limit > 0) in.spin = ix->opts.spin_limit;
+    in.small_buffers = (ix->opts.flags & GRNG_FLAG_SMALL_BUFFERS) ? 1 : 0;
+    LevelOut lo;
+    lo.edges = &E;
+    LevelStats st;
+    run_pairs(in, lo, st, s, surv.as<int2>(), nsurv, W.knn_i.as<int32_t>(), W.knn_k.as<float>(), false);
+    // ---- CSR over the queries ----------------------------------------------------------------
+    const int64_t ne = lo.n_edges;
+    GRNG_CUDA(W.off.alloc((size_t)(m + 1) * 8));
+    GRNG_CUDA(W.nbrs.alloc((size_t)std::max<int64_t>(ne, 1) * 4));
+    if (ne) {
+      search_key_kernel<<<nblk(ne), 256, 0, s>>>(E.as<uint64_t>(), ne, n); note_launch();
+      DevBuf tmp;
+      if (ne > 1) sort_u64(E.as<uint64_t>(), ne, tmp, s);
+    }
+    search_csr_kernel<<<nblk(ne + 1), 256, 0, s>>>(E.p ? E.as<uint64_t>() : nullptr, ne, m, W.off.as<int64_t>(),
+                                                   W.nbrs.as<int32_t>()); note_launch();
+    GRNG_CUDA(cudaGetLastError());
+    GRNG_CUDA(cudaStreamSynchronize(s));
+    W.m = m;
+    W.total = ne;
+    W.neighbours += ne;
+    W.batches += 1;
+    W.queries += m;
+    W.last_ms = tm.stop();
+    W.ms += W.last_ms;
+    if (total) *total = ne;
+  });
+}
+
+grng_status rng_search_result(const grng_index* cix, int64_t* off, int32_t* nbrs, int64_t cap) {
+  grng_index* ix = const_cast<grng_index*>(cix);
+  if (!ix) {
+    g_last_error = "index is NULL";
+    return GRNG_EINVAL;
+  }
+  return guarded(ix, [&] {
+    auto& W = ix->srch;
+    if (W.m == 0) fail(GRNG_ESTATE, "no search result");
+    cudaStream_t s = ix->stream;
+    copy_out(off, W.off.p, (size_t)(W.m + 1) * 8, s);
+    GRNG_CUDA(cudaStreamSynchronize(s));
+    if (!nbrs) return;
+    if (cap < W.total) fail(GRNG_ETRUNC, "neighbour buffer too small");
+    copy_out(nbrs, W.nbrs.p, (size_t)W.total * 4, s);
+    GRNG_CUDA(cudaStreamSynchronize(s));
+  });
+}
+
 grng_status rng_edges(const grng_index* cix, int32_t* ij, int64_t cap, int64_t* n_edges) {
   grng_index* ix = const_cast<grng_index*>(cix);
   if (!ix) {
@@ -952,11 +1158,14 @@ grng_status grng_stats(const grng_index* cix, char* json, size_t cap) {
            "\"insert\":{\"batches\":%lld,\"points\":%lld,\"ms\":%.4f,\"changed_pivots\":%lld,"
            "\"grng_pairs\":%lld,\"grng_links_added\":%lld,\"candidate_pairs\":%lld,\"tier1_survivors\":%lld,"
            "\"stage7_candidates\":%lld,\"stage7_tests\":%lld,\"stage7_fp64\":%lld,\"new_edges\":%lld,"
-           "\"removed_edges\":%lld},",
+           "\"removed_edges\":%lld},"
+           "\"search\":{\"batches\":%lld,\"queries\":%lld,\"ms\":%.4f,\"last_ms\":%.4f,\"outside_ball\":%lld,"
+           "\"candidate_pairs\":%lld,\"tier1_survivors\":%lld,\"neighbours\":%lld},",
            (int)ix->rng_built, (long long)ix->n_edges, ix->rng_ms, ix->rng_tile_ms, (long long)ix->insert_batches,
            (long long)ix->inserted, ix->insert_ms, ix->ins.changed_pivots, ix->ins.grng_pairs, ix->ins.grng_linked,
            ix->ins.candidates, ix->ins.survivors, ix->ins.s7_candidates, ix->ins.s7_tests, ix->ins.s7_fp64,
-           ix->ins.new_edges, ix->ins.removed_edges);
+           ix->ins.new_edges, ix->ins.removed_edges, ix->srch.batches, ix->srch.queries, ix->srch.ms,
+           ix->srch.last_ms, ix->srch.outside, ix->srch.candidates, ix->srch.survivors, ix->srch.neighbours);
   js += buf;
   level_json(js, "rng", ix->rng_st);
   js += "}";

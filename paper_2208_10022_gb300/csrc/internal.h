@@ -125,6 +125,8 @@ struct LevelIn {
   int mlp_record = 0;                 // RNG level: record features and labels of the tier-3 pairs' pools
   int small_buffers = 0;              // testing: tiny first capacities, so every retry and fallback runs
   int lists = 1;                      // GRNG levels: range lists for the pairs tier 2 leaves open
+  int64_t npts = 0;                   // rows [0, npts) may block a pair (0: all n); the rows
+                                      // beyond are search queries, endpoints only
 };
 
 // ---- tensor-core tiles (kernels_tc.cu) ------------------------------------------------------
@@ -262,6 +264,8 @@ struct InsertSweep {
   const uint32_t* gpar;   // finest layer's guidance bitmask
   int64_t gpar_words;
   const float* maxe;      // [n] FP32 upper bound of each old point's longest edge key (0: none)
+  int search = 0;         // 1: the rows are queries (search): they neither block one another's
+                          // pairs nor take part in Stage VII; AB, nbrB, is_new and maxe may be null
 };
 // candidate pairs (row, point) of the batch rows left open by tier 1, Stage VII candidates
 // (row, old point, key) and the rows' exact K nearest neighbours (written at their sorted

@@ -229,6 +229,8 @@ struct InsertParams {
   int2* surv; unsigned long long* surv_cnt; unsigned long long surv_cap;
   int4* s7; unsigned long long* s7_cnt; unsigned long long s7_cap;  // (row pos, old pos, key bits, 0)
   unsigned long long* stats;  // [0] candidate pairs [1] Stage VII candidates
+  int search;                 // 1: the rows are queries, not points: no row blocks another row's
+                              // pair, and there is no Stage VII (AB, nbrB, is_new, maxe unused)
 };
 
 #define IS_U 66048  // max(2 * 32 * 132 * 4, 128 * 129 * 4): the operand chunks, then the key tile
@@ -274,13 +276,15 @@ __global__ void __launch_bounds__(GRNG_THREADS, 1) insert_sweep_kernel(InsertPar
   const Err e = err_fp32(Dp);
   unsigned long long st_cand = 0, st_s7 = 0;
   {
-    const uint4* src = reinterpret_cast<const uint4*>(p.AB + blockIdx.x * 16384);
-    uint4* dst = reinterpret_cast<uint4*>(AX);
-    for (int i = tid; i < 16384 / 8; i += GRNG_THREADS) dst[i] = src[i];
-    for (int i = tid; i < 128 * GRNG_KIN; i += GRNG_THREADS) {
-      const bool ok = i / GRNG_KIN < nr;
-      nbrXi[i] = ok ? p.nbrB_i[xb * GRNG_KIN + i] : (uint8_t)255;
-      nbrXk[i] = ok ? p.nbrB_k[xb * GRNG_KIN + i] : inf_ins();
+    if (!p.search) {  // the strip's own keys and neighbours: interceptors among the rows
+      const uint4* src = reinterpret_cast<const uint4*>(p.AB + blockIdx.x * 16384);
+      uint4* dst = reinterpret_cast<uint4*>(AX);
+      for (int i = tid; i < 16384 / 8; i += GRNG_THREADS) dst[i] = src[i];
+      for (int i = tid; i < 128 * GRNG_KIN; i += GRNG_THREADS) {
+        const bool ok = i / GRNG_KIN < nr;
+        nbrXi[i] = ok ? p.nbrB_i[xb * GRNG_KIN + i] : (uint8_t)255;
+        nbrXk[i] = ok ? p.nbrB_k[xb * GRNG_KIN + i] : inf_ins();
+      }
     }
     if (tid < 128) {
       rowp[tid] = tid < nr ? p.rowpos[xb + tid] : -1;
@@ -319,7 +323,7 @@ __global__ void __launch_bounds__(GRNG_THREADS, 1) insert_sweep_kernel(InsertPar
       if (tid < 128) {
         const bool ok = tid < nc;
         parY[tid] = ok ? p.parent[yb + tid] : 0;
-        newY[tid] = ok ? p.is_new[yb + tid] : 1;
+        newY[tid] = ok ? (p.is_new ? p.is_new[yb + tid] : 0) : 1;
       }
     }
     __syncthreads();
@@ -349,7 +353,7 @@ __global__ void __launch_bounds__(GRNG_THREADS, 1) insert_sweep_kernel(InsertPar
         }
         rmin1[r] = m1; rmin2[r] = m2; rarg1[r] = a1; rarg2[r] = a2;
       }
-    } else {
+    } else if (!p.search) {
       const int c = tid - 128;
       float m1 = inf_ins(), m2 = inf_ins();
       int a1 = -1, a2 = -1;
@@ -377,7 +381,7 @@ __global__ void __launch_bounds__(GRNG_THREADS, 1) insert_sweep_kernel(InsertPar
         const bool valid = c < nc && v < inf_ins();
         // a pair of two batch points is taken from the row of its lower sorted position
         bool cand = valid && !(newY[c] && y < x);
-        if (cand && p.gpar) {
+        if (cand && p.gpar && px >= 0) {  // px < 0: a query outside its pivot's ball, no filter
           const int qy = parY[c];
           if (qy != px) {
             const int a = min(px, qy), b = max(px, qy);
@@ -392,11 +396,11 @@ __global__ void __launch_bounds__(GRNG_THREADS, 1) insert_sweep_kernel(InsertPar
             const int z = (rarg1[r] != c) ? rarg1[r] : rarg2[r];
             if (z >= 0) blocked = block_state(T[r * 129 + z], __half2float(AY[z * 128 + c]), P, e) == 2;
           }
-          if (!blocked) {  // column minimum of y over the batch strip
+          if (!blocked && !p.search) {  // column minimum of y over the batch strip
             const int z = (carg1[c] != r) ? carg1[c] : carg2[c];
             if (z >= 0) blocked = block_state(__half2float(AX[r * 128 + z]), T[z * 129 + c], P, e) == 2;
           }
-          for (int t = 0; t < GRNG_KIN && !blocked; ++t) {  // in-strip neighbours of x
+          for (int t = 0; t < GRNG_KIN && !blocked && !p.search; ++t) {  // in-strip neighbours of x
             const int z = nbrXi[r * GRNG_KIN + t];
             if (z == 255) break;
             blocked = block_state(nbrXk[r * GRNG_KIN + t], T[z * 129 + c], P, e) == 2;
@@ -422,7 +426,7 @@ __global__ void __launch_bounds__(GRNG_THREADS, 1) insert_sweep_kernel(InsertPar
           }
         }
         // Stage VII: x may lie in the lune of an old edge (y, w) only if key(x, y) < key(y, w)
-        const bool s7 = valid && !newY[c] && lo_b(v, e) < p.maxe[y];
+        const bool s7 = p.maxe && valid && !newY[c] && lo_b(v, e) < p.maxe[y];
         st_s7 += s7 ? 1 : 0;
         const unsigned sm7 = __ballot_sync(FULLMASK, s7);
         if (sm7) {
@@ -514,7 +518,7 @@ void insert_sweep(const InsertSweep& S, DevBuf& surv, int64_t* nsurv, DevBuf& s7
   GRNG_CUDA(ci.alloc((size_t)strips * 128 * nchunks * S.K * 4));
   GRNG_CUDA(ctr.alloc(4 * 8));
   unsigned long long scap = std::max<unsigned long long>(1 << 16, (unsigned long long)S.mb * 256);
-  unsigned long long s7cap = std::max<unsigned long long>(1 << 16, (unsigned long long)S.mb * 64);
+  unsigned long long s7cap = S.search ? 1 : std::max<unsigned long long>(1 << 16, (unsigned long long)S.mb * 64);
   for (int attempt = 0;; ++attempt) {
     GRNG_CUDA(surv.alloc(scap * sizeof(int2)));
     GRNG_CUDA(s7.alloc(s7cap * sizeof(int4)));
@@ -523,6 +527,7 @@ void insert_sweep(const InsertSweep& S, DevBuf& surv, int64_t* nsurv, DevBuf& s7
     p.XB = S.XB; p.rowpos = S.rowpos; p.mb = S.mb; p.AB = S.AB; p.nbrB_i = S.nbrB_i; p.nbrB_k = S.nbrB_k;
     p.X = S.X; p.n = S.n; p.Dp = S.Dp; p.K = S.K; p.A = S.A; p.nbr_i = S.nbr_i; p.nbr_k = S.nbr_k;
     p.is_new = S.is_new; p.parent = S.parent; p.gpar = S.gpar; p.gpar_words = S.gpar_words; p.maxe = S.maxe;
+    p.search = S.search;
     p.bpc = bpc; p.nchunks = nchunks; p.knn_k = ck.as<float>(); p.knn_i = ci.as<int32_t>();
     unsigned long long* dc = ctr.as<unsigned long long>();
     p.surv = surv.as<int2>(); p.surv_cnt = dc; p.surv_cap = scap;

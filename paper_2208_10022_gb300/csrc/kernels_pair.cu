@@ -576,6 +576,7 @@ struct Front {
 struct Tier3Params {
   const float* X;
   int64_t n;
+  int64_t npts;    // rows [0, npts) are points that may block; rows beyond are queries
   int Dp, metric, guide;
   const float* rlo;
   const float* rhi;
@@ -705,7 +706,7 @@ __global__ void __launch_bounds__(T3_T, T3_MINB) tier3_kernel(Tier3Params p) {
     if (tid == 0) {
       s_block = 0;
       s_best = ~0ull;
-      bufA[0] = Front{0, (int)(p.anc.n ? p.anc.m[0] : p.n), 0.0f, 0.0f, 0.0f, 0.0f};
+      bufA[0] = Front{0, (int)(p.anc.n ? p.anc.m[0] : p.npts), 0.0f, 0.0f, 0.0f, 0.0f};
     }
     __syncthreads();
     if (tid == 0) s_v = key32(gs, os, p.Dp, p.metric);
@@ -1048,7 +1049,7 @@ __global__ void __launch_bounds__(T3_T, T3_MINB) tier3_kernel(Tier3Params p) {
         }
       }
       if (all) {  // frontier too large: test every node (still exact)
-        for (int i = gid; i < (int)p.n; i += T3_T / 8) {
+        for (int i = gid; i < (int)p.npts; i += T3_T / 8) {
           if (__shfl_sync(gmask, *(volatile int*)&s_block, 0, 8)) break;
           if (i == g || i == o) continue;
           float ka, kb;
@@ -2089,7 +2090,8 @@ static void finish_level(const LevelIn& in, LevelOut& out, LevelStats& st, cudaS
           std::swap(unres2, gpairs);
         }
         Tier3Params pp{};
-        pp.X = in.X; pp.n = n; pp.Dp = in.Dp; pp.metric = in.metric; pp.guide = in.grng;
+        pp.X = in.X; pp.n = n; pp.npts = in.npts ? in.npts : n; pp.Dp = in.Dp; pp.metric = in.metric;
+        pp.guide = in.grng;
         pp.rlo = in.rlo; pp.rhi = in.rhi; pp.pairs = unres2.as<int2>(); pp.m = (int64_t)nun2;
         pp.anc = in.anc;
         for (int a = 0; a < in.anc.n; ++a) pp.anc.toff[a] = toff[a];
@@ -2236,7 +2238,8 @@ static void finish_level(const LevelIn& in, LevelOut& out, LevelStats& st, cudaS
     GRNG_CUDA(cudaMemsetAsync(pflag.p, 0, (size_t)std::max<unsigned long long>(npend + nun2, 1) * 4, s));
     if (nun2) {
       Tier3Params t3;
-      t3.X = in.X; t3.n = n; t3.Dp = in.Dp; t3.metric = in.metric; t3.guide = in.grng;
+      t3.X = in.X; t3.n = n; t3.npts = in.npts ? in.npts : n; t3.Dp = in.Dp; t3.metric = in.metric;
+      t3.guide = in.grng;
       t3.rlo = in.rlo; t3.rhi = in.rhi; t3.pairs = t3pairs; t3.m = (int64_t)nun2;
       t3.pend = pend.as<int2>(); t3.pflag = pflag.as<int>(); t3.slot0 = (int64_t)npend;
       t3.amb = amb.as<int2>(); t3.amb_cnt = dc + 19; t3.amb_cap = amb_cap;
