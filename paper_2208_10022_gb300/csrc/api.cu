@@ -197,7 +197,9 @@ struct grng_index {
     DevBuf off, nbrs;
     int64_t m = 0, total = 0;
     long long batches = 0, queries = 0, outside = 0, candidates = 0, survivors = 0, neighbours = 0;
-    double ms = 0, last_ms = 0;
+    long long queued = 0, retries = 0;
+    double ms = 0, last_ms = 0, assign_ms = 0, sweep_ms = 0, tiers_ms = 0;  // last batch's phases
+    LevelStats st{};                                                     // last batch's tiers
   } srch;
 };
 
@@ -1005,7 +1007,8 @@ grng_status rng_search_batch(grng_index* ix, const float* queries, int64_t m, in
     GRNG_CUDA(cudaMemcpy2DAsync(Xq, (size_t)Dp * 4, queries, (size_t)D * 4, (size_t)D * 4, (size_t)m,
                                 cudaMemcpyDefault, s));
     // ---- nearest finest pivot (Eq. 2), and whether its ball holds the query ----------------
-    DevBuf ab, db, rb, ddb, ctr, surv, s7, E;
+    DevBuf ab, db, rb, ddb, ctr, surv, E;
+    Timer ta(s);
     {
       const int64_t M = fin.m;
       GRNG_CUDA(ab.alloc((size_t)m * 4));
@@ -1027,20 +1030,25 @@ grng_status rng_search_batch(grng_index* ix, const float* queries, int64_t m, in
       GRNG_CUDA(cudaStreamSynchronize(s));
       W.outside += (long long)outside;
     }
+    W.assign_ms = ta.stop();
+    Timer tsw(s);
     // ---- Stages I-V: the query rows against every index point (tier 1, K nearest) -------
-    InsertSweep S;
-    S.XB = Xq; S.rowpos = W.orig.as<int32_t>() + n; S.mb = m;  // row j sits at position n + j
-    S.AB = nullptr; S.nbrB_i = nullptr; S.nbrB_k = nullptr;
+    SearchSweep S;
+    S.XQ = Xq; S.mq = m; S.row0 = n; S.rowpos = W.orig.as<int32_t>() + n;  // row j sits at n + j
+    S.qparent = W.parent.as<int32_t>() + n;
     S.X = W.X.as<float>(); S.n = n; S.Dp = Dp; S.K = K; S.metric = metric;
     S.A = W.A.as<__half>(); S.nbr_i = W.nb_i.as<uint8_t>(); S.nbr_k = W.nb_k.as<float>();
-    S.is_new = nullptr; S.parent = W.parent.as<int32_t>();
-    S.gpar = fin.gg.as<uint32_t>(); S.gpar_words = fin.words; S.maxe = nullptr;
-    S.search = 1;
-    int64_t nsurv = 0, ns7 = 0;
-    unsigned long long sst[2] = {0, 0};
-    insert_sweep(S, surv, &nsurv, s7, &ns7, W.knn_k.as<float>(), W.knn_i.as<int32_t>(), sst, s);
+    S.parent = W.parent.as<int32_t>(); S.gpar = fin.gg.as<uint32_t>(); S.gpar_words = fin.words;
+    S.small_buffers = (ix->opts.flags & GRNG_FLAG_SMALL_BUFFERS) ? 1 : 0;
+    int64_t nsurv = 0;
+    unsigned long long sst[3] = {0, 0, 0};
+    search_sweep(S, surv, &nsurv, W.knn_k.as<float>(), W.knn_i.as<int32_t>(), sst, s);
     W.candidates += (long long)sst[0];
+    W.queued += (long long)sst[1];
+    W.retries += (long long)sst[2];
     W.survivors += nsurv;
+    W.sweep_ms = tsw.stop();
+    Timer tt(s);
     // ---- Stage VI: tiers 2 (the queries' K nearest) and 3, FP64 recheck -------------------
     LevelIn in{};
     in.X = W.X.as<float>();
@@ -1063,6 +1071,8 @@ grng_status rng_search_batch(grng_index* ix, const float* queries, int64_t m, in
     lo.edges = &E;
     LevelStats st;
     run_pairs(in, lo, st, s, surv.as<int2>(), nsurv, W.knn_i.as<int32_t>(), W.knn_k.as<float>(), false);
+    W.tiers_ms = tt.stop();
+    W.st = st;
     // ---- CSR over the queries ----------------------------------------------------------------
     const int64_t ne = lo.n_edges;
     GRNG_CUDA(W.off.alloc((size_t)(m + 1) * 8));
@@ -1160,13 +1170,18 @@ grng_status grng_stats(const grng_index* cix, char* json, size_t cap) {
            "\"stage7_candidates\":%lld,\"stage7_tests\":%lld,\"stage7_fp64\":%lld,\"new_edges\":%lld,"
            "\"removed_edges\":%lld},"
            "\"search\":{\"batches\":%lld,\"queries\":%lld,\"ms\":%.4f,\"last_ms\":%.4f,\"outside_ball\":%lld,"
-           "\"candidate_pairs\":%lld,\"tier1_survivors\":%lld,\"neighbours\":%lld},",
+           "\"candidate_pairs\":%lld,\"tier1_survivors\":%lld,\"neighbours\":%lld,"
+           "\"tier1_queued\":%lld,\"sweep_retries\":%lld,"
+           "\"last_assign_ms\":%.4f,\"last_sweep_ms\":%.4f,\"last_tiers_ms\":%.4f,",
            (int)ix->rng_built, (long long)ix->n_edges, ix->rng_ms, ix->rng_tile_ms, (long long)ix->insert_batches,
            (long long)ix->inserted, ix->insert_ms, ix->ins.changed_pivots, ix->ins.grng_pairs, ix->ins.grng_linked,
            ix->ins.candidates, ix->ins.survivors, ix->ins.s7_candidates, ix->ins.s7_tests, ix->ins.s7_fp64,
            ix->ins.new_edges, ix->ins.removed_edges, ix->srch.batches, ix->srch.queries, ix->srch.ms,
-           ix->srch.last_ms, ix->srch.outside, ix->srch.candidates, ix->srch.survivors, ix->srch.neighbours);
+           ix->srch.last_ms, ix->srch.outside, ix->srch.candidates, ix->srch.survivors, ix->srch.neighbours,
+           ix->srch.queued, ix->srch.retries, ix->srch.assign_ms, ix->srch.sweep_ms, ix->srch.tiers_ms);
   js += buf;
+  level_json(js, "last_tiers", ix->srch.st);
+  js += "},";
   level_json(js, "rng", ix->rng_st);
   js += "}";
   if (js.size() + 1 > cap) {

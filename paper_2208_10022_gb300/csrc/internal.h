@@ -264,14 +264,34 @@ struct InsertSweep {
   const uint32_t* gpar;   // finest layer's guidance bitmask
   int64_t gpar_words;
   const float* maxe;      // [n] FP32 upper bound of each old point's longest edge key (0: none)
-  int search = 0;         // 1: the rows are queries (search): they neither block one another's
-                          // pairs nor take part in Stage VII; AB, nbrB, is_new and maxe may be null
 };
 // candidate pairs (row, point) of the batch rows left open by tier 1, Stage VII candidates
 // (row, old point, key) and the rows' exact K nearest neighbours (written at their sorted
 // positions of knn_k / knn_i [n][K]); stats[0] += candidate pairs, stats[1] += Stage VII ones
 void insert_sweep(const InsertSweep& S, DevBuf& surv, int64_t* nsurv, DevBuf& s7, int64_t* ns7, float* knn_k,
                   int32_t* knn_i, unsigned long long* stats, cudaStream_t s);
+// RNG search: query rows against every index point (tier 1 and the queries' K nearest)
+struct SearchSweep {
+  const float* XQ;         // [mq][Dp] query rows (zero padded to Dp)
+  int64_t mq;
+  int64_t row0;            // level position of query row 0; the rows are row0 .. row0+mq-1
+  const int32_t* rowpos;   // [mq] row0 + j
+  const int32_t* qparent;  // [mq] finest pivot (sorted position) whose ball holds the query, or -1
+  const float* X;          // index points in sorted order [n][Dp]
+  int64_t n;
+  int Dp, K, metric;
+  const __half* A;         // block_prep of X
+  const uint8_t* nbr_i;
+  const float* nbr_k;
+  const int32_t* parent;   // [n] finest pivot, sorted position
+  const uint32_t* gpar;    // finest layer's guidance bitmask
+  int64_t gpar_words;
+  int small_buffers = 0;   // testing: a tiny first survivor buffer, so the retry runs
+};
+// pairs (row0 + j, point) tier 1 leaves open, and the rows' exact K nearest (written at their
+// positions of knn_k / knn_i); stats[0] += candidate pairs, [1] += queued tests, [2] += retries
+void search_sweep(const SearchSweep& S, DevBuf& surv, int64_t* nsurv, float* knn_k, int32_t* knn_i,
+                  unsigned long long* stats, cudaStream_t s);
 // maxe[sorted position] = FP32 upper bound of the point's longest edge key (edges in original ids)
 void edge_max_keys(const uint64_t* edges, int64_t ne, const int32_t* rank, const float* X, int Dp, int metric,
                    float* maxe, int64_t n, cudaStream_t s);

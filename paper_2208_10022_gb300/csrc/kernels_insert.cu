@@ -229,8 +229,6 @@ struct InsertParams {
   int2* surv; unsigned long long* surv_cnt; unsigned long long surv_cap;
   int4* s7; unsigned long long* s7_cnt; unsigned long long s7_cap;  // (row pos, old pos, key bits, 0)
   unsigned long long* stats;  // [0] candidate pairs [1] Stage VII candidates
-  int search;                 // 1: the rows are queries, not points: no row blocks another row's
-                              // pair, and there is no Stage VII (AB, nbrB, is_new, maxe unused)
 };
 
 #define IS_U 66048  // max(2 * 32 * 132 * 4, 128 * 129 * 4): the operand chunks, then the key tile
@@ -276,15 +274,13 @@ __global__ void __launch_bounds__(GRNG_THREADS, 1) insert_sweep_kernel(InsertPar
   const Err e = err_fp32(Dp);
   unsigned long long st_cand = 0, st_s7 = 0;
   {
-    if (!p.search) {  // the strip's own keys and neighbours: interceptors among the rows
-      const uint4* src = reinterpret_cast<const uint4*>(p.AB + blockIdx.x * 16384);
-      uint4* dst = reinterpret_cast<uint4*>(AX);
-      for (int i = tid; i < 16384 / 8; i += GRNG_THREADS) dst[i] = src[i];
-      for (int i = tid; i < 128 * GRNG_KIN; i += GRNG_THREADS) {
-        const bool ok = i / GRNG_KIN < nr;
-        nbrXi[i] = ok ? p.nbrB_i[xb * GRNG_KIN + i] : (uint8_t)255;
-        nbrXk[i] = ok ? p.nbrB_k[xb * GRNG_KIN + i] : inf_ins();
-      }
+    const uint4* src = reinterpret_cast<const uint4*>(p.AB + blockIdx.x * 16384);
+    uint4* dst = reinterpret_cast<uint4*>(AX);
+    for (int i = tid; i < 16384 / 8; i += GRNG_THREADS) dst[i] = src[i];
+    for (int i = tid; i < 128 * GRNG_KIN; i += GRNG_THREADS) {
+      const bool ok = i / GRNG_KIN < nr;
+      nbrXi[i] = ok ? p.nbrB_i[xb * GRNG_KIN + i] : (uint8_t)255;
+      nbrXk[i] = ok ? p.nbrB_k[xb * GRNG_KIN + i] : inf_ins();
     }
     if (tid < 128) {
       rowp[tid] = tid < nr ? p.rowpos[xb + tid] : -1;
@@ -323,7 +319,7 @@ __global__ void __launch_bounds__(GRNG_THREADS, 1) insert_sweep_kernel(InsertPar
       if (tid < 128) {
         const bool ok = tid < nc;
         parY[tid] = ok ? p.parent[yb + tid] : 0;
-        newY[tid] = ok ? (p.is_new ? p.is_new[yb + tid] : 0) : 1;
+        newY[tid] = ok ? p.is_new[yb + tid] : 1;
       }
     }
     __syncthreads();
@@ -353,7 +349,7 @@ __global__ void __launch_bounds__(GRNG_THREADS, 1) insert_sweep_kernel(InsertPar
         }
         rmin1[r] = m1; rmin2[r] = m2; rarg1[r] = a1; rarg2[r] = a2;
       }
-    } else if (!p.search) {
+    } else {
       const int c = tid - 128;
       float m1 = inf_ins(), m2 = inf_ins();
       int a1 = -1, a2 = -1;
@@ -381,7 +377,7 @@ __global__ void __launch_bounds__(GRNG_THREADS, 1) insert_sweep_kernel(InsertPar
         const bool valid = c < nc && v < inf_ins();
         // a pair of two batch points is taken from the row of its lower sorted position
         bool cand = valid && !(newY[c] && y < x);
-        if (cand && p.gpar && px >= 0) {  // px < 0: a query outside its pivot's ball, no filter
+        if (cand && p.gpar) {
           const int qy = parY[c];
           if (qy != px) {
             const int a = min(px, qy), b = max(px, qy);
@@ -396,11 +392,11 @@ __global__ void __launch_bounds__(GRNG_THREADS, 1) insert_sweep_kernel(InsertPar
             const int z = (rarg1[r] != c) ? rarg1[r] : rarg2[r];
             if (z >= 0) blocked = block_state(T[r * 129 + z], __half2float(AY[z * 128 + c]), P, e) == 2;
           }
-          if (!blocked && !p.search) {  // column minimum of y over the batch strip
+          if (!blocked) {  // column minimum of y over the batch strip
             const int z = (carg1[c] != r) ? carg1[c] : carg2[c];
             if (z >= 0) blocked = block_state(__half2float(AX[r * 128 + z]), T[z * 129 + c], P, e) == 2;
           }
-          for (int t = 0; t < GRNG_KIN && !blocked && !p.search; ++t) {  // in-strip neighbours of x
+          for (int t = 0; t < GRNG_KIN && !blocked; ++t) {  // in-strip neighbours of x
             const int z = nbrXi[r * GRNG_KIN + t];
             if (z == 255) break;
             blocked = block_state(nbrXk[r * GRNG_KIN + t], T[z * 129 + c], P, e) == 2;
@@ -426,7 +422,7 @@ __global__ void __launch_bounds__(GRNG_THREADS, 1) insert_sweep_kernel(InsertPar
           }
         }
         // Stage VII: x may lie in the lune of an old edge (y, w) only if key(x, y) < key(y, w)
-        const bool s7 = p.maxe && valid && !newY[c] && lo_b(v, e) < p.maxe[y];
+        const bool s7 = valid && !newY[c] && lo_b(v, e) < p.maxe[y];
         st_s7 += s7 ? 1 : 0;
         const unsigned sm7 = __ballot_sync(FULLMASK, s7);
         if (sm7) {
@@ -518,7 +514,7 @@ void insert_sweep(const InsertSweep& S, DevBuf& surv, int64_t* nsurv, DevBuf& s7
   GRNG_CUDA(ci.alloc((size_t)strips * 128 * nchunks * S.K * 4));
   GRNG_CUDA(ctr.alloc(4 * 8));
   unsigned long long scap = std::max<unsigned long long>(1 << 16, (unsigned long long)S.mb * 256);
-  unsigned long long s7cap = S.search ? 1 : std::max<unsigned long long>(1 << 16, (unsigned long long)S.mb * 64);
+  unsigned long long s7cap = std::max<unsigned long long>(1 << 16, (unsigned long long)S.mb * 64);
   for (int attempt = 0;; ++attempt) {
     GRNG_CUDA(surv.alloc(scap * sizeof(int2)));
     GRNG_CUDA(s7.alloc(s7cap * sizeof(int4)));
@@ -527,7 +523,6 @@ void insert_sweep(const InsertSweep& S, DevBuf& surv, int64_t* nsurv, DevBuf& s7
     p.XB = S.XB; p.rowpos = S.rowpos; p.mb = S.mb; p.AB = S.AB; p.nbrB_i = S.nbrB_i; p.nbrB_k = S.nbrB_k;
     p.X = S.X; p.n = S.n; p.Dp = S.Dp; p.K = S.K; p.A = S.A; p.nbr_i = S.nbr_i; p.nbr_k = S.nbr_k;
     p.is_new = S.is_new; p.parent = S.parent; p.gpar = S.gpar; p.gpar_words = S.gpar_words; p.maxe = S.maxe;
-    p.search = S.search;
     p.bpc = bpc; p.nchunks = nchunks; p.knn_k = ck.as<float>(); p.knn_i = ci.as<int32_t>();
     unsigned long long* dc = ctr.as<unsigned long long>();
     p.surv = surv.as<int2>(); p.surv_cnt = dc; p.surv_cap = scap;
@@ -551,6 +546,349 @@ void insert_sweep(const InsertSweep& S, DevBuf& surv, int64_t* nsurv, DevBuf& s7
     s7cap = std::max(s7cap, h[1] + h[1] / 8);
   }
   knn_merge_kernel<<<nblk_ins(S.mb), 256, 0, s>>>(ck.as<float>(), ci.as<int32_t>(), S.mb, nchunks, S.K, S.rowpos,
+                                                   knn_k, knn_i); note_launch();
+  GRNG_CUDA(cudaGetLastError());
+  GRNG_CUDA(cudaStreamSynchronize(s));
+}
+
+// ---- search: query rows against every index point ---------------------------------------------
+// One CTA takes a strip of 128 queries and a contiguous range of the index's 128-point column
+// blocks.  Per tile: the FP32 keys (direct differences, as the build's tiles), then each
+// query's two nearest points of the block and its K nearest so far (two threads per row, each
+// with its own list over half the columns), then the tier-1 filter: Theorem 1 on the queries
+// that lie in their pivot's ball, and a uniform test of every pair (q, y) against the block
+// point nearest to q; the pairs it leaves are queued in shared memory and tested by all threads
+// against the other of the two nearest points and y's in-block neighbours (Stage V's select
+// group).  Only index points ever block: the queries are not points of the index.
+struct SearchParams {
+  const float* XQ;            // [strips * 128][Dp] query rows
+  int64_t mq;
+  int64_t row0;               // level position of query row 0
+  const int32_t* qparent;     // [mq] sorted position of the query's finest pivot, or -1
+  const float* X;             // index points in sorted order [n][Dp]
+  int64_t n;
+  int Dp, K;
+  const __half* A;            // in-block FP16 keys (rounded up) and neighbours of the index blocks
+  const uint8_t* nbr_i;
+  const float* nbr_k;
+  const int32_t* parent;      // [n] finest pivot (sorted position)
+  const uint32_t* gpar;       // finest layer's guidance bitmask
+  int64_t gpar_words;
+  int64_t bpc;                // column blocks per chunk
+  int nchunks;
+  float* knn_k;               // [mq_pad][2 * nchunks][K] half-row lists per chunk
+  int32_t* knn_i;
+  int2* surv; unsigned long long* surv_cnt; unsigned long long surv_cap;
+  unsigned long long* stats;  // [0] candidate pairs [1] queued pairs
+};
+
+#define SS_QCAP 4096
+static __host__ __device__ constexpr size_t ss_bytes(int K) {
+  return (size_t)IS_U + 32768 + 128 * GRNG_KIN * 5 + 128 * 6 * 4 + (size_t)128 * 2 * K * 8 + SS_QCAP * 4 + 16;
+}
+
+__device__ __forceinline__ void ss_cp16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+               "l"(src)
+               : "memory");
+}
+
+template <int KC, int METRIC>
+__global__ void __launch_bounds__(GRNG_THREADS, 1) search_sweep_kernel(SearchParams p) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  float* sA = reinterpret_cast<float*>(sm_raw);
+  float* sB = sA + KC * GRNG_SSTRIDE;
+  float* T = reinterpret_cast<float*>(sm_raw);
+  unsigned char* q = sm_raw + IS_U;
+  __half* AY = reinterpret_cast<__half*>(q); q += 32768;
+  float* nbrYk = reinterpret_cast<float*>(q); q += 128 * GRNG_KIN * 4;
+  uint8_t* nbrYi = q; q += 128 * GRNG_KIN;
+  q += 512;
+  int* ra1 = reinterpret_cast<int*>(q); q += 512;
+  int* ra2 = reinterpret_cast<int*>(q); q += 512;
+  int* parY = reinterpret_cast<int*>(q); q += 512;
+  int* parX = reinterpret_cast<int*>(q); q += 512;
+  q += 512;
+  const int K = p.K;
+  float* lk = reinterpret_cast<float*>(q); q += (size_t)128 * 2 * K * 4;  // [row][half][K]
+  int* li = reinterpret_cast<int*>(q); q += (size_t)128 * 2 * K * 4;
+  int* queue = reinterpret_cast<int*>(q); q += SS_QCAP * 4;
+  int* s_qn = reinterpret_cast<int*>(q);
+
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int Dp = p.Dp;
+  const int64_t xb = (int64_t)blockIdx.x * 128;
+  const int nr = (int)(p.mq - xb < 128 ? p.mq - xb : 128);
+  const int64_t nb = (p.n + 127) / 128;
+  const int64_t by0 = (int64_t)blockIdx.y * p.bpc, by1 = min(nb, by0 + p.bpc);
+  const Err e = err_fp32(Dp);
+  unsigned long long st_cand = 0, st_queued = 0;
+  if (tid < 128) parX[tid] = tid < nr ? p.qparent[xb + tid] : -1;
+  for (int i = tid; i < 128 * 2 * K; i += GRNG_THREADS) {
+    lk[i] = inf_ins();
+    li[i] = -1;
+  }
+  // the row pass: thread = (row, half); the odd half walks its columns rotated by 16 so that
+  // the two threads of a row read different banks
+  const int pr = tid >> 1, ph = tid & 1;
+  for (int64_t by = by0; by < by1; ++by) {
+    const int64_t yb = by * 128;
+    const int nc = (int)(p.n - yb < 128 ? p.n - yb : 128);
+    __syncthreads();  // the previous tile's filter and queue are done with T, AY, nbrY, parY
+    {  // the block's in-block keys and neighbours arrive while the keys are computed
+      const char* srcA = reinterpret_cast<const char*>(p.A + by * 16384);
+      for (int i = tid; i < 2048; i += GRNG_THREADS) ss_cp16(reinterpret_cast<char*>(AY) + i * 16, srcA + i * 16);
+      const char* srcK = reinterpret_cast<const char*>(p.nbr_k + yb * GRNG_KIN);
+      for (int i = tid; i < 128 * GRNG_KIN / 4; i += GRNG_THREADS)
+        ss_cp16(reinterpret_cast<char*>(nbrYk) + i * 16, srcK + i * 16);
+      const char* srcI = reinterpret_cast<const char*>(p.nbr_i + yb * GRNG_KIN);
+      for (int i = tid; i < 128 * GRNG_KIN / 16; i += GRNG_THREADS)
+        ss_cp16(reinterpret_cast<char*>(nbrYi) + i * 16, srcI + i * 16);
+      asm volatile("cp.async.commit_group;" ::: "memory");
+    }
+    float acc[8][8];
+    tile_keys<KC, METRIC>(p.XQ + xb * Dp, nr, p.X + yb * Dp, nc, Dp, sA, sB, acc);
+    __syncthreads();  // every thread is done with sA/sB: T may overwrite them
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int r = tile_row(i), c = tile_col(j);
+        T[r * 129 + c] = (r < nr && c < nc) ? acc[i][j] : inf_ins();
+      }
+    if (tid < 128) parY[tid] = tid < nc ? p.parent[yb + tid] : 0;
+    if (tid == 0) *s_qn = 0;
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    __syncthreads();
+    {  // ---- row pass: two nearest of the block, and the half-row's K nearest so far ----------
+      float* kk = lk + (pr * 2 + ph) * K;
+      int* ki = li + (pr * 2 + ph) * K;
+      float thr = kk[K - 1];
+      float m1 = inf_ins(), m2 = inf_ins();
+      int a1 = -1, a2 = -1;
+      const float* Tr = T + pr * 129;
+      for (int i = 0; i < 64; ++i) {
+        const int c = ph ? 64 + ((i + 16) & 63) : i;
+        const float v = Tr[c];
+        if (v < m2) {
+          if (v < m1) { m2 = m1; a2 = a1; m1 = v; a1 = c; }
+          else { m2 = v; a2 = c; }
+        }
+        if (v < thr) {
+          int pos = K - 1;
+          while (pos > 0 && kk[pos - 1] > v) { kk[pos] = kk[pos - 1]; ki[pos] = ki[pos - 1]; --pos; }
+          kk[pos] = v;
+          ki[pos] = (int)(yb + c);
+          thr = kk[K - 1];
+        }
+      }
+      // merge the two halves' nearest pairs (lanes 2r and 2r+1 of one warp)
+      const float o1 = __shfl_xor_sync(FULLMASK, m1, 1), o2 = __shfl_xor_sync(FULLMASK, m2, 1);
+      const int b1 = __shfl_xor_sync(FULLMASK, a1, 1), b2 = __shfl_xor_sync(FULLMASK, a2, 1);
+      if (ph == 0) {
+        float n1, n2;
+        int c1, c2;
+        if (o1 < m1 || (o1 == m1 && b1 < a1)) {
+          n1 = o1; c1 = b1;
+          if (m1 < o2) { n2 = m1; c2 = a1; } else { n2 = o2; c2 = b2; }
+        } else {
+          n1 = m1; c1 = a1;
+          if (o1 < m2) { n2 = o1; c2 = b1; } else { n2 = m2; c2 = a2; }
+        }
+        (void)n1;
+        (void)n2;
+        ra1[pr] = c1;
+        ra2[pr] = c2;
+      }
+    }
+    __syncthreads();
+    // ---- tier-1 filter, uniform part: Theorem 1, then the block point nearest to q ----------
+    for (int rr = 0; rr < 16; ++rr) {
+      const int r = warp * 16 + rr;
+      if (r >= nr) break;
+      const int px = parX[r];
+      const int z1 = ra1[r], z2 = ra2[r];
+      const float* Tr = T + r * 129;
+      for (int cb = 0; cb < 4; ++cb) {
+        if (cb * 32 >= nc) break;
+        const int c = cb * 32 + lane;
+        const float v = Tr[c];
+        bool cand = c < nc && v < inf_ins();
+        if (cand && p.gpar && px >= 0) {
+          const int qy = parY[c];
+          if (qy != px) {
+            const int a = min(px, qy), b = max(px, qy);
+            cand = (__ldg(p.gpar + (int64_t)a * p.gpar_words + (b >> 5)) >> (b & 31)) & 1u;
+          }
+        }
+        st_cand += cand ? 1 : 0;
+        bool open = false;
+        if (cand) {
+          const PairThr P = pair_thresholds(v, 0.0f, 0.0f, 0.0f, 0.0f, METRIC, e, 0);
+          const int z = (z1 != c) ? z1 : z2;
+          open = !(z >= 0 && block_state(Tr[z], __half2float(AY[z * 128 + c]), P, e) == 2);
+        }
+        const unsigned om = __ballot_sync(FULLMASK, open);
+        if (om) {
+          int base = 0;
+          if (lane == 0) base = atomicAdd(s_qn, __popc(om));
+          base = __shfl_sync(FULLMASK, base, 0);
+          const int pos = base + __popc(om & ((1u << lane) - 1u));
+          if (open && pos < SS_QCAP) queue[pos] = (r << 8) | c;
+          st_queued += open ? 1 : 0;
+        }
+      }
+    }
+    __syncthreads();
+    // ---- tier-1 filter, queued part (all threads): the other nearest point and the in-block
+    // neighbours of y; the pairs none of them certainly blocks go on to tiers 2 and 3 ----------
+    const int qn = *s_qn;
+    auto full_test = [&](int r, int c) -> bool {
+      const float v = T[r * 129 + c];
+      const PairThr P = pair_thresholds(v, 0.0f, 0.0f, 0.0f, 0.0f, METRIC, e, 0);
+      const int z1 = ra1[r], z2 = ra2[r];
+      const int zo = (z1 != c) ? z2 : -1;  // the nearest was tested already, unless it was y
+      if (zo >= 0 && zo != c && block_state(T[r * 129 + zo], __half2float(AY[zo * 128 + c]), P, e) == 2)
+        return false;
+      for (int t = 0; t < GRNG_KIN; ++t) {
+        const int z = nbrYi[c * GRNG_KIN + t];
+        if (z == 255) break;
+        if (block_state(T[r * 129 + z], nbrYk[c * GRNG_KIN + t], P, e) == 2) return false;
+      }
+      return true;
+    };
+    auto push = [&](bool surv, int r, int c) {
+      const unsigned sm = __ballot_sync(FULLMASK, surv);
+      if (sm) {
+        unsigned long long base = 0;
+        if (lane == 0) base = atomicAdd(p.surv_cnt, (unsigned long long)__popc(sm));
+        base = __shfl_sync(FULLMASK, base, 0);
+        if (surv) {
+          const unsigned long long pos = base + __popc(sm & ((1u << lane) - 1u));
+          if (pos < p.surv_cap) p.surv[pos] = make_int2((int)(p.row0 + xb + r), (int)(yb + c));
+        }
+      }
+    };
+    if (qn <= SS_QCAP) {
+      for (int b0 = 0; b0 < qn; b0 += GRNG_THREADS) {
+        const int i = b0 + tid;
+        bool surv = false;
+        int r = 0, c = 0;
+        if (i < qn) {
+          r = queue[i] >> 8;
+          c = queue[i] & 255;
+          surv = full_test(r, c);
+        }
+        push(surv, r, c);
+      }
+    } else {  // the queue overflowed: every pair of the tile lane by lane instead (rare)
+      for (int rr = 0; rr < 16; ++rr) {
+        const int r = warp * 16 + rr;
+        if (r >= nr) break;
+        const int px = parX[r];
+        for (int cb = 0; cb < 4; ++cb) {
+          if (cb * 32 >= nc) break;
+          const int c = cb * 32 + lane;
+          const float v = T[r * 129 + c];
+          bool cand = c < nc && v < inf_ins();
+          if (cand && p.gpar && px >= 0) {
+            const int qy = parY[c];
+            if (qy != px) {
+              const int a = min(px, qy), b = max(px, qy);
+              cand = (__ldg(p.gpar + (int64_t)a * p.gpar_words + (b >> 5)) >> (b & 31)) & 1u;
+            }
+          }
+          bool surv = false;
+          if (cand) {
+            const PairThr P = pair_thresholds(v, 0.0f, 0.0f, 0.0f, 0.0f, METRIC, e, 0);
+            const int z1 = ra1[r], z2 = ra2[r];
+            const int z = (z1 != c) ? z1 : z2;
+            surv = !(z >= 0 && block_state(T[r * 129 + z], __half2float(AY[z * 128 + c]), P, e) == 2) &&
+                   full_test(r, c);
+          }
+          push(surv, r, c);
+        }
+      }
+    }
+  }
+  __syncthreads();
+  if (pr < nr) {
+    const float* kk = lk + (pr * 2 + ph) * K;
+    const int* ki = li + (pr * 2 + ph) * K;
+    const int64_t o = ((xb + pr) * (2 * p.nchunks) + 2 * blockIdx.y + ph) * K;
+    for (int j = 0; j < K; ++j) {
+      p.knn_k[o + j] = kk[j];
+      p.knn_i[o + j] = ki[j];
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    st_cand += __shfl_down_sync(FULLMASK, st_cand, o);
+    st_queued += __shfl_down_sync(FULLMASK, st_queued, o);
+  }
+  if (lane == 0) {
+    atomicAdd(p.stats + 0, st_cand);
+    atomicAdd(p.stats + 1, st_queued);
+  }
+}
+
+template <int KC>
+static void launch_search_kc(const SearchParams& p, int metric, unsigned strips, cudaStream_t s) {
+  const size_t smem = ss_bytes(p.K);
+  dim3 grid(strips, (unsigned)p.nchunks);
+  if (metric == L2) {
+    GRNG_CUDA(cudaFuncSetAttribute(search_sweep_kernel<KC, L2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    search_sweep_kernel<KC, L2><<<grid, GRNG_THREADS, smem, s>>>(p); note_launch();
+  } else {
+    GRNG_CUDA(cudaFuncSetAttribute(search_sweep_kernel<KC, L1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    search_sweep_kernel<KC, L1><<<grid, GRNG_THREADS, smem, s>>>(p); note_launch();
+  }
+  GRNG_CUDA(cudaGetLastError());
+}
+
+void search_sweep(const SearchSweep& S, DevBuf& surv, int64_t* nsurv, float* knn_k, int32_t* knn_i,
+                  unsigned long long* stats, cudaStream_t s) {
+  const int64_t nb = (S.n + 127) / 128;
+  const unsigned strips = (unsigned)((S.mq + 127) / 128);
+  int sms = 0, dev = 0;
+  GRNG_CUDA(cudaGetDevice(&dev));
+  GRNG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  // one CTA per SM (their shared memory allows no second), each with a contiguous range of
+  // column blocks; a batch of more strips than SMs takes whole rows of blocks
+  const int64_t want = std::max<int64_t>(1, (int64_t)sms / strips);
+  const int64_t bpc = std::max<int64_t>(1, (nb + want - 1) / want);
+  const int nchunks = (int)((nb + bpc - 1) / bpc);
+  DevBuf ck, ci, ctr;
+  GRNG_CUDA(ck.alloc((size_t)strips * 128 * 2 * nchunks * S.K * 4));
+  GRNG_CUDA(ci.alloc((size_t)strips * 128 * 2 * nchunks * S.K * 4));
+  GRNG_CUDA(ctr.alloc(4 * 8));
+  unsigned long long scap = S.small_buffers ? 64ull : std::max<unsigned long long>(1 << 20, (unsigned long long)S.mq * 16384);
+  for (int attempt = 0;; ++attempt) {
+    GRNG_CUDA(surv.alloc(scap * sizeof(int2)));
+    GRNG_CUDA(cudaMemsetAsync(ctr.p, 0, 4 * 8, s));
+    SearchParams p;
+    p.XQ = S.XQ; p.mq = S.mq; p.row0 = S.row0; p.qparent = S.qparent;
+    p.X = S.X; p.n = S.n; p.Dp = S.Dp; p.K = S.K; p.A = S.A; p.nbr_i = S.nbr_i; p.nbr_k = S.nbr_k;
+    p.parent = S.parent; p.gpar = S.gpar; p.gpar_words = S.gpar_words;
+    p.bpc = bpc; p.nchunks = nchunks; p.knn_k = ck.as<float>(); p.knn_i = ci.as<int32_t>();
+    unsigned long long* dc = ctr.as<unsigned long long>();
+    p.surv = surv.as<int2>(); p.surv_cnt = dc; p.surv_cap = scap;
+    p.stats = dc + 1;
+    const int KC = S.Dp % 32 == 0 ? 32 : (S.Dp % 16 == 0 ? 16 : 8);
+    if (KC == 32) launch_search_kc<32>(p, S.metric, strips, s);
+    else if (KC == 16) launch_search_kc<16>(p, S.metric, strips, s);
+    else launch_search_kc<8>(p, S.metric, strips, s);
+    unsigned long long h[3];
+    GRNG_CUDA(cudaMemcpyAsync(h, dc, sizeof(h), cudaMemcpyDeviceToHost, s));
+    GRNG_CUDA(cudaStreamSynchronize(s));
+    if (h[0] <= scap) {
+      *nsurv = (int64_t)h[0];
+      if (stats) { stats[0] += h[1]; stats[1] += h[2]; stats[2] += (unsigned long long)attempt; }
+      break;
+    }
+    if (attempt >= 3) fail(6, "search sweep buffer overflow");
+    scap = std::max(scap, h[0] + h[0] / 8);
+  }
+  knn_merge_kernel<<<nblk_ins(S.mq), 256, 0, s>>>(ck.as<float>(), ci.as<int32_t>(), S.mq, 2 * nchunks, S.K, S.rowpos,
                                                    knn_k, knn_i); note_launch();
   GRNG_CUDA(cudaGetLastError());
   GRNG_CUDA(cudaStreamSynchronize(s));
