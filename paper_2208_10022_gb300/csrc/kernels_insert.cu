@@ -703,24 +703,35 @@ __global__ void __launch_bounds__(GRNG_THREADS, 1) search_sweep_kernel(SearchPar
     }
     __syncthreads();
     // ---- tier-1 filter, uniform part: Theorem 1, then the block point nearest to q ----------
+    // The guidance bits of the warp's 16 rows x the lane's 4 columns are loaded together
+    // first: one memory latency per tile instead of one per row.
+    unsigned long long link = ~0ull;  // bit rr * 4 + cb
+    if (p.gpar) {
+      unsigned wv[64];
+#pragma unroll
+      for (int t = 0; t < 64; ++t) {
+        const int r = warp * 16 + (t >> 2), c = (t & 3) * 32 + lane;
+        const int px = parX[r], qy = parY[c];
+        wv[t] = ~0u;
+        if (r < nr && c < nc && px >= 0 && qy != px) {
+          const int a = min(px, qy), b = max(px, qy);
+          wv[t] = __ldg(p.gpar + (int64_t)a * p.gpar_words + (b >> 5)) >> (b & 31);
+        }
+      }
+#pragma unroll
+      for (int t = 0; t < 64; ++t)
+        if (!(wv[t] & 1u)) link &= ~(1ull << t);
+    }
     for (int rr = 0; rr < 16; ++rr) {
       const int r = warp * 16 + rr;
       if (r >= nr) break;
-      const int px = parX[r];
       const int z1 = ra1[r], z2 = ra2[r];
       const float* Tr = T + r * 129;
       for (int cb = 0; cb < 4; ++cb) {
         if (cb * 32 >= nc) break;
         const int c = cb * 32 + lane;
         const float v = Tr[c];
-        bool cand = c < nc && v < inf_ins();
-        if (cand && p.gpar && px >= 0) {
-          const int qy = parY[c];
-          if (qy != px) {
-            const int a = min(px, qy), b = max(px, qy);
-            cand = (__ldg(p.gpar + (int64_t)a * p.gpar_words + (b >> 5)) >> (b & 31)) & 1u;
-          }
-        }
+        const bool cand = c < nc && v < inf_ins() && ((link >> (rr * 4 + cb)) & 1ull);
         st_cand += cand ? 1 : 0;
         bool open = false;
         if (cand) {
@@ -785,19 +796,11 @@ __global__ void __launch_bounds__(GRNG_THREADS, 1) search_sweep_kernel(SearchPar
       for (int rr = 0; rr < 16; ++rr) {
         const int r = warp * 16 + rr;
         if (r >= nr) break;
-        const int px = parX[r];
         for (int cb = 0; cb < 4; ++cb) {
           if (cb * 32 >= nc) break;
           const int c = cb * 32 + lane;
           const float v = T[r * 129 + c];
-          bool cand = c < nc && v < inf_ins();
-          if (cand && p.gpar && px >= 0) {
-            const int qy = parY[c];
-            if (qy != px) {
-              const int a = min(px, qy), b = max(px, qy);
-              cand = (__ldg(p.gpar + (int64_t)a * p.gpar_words + (b >> 5)) >> (b & 31)) & 1u;
-            }
-          }
+          const bool cand = c < nc && v < inf_ins() && ((link >> (rr * 4 + cb)) & 1ull);
           bool surv = false;
           if (cand) {
             const PairThr P = pair_thresholds(v, 0.0f, 0.0f, 0.0f, 0.0f, METRIC, e, 0);
