@@ -225,7 +225,7 @@ def train_shortlist(g, wl, kind, n_train=200000, k=8):
 
 # Revision tags of the kernels whose DRAM traffic was captured with ncu (profiles/*traffic*.json);
 # a kernel changed since its capture gets a new tag here, and its traffic reads as null.
-KERNEL_REVS = {"tc_sweep_kernel": "two-tests-queue-prefetch"}  # the form captured at 1M
+KERNEL_REVS = {"tc_sweep_kernel": "chunk-bound"}  # the form captured at 1M
 
 
 def measured_traffic(kernel, n):

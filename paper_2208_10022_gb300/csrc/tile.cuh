@@ -6,7 +6,8 @@
 // KC dimensions, transposed to [KC][132]; the next chunk is prefetched into registers
 // while the current one is consumed.  Keys accumulate over the dimensions in order,
 // one FMA (L2) or one add of |a-b| (L1) per dimension, so T[x][y] and T[y][x] are
-// bit-identical wherever they are computed.
+// bit-identical wherever they are computed.  L2 runs on packed pairs of columns (one packed
+// subtraction and one packed FMA per pair), which round each half as the scalar forms do.
 #pragma once
 #include "common.cuh"
 
@@ -16,6 +17,25 @@ namespace grng {
 
 __device__ __forceinline__ float4 ldg4_or_zero(const float* p, bool ok) {
   return ok ? __ldg(reinterpret_cast<const float4*>(p)) : make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
+// Packed pairs of FP32 values (sm_100 and later): each half is rounded exactly as the scalar
+// operation rounds it, so a packed key equals the scalar one bit for bit.
+__device__ __forceinline__ unsigned long long f2pack(float lo, float hi) {
+  unsigned long long r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ void f2unpack(unsigned long long v, float& lo, float& hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+// acc + (a - b)^2 per half: one packed subtraction, one packed FMA
+__device__ __forceinline__ unsigned long long f2_sqdiff_acc(unsigned long long a, unsigned long long b,
+                                                           unsigned long long acc) {
+  unsigned long long t, r;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(t) : "l"(a), "l"(b));
+  asm("fma.rn.f32x2 %0, %1, %1, %2;" : "=l"(r) : "l"(t), "l"(acc));
+  return r;
 }
 
 __device__ __forceinline__ int tile_row(int i) {
@@ -43,6 +63,11 @@ __device__ __forceinline__ void tile_keys(const float* __restrict__ Xr, int nr,
   for (int i = 0; i < 8; ++i)
 #pragma unroll
     for (int j = 0; j < 8; ++j) acc[i][j] = 0.0f;
+  unsigned long long acc2[8][4];  // L2: the accumulators as packed column pairs
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int jp = 0; jp < 4; ++jp) acc2[i][jp] = 0ull;
 
   auto gload = [&](int k0) {
 #pragma unroll
@@ -74,18 +99,29 @@ __device__ __forceinline__ void tile_keys(const float* __restrict__ Xr, int nr,
       const float4 b0 = *reinterpret_cast<const float4*>(sB + kk * GRNG_SSTRIDE + tx * 4);
       const float4 b1 = *reinterpret_cast<const float4*>(sB + kk * GRNG_SSTRIDE + 64 + tx * 4);
       const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-      const float b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+      if (METRIC == L2) {  // columns in packed pairs: half the instructions of the scalar loop
+        const unsigned long long bp[4] = {f2pack(b0.x, b0.y), f2pack(b0.z, b0.w), f2pack(b1.x, b1.y),
+                                          f2pack(b1.z, b1.w)};
 #pragma unroll
-      for (int i = 0; i < 8; ++i)
+        for (int i = 0; i < 8; ++i) {
+          const unsigned long long ap = f2pack(a[i], a[i]);
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          float t = a[i] - b[j];
-          if (METRIC == L2)
-            acc[i][j] = fmaf(t, t, acc[i][j]);
-          else
-            acc[i][j] = acc[i][j] + fabsf(t);
+          for (int jp = 0; jp < 4; ++jp) acc2[i][jp] = f2_sqdiff_acc(ap, bp[jp], acc2[i][jp]);
         }
+      } else {
+        const float b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+#pragma unroll
+          for (int j = 0; j < 8; ++j) acc[i][j] = acc[i][j] + fabsf(a[i] - b[j]);
+      }
     }
+  }
+  if (METRIC == L2) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+      for (int jp = 0; jp < 4; ++jp) f2unpack(acc2[i][jp], acc[i][2 * jp], acc[i][2 * jp + 1]);
   }
 }
 

@@ -43,7 +43,7 @@ def test_fp32_sweep_reports_lane_peak():
 def test_measured_traffic_lookup():
     """roofline.traffic comes from the committed capture only for the same kernel, size and revision."""
     k = "tc_sweep_kernel (exemplar Gram tiles, tcgen05 split-BF16)"
-    assert bench.measured_traffic(k, 1_000_000) == 3_126_235_908_096 + 12_864_667_648
+    assert bench.measured_traffic(k, 1_000_000) == 3_119_250_631_168 + 12_933_911_040
     assert bench.measured_traffic(k, 999_999) is None                      # another size
     assert bench.measured_traffic("tier3_kernel (pivot layer m=131072)", 1_000_000) is None  # never captured
     saved = dict(bench.KERNEL_REVS)
