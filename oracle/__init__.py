@@ -41,6 +41,8 @@ def lib():
         _lib.orc_rng_rows.restype = i32
         _lib.orc_rng_rows.argtypes = [P, i64, i32, i32, P, i64, P, i64, P]
         _lib.orc_rng_search.restype = i32
+        _lib.orc_beta_brute.restype = i64
+        _lib.orc_beta_brute.argtypes = [P, i64, i32, ctypes.c_double, P, i64]
         _lib.orc_rng_search.argtypes = [P, i64, P, i64, i32, i32, P, i64, P]
         _lib.orc_verify_witness.restype = i32
         _lib.orc_verify_witness.argtypes = [P, i32, i32, i64, i64, i64]
@@ -159,6 +161,22 @@ def rng_search(X, Q, metric=L2, row_cap=4096):
     if m and cnt.max() > row_cap:
         raise ValueError("a neighbourhood exceeds row_cap")
     return [nb[t, :cnt[t]].copy() for t in range(m)]
+
+
+def beta_skeleton(X, beta):
+    """Lune-based beta-skeleton of X for 1 <= beta <= 2 (L2; beta = 1 the Gabriel graph, 2 the
+    RNG), all triples: sorted (i<j) int32 edges [E,2]."""
+    X = _f32(X)
+    fn = lib().orc_beta_brute
+    args = (_p(X), X.shape[0], X.shape[1], float(beta))
+    cnt = fn(*args, None, 0)
+    if cnt == -2:
+        raise ValueError("beta must lie in [1, 2]")
+    if cnt < 0:
+        raise MemoryError("oracle allocation failed")
+    out = np.zeros((max(cnt, 1), 2), dtype=np.int32)
+    assert fn(*args, _p(out), cnt) == cnt
+    return out[:cnt]
 
 
 def rng_guided(X, layers, metric=L2, with_stats=False):

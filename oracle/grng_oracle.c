@@ -258,6 +258,53 @@ int32_t orc_rng_search(const float *X, int64_t n, const float *Q, int64_t m, int
     return failed ? -1 : 0;
 }
 
+/* ---- lune-based beta-skeletons, 1 <= beta <= 2, L2 (Sec. 1: the empty-region graphs
+ * that contain the RNG; beta = 1 is the Gabriel graph, beta = 2 the RNG) -------------
+ * (x, y) is an edge iff no third point z lies strictly inside both balls of radius
+ * beta d(x,y) / 2 centred at (1 - beta/2) x + (beta/2) y and (beta/2) x + (1 - beta/2) y.
+ * With lam = beta / 2 and the keys a = d(z,x)^2, b = d(z,y)^2, v = d(x,y)^2, the squared
+ * distance of z to the first centre is (1-lam) a + lam b - lam (1-lam) v (Stewart's
+ * theorem), so z is inside the first ball iff (1-lam) a + lam b < lam v and inside the
+ * second iff lam a + (1-lam) b < lam v.  Canonical FP64: each side as written, the two
+ * products first, then their sum.  Edges (i<j) in lexicographic order into edges[cap][2];
+ * returns the count (which may exceed cap), -1 on allocation failure, -2 for beta outside
+ * [1, 2]. */
+int64_t orc_beta_brute(const float *X, int64_t n, int32_t D, double beta, int32_t *edges, int64_t cap) {
+    if (!(beta >= 1.0 && beta <= 2.0)) return -2;
+    if (n < 2) return 0;
+    const double lam = beta / 2.0, mu = 1.0 - lam;
+    double *K = key_matrix(X, n, D, ORC_L2);
+    if (!K) return -1;
+    unsigned char *lnk = (unsigned char *)calloc((size_t)n * (size_t)n, 1);
+    if (!lnk) { free(K); return -1; }
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t i = 0; i < n; ++i) {
+        for (int64_t j = i + 1; j < n; ++j) {
+            double v = K[i * n + j];
+            double t = lam * v;
+            int blocked = 0;
+            for (int64_t k = 0; k < n && !blocked; ++k) {
+                if (k == i || k == j) continue;
+                double a = K[k * n + i], b = K[k * n + j];
+                double in1 = mu * a + lam * b;             /* against the first centre */
+                double in2 = lam * a + mu * b;             /* against the second centre */
+                if (in1 < t && in2 < t) blocked = 1;      /* strictly inside both balls */
+            }
+            lnk[i * n + j] = (unsigned char)!blocked;
+        }
+    }
+    int64_t cnt = 0;
+    for (int64_t i = 0; i < n; ++i)
+        for (int64_t j = i + 1; j < n; ++j)
+            if (lnk[i * n + j]) {
+                if (cnt < cap) { edges[2 * cnt] = (int32_t)i; edges[2 * cnt + 1] = (int32_t)j; }
+                ++cnt;
+            }
+    free(lnk);
+    free(K);
+    return cnt;
+}
+
 /* Witness check (Eq. 1): 1 if z is a point other than x and y lying strictly inside
  * the open lune of (x, y), i.e. max(d(x,z), d(y,z)) < d(x,y), so that z proves the pair
  * is not an RNG edge; else 0. */

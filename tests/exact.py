@@ -41,6 +41,36 @@ def rng_search(X, Q, metric):
     return out
 
 
+def beta_skeleton(X, lam):
+    """Edges (i<j) of the lune-based beta-skeleton (L2), lam = beta / 2 a Fraction in [1/2, 1]:
+    z blocks (x, y) iff (1-lam) a + lam b < lam v and lam a + (1-lam) b < lam v (squared
+    distances a = |z-x|^2, b = |z-y|^2, v = |x-y|^2)."""
+    n = len(X)
+    lam = F(lam)
+    K = [[key(X[i], X[j], L2) for j in range(n)] for i in range(n)]
+    out = []
+    for i, j in combinations(range(n), 2):
+        v = K[i][j]
+        if not any((1 - lam) * K[k][i] + lam * K[k][j] < lam * v and lam * K[k][i] + (1 - lam) * K[k][j] < lam * v
+                   for k in range(n) if k not in (i, j)):
+            out.append((i, j))
+    return out
+
+
+def gabriel(X):
+    """Edges (i<j) of the Gabriel graph from coordinates: no z strictly inside the ball with
+    diameter xy, i.e. |2z - x - y|^2 < |x - y|^2."""
+    n = len(X)
+    out = []
+    for i, j in combinations(range(n), 2):
+        xi, xj = [F(t) for t in X[i]], [F(t) for t in X[j]]
+        dd = sum((a - b) ** 2 for a, b in zip(xi, xj))
+        if not any(sum((2 * F(zk) - a - b) ** 2 for zk, a, b in zip(X[k], xi, xj)) < dd
+                   for k in range(n) if k not in (i, j)):
+            out.append((i, j))
+    return out
+
+
 def _sqrt_lt_sqrt_minus(a, b, c):
     """Exactly decide sqrt(a) < sqrt(b) - c for rationals a, b >= 0 and c >= 0."""
     # sqrt(a) + c < sqrt(b)  <=>  a + c^2 + 2c sqrt(a) < b

@@ -20,6 +20,9 @@ What pins what:
                               every non-edge of Eq. 1 has a witness
   spanning_trees           -- Prim's tree has the weight of an exact Kruskal over all
                               pairs and lies in the RNG
+  skeletons                -- beta-skeletons (1 <= beta <= 2) against the exact rational
+                              predicate, beta = 1 against the Gabriel graph from the
+                              midpoint, beta = 2 against the RNG, and nesting in beta
   search                   -- RNG search (Algorithm 1 without Stage VII) against the exact
                               rational restatement, against the brute-force RNG of the
                               index plus that one query, and batch = one query at a time
@@ -321,5 +324,25 @@ def search(orc, trials=30, seed=18):
             assert 7 in set(map(int, got[0]))                        # a duplicate is always linked
 
 
+def skeletons(orc, trials=30, seed=19):
+    from fractions import Fraction
+    rng = np.random.default_rng(seed)
+    for t in range(trials):  # small integers: exact ties
+        n = int(rng.integers(3, 10))
+        d = int(rng.integers(1, 4))
+        X = _rand_int_points(rng, n, d, 4)
+        for beta in (Fraction(1), Fraction(5, 4), Fraction(3, 2), Fraction(2)):
+            want = set(exact.beta_skeleton(X.tolist(), beta / 2))
+            got = _as_set(orc.beta_skeleton(X, float(beta)))
+            assert got == want, (t, float(beta), X.tolist(), sorted(want ^ got))
+        assert _as_set(orc.beta_skeleton(X, 1.0)) == set(exact.gabriel(X.tolist())), (t, X.tolist())
+    for t in range(4):  # beta = 2 is the RNG; a larger beta keeps a subset of the edges
+        X = rng.standard_normal((90, 4)).astype(np.float32)
+        E = [_as_set(orc.beta_skeleton(X, b)) for b in (1.0, 1.25, 1.5, 1.75, 2.0)]
+        assert E[-1] == _as_set(orc.rng_brute(X, exact.L2))
+        assert all(E[k + 1] <= E[k] for k in range(len(E) - 1))
+        assert len(E[0]) > len(E[-1])
+
+
 ALL = [exact_rng, exact_grng, worked_examples, invariants, theorems, cross_checks, layer_examples, witnesses,
-       spanning_trees, search]
+       spanning_trees, search, skeletons]

@@ -35,6 +35,10 @@ MUTANTS = {
     "search_closed_lune": ("if (dxz < dqx) blocked = 1;", "if (dxz <= dqx) blocked = 1;"),
     "search_scan_stops_early": ("if (!(o[t].k < dqx)) break;", "if (!(o[t].k < 0.5 * dqx)) break;"),
     "search_scan_not_strict": ("if (!(o[t].k < dqx)) break;", "if (!(o[t].k <= dqx)) break;"),
+    "beta_closed": ("if (in1 < t && in2 < t) blocked = 1;", "if (in1 <= t && in2 <= t) blocked = 1;"),
+    "beta_one_ball": ("if (in1 < t && in2 < t) blocked = 1;", "if (in1 < t) blocked = 1;"),
+    "beta_swapped_weights": ("double in1 = mu * a + lam * b;", "double in1 = lam * a + mu * b;"),
+    "beta_radius_not_scaled": ("double t = lam * v;", "double t = v;"),
     "emst_wrong_endpoint": ("edges[2 * (e - 1)] = (int32_t)from[u];",
                             "edges[2 * (e - 1)] = (int32_t)(u > 0 ? u - 1 : 1);"),
 }
