@@ -62,6 +62,9 @@ def parse():
                     help="instead of the build benchmark: insert B batches of uneven size (log-uniform in "
                          "[1,000, 65,536] points, scaled to --n) into an index built on the rest, and print "
                          "points/s and per-batch latency")
+    ap.add_argument("--skeleton", type=float, default=0.0, metavar="BETA",
+                    help="instead of the build benchmark: the lune-based beta-skeleton (1 <= BETA <= 2) of the "
+                         "workload, timed after the pivot layers")
     ap.add_argument("--search", type=int, default=0, metavar="B",
                     help="instead of the build benchmark: B batches of --search-m queries (RNG search)")
     ap.add_argument("--search-m", type=int, default=1000, help="queries per search batch")
@@ -740,6 +743,80 @@ def run_search(a, rank):
     return 0
 
 
+def _canonical_keys_to(X64, i):
+    """FP64 keys of every point to point i, the squared differences added in dimension order."""
+    import numpy as np
+    acc = np.zeros(X64.shape[0])
+    for d in range(X64.shape[1]):
+        t = X64[:, d] - X64[i, d]
+        acc = acc + t * t
+    return acc
+
+
+def run_skeleton(a, rank):
+    """Lune-based beta-skeleton (rng_build_skeleton): the pivot layers are built and linked,
+    then the skeleton of all points is timed with CUDA events per step (no Theorem 1 below
+    beta = 2: every pair is a candidate).  Sampled edges are checked to have no point inside
+    their beta-lune, in canonical FP64 against every point; the FP64 oracle's brute force on a
+    bounded sample is the CPU baseline."""
+    import numpy as np
+    import torch
+
+    import paper_2208_10022_gb300 as g
+    from paper_2208_10022_gb300 import build as gb
+    from paper_2208_10022_gb300 import workloads as wl
+    gb.build()
+    beta = a.skeleton
+    w = wl.make(a.kind, n=a.n)
+    stream = torch.cuda.current_stream()
+    Xd = torch.from_numpy(w.X).cuda()
+    ix, _ = g.build_all(Xd, w.layers, stream=stream)
+    lat = []
+    for it in range(a.warmup + a.steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ix.rng_build_skeleton(beta)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if it >= a.warmup:
+            lat.append(e0.elapsed_time(e1))
+    E = ix.rng_edges()
+    st = ix.stats()["rng"]
+    X64 = w.X.astype(np.float64)
+    lam, mu = beta / 2.0, 1.0 - beta / 2.0
+    bad = 0
+    sample = E[np.random.default_rng(7).choice(E.shape[0], size=min(100, E.shape[0]), replace=False)]
+    for i, j in sample:
+        ka, kb = _canonical_keys_to(X64, int(i)), _canonical_keys_to(X64, int(j))
+        t = lam * ka[int(j)]
+        inside = (mu * ka + lam * kb < t) & (lam * ka + mu * kb < t)
+        inside[[int(i), int(j)]] = False
+        bad += int(inside.any())
+    cpu = None
+    if rank == 0 and a.cpu_sample:
+        import oracle
+        k = min(a.cpu_sample, 2500, w.n)
+        Xs = wl.subsample(w, k, 11).X
+        t0 = time.perf_counter()
+        Ec = oracle.beta_skeleton(Xs, beta)
+        cs = time.perf_counter() - t0
+        cpu = {"value": len(Ec) / cs, "unit": "edges/s", "cores": oracle.max_threads(), "kind": "oracle",
+               "sample": f"beta_skeleton brute force on a seeded {k}-point subsample ({len(Ec)} edges in {cs:.2f} s)"}
+    ms = float(np.mean(lat))
+    line = {"metric": f"beta-skeleton edges/s (beta={beta:g})", "value": E.shape[0] / (ms / 1000.0), "unit": "edges/s",
+            "higher_is_better": True, "n_gpus": 1, "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms,
+            "edges": int(E.shape[0]), "sampled_edges_checked": int(sample.shape[0]), "sampled_edges_with_a_point_inside": bad,
+            "cpu_baseline": cpu,
+            "work": {k: st[k] for k in ("candidate_pairs", "tier1_survivors", "tier2a_links", "tier2a_blocked",
+                                        "tier3_pairs", "fp64_triples", "edges")},
+            "phase_ms": st["phase_ms"],
+            "config": {"workload": f"{a.kind}: {w.n:,} x {w.dim} FP32, L2, nested random pivot layers "
+                                   f"{'/'.join(str(len(l)) for l in w.layers)}", "beta": beta, "precision": "fp32"}}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     a = parse()
     rank, world, local = dist_env()
@@ -749,6 +826,8 @@ def main():
         return run_insert(a, rank)
     if a.search:
         return run_search(a, rank)
+    if a.skeleton:
+        return run_skeleton(a, rank)
     return run_gpu(a, rank, world, local)
 
 

@@ -136,6 +136,20 @@ grng_status grng_adjacency_rows(grng_index* idx, int32_t layer, int64_t row_begi
  * tested for an empty lune.  Every layer must be built and linked. */
 grng_status rng_build_exact(grng_index* idx);
 
+/* Lune-based beta-skeleton of all points for 1 <= beta <= 2 (Sec. 1: the empty-region
+ * graphs that contain the RNG; beta = 1 is the Gabriel graph, beta = 2 the RNG): (x, y) is
+ * an edge iff no third point lies strictly inside both balls of radius beta d(x,y) / 2
+ * centred at (1 - beta/2) x + (beta/2) y and (beta/2) x + (1 - beta/2) y.  The edges
+ * replace the stored graph (read with rng_edges, same format); beta = 2 is exactly
+ * rng_build_exact.  Below 2 Theorem 1 does not restrict the candidates (a GRNG non-link
+ * proves a point inside the lune of Eq. 1, not inside the smaller beta-lune), so every pair
+ * is a candidate; the interceptor tiers, the exhaustive search over the pivot layers and the
+ * FP64 recheck are those of the RNG with the lune test replaced; FP32 tiles, no learned
+ * shortlist.  Every layer must be built and linked.  Errors: GRNG_EINVAL for beta outside
+ * [1, 2] or, below 2, an L1 index; GRNG_ESTATE when a layer is not linked.  rng_insert_batch
+ * refuses an index whose stored graph is a skeleton with beta < 2 (GRNG_ESTATE). */
+grng_status rng_build_skeleton(grng_index* idx, double beta);
+
 /* Insert m new points pts[m][dim] (host or device) so that the stored RNG becomes
  * the RNG of the enlarged set (Algorithm 1 and Stage VII, Sec. 2).  Requires a
  * built RNG.  The new points get ids n .. n+m-1 and join the finest layer's domains;

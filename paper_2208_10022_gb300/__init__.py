@@ -30,8 +30,8 @@ FP32, BF16, FP8 = 0, 1, 2
 
 EXPORTS = [
     "grng_default_opts", "grng_create", "grng_build_layer", "grng_link_pivots", "grng_adjacency_rows",
-    "rng_build_exact", "rng_insert_batch", "rng_search_batch", "rng_search_result", "rng_edges", "grng_stats",
-    "grng_destroy", "grng_last_error",
+    "rng_build_exact", "rng_build_skeleton", "rng_insert_batch", "rng_search_batch", "rng_search_result",
+    "rng_edges", "grng_stats", "grng_destroy", "grng_last_error",
 ]
 
 
@@ -68,6 +68,7 @@ def lib():
         L.grng_link_pivots.argtypes = [P, i32, P, P, P, i64, ctypes.POINTER(i64)]
         L.grng_adjacency_rows.argtypes = [P, i32, i64, i64, P, P, i64, ctypes.POINTER(i64)]
         L.rng_build_exact.argtypes = [P]
+        L.rng_build_skeleton.argtypes = [P, ctypes.c_double]
         L.rng_insert_batch.argtypes = [P, P, i64]
         L.rng_search_batch.argtypes = [P, P, i64, ctypes.POINTER(i64)]
         L.rng_search_result.argtypes = [P, P, P, i64]
@@ -86,7 +87,8 @@ def lib():
         L.grng_mlp_dataset.argtypes = [P, P, P, i64, ctypes.POINTER(i64)]
         L.grng_tc_keys.argtypes = [P, i64, i32, P]
         for f in ("grng_create", "grng_build_layer", "grng_link_pivots", "grng_adjacency_rows",
-                  "rng_build_exact", "rng_insert_batch", "rng_search_batch", "rng_search_result", "rng_edges",
+                  "rng_build_exact", "rng_build_skeleton", "rng_insert_batch", "rng_search_batch",
+                  "rng_search_result", "rng_edges",
                   "grng_stats", "grng_mlp_score",
                   "grng_mlp_loss_grad", "grng_mlp_train", "grng_mlp_dataset", "grng_tc_keys"):
             getattr(L, f).restype = i32
@@ -196,6 +198,10 @@ class Index:
 
     def rng_build_exact(self):
         _check(lib().rng_build_exact(self._h))
+
+    def rng_build_skeleton(self, beta):
+        """Lune-based beta-skeleton (1 <= beta <= 2, L2) as the stored graph; read it with rng_edges."""
+        _check(lib().rng_build_skeleton(self._h, float(beta)))
 
     def rng_insert_batch(self, points):
         pts = _contig(points, np.float32)

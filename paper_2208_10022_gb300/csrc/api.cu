@@ -189,6 +189,7 @@ struct grng_index {
   DevBuf mlp;            // ranking network parameters (learned shortlist), or empty
   DevBuf rec_f, rec_y;   // recorded training samples of the last RNG build
   int64_t rec_n = 0;
+  double skel_beta = 2.0;  // the stored graph: the RNG (2) or a beta-skeleton (1 <= beta < 2)
   int64_t version = 0;   // bumped whenever the points, their order or their parents change
   struct {               // search: rows kept for one index version, and the last result
     int64_t version = -1, cap = 0;
@@ -646,51 +647,72 @@ grng_status grng_adjacency_rows(grng_index* ix, int32_t layer, int64_t row_begin
   });
 }
 
+// The exemplar level: the RNG (beta = 2) or a lune-based beta-skeleton with 1 <= beta < 2.
+// A skeleton below 2 takes no guidance (Theorem 1 proves a point inside the lune of Eq. 1,
+// not inside the smaller beta-lune), FP32 tiles and no learned shortlist; every bound the
+// tiers derive from the lune of Eq. 1 still holds, since it contains the beta-lune.
+static void build_exemplar_graph(grng_index* ix, double beta) {
+  for (auto& l : ix->layers)
+    if (!l.linked) fail(GRNG_ESTATE, "every layer must be built and linked");
+  ensure_sorted(ix);
+  cudaStream_t s = ix->stream;
+  Layer& fin = ix->layers.back();
+  const bool skel = beta < 2.0;
+  Timer tm(s);
+  LevelIn in{};
+  in.X = ix->Xs.as<float>();
+  in.n = ix->n;
+  in.D = ix->D;
+  in.Dp = ix->Dp;
+  in.metric = ix->metric;
+  in.grng = 0;
+  in.K = ix->K;
+  in.parent = skel ? nullptr : ix->xparent.as<int32_t>();
+  in.gpar = skel ? nullptr : fin.gg.as<uint32_t>();
+  in.gpar_words = skel ? 0 : fin.words;
+  in.orig = ix->xorder.as<int32_t>();
+  in.anc = ancestors_of(ix, (int)ix->layers.size());
+  in.pdist_hi = ix->xpdh.as<float>();
+  in.precision = (!skel && ix->opts.precision == GRNG_BF16) ? 1 : 0;
+  if (ix->opts.spin_limit > 0) in.spin = ix->opts.spin_limit;
+  in.mlp_params = (!skel && ix->mlp.p) ? ix->mlp.as<float>() : nullptr;
+  in.kshort = (!skel && ix->mlp.p) ? ix->opts.k_shortlist : 0;
+  in.mlp_record = (!skel && (ix->opts.flags & GRNG_FLAG_RECORD_MLP)) ? 1 : 0;
+  in.small_buffers = (ix->opts.flags & GRNG_FLAG_SMALL_BUFFERS) ? 1 : 0;
+  in.beta_lam = beta / 2.0;
+  LevelOut lo;
+  lo.edges = &ix->edges;
+  lo.rec_f = &ix->rec_f;
+  lo.rec_y = &ix->rec_y;
+  float tile_ms = 0;
+  run_level(in, lo, ix->rng_st, s, &tile_ms);
+  ix->n_edges = lo.n_edges;
+  ix->rec_n = lo.rec_n;
+  DevBuf tmp;
+  if (ix->n_edges > 1) sort_u64(ix->edges.as<uint64_t>(), ix->n_edges, tmp, s);
+  ix->rng_tile_ms = tile_ms;
+  ix->rng_ms = tm.stop();
+  ix->rng_built = true;
+  ix->skel_beta = beta;
+}
+
 grng_status rng_build_exact(grng_index* ix) {
   if (!ix) {
     g_last_error = "index is NULL";
     return GRNG_EINVAL;
   }
+  return guarded(ix, [&] { build_exemplar_graph(ix, 2.0); });
+}
+
+grng_status rng_build_skeleton(grng_index* ix, double beta) {
+  if (!ix) {
+    g_last_error = "index is NULL";
+    return GRNG_EINVAL;
+  }
   return guarded(ix, [&] {
-    for (auto& l : ix->layers)
-      if (!l.linked) fail(GRNG_ESTATE, "every layer must be built and linked");
-    ensure_sorted(ix);
-    cudaStream_t s = ix->stream;
-    Layer& fin = ix->layers.back();
-    Timer tm(s);
-    LevelIn in{};
-    in.X = ix->Xs.as<float>();
-    in.n = ix->n;
-    in.D = ix->D;
-    in.Dp = ix->Dp;
-    in.metric = ix->metric;
-    in.grng = 0;
-    in.K = ix->K;
-    in.parent = ix->xparent.as<int32_t>();
-    in.gpar = fin.gg.as<uint32_t>();
-    in.gpar_words = fin.words;
-    in.orig = ix->xorder.as<int32_t>();
-    in.anc = ancestors_of(ix, (int)ix->layers.size());
-    in.pdist_hi = ix->xpdh.as<float>();
-    in.precision = ix->opts.precision == GRNG_BF16 ? 1 : 0;
-    if (ix->opts.spin_limit > 0) in.spin = ix->opts.spin_limit;
-    in.mlp_params = ix->mlp.p ? ix->mlp.as<float>() : nullptr;
-    in.kshort = ix->mlp.p ? ix->opts.k_shortlist : 0;
-    in.mlp_record = (ix->opts.flags & GRNG_FLAG_RECORD_MLP) ? 1 : 0;
-    in.small_buffers = (ix->opts.flags & GRNG_FLAG_SMALL_BUFFERS) ? 1 : 0;
-    LevelOut lo;
-    lo.edges = &ix->edges;
-    lo.rec_f = &ix->rec_f;
-    lo.rec_y = &ix->rec_y;
-    float tile_ms = 0;
-    run_level(in, lo, ix->rng_st, s, &tile_ms);
-    ix->n_edges = lo.n_edges;
-    ix->rec_n = lo.rec_n;
-    DevBuf tmp;
-    if (ix->n_edges > 1) sort_u64(ix->edges.as<uint64_t>(), ix->n_edges, tmp, s);
-    ix->rng_tile_ms = tile_ms;
-    ix->rng_ms = tm.stop();
-    ix->rng_built = true;
+    if (!(beta >= 1.0 && beta <= 2.0)) fail(GRNG_EINVAL, "beta must lie in [1, 2]");
+    if (ix->metric != GRNG_L2 && beta < 2.0) fail(GRNG_EINVAL, "beta-skeletons below 2 need the L2 metric");
+    build_exemplar_graph(ix, beta);
   });
 }
 
@@ -724,6 +746,7 @@ grng_status rng_insert_batch(grng_index* ix, const float* pts, int64_t m) {
   return guarded(ix, [&] {
     if (!pts || m < 1) fail(GRNG_EINVAL, "need pts and m >= 1");
     if (!ix->rng_built) fail(GRNG_ESTATE, "the RNG is not built");
+    if (ix->skel_beta < 2.0) fail(GRNG_ESTATE, "the stored graph is a beta-skeleton, not the RNG");
     if (ix->n + m >= (int64_t)1 << 31) fail(GRNG_EINVAL, "n + m must stay below 2^31");
     cudaStream_t s = ix->stream;
     Timer tm(s);
@@ -1164,7 +1187,7 @@ grng_status grng_stats(const grng_index* cix, char* json, size_t cap) {
     js += "}";
   }
   snprintf(buf, sizeof(buf),
-           "],\"rng_built\":%d,\"n_edges\":%lld,\"rng_ms\":%.4f,\"rng_tile_ms\":%.4f,"
+           "],\"rng_built\":%d,\"skeleton_beta\":%.17g,\"n_edges\":%lld,\"rng_ms\":%.4f,\"rng_tile_ms\":%.4f,"
            "\"insert\":{\"batches\":%lld,\"points\":%lld,\"ms\":%.4f,\"changed_pivots\":%lld,"
            "\"grng_pairs\":%lld,\"grng_links_added\":%lld,\"candidate_pairs\":%lld,\"tier1_survivors\":%lld,"
            "\"stage7_candidates\":%lld,\"stage7_tests\":%lld,\"stage7_fp64\":%lld,\"new_edges\":%lld,"
@@ -1173,7 +1196,7 @@ grng_status grng_stats(const grng_index* cix, char* json, size_t cap) {
            "\"candidate_pairs\":%lld,\"tier1_survivors\":%lld,\"neighbours\":%lld,"
            "\"tier1_queued\":%lld,\"sweep_retries\":%lld,"
            "\"last_assign_ms\":%.4f,\"last_sweep_ms\":%.4f,\"last_tiers_ms\":%.4f,",
-           (int)ix->rng_built, (long long)ix->n_edges, ix->rng_ms, ix->rng_tile_ms, (long long)ix->insert_batches,
+           (int)ix->rng_built, ix->skel_beta, (long long)ix->n_edges, ix->rng_ms, ix->rng_tile_ms, (long long)ix->insert_batches,
            (long long)ix->inserted, ix->insert_ms, ix->ins.changed_pivots, ix->ins.grng_pairs, ix->ins.grng_linked,
            ix->ins.candidates, ix->ins.survivors, ix->ins.s7_candidates, ix->ins.s7_tests, ix->ins.s7_fp64,
            ix->ins.new_edges, ix->ins.removed_edges, ix->srch.batches, ix->srch.queries, ix->srch.ms,

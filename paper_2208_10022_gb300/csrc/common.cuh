@@ -110,14 +110,19 @@ __device__ __forceinline__ float key32(const float* __restrict__ a, const float*
 struct PairThr {
   float t1lo, t1hi, t2lo, t2hi;
   int quick;  // 1: no k can satisfy one of the conditions (certainly linked)
+  float lam;  // zero radii, L2: beta / 2 of a lune-based beta-skeleton (1: the lune of Eq. 1)
 };
 
 // v = FP32 key of (x, y); rx*/ry* = FP32 lower/upper bounds of the FP64 radii.
-// guide = 1 applies the guidance margin to the "certainly true" side.
+// guide = 1 applies the guidance margin to the "certainly true" side.  lam < 1 (zero radii,
+// L2 only) asks for the beta-skeleton test: the thresholds stay those of Eq. 1, whose lune
+// holds every beta-lune with beta <= 2, so every bound derived from them stays valid.
 __device__ __forceinline__ PairThr pair_thresholds(float v, float rxlo, float rxhi, float rylo,
-                                                   float ryhi, int metric, Err e, int guide) {
+                                                   float ryhi, int metric, Err e, int guide,
+                                                   float lam = 1.0f) {
   PairThr p;
   p.quick = 0;
+  p.lam = (rxhi == 0.0f && ryhi == 0.0f) ? lam : 1.0f;
   const float u2 = 1.1920928955078125e-07f;  // 2 u
   if (rxhi == 0.0f && ryhi == 0.0f) {        // zero radii: key comparisons (Eq. 1)
     float vlo = lo_b(v, e), vhi = hi_b(v, e);
@@ -165,24 +170,53 @@ __device__ __forceinline__ PairThr pair_thresholds(float v, float rxlo, float rx
   return p;
 }
 
+// Lune-based beta-skeleton (L2 keys a = |k-x|^2, b = |k-y|^2, v = |x-y|^2, lam = beta/2):
+// k lies strictly inside both balls of the beta-lune iff (1-lam) a + lam b < lam v and
+// lam a + (1-lam) b < lam v (Stewart's theorem for the distance to each centre).  The
+// brackets of a, b and v carry their FP32 errors; 8u (a + b) and 4u of the threshold cover
+// the rounding of the combinations and the FP32 rounding of lam.
+__device__ __forceinline__ int beta_state(float a, float b, const PairThr& p, Err e) {
+  const float u = 5.9604644775390625e-8f;
+  const float lam = p.lam, mu = 1.0f - lam;
+  const float ah = hi_b(a, e), bh = hi_b(b, e);
+  const float al = fmaxf(lo_b(a, e), 0.0f), bl = fmaxf(lo_b(b, e), 0.0f);
+  const float tlo = lam * p.t1lo * (1.0f - 4.0f * u), thi = lam * p.t1hi * (1.0f + 4.0f * u);
+  const float sh = 8.0f * u * (ah + bh), sl = 8.0f * u * (al + bl);
+  if (mu * ah + lam * bh + sh < tlo && lam * ah + mu * bh + sh < tlo) return 2;
+  if (mu * al + lam * bl - sl >= thi || lam * al + mu * bl - sl >= thi) return 0;
+  return 1;
+}
+
 // 2 = certainly blocks, 0 = certainly does not block, 1 = ambiguous.
 // a = FP32 key(k, x), b = FP32 key(k, y).
 __device__ __forceinline__ int block_state(float a, float b, const PairThr& p, Err e) {
+  if (p.lam < 1.0f) return beta_state(a, b, p, e);
   if (hi_b(a, e) < p.t1lo && hi_b(b, e) < p.t2lo) return 2;
   if (lo_b(a, e) >= p.t1hi || lo_b(b, e) >= p.t2hi) return 0;
   return 1;
 }
 
 // Canonical FP64 decision for one triple, exactly as the CPU definition evaluates it.
-// Returns bit0 = blocks (definition), bit1 = blocks with the guidance margin.
+// Returns bit0 = blocks (definition), bit1 = blocks with the guidance margin.  lam < 1 (zero
+// radii): the beta-skeleton test, each side as the definition writes it (two products, then
+// their sum), which is symmetric in x and y.
 __device__ __forceinline__ int block64(const float* __restrict__ X, int D, int Dp, int metric,
-                                       int64_t x, int64_t y, int64_t k, double rx, double ry) {
+                                       int64_t x, int64_t y, int64_t k, double rx, double ry,
+                                       double lam = 1.0) {
   const float* px = X + x * Dp;
   const float* py = X + y * Dp;
   const float* pk = X + k * Dp;
   double kxy = key64(px, py, D, metric);
   double kkx = key64(pk, px, D, metric);
   double kky = key64(pk, py, D, metric);
+  if (rx == 0.0 && ry == 0.0 && lam < 1.0) {
+    const double mu = __dsub_rn(1.0, lam);
+    const double t = __dmul_rn(lam, kxy);
+    const double in1 = __dadd_rn(__dmul_rn(mu, kkx), __dmul_rn(lam, kky));
+    const double in2 = __dadd_rn(__dmul_rn(lam, kkx), __dmul_rn(mu, kky));
+    const int b = in1 < t && in2 < t;
+    return b | (b << 1);
+  }
   if (rx == 0.0 && ry == 0.0) {
     double m = kkx > kky ? kkx : kky;
     int b = m < kxy;

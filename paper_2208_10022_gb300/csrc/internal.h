@@ -127,6 +127,8 @@ struct LevelIn {
   int lists = 1;                      // GRNG levels: range lists for the pairs tier 2 leaves open
   int64_t npts = 0;                   // rows [0, npts) may block a pair (0: all n); the rows
                                       // beyond are search queries, endpoints only
+  double beta_lam = 1.0;              // RNG level, L2: beta / 2 of a lune-based beta-skeleton
+                                      // (1: the RNG; below 1 needs parent = gpar = null, FP32)
 };
 
 // ---- tensor-core tiles (kernels_tc.cu) ------------------------------------------------------

@@ -161,6 +161,7 @@ struct TileParams {
   int* strip_ctr;
   unsigned long long* stats;  // [0] candidate pairs [1] linked in the tile [2] of which certified by a list
   int mode;  // 0: lists + filter in one sweep; 1: lists only; 2: filter with the lists of sweep 1
+  float lam;  // beta / 2 of the lune test (1: Eq. 1)
 };
 
 // shared-memory layout of the tile sweep (bytes)
@@ -356,7 +357,7 @@ __global__ void __launch_bounds__(GRNG_THREADS, 1) tile_pass_kernel(TileParams p
             bool quick = false, surv = false;
             if (cand) {
               const float v = T[r * 129 + c];
-              PairThr P = pair_thresholds(v, rxl, rxh, rylo[c], ryhi[c], METRIC, e, p.guide);
+              PairThr P = pair_thresholds(v, rxl, rxh, rylo[c], ryhi[c], METRIC, e, p.guide, p.lam);
               if (P.quick) {
                 quick = true;
               } else if (p.mode == 2 &&
@@ -462,6 +463,7 @@ struct Tier2Params {
   int2* pend; unsigned long long* pend_cnt; unsigned long long pend_cap;
   int2* amb; unsigned long long* amb_cnt; unsigned long long amb_cap;
   unsigned long long* stats;  // [0] links [1] pendings [2] unresolved [3] blocked
+  float lam;                  // beta / 2 of the lune test (1: Eq. 1)
 };
 
 __device__ __forceinline__ void push_pair(int2* buf, unsigned long long* cnt,
@@ -511,7 +513,7 @@ __global__ void __launch_bounds__(128) tier2_kernel(Tier2Params p) {
       for (int sh = 16; sh > 0; sh >>= 1) part += __shfl_xor_sync(FULLMASK, part, sh);
       const float v = part;
       const float rol = p.rlo ? p.rlo[o] : 0.0f, roh = p.rhi ? p.rhi[o] : 0.0f;
-      PairThr P = pair_thresholds(v, rgl, rgh, rol, roh, p.metric, e, p.guide);
+      PairThr P = pair_thresholds(v, rgl, rgh, rol, roh, p.metric, e, p.guide, p.lam);
       if (P.quick) {
         if (lane == 0) push_pair(p.links, p.link_cnt, p.link_cap, make_int2((int)g, o));
         c_link += lane == 0;
@@ -598,6 +600,7 @@ struct Tier3Params {
   unsigned long long* stats;  // [0] frontier overflows, [1] nodes tested, [2] pairs blocked, [3] by the descent
   unsigned long long* prof;   // SM cycles of thread 0: [0] top level and descents [1] lower ancestor levels
                               // [2] node level; [3] pairs reaching the lower ancestor levels
+  float lam;                  // beta / 2 of the lune test (1: Eq. 1)
 };
 
 // asynchronous 16-byte copy global -> shared (src_bytes < 16: the rest is zero-filled, 0: no read)
@@ -714,7 +717,7 @@ __global__ void __launch_bounds__(T3_T, T3_MINB) tier3_kernel(Tier3Params p) {
     const float v = s_v;
     PairThr P = pair_thresholds(v, p.rlo ? p.rlo[g] : 0.0f, p.rhi ? p.rhi[g] : 0.0f,
                                 p.rlo ? p.rlo[o] : 0.0f, p.rhi ? p.rhi[o] : 0.0f, p.metric, e,
-                                p.guide);
+                                p.guide, p.lam);
     const int64_t slot = p.slot0 + t;
     // a pair the learned shortlist has already blocked needs no exhaustive scan
     const bool pre = p.pflag[slot] == 3;
@@ -731,7 +734,9 @@ __global__ void __launch_bounds__(T3_T, T3_MINB) tier3_kernel(Tier3Params p) {
       float lam = 0.5f, rho2 = -1.0f;
       if (p.metric == L2) {
         lam = fminf(fmaxf((vhi + P.t1hi - P.t2hi) / (2.0f * fmaxf(vhi, 1e-30f)), 0.0f), 1.0f);
-        const float m1 = (1.0f - lam) * P.t1hi + lam * P.t2hi;
+        // a beta-lune (zero radii, so lam = 1/2 here): its two ball conditions averaged give
+        // (a + b) / 2 < (beta / 2) v, so the bound m1 of the lune of Eq. 1 scales by beta / 2
+        const float m1 = ((1.0f - lam) * P.t1hi + lam * P.t2hi) * (P.lam < 1.0f ? P.lam : 1.0f);
         rho2 = m1 - lam * (1.0f - lam) * vlo + 8.0f * u2 * (m1 + lam * (1.0f - lam) * vhi);
       }
       const float rho = rho2 >= 0.0f ? sqrtf(rho2) * (1.0f + u2) : 0.0f;
@@ -1119,7 +1124,8 @@ __global__ void __launch_bounds__(T3P_WARPS * 32) tier3_probe_kernel(Tier3Params
     if (lane == 0) v = key32(gs, os, p.Dp, p.metric);
     v = __shfl_sync(FULLMASK, v, 0);
     const PairThr P = pair_thresholds(v, p.rlo ? p.rlo[g] : 0.0f, p.rhi ? p.rhi[g] : 0.0f,
-                                      p.rlo ? p.rlo[o] : 0.0f, p.rhi ? p.rhi[o] : 0.0f, p.metric, e, p.guide);
+                                      p.rlo ? p.rlo[o] : 0.0f, p.rhi ? p.rhi[o] : 0.0f, p.metric, e, p.guide,
+                                      p.lam);
     bool blocked = false;
     if (!P.quick) {
       const float vlo = fmaxf(lo_b(v, e), 0.0f), vhi = hi_b(v, e);
@@ -1825,13 +1831,13 @@ __global__ void __launch_bounds__(LT_WARPS * 32, 3) list_tier_kernel(ListParams 
 __global__ void recheck_kernel(const float* __restrict__ X, int D, int Dp, int metric,
                                const double* __restrict__ r64, const int2* __restrict__ amb,
                                int64_t m, const int2* __restrict__ pend, int* __restrict__ pflag,
-                               unsigned long long* stats) {
+                               unsigned long long* stats, double lam) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= m) return;
   int2 a = amb[i];
   int2 pr = pend[a.x];
   double rx = r64 ? r64[pr.x] : 0.0, ry = r64 ? r64[pr.y] : 0.0;
-  int bits = block64(X, D, Dp, metric, pr.x, pr.y, a.y, rx, ry);
+  int bits = block64(X, D, Dp, metric, pr.x, pr.y, a.y, rx, ry, lam);
   if (bits) {
     atomicOr(pflag + a.x, bits);
     atomicAdd(stats, 1ull);
@@ -2022,6 +2028,7 @@ static void finish_level(const LevelIn& in, LevelOut& out, LevelStats& st, cudaS
     GRNG_CUDA(cudaMemsetAsync(dc + 8, 0, 16 * sizeof(unsigned long long), s));
     Tier2Params t2;
     t2.X = in.X; t2.n = n; t2.Dp = in.Dp; t2.metric = in.metric; t2.guide = in.grng; t2.K = in.K;
+    t2.lam = (float)in.beta_lam;
     t2.rlo = in.rlo; t2.rhi = in.rhi; t2.knn_idx = knn_idx; t2.knn_key = knn_key;
     t2.knn_rb = knn_rb;
     t2.off = off.as<int64_t>(); t2.other = oth.as<int32_t>();
@@ -2092,6 +2099,7 @@ static void finish_level(const LevelIn& in, LevelOut& out, LevelStats& st, cudaS
         Tier3Params pp{};
         pp.X = in.X; pp.n = n; pp.npts = in.npts ? in.npts : n; pp.Dp = in.Dp; pp.metric = in.metric;
         pp.guide = in.grng;
+        pp.lam = (float)in.beta_lam;
         pp.rlo = in.rlo; pp.rhi = in.rhi; pp.pairs = unres2.as<int2>(); pp.m = (int64_t)nun2;
         pp.anc = in.anc;
         for (int a = 0; a < in.anc.n; ++a) pp.anc.toff[a] = toff[a];
@@ -2240,6 +2248,7 @@ static void finish_level(const LevelIn& in, LevelOut& out, LevelStats& st, cudaS
       Tier3Params t3;
       t3.X = in.X; t3.n = n; t3.npts = in.npts ? in.npts : n; t3.Dp = in.Dp; t3.metric = in.metric;
       t3.guide = in.grng;
+      t3.lam = (float)in.beta_lam;
       t3.rlo = in.rlo; t3.rhi = in.rhi; t3.pairs = t3pairs; t3.m = (int64_t)nun2;
       t3.pend = pend.as<int2>(); t3.pflag = pflag.as<int>(); t3.slot0 = (int64_t)npend;
       t3.amb = amb.as<int2>(); t3.amb_cnt = dc + 19; t3.amb_cap = amb_cap;
@@ -2346,7 +2355,7 @@ static void finish_level(const LevelIn& in, LevelOut& out, LevelStats& st, cudaS
     if (namb) {
       recheck_kernel<<<(unsigned)((namb + 255) / 256), 256, 0, s>>>(
           in.X, in.D, in.Dp, in.metric, in.r64, amb.as<int2>(), (int64_t)namb, pend.as<int2>(),
-          pflag.as<int>(), dc + 22); note_launch();
+          pflag.as<int>(), dc + 22, in.beta_lam); note_launch();
       GRNG_CUDA(cudaGetLastError());
     }
     // ---- emission ----------------------------------------------------------------------
@@ -2461,6 +2470,7 @@ void run_level(const LevelIn& in, LevelOut& out, LevelStats& st, cudaStream_t s,
     }
     TileParams tp;
     tp.X = in.X; tp.n = n; tp.Dp = in.Dp; tp.grng = in.grng; tp.guide = in.grng; tp.K = in.K;
+    tp.lam = (float)in.beta_lam;
     tp.parent = in.parent; tp.gpar = in.gpar; tp.gpar_words = in.gpar_words;
     tp.rlo = in.rlo; tp.rhi = in.rhi; tp.A = A.as<__half>(); tp.nbr_idx = nbi.as<uint8_t>();
     tp.nbr_key = nbk.as<float>(); tp.knn_idx = knni.as<int32_t>(); tp.knn_key = knnk.as<float>();
