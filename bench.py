@@ -68,6 +68,8 @@ def parse():
     ap.add_argument("--search", type=int, default=0, metavar="B",
                     help="instead of the build benchmark: B batches of --search-m queries (RNG search)")
     ap.add_argument("--search-m", type=int, default=1000, help="queries per search batch")
+    ap.add_argument("--no-search-leg", action="store_true",
+                    help="build benchmark: skip the search of 5 x 1,000 queries on an index of the workload")
     ap.add_argument("--search-check", type=int, default=32,
                     help="queries of the first batch compared with the oracle (FP64 on the host)")
     ap.add_argument("--insert-verify", action="store_true",
@@ -575,6 +577,11 @@ def run_gpu(a, rank, world, local):
         del e32
     if prec == g.BF16 and metric == wl.L2:
         line["tc_key_error"] = tc_key_error(g, w.X)
+    if rank == 0 and not a.no_search_leg:
+        try:
+            line["search"] = search_leg(g, wl, a, w, Xd, piv_d, prec, metric, mlp, stream)
+        except Exception as ex:  # a failed extra leg must not hide the build's line
+            line["search"] = {"error": f"{type(ex).__name__}: {ex}"}
     if rank == 0 and a.check_rows > 0:
         line["rng_row_check"] = check_rows(w.X, e_last.cpu().numpy(), a.check_rows, metric=metric)
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
@@ -588,6 +595,50 @@ def run_gpu(a, rank, world, local):
     if pg:
         pg.destroy_process_group()
     return 0
+
+
+def search_leg(g, wl, a, w, Xd, piv_d, prec, metric, mlp, stream, batches=5, m=1000, check=16):
+    """RNG search on an index of the build's workload (built untimed): `batches` batches of m
+    further points of the same generator, each timed with CUDA events; `check` queries of the
+    first batch compared with the FP64 oracle."""
+    import numpy as np
+    import torch
+    L = len(piv_d)
+    ix = g.Index(Xd, n_layers=L, stream=stream, precision=prec, metric=metric, **mlp)
+    for li in range(L - 1, -1, -1):
+        ix.build_layer(li, piv_d[li], outputs=False)
+    for li in range(L):
+        ix.link_pivots(li, want_adjacency=False)
+    ds = wl.SPECS[a.kind][3]
+    Q = wl.gen_points(a.kind, w.n + batches * m, ds)[w.n:]
+    Qd = torch.from_numpy(Q).cuda()
+    ix.rng_search_batch(Qd[:64])  # the cached index rows and block keys
+    lat, first = [], None
+    for b in range(batches):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ix.rng_search_batch(Qd[b * m:(b + 1) * m])
+        e1.record(stream)
+        torch.cuda.synchronize()
+        lat.append(e0.elapsed_time(e1))
+        if b == 0:
+            first = ix.rng_search_result()
+    st = ix.stats()["search"]
+    ix.close()
+    out = {"metric": "RNG search queries/s", "value": batches * m / (sum(lat) / 1000.0), "unit": "queries/s",
+           "batches": batches, "queries_per_batch": m, "p50_ms": float(np.percentile(lat, 50)),
+           "neighbours_per_query": st["neighbours"] / max(st["queries"], 1)}
+    if check:  # the CPU baseline of the search: the FP64 oracle on the first queries, its answers compared
+        import oracle
+        off, nb = first
+        t0 = time.perf_counter()
+        want = oracle.rng_search(w.X, Q[:check], metric)
+        cs = time.perf_counter() - t0
+        out["cpu_baseline"] = {"value": check / cs, "unit": "queries/s", "cores": oracle.max_threads(),
+                               "kind": "oracle", "sample": f"{check} queries against all {w.n:,} index points"}
+        out["oracle_check"] = {"queries": check, "mismatches": int(sum(
+            0 if np.array_equal(nb[off[j]:off[j + 1]], want[j]) else 1 for j in range(check)))}
+    return out
 
 
 def run_insert(a, rank):
