@@ -55,3 +55,20 @@ def test_learned_entry_points_host_checks():
     assert L.grng_mlp_train(None, None, None, 0, 1, 1, ctypes.c_float(1e-3), None, None) == g.GRNG_EINVAL
     assert L.grng_mlp_dataset(None, None, None, 0, None) == g.GRNG_EINVAL
     assert b"must" in L.grng_last_error() or b"NULL" in L.grng_last_error()
+
+
+def test_search_and_skeleton_entry_points_host_checks():
+    """The search and skeleton entry points refuse a NULL index on the host, before any device
+    work (so this runs without a GPU)."""
+    import ctypes
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2208_10022_gb300 as g
+    L = g.lib()
+    tot = ctypes.c_int64(-1)
+    assert L.rng_search_batch(None, None, 1, ctypes.byref(tot)) == g.GRNG_EINVAL
+    assert tot.value == -1
+    assert L.rng_search_result(None, None, None, 0) == g.GRNG_EINVAL
+    assert L.rng_build_skeleton(None, ctypes.c_double(1.0)) == g.GRNG_EINVAL
+    assert b"NULL" in L.grng_last_error()
