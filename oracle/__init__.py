@@ -53,6 +53,8 @@ def lib():
         if hasattr(_lib, "orc_rng_guided"):  # absent from single-file builds of the pin tests
             _lib.orc_rng_guided.restype = i64
             _lib.orc_rng_guided.argtypes = [P, i64, i32, i32, P, P, i32, P, i64, P]
+            _lib.orc_candidates_rules.restype = i32
+            _lib.orc_candidates_rules.argtypes = [P, i64, i32, i32, P, i32, ctypes.c_double, i32, P, P, P]
         _lib.orc_emst.restype = i64
         _lib.orc_emst.argtypes = [P, i64, i32, i32, P]
         _lib.orc_grng_brute.restype = i64
@@ -195,6 +197,31 @@ def rng_guided(X, layers, metric=L2, with_stats=False):
     cnt2 = lib().orc_rng_guided(*args, _p(out), cnt, _p(st))
     assert cnt2 == cnt
     return (out[:cnt], tuple(int(v) for v in st)) if with_stats else out[:cnt]
+
+
+def candidate_rules(X, piv, r, metric=L2, want_sets=False, promote=False):
+    """Stage I candidate pairs of one pivot layer under the nearest-pivot rule with per-pivot
+    radii (A) and under the uniform radius r with every pivot within r a parent (B), each with
+    its own GRNG (Sec. 2, Theorem 1); promote makes every point with no pivot within r a pivot
+    under B first.  {"a": count, "b": count, "no_parent": points, "memberships": parent links
+    under B, "pivots_b": B's pivots, "a_on_b_pivots": rule A's count on B's pivots}; with want_sets
+    also the candidate sets of pairs i < j."""
+    X = _f32(X)
+    piv = np.ascontiguousarray(piv, dtype=np.int32)
+    n = X.shape[0]
+    st = np.zeros(6, np.int64)
+    ca = np.zeros((n, n), np.uint8) if want_sets else None
+    cb = np.zeros((n, n), np.uint8) if want_sets else None
+    rc = lib().orc_candidates_rules(_p(X), n, X.shape[1], metric, _p(piv), len(piv), float(r), int(promote),
+                                    _p(ca) if want_sets else None, _p(cb) if want_sets else None, _p(st))
+    if rc != 0:
+        raise MemoryError("oracle allocation failed")
+    out = {"a": int(st[0]), "b": int(st[1]), "no_parent": int(st[2]), "memberships": int(st[3]),
+           "pivots_b": int(st[4]), "a_on_b_pivots": int(st[5])}
+    if want_sets:
+        out["set_a"] = {(int(i), int(j)) for i, j in zip(*np.nonzero(np.triu(ca, 1)))}
+        out["set_b"] = {(int(i), int(j)) for i, j in zip(*np.nonzero(np.triu(cb, 1)))}
+    return out
 
 
 def verify_witness(X, x, y, z, metric=L2):

@@ -305,3 +305,125 @@ int64_t orc_rng_guided(const float *X, int64_t n, int32_t D, int32_t metric, con
     free(Ls);
     return cnt;
 }
+
+/* ---- Stage I candidates under two membership rules (Sec. 2) --------------------------
+ * One pivot layer piv[m] over the points X[n].  Rule A (this project's, readings 4-5): every
+ * point joins its nearest pivot, whose radius is the largest member distance (Eq. 2).
+ * Rule B (the paper's uniform radius): every pivot within distance r of a point is a parent of
+ * it, all radii are r.  Each rule's GRNG is the definition over all pivot pairs, with the
+ * guidance margin.  Theorem 1 holds for every parent pair, so under rule B a pair (x, y) stays
+ * a candidate only when each parent of x and each parent of y are equal or linked; a point
+ * without a parent restricts nothing.  With promote = 1, rule B first makes every point that
+ * has no pivot within r a pivot itself, in index order (a new point with no parent becomes a
+ * pivot, Sec. 2), so that every point has a parent.
+ * cand_a / cand_b (n*n bytes each, may be NULL) receive the candidate flags of the pairs i < j
+ * at [i*n + j].  stats (may be NULL): [0] candidates under A, [1] under B, [2] points without a
+ * parent under B, [3] parent memberships under B (sum over the points), [4] pivots under B,
+ * [5] candidates under rule A on B's pivots (the two rules at equal pivot sets).
+ * Returns 0, -1 on allocation failure. */
+int32_t orc_candidates_rules(const float *X, int64_t n, int32_t D, int32_t metric, const int32_t *piv0,
+                             int32_t m0, double r, int32_t promote, unsigned char *cand_a, unsigned char *cand_b,
+                             int64_t *stats) {
+    if (m0 < 1) return -1;
+    /* rule B's pivots: the given ones, then (promote) every point not covered by them yet */
+    int32_t *pivb = (int32_t *)malloc(sizeof(int32_t) * (size_t)(m0 + (n > 0 ? n : 1)));
+    if (!pivb) return -1;
+    memcpy(pivb, piv0, sizeof(int32_t) * (size_t)m0);
+    int32_t mb = m0;
+    if (promote)
+        for (int64_t x = 0; x < n; ++x) {
+            int covered = 0;
+            for (int32_t p = 0; p < mb && !covered; ++p)
+                covered = g_dist_of(g_key(X + x * D, X + (int64_t)pivb[p] * D, D, metric), metric) <= r;
+            if (!covered) pivb[mb++] = (int32_t)x;
+        }
+    const int32_t *piv = piv0;
+    const int32_t m = m0;
+    g_layer A, B;
+    memset(&A, 0, sizeof(A));
+    memset(&B, 0, sizeof(B));
+    A.m = m;
+    A.piv = piv;
+    B.m = mb;
+    B.piv = pivb;
+    int32_t *members = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+    A.assign = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+    A.mdist = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    A.radius = (double *)malloc(sizeof(double) * (size_t)m);
+    A.dmax = (double *)malloc(sizeof(double) * (size_t)m);
+    B.radius = (double *)malloc(sizeof(double) * (size_t)mb);
+    B.dmax = (double *)malloc(sizeof(double) * (size_t)mb);
+    int32_t *pcnt = (int32_t *)calloc((size_t)(n > 0 ? n : 1), sizeof(int32_t));
+    int32_t *plist = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1) * (size_t)mb);
+    if (!members || !A.assign || !A.mdist || !A.radius || !A.dmax || !B.radius || !B.dmax || !pcnt || !plist) {
+        free(members); free(A.assign); free(A.mdist); free(A.radius); free(A.dmax); free(B.radius);
+        free(B.dmax); free(pcnt); free(plist); free(pivb);
+        return -1;
+    }
+    for (int64_t t = 0; t < n; ++t) members[t] = (int32_t)t;
+    int64_t nd = 0;
+    g_assign(X, D, metric, members, n, NULL, &A, &nd);  /* rule A: nearest pivot, own radius */
+    g_link(X, D, metric, &A, NULL, NULL, &nd);
+    for (int32_t p = 0; p < mb; ++p) B.radius[p] = B.dmax[p] = r;
+    g_link(X, D, metric, &B, NULL, NULL, &nd);          /* rule B: every radius r */
+    int64_t memberships = 0, orphans = 0;
+    for (int64_t x = 0; x < n; ++x) {                    /* rule B parents: every pivot within r */
+        for (int32_t p = 0; p < mb; ++p)
+            if (g_dist_of(g_key(X + x * D, X + (int64_t)pivb[p] * D, D, metric), metric) <= r)
+                plist[x * mb + pcnt[x]++] = p;
+        memberships += pcnt[x];
+        orphans += pcnt[x] == 0;
+    }
+    int64_t ca = 0, cb = 0;
+#pragma omp parallel for schedule(dynamic, 16) reduction(+ : ca, cb)
+    for (int64_t i = 0; i < n; ++i) {
+        for (int64_t j = i + 1; j < n; ++j) {
+            int32_t a = A.assign[i], b = A.assign[j];
+            int in_a = a == b || A.gg[(int64_t)(a < b ? a : b) * m + (a < b ? b : a)];
+            int in_b = 1;
+            for (int32_t s = 0; s < pcnt[i] && in_b; ++s)
+                for (int32_t t = 0; t < pcnt[j] && in_b; ++t) {
+                    int32_t p = plist[i * mb + s], q = plist[j * mb + t];
+                    if (p != q && !B.gg[(int64_t)(p < q ? p : q) * mb + (p < q ? q : p)]) in_b = 0;
+                }
+            ca += in_a;
+            cb += in_b;
+            if (cand_a) cand_a[i * n + j] = (unsigned char)in_a;
+            if (cand_b) cand_b[i * n + j] = (unsigned char)in_b;
+        }
+    }
+    /* rule A again, on B's pivots */
+    int64_t ca2 = ca;
+    if (mb != m) {
+        g_layer A2;
+        memset(&A2, 0, sizeof(A2));
+        A2.m = mb;
+        A2.piv = pivb;
+        A2.assign = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+        A2.mdist = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+        A2.radius = (double *)malloc(sizeof(double) * (size_t)mb);
+        A2.dmax = (double *)malloc(sizeof(double) * (size_t)mb);
+        if (!A2.assign || !A2.mdist || !A2.radius || !A2.dmax) {
+            ca2 = -1;
+        } else {
+            g_assign(X, D, metric, members, n, NULL, &A2, &nd);
+            g_link(X, D, metric, &A2, NULL, NULL, &nd);
+            ca2 = 0;
+#pragma omp parallel for schedule(dynamic, 16) reduction(+ : ca2)
+            for (int64_t i = 0; i < n; ++i)
+                for (int64_t j = i + 1; j < n; ++j) {
+                    int32_t a = A2.assign[i], b = A2.assign[j];
+                    ca2 += a == b || A2.gg[(int64_t)(a < b ? a : b) * mb + (a < b ? b : a)];
+                }
+        }
+        free(A2.assign); free(A2.mdist); free(A2.radius); free(A2.dmax); free(A2.coff); free(A2.cidx);
+        free(A2.gx); free(A2.gg);
+    }
+    if (stats) {
+        stats[0] = ca; stats[1] = cb; stats[2] = orphans; stats[3] = memberships; stats[4] = mb; stats[5] = ca2;
+    }
+    free(members); free(A.assign); free(A.mdist); free(A.radius); free(A.dmax); free(A.coff); free(A.cidx);
+    free(A.gx); free(A.gg); free(B.radius); free(B.dmax); free(B.gx); free(B.gg); free(pcnt); free(plist);
+    free(pivb);
+    return 0;
+}

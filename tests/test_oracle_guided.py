@@ -36,3 +36,40 @@ def test_guided_ties_duplicates_and_layer_counts():
         top = np.sort(rng.choice(mid, 3, replace=False)).astype(np.int32)
         for layers in ([fine], [mid, fine], [top, mid, fine]):
             assert _eq(oracle.rng_guided(X, layers, metric), want), (metric, len(layers))
+
+
+def test_candidate_rules_sound_and_restated():
+    """Stage I candidates under the nearest-pivot rule (per-pivot radii) and under the paper's
+    uniform radius with every pivot within r a parent: both keep every RNG edge (Theorem 1),
+    and each candidate set equals its restatement through the definitions' oracle functions
+    (assignment, GRNG by its definition)."""
+    import numpy as np
+
+    import oracle
+    rng = np.random.default_rng(41)
+    for t in range(6):
+        n = int(rng.integers(40, 110))
+        d = int(rng.integers(2, 5))
+        X = rng.standard_normal((n, d)).astype(np.float32)
+        piv = np.sort(rng.choice(n, int(rng.integers(4, 12)), replace=False)).astype(np.int32)
+        for metric in (oracle.L2, oracle.L1):
+            dist = np.array([[oracle.dist(X[i], X[p], metric) for p in piv] for i in range(n)])
+            promote = t % 2 == 1
+            r = float(dist.min(1).max()) * (0.6 if promote else 1.0)
+            res = oracle.candidate_rules(X, piv, r, metric, want_sets=True, promote=promote)
+            E = {tuple(e) for e in oracle.rng_brute(X, metric).tolist()}
+            assert E <= res["set_a"] and E <= res["set_b"], (t, metric)
+            a, _, rad, _ = oracle.assign(X, np.arange(n), piv, metric=metric)
+            G = {tuple(e) for e in oracle.grng_brute(X[piv], rad, metric).tolist()}
+            want_a = {(i, j) for i in range(n) for j in range(i + 1, n)
+                      if a[i] == a[j] or (min(a[i], a[j]), max(a[i], a[j])) in G}
+            assert res["set_a"] == want_a, (t, metric)
+            if not promote:
+                assert res["no_parent"] == 0 and res["pivots_b"] == len(piv)
+                GB = {tuple(e) for e in oracle.grng_brute(X[piv], np.full(len(piv), r), metric).tolist()}
+                par = [[p for p in range(len(piv)) if dist[i, p] <= r] for i in range(n)]
+                want_b = {(i, j) for i in range(n) for j in range(i + 1, n)
+                          if all(p == q or (min(p, q), max(p, q)) in GB for p in par[i] for q in par[j])}
+                assert res["set_b"] == want_b, (t, metric)
+            else:
+                assert res["no_parent"] == 0 and res["pivots_b"] >= len(piv)
