@@ -19,6 +19,10 @@
 //    edge reaches q are visited (the per-point maximum of Prop. 6), and each of their edges
 //    is tested, in FP32 with the error bound and in canonical FP64 where the bound cannot
 //    decide.
+//
+// RNG search (Algorithm 1 without Stage VII) shares the file: query rows are swept against
+// every index point as batch rows are, but a query is not a point of the index, so no row
+// ever blocks another row's pair and nothing of the index changes.
 #include <algorithm>
 #include <cstring>
 #include <vector>
