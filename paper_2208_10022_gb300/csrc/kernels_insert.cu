@@ -868,7 +868,12 @@ void search_sweep(const SearchSweep& S, DevBuf& surv, int64_t* nsurv, float* knn
   GRNG_CUDA(ck.alloc((size_t)strips * 128 * 2 * nchunks * S.K * 4));
   GRNG_CUDA(ci.alloc((size_t)strips * 128 * 2 * nchunks * S.K * 4));
   GRNG_CUDA(ctr.alloc(4 * 8));
-  unsigned long long scap = S.small_buffers ? 64ull : std::max<unsigned long long>(1 << 20, (unsigned long long)S.mq * 16384);
+  // about 9,000 pairs per query leave tier 1 at intrinsic dimension 8; a first buffer of up to
+  // 2^28 pairs (2 GB), and a larger batch that needs more is swept again with the exact size
+  unsigned long long scap = S.small_buffers
+                                ? 64ull
+                                : std::min<unsigned long long>(
+                                      1ull << 28, std::max<unsigned long long>(1 << 20, (unsigned long long)S.mq * 16384));
   for (int attempt = 0;; ++attempt) {
     GRNG_CUDA(surv.alloc(scap * sizeof(int2)));
     GRNG_CUDA(cudaMemsetAsync(ctr.p, 0, 4 * 8, s));
