@@ -42,6 +42,8 @@ def lib():
         _lib.orc_rng_rows.argtypes = [P, i64, i32, i32, P, i64, P, i64, P]
         _lib.orc_rng_search.restype = i32
         _lib.orc_beta_brute.restype = i64
+        _lib.orc_grng_insert_pivot.restype = i32
+        _lib.orc_grng_insert_pivot.argtypes = [P, P, i64, i32, i32, P, P, P]
         _lib.orc_beta_brute.argtypes = [P, i64, i32, ctypes.c_double, P, i64]
         _lib.orc_rng_search.argtypes = [P, i64, P, i64, i32, i32, P, i64, P]
         _lib.orc_verify_witness.restype = i32
@@ -257,6 +259,24 @@ def grng_row(P, r, i, metric=L2):
     if cnt < 0:
         raise MemoryError("oracle allocation failed")
     return out[:cnt]
+
+
+def grng_insert_pivot(P, r, edges, metric=L2):
+    """GRNG after a new pivot joins (Stage VII): P[m+1, D] with the new pivot last, r[m+1],
+    edges = the GRNG of the first m (pairs i < j).  Returns (sorted edges [E, 2] of all m+1,
+    (old links tested, old links removed, links of the new pivot))."""
+    P = _f32(P)
+    r = np.ascontiguousarray(r, dtype=np.float64)
+    m = P.shape[0] - 1
+    links = np.zeros((max(m, 1), max(m, 1)), np.uint8)
+    for i, j in np.asarray(edges, dtype=np.int64).reshape(-1, 2):
+        links[min(i, j), max(i, j)] = 1
+    out = np.zeros((m + 1, m + 1), np.uint8)
+    st = np.zeros(3, np.int64)
+    if lib().orc_grng_insert_pivot(_p(P), _p(r), m, P.shape[1], metric, _p(links), _p(out), _p(st)) != 0:
+        raise MemoryError("oracle allocation failed")
+    E = np.argwhere(np.triu(out, 1)).astype(np.int32)
+    return E, tuple(int(v) for v in st)
 
 
 def assign(X, members, pivots, member_r=None, metric=L2):

@@ -380,6 +380,71 @@ static int g_blocks(double dij, double dki, double dkj, double kij, double kki,
     return (dki < t1) && (dkj < t2);
 }
 
+/* ---- GRNG Stage VII: a new pivot joins a layer (Sec. 3, the GRNG's Stage VII) --------
+ * P[m+1][D] holds the layer's pivots with the new one last, r[m+1] their radii, links[m*m]
+ * the GRNG of the first m ([i*m + j], i < j).  Writes out[(m+1)*(m+1)] ([i*(m+1) + j], i < j),
+ * the GRNG of all m+1: an old link survives unless the new pivot lies in its generalized lune
+ * (a non-link stays one: the new pivot only adds interceptors), and the new pivot's own links
+ * are decided over all m+1 pivots.  The new pivot k can block a link (i, j) only when
+ * d(k, i) < d(i, j) - (2 r_i + r_j) <= mu_i - 2 r_i, mu_i the longest link at p_i (and likewise
+ * at j), so a link is tested only when both ends lie that close to k.  stats (may be NULL):
+ * [0] old links tested, [1] old links removed, [2] links of the new pivot.  Returns 0 or -1. */
+int32_t orc_grng_insert_pivot(const float *P, const double *r, int64_t m, int32_t D, int32_t metric,
+                              const unsigned char *links, unsigned char *out, int64_t *stats) {
+    const int64_t m1 = m + 1;
+    const float *pk = P + m * D;
+    double *mu = (double *)calloc((size_t)(m > 0 ? m : 1), sizeof(double));
+    double *dk = (double *)malloc(sizeof(double) * (size_t)(m > 0 ? m : 1));
+    double *kk = (double *)malloc(sizeof(double) * (size_t)(m > 0 ? m : 1));
+    if (!mu || !dk || !kk) { free(mu); free(dk); free(kk); return -1; }
+    for (int64_t i = 0; i < m; ++i) {
+        kk[i] = orc_key(pk, P + i * D, D, metric);
+        dk[i] = metric == ORC_L2 ? sqrt(kk[i]) : kk[i];
+    }
+    for (int64_t i = 0; i < m; ++i)  /* longest link at each old pivot */
+        for (int64_t j = i + 1; j < m; ++j)
+            if (links[i * m + j]) {
+                double d = orc_dist(P + i * D, P + j * D, D, metric);
+                if (d > mu[i]) mu[i] = d;
+                if (d > mu[j]) mu[j] = d;
+            }
+    int64_t tested = 0, removed = 0, added = 0;
+    memset(out, 0, (size_t)m1 * (size_t)m1);
+    for (int64_t i = 0; i < m; ++i)
+        for (int64_t j = i + 1; j < m; ++j) {
+            if (!links[i * m + j]) continue;
+            int keep = 1;
+            /* reachable from k at both ends (with a margin far above the FP64 rounding) */
+            double ri = r[i], rj = r[j];
+            double bi = mu[i] - 2.0 * ri, bj = mu[j] - 2.0 * rj;
+            int near_i = dk[i] < bi + 1e-9 * (dk[i] + mu[i] + 2.0 * ri);
+            int near_j = dk[j] < bj + 1e-9 * (dk[j] + mu[j] + 2.0 * rj);
+            if (near_i && near_j) {
+                ++tested;
+                double kij = orc_key(P + i * D, P + j * D, D, metric);
+                double dij = metric == ORC_L2 ? sqrt(kij) : kij;
+                if (g_blocks(dij, dk[i], dk[j], kij, kk[i], kk[j], ri, rj)) { keep = 0; ++removed; }
+            }
+            out[i * m1 + j] = (unsigned char)keep;
+        }
+    for (int64_t i = 0; i < m; ++i) {  /* the new pivot's links, by the definition */
+        double kij = kk[i], dij = dk[i];
+        int blocked = 0;
+        for (int64_t q = 0; q < m && !blocked; ++q) {
+            if (q == i) continue;
+            double kqi = orc_key(P + q * D, P + i * D, D, metric);
+            double kqk = orc_key(P + q * D, pk, D, metric);
+            double dqi = metric == ORC_L2 ? sqrt(kqi) : kqi, dqk = metric == ORC_L2 ? sqrt(kqk) : kqk;
+            blocked = g_blocks(dij, dqi, dqk, kij, kqi, kqk, r[i], r[m]);
+        }
+        out[i * m1 + m] = (unsigned char)!blocked;
+        added += !blocked;
+    }
+    if (stats) { stats[0] = tested; stats[1] = removed; stats[2] = added; }
+    free(mu); free(dk); free(kk);
+    return 0;
+}
+
 /* Brute GRNG over m pivots given by their coordinates P[m][D] and radii r[m].
  * Edges i<j in lexicographic order; returns count (may exceed cap) or -1. */
 int64_t orc_grng_brute(const float *P, const double *r, int64_t m, int32_t D,

@@ -23,6 +23,8 @@ What pins what:
   skeletons                -- beta-skeletons (1 <= beta <= 2) against the exact rational
                               predicate, beta = 1 against the Gabriel graph from the
                               midpoint, beta = 2 against the RNG, and nesting in beta
+  pivot_insertion          -- the GRNG after a new pivot joins (its Stage VII) against the
+                              definition's GRNG of all pivots
   search                   -- RNG search (Algorithm 1 without Stage VII) against the exact
                               rational restatement, against the brute-force RNG of the
                               index plus that one query, and batch = one query at a time
@@ -344,5 +346,25 @@ def skeletons(orc, trials=30, seed=19):
         assert len(E[0]) > len(E[-1])
 
 
+def pivot_insertion(orc, trials=12, seed=20):
+    """Stage VII of the GRNG: the links after a new pivot joins equal the definition's GRNG of
+    all pivots, for dyadic and zero radii, both metrics."""
+    rng = np.random.default_rng(seed)
+    pruned = 0
+    for t in range(trials):
+        m = int(rng.integers(6, 40))
+        d = int(rng.integers(1, 4))
+        P = rng.standard_normal((m + 1, d)).astype(np.float32)
+        r = rng.integers(0, 3, size=m + 1) / 16.0 if t % 3 else np.zeros(m + 1)
+        for metric in (exact.L2, exact.L1):
+            old = orc.grng_brute(P[:m], r[:m], metric)
+            got, (tested, removed, added) = orc.grng_insert_pivot(P, r, old, metric)
+            want = _as_set(orc.grng_brute(P, r, metric))
+            assert _as_set(got) == want, (t, metric)
+            assert removed == len(_as_set(old) - want) and added == sum(1 for e in want if e[1] == m)
+            pruned += len(old) - tested
+    assert pruned > 0  # the longest-link bound skips some links
+
+
 ALL = [exact_rng, exact_grng, worked_examples, invariants, theorems, cross_checks, layer_examples, witnesses,
-       spanning_trees, search, skeletons]
+       spanning_trees, search, skeletons, pivot_insertion]

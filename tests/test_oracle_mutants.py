@@ -39,6 +39,9 @@ MUTANTS = {
     "beta_one_ball": ("if (in1 < t && in2 < t) blocked = 1;", "if (in1 < t) blocked = 1;"),
     "beta_swapped_weights": ("double in1 = mu * a + lam * b;", "double in1 = lam * a + mu * b;"),
     "beta_radius_not_scaled": ("double t = lam * v;", "double t = v;"),
+    "insert_pivot_no_removal": ("{ keep = 0; ++removed; }", "{ ++removed; }"),
+    "insert_pivot_prune_too_far": ("double bi = mu[i] - 2.0 * ri, bj = mu[j] - 2.0 * rj;",
+                                   "double bi = mu[i] - 3.0 * ri - 0.3 * mu[i], bj = mu[j] - 3.0 * rj - 0.3 * mu[j];"),
     "emst_wrong_endpoint": ("edges[2 * (e - 1)] = (int32_t)from[u];",
                             "edges[2 * (e - 1)] = (int32_t)(u > 0 ? u - 1 : 1);"),
 }
