@@ -56,6 +56,8 @@ def lib():
             _lib.orc_rng_guided.restype = i64
             _lib.orc_rng_guided.argtypes = [P, i64, i32, i32, P, P, i32, P, i64, P]
             _lib.orc_candidates_rules.restype = i32
+            _lib.orc_rng_search_guided.restype = i32
+            _lib.orc_rng_search_guided.argtypes = [P, i64, i32, i32, P, i32, P, i64, P, i64, P, P]
             _lib.orc_candidates_rules.argtypes = [P, i64, i32, i32, P, i32, ctypes.c_double, i32, P, P, P]
         _lib.orc_emst.restype = i64
         _lib.orc_emst.argtypes = [P, i64, i32, i32, P]
@@ -199,6 +201,28 @@ def rng_guided(X, layers, metric=L2, with_stats=False):
     cnt2 = lib().orc_rng_guided(*args, _p(out), cnt, _p(st))
     assert cnt2 == cnt
     return (out[:cnt], tuple(int(v) for v in st)) if with_stats else out[:cnt]
+
+
+def rng_search_guided(X, piv, Q, metric=L2, row_cap=4096):
+    """RNG search by the paper's Stages I-VI over one pivot layer (Algorithm 1 without Stage
+    VII): (list of ascending int32 neighbour arrays per query, {"distances": computations,
+    "after_stage1"/"after_stage2"/"after_stage3": exemplars left, summed over the queries})."""
+    X = _f32(X)
+    Q = _f32(Q)
+    piv = np.ascontiguousarray(piv, dtype=np.int32)
+    m = Q.shape[0]
+    nb = np.zeros((max(m, 1), row_cap), np.int32)
+    cnt = np.zeros(max(m, 1), np.int64)
+    st = np.zeros(4, np.int64)
+    rc = lib().orc_rng_search_guided(_p(X), X.shape[0], X.shape[1], metric, _p(piv), len(piv), _p(Q), m,
+                                     _p(nb), row_cap, _p(cnt), _p(st))
+    if rc != 0:
+        raise MemoryError("oracle allocation failed")
+    if m and cnt.max() > row_cap:
+        raise ValueError("a neighbourhood exceeds row_cap")
+    return ([nb[t, :cnt[t]].copy() for t in range(m)],
+            {"distances": int(st[0]), "after_stage1": int(st[1]), "after_stage2": int(st[2]),
+             "after_stage3": int(st[3])})
 
 
 def candidate_rules(X, piv, r, metric=L2, want_sets=False, promote=False):

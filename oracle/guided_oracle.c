@@ -427,3 +427,166 @@ int32_t orc_candidates_rules(const float *X, int64_t n, int32_t D, int32_t metri
     free(pivb);
     return 0;
 }
+
+/* ---- RNG search by the paper's stages (Algorithm 1 without Stage VII, Sec. 2) -----------
+ * One pivot layer piv[m] over the index X[n] (each point joins its nearest pivot, whose radius
+ * is its largest member distance), its GRNG with the guidance margin, then for each query q of
+ * Q[mq] (q joins nothing; only index points block):
+ *   Stage I:   q's parents are the pivots whose ball holds q; a pivot stays only if it equals or
+ *              is linked to every parent (Theorem 1); with no parent every pivot stays.
+ *   Stage II:  q as a virtual zero-radius pivot: the domain of p_j is dropped when some pivot
+ *              p_k has d(q,p_k) < d(q,p_j) - r_j and d(p_j,p_k) < d(q,p_j) - 2 r_j.
+ *   Stage III: an exemplar x of a surviving domain p_j as a virtual zero-radius pivot against a
+ *              parent p_i of q: x is dropped when some pivot p_k has d(p_k,p_i) < d(p_i,x) - 2 r_i
+ *              and d(p_k,x) < d(p_i,x) - r_i, the latter through d(p_k,x) <= d(p_k,p_j) + d(x,p_j).
+ *   Stages IV-VI: for each remaining x, the pivots in increasing d(q,p) as interceptors, then
+ *              their members unless Prop. 4 excludes the domain, until no domain can hold a
+ *              point closer to q than x.
+ * Every pruning is taken with the relative margin of the construction above; every decision on
+ * a triple is the canonical key comparison.  Query t's neighbours (ascending) go to
+ * nbrs[t * row_cap ...], their count to cnt[t].  stats (may be NULL): [0] distance computations
+ * (query-pivot, query-point, point-point; the layer's own are not counted), [1] exemplars left
+ * after Stage I, [2] after Stage II, [3] after Stage III.  Returns 0, -1 on allocation failure. */
+int32_t orc_rng_search_guided(const float *X, int64_t n, int32_t D, int32_t metric, const int32_t *piv, int32_t m,
+                              const float *Q, int64_t mq, int32_t *nbrs, int64_t row_cap, int64_t *cnt,
+                              int64_t *stats) {
+    if (m < 1 || n < 1) return -1;
+    g_layer F;
+    memset(&F, 0, sizeof(F));
+    F.m = m;
+    F.piv = piv;
+    int32_t *members = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    F.assign = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    F.mdist = (double *)malloc(sizeof(double) * (size_t)n);
+    F.radius = (double *)malloc(sizeof(double) * (size_t)m);
+    F.dmax = (double *)malloc(sizeof(double) * (size_t)m);
+    double *Dpp = (double *)malloc(sizeof(double) * (size_t)m * (size_t)m);
+    if (!members || !F.assign || !F.mdist || !F.radius || !F.dmax || !Dpp) {
+        free(members); free(F.assign); free(F.mdist); free(F.radius); free(F.dmax); free(Dpp);
+        return -1;
+    }
+    for (int64_t t = 0; t < n; ++t) members[t] = (int32_t)t;
+    int64_t nd0 = 0;
+    g_assign(X, D, metric, members, n, NULL, &F, &nd0);
+    g_link(X, D, metric, &F, NULL, NULL, &nd0);
+#pragma omp parallel for schedule(dynamic, 8)
+    for (int32_t i = 0; i < m; ++i)
+        for (int32_t k = 0; k < m; ++k)
+            Dpp[(int64_t)i * m + k] = g_dist_of(g_key(X + (int64_t)piv[i] * D, X + (int64_t)piv[k] * D, D, metric), metric);
+    double dmax_all = 0.0;
+    for (int32_t p = 0; p < m; ++p) if (F.dmax[p] > dmax_all) dmax_all = F.dmax[p];
+    int64_t sd = 0, s1 = 0, s2 = 0, s3 = 0;
+    int failed = 0;
+#pragma omp parallel reduction(+ : sd, s1, s2, s3)
+    {
+        g_dp *order = (g_dp *)malloc(sizeof(g_dp) * (size_t)m);
+        double *dq = (double *)malloc(sizeof(double) * (size_t)m);
+        double *kqz = (double *)malloc(sizeof(double) * (size_t)n);  /* cached keys of q to points */
+        unsigned char *keep = (unsigned char *)malloc((size_t)m);
+        unsigned char *isn = (unsigned char *)malloc((size_t)n);
+        int32_t *par = (int32_t *)malloc(sizeof(int32_t) * (size_t)m);
+        if (!order || !dq || !kqz || !keep || !isn || !par) {
+#pragma omp atomic write
+            failed = 1;
+        }
+#pragma omp for schedule(dynamic, 1)
+        for (int64_t t = 0; t < mq; ++t) {
+            if (!order || !dq || !kqz || !keep || !isn || !par) continue;
+            const float *q = Q + t * D;
+            for (int64_t z = 0; z < n; ++z) { kqz[z] = -1.0; isn[z] = 0; }
+            for (int32_t p = 0; p < m; ++p) {
+                dq[p] = g_dist_of(g_key(q, X + (int64_t)piv[p] * D, D, metric), metric);
+                order[p].d = dq[p];
+                order[p].p = p;
+            }
+            sd += m;
+            qsort(order, (size_t)m, sizeof(g_dp), g_dp_cmp);
+            int32_t np = 0;
+            for (int32_t p = 0; p < m; ++p) if (dq[p] <= F.radius[p]) par[np++] = p;
+            /* Stage I */
+            for (int32_t j = 0; j < m; ++j) {
+                int ok = 1;
+                for (int32_t s = 0; s < np && ok; ++s) {
+                    const int32_t i = par[s];
+                    if (i != j && !F.gg[(int64_t)(i < j ? i : j) * m + (i < j ? j : i)]) ok = 0;
+                }
+                keep[j] = (unsigned char)ok;
+                if (ok) s1 += F.coff[j + 1] - F.coff[j];
+            }
+            /* Stage II */
+            for (int32_t j = 0; j < m; ++j) {
+                if (!keep[j]) continue;
+                const double a1 = dq[j] - F.radius[j], a2 = dq[j] - 2.0 * F.radius[j];
+                for (int32_t k = 0; k < m; ++k) {
+                    if (k == j) continue;
+                    const double b = Dpp[(int64_t)j * m + k];
+                    if (dq[k] < a1 - G_MARGIN * (dq[k] + fabs(a1) + dq[j]) &&
+                        b < a2 - G_MARGIN * (b + fabs(a2) + dq[j])) { keep[j] = 0; break; }
+                }
+                if (keep[j]) s2 += F.coff[j + 1] - F.coff[j];
+            }
+            /* Stage III, then Stages IV-VI for what is left */
+            for (int32_t j = 0; j < m; ++j) {
+                if (!keep[j]) continue;
+                for (int32_t u = F.coff[j]; u < F.coff[j + 1]; ++u) {
+                    const int64_t x = F.cidx[u];
+                    const float *px = X + x * D;
+                    int dropped = 0;
+                    for (int32_t s = 0; s < np && !dropped; ++s) {
+                        const int32_t i = par[s];
+                        const double dpx = g_dist_of(g_key(X + (int64_t)piv[i] * D, px, D, metric), metric);
+                        ++sd;
+                        const double c1 = dpx - 2.0 * F.radius[i], c2 = dpx - F.radius[i];
+                        for (int32_t k = 0; k < m && !dropped; ++k) {
+                            const double e1 = Dpp[(int64_t)k * m + i];
+                            const double e2 = Dpp[(int64_t)k * m + j] + F.mdist[x];  /* >= d(p_k, x) */
+                            if (e1 < c1 - G_MARGIN * (e1 + fabs(c1) + dpx) && e2 < c2 - G_MARGIN * (e2 + fabs(c2) + dpx))
+                                dropped = 1;
+                        }
+                    }
+                    if (dropped) continue;
+                    ++s3;
+                    if (kqz[x] < 0.0) { kqz[x] = g_key(q, px, D, metric); ++sd; }
+                    const double kqx = kqz[x], dqx = g_dist_of(kqx, metric);
+                    int blocked = 0;
+                    for (int32_t w = 0; w < m && !blocked; ++w) {
+                        const int32_t p = order[w].p;
+                        const double dqp = order[w].d, dm = F.dmax[p];
+                        if (dqp - dmax_all >= dqx + G_MARGIN * (dqp + dmax_all + dqx)) break;
+                        const int64_t pid = piv[p];
+                        double kxp = -1.0;
+                        if (pid != x) {  /* Stage IV: the pivot itself */
+                            if (kqz[pid] < 0.0) { kqz[pid] = g_key(q, X + pid * D, D, metric); ++sd; }
+                            kxp = g_key(px, X + pid * D, D, metric);
+                            ++sd;
+                            if (kqz[pid] < kqx && kxp < kqx) { blocked = 1; break; }
+                        }
+                        if (dqp - dm >= dqx + G_MARGIN * (dqp + dm + dqx)) continue;  /* Prop. 4 */
+                        if (kxp < 0.0) { kxp = g_key(px, X + pid * D, D, metric); ++sd; }
+                        const double dxp = g_dist_of(kxp, metric);
+                        if (dxp - dm >= dqx + G_MARGIN * (dxp + dm + dqx)) continue;
+                        for (int32_t v = F.coff[p]; v < F.coff[p + 1] && !blocked; ++v) {  /* Stage VI */
+                            const int64_t z = F.cidx[v];
+                            if (z == x || z == pid) continue;
+                            if (kqz[z] < 0.0) { kqz[z] = g_key(q, X + z * D, D, metric); ++sd; }
+                            if (!(kqz[z] < kqx)) continue;
+                            const double kxz = g_key(px, X + z * D, D, metric);
+                            ++sd;
+                            if (kxz < kqx) blocked = 1;  /* strictly inside the open lune */
+                        }
+                    }
+                    if (!blocked) isn[x] = 1;
+                }
+            }
+            int64_t c = 0;
+            for (int64_t x = 0; x < n; ++x)
+                if (isn[x]) { if (c < row_cap) nbrs[t * row_cap + c] = (int32_t)x; ++c; }
+            cnt[t] = c;
+        }
+        free(order); free(dq); free(kqz); free(keep); free(isn); free(par);
+    }
+    if (stats) { stats[0] = sd; stats[1] = s1; stats[2] = s2; stats[3] = s3; }
+    free(members); free(F.assign); free(F.mdist); free(F.radius); free(F.dmax); free(F.coff); free(F.cidx);
+    free(F.gx); free(F.gg); free(Dpp);
+    return failed ? -1 : 0;
+}

@@ -73,3 +73,29 @@ def test_candidate_rules_sound_and_restated():
                 assert res["set_b"] == want_b, (t, metric)
             else:
                 assert res["no_parent"] == 0 and res["pivots_b"] >= len(piv)
+
+
+def test_search_by_stages_equals_definition():
+    """RNG search by the paper's Stages I-VI (Theorem 1, the virtual-pivot prunes of Stages II
+    and III, pivots and members as interceptors) returns exactly the definition's neighbours,
+    on random points (L2, L1) and on small integers with ties and duplicates."""
+    import numpy as np
+
+    import oracle
+    rng = np.random.default_rng(43)
+    for t in range(8):
+        n = int(rng.integers(150, 500))
+        d = int(rng.integers(1, 5))
+        if t % 4 == 3:
+            X = rng.integers(0, 5, size=(n, d)).astype(np.float32)
+            Q = np.concatenate([rng.integers(0, 5, size=(20, d)), X[:3]]).astype(np.float32)
+        else:
+            X = rng.standard_normal((n, d)).astype(np.float32)
+            Q = np.concatenate([rng.standard_normal((20, d)) * 1.3, X[:3], X[:1] * 9.0]).astype(np.float32)
+        piv = np.sort(rng.choice(n, int(rng.integers(5, 40)), replace=False)).astype(np.int32)
+        for metric in (oracle.L2, oracle.L1):
+            got, st = oracle.rng_search_guided(X, piv, Q, metric)
+            want = oracle.rng_search(X, Q, metric)
+            bad = [j for j in range(len(Q)) if not np.array_equal(got[j], want[j])]
+            assert not bad, (t, metric, bad[:3])
+            assert st["after_stage3"] <= st["after_stage2"] <= st["after_stage1"] <= n * len(Q)
