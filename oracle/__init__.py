@@ -1,6 +1,7 @@
 """ctypes binding of the FP64 CPU oracle (test infrastructure only).
 
-Only the tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench.py``
+Only the tests, ``__graft_entry__.smoke()``, the CPU-baseline legs of ``bench.py`` and the
+oracle's own host studies (``python -m oracle.pivoting_study``, ``python -m oracle.search_study``)
 import this package.  The product library never does.
 """
 import ctypes
