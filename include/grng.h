@@ -168,8 +168,11 @@ grng_status rng_insert_batch(grng_index* idx, const float* pts, int64_t m);
  * layer must be built and linked (the finest GRNG restricts each query's candidates by
  * Theorem 1 when the query lies in its nearest finest pivot's ball).  *total (if not
  * NULL) receives the number of (query, neighbour) pairs; the result stays in the index
- * until the next search and is read with rng_search_result.  Errors: GRNG_EINVAL for
- * NULL queries, m < 1 or n + m >= 2^31; GRNG_ESTATE when a layer is not linked. */
+ * until the next search and is read with rng_search_result.  Between searches the index keeps
+ * its points in sorted order with room for the largest batch so far (n + m rows), their
+ * in-block keys and neighbour lists, and the rows' K-nearest lists (8 K bytes per row); they are
+ * rebuilt after an insertion.  Errors: GRNG_EINVAL for NULL queries, m < 1 or n + m >= 2^31;
+ * GRNG_ESTATE when a layer is not linked; GRNG_ENOMEM when the device memory runs out. */
 grng_status rng_search_batch(grng_index* idx, const float* queries, int64_t m, int64_t* total);
 
 /* The last search's result as CSR over the queries in input order: off[m+1] (int64) and
