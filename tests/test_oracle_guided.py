@@ -99,3 +99,19 @@ def test_search_by_stages_equals_definition():
             bad = [j for j in range(len(Q)) if not np.array_equal(got[j], want[j])]
             assert not bad, (t, metric, bad[:3])
             assert st["after_stage3"] <= st["after_stage2"] <= st["after_stage1"] <= n * len(Q)
+
+
+def test_search_by_stages_on_the_workload_generators():
+    """The two search routes agree on the mixture and lin96 generators (three pivot counts)."""
+    import numpy as np
+
+    import oracle
+    from paper_2208_10022_gb300 import workloads as wl
+    for kind, n in (("mix16", 1500), ("lin96", 1200)):
+        allp = wl.gen_points(kind, n + 12, 77)
+        X, Q = allp[:n], allp[n:]
+        for m in (8, 40, 160):
+            piv = wl.nested_pivots(n, [m], 5 + m)[0]
+            got, _ = oracle.rng_search_guided(X, piv, Q)
+            want = oracle.rng_search(X, Q)
+            assert all(np.array_equal(a, b) for a, b in zip(got, want)), (kind, m)
