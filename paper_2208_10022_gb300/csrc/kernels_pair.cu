@@ -23,6 +23,10 @@
 //           after greedy descents towards that ball's centre; at the exemplar level
 //           the learned shortlist (kernels_mlp.cu) may decide a pair first.
 // Comparisons whose FP32 brackets overlap are re-decided in canonical FP64.
+// The exemplar level also builds lune-based beta-skeletons (1 <= beta <= 2): only the test of
+// one interceptor changes (block_state, block64 with lam = beta / 2); every bound above is a
+// bound on the lune of Eq. 1, which holds each beta-lune, so it stays valid as it is, and no
+// guidance filters the pairs.
 #include <algorithm>
 #include <chrono>
 #include <cstring>
