@@ -15,9 +15,10 @@
 //           reaches past the first G-lune threshold of that endpoint, every node
 //           that could satisfy that condition is in the list, so the test is exact
 //           (the exhaustive check of Stage VI restricted by a ball bound).
-//   lists   (pivot layers) per-node range lists, cut to about 8,192 nodes by a key
-//           histogram; a pair whose threshold one endpoint's list reaches is decided
-//           from that list alone.
+//   lists   (pivot layers) per-node range lists of up to 16,384 nodes, cut by a key
+//           histogram and kept in key bands; a pair whose threshold one endpoint's list
+//           reaches is decided from that list alone, after warp-per-pair descents towards
+//           the ball around its G-lune have dropped the pairs a node certainly blocks.
 //   tier 3  the exhaustive Stage VI search down the pivot tree, pruned by domain
 //           bounds (Prop. 4 / GRNG_S6, Prop. 5) and by the ball around the G-lune,
 //           after greedy descents towards that ball's centre; at the exemplar level
