@@ -3,9 +3,11 @@
 // itself), FP64 member distance, radius = max(dist + member radius) and
 // delta_max = max(dist).
 //
-// The member x pivot keys come from the FP32 distance tile; a member whose two best
-// FP32 keys cannot be separated under the error bound is re-decided in FP64 against
-// every pivot whose key could tie the minimum.
+// The member x pivot keys come from the FP32 distance tile, or, in the precision form for
+// layers of 256 pivots or more, from split-BF16 Gram keys on the tensor cores
+// (kernels_tc.cu), where each member keeps its four best candidates and a lower bound on
+// the rest.  A member whose best key cannot be separated from the others under the error
+// bound is re-decided in FP64 against every pivot whose key could tie the minimum.
 #include <algorithm>
 #include <mutex>
 #include <string>
