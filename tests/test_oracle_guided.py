@@ -47,11 +47,15 @@ def test_candidate_rules_sound_and_restated():
 
     import oracle
     rng = np.random.default_rng(41)
-    for t in range(6):
+    for t in range(10):
         n = int(rng.integers(40, 110))
-        d = int(rng.integers(2, 5))
+        if t < 4:  # dense pivots on a line or a plane: sparse GRNGs, several parents per point
+            d = 1 + t // 2
+            piv = np.sort(rng.choice(n, n // 4, replace=False)).astype(np.int32)
+        else:
+            d = int(rng.integers(2, 5))
+            piv = np.sort(rng.choice(n, int(rng.integers(4, 12)), replace=False)).astype(np.int32)
         X = rng.standard_normal((n, d)).astype(np.float32)
-        piv = np.sort(rng.choice(n, int(rng.integers(4, 12)), replace=False)).astype(np.int32)
         for metric in (oracle.L2, oracle.L1):
             dist = np.array([[oracle.dist(X[i], X[p], metric) for p in piv] for i in range(n)])
             promote = t % 2 == 1
